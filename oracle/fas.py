@@ -1,0 +1,164 @@
+"""Multigrid cycles (Sec. 4.1-4.2, Algs. 1, 2, 5, 6), FP64.
+
+Hierarchy: a list of levels (root first) with global refinement, so every
+element of a non-top level is a twig and the top level holds the leaves.
+
+* `was` is Alg. 5 (residual, then u += weighted Schwarz correction).
+* `fas_vcycle` is Alg. 2; the projected solution P u_l of the down leg is kept
+  and reused for the correction u_l += I (u_{l-1} - P u_l) of the up leg
+  (u_l does not change in between).
+* `cs_vcycle` is Alg. 1 (used to pin the FAS cycle: for a linear operator the
+  FAS correction u_{l-1} - P u_l equals the CS correction, so both produce
+  the same iterates up to round-off).
+* `solve` runs V-cycles with crossover smoothing (Sec. 6.1 naming
+  X-Y-S(n_s1,n_s2,n_sc)): n_s1 top sweeps before the first cycle and n_sc top
+  sweeps between consecutive cycles in place of n_s2 + n_s1; the residual of
+  the first down-leg step of each cycle is the stopping test
+  r_2 <= rtol * r_2^0 (Euclidean norm over the leaf DoF, Sec. 6.1).
+* The root problem is solved exactly (dense Cholesky of the assembled root
+  matrix).
+* `scg` is Alg. 6.
+"""
+import numpy as np
+import scipy.linalg as sla
+
+from .sip import LevelOps, apply, assemble
+from .schwarz import Schwarz
+from .transfer import Transfer
+
+
+class Hierarchy:
+    def __init__(self, levels, mu_star, delta, s1=2, s2=2, sc=4, nu=1.0, kappa=0.0,
+                 gcoefs=None, smoother="was"):
+        self.levels = levels
+        self.smoother = smoother
+        self.s1, self.s2, self.sc = s1, s2, sc
+        self.ops = [LevelOps(lv, mu_star, nu, kappa) for lv in levels]
+        self.sw = [None] + [Schwarz(lv, delta, mu_star, nu, kappa,
+                                    None if gcoefs is None else gcoefs[l])
+                            for l, lv in enumerate(levels) if l > 0]
+        self.tr = [None] + [Transfer(levels[l - 1], levels[l]) for l in range(1, len(levels))]
+        A0 = assemble(self.ops[0]).toarray()
+        self.root_chol = sla.cho_factor(A0)
+
+    @property
+    def L(self):
+        return len(self.levels) - 1
+
+    def A(self, l, u):
+        return apply(self.ops[l], u).reshape(-1)
+
+    def residual(self, l, u, g):
+        return g - self.A(l, u)
+
+    def smooth(self, l, u, g, n):
+        """The level smoother: WAS (Alg. 5) or SCG (Alg. 6) with n steps."""
+        if self.smoother == "scg":
+            return self.scg(l, u, g, n, 0.0)
+        return self.was(l, u, g, n)
+
+    def was(self, l, u, g, n):
+        """Alg. 5."""
+        for _ in range(n):
+            r = self.residual(l, u, g)
+            u = u + self.sw[l].correction(r)
+        return u
+
+    def root_solve(self, g):
+        return sla.cho_solve(self.root_chol, g)
+
+    def _down_up(self, u, f, r_top):
+        """Alg. 2 below the top pre-smoothing: given the top residual r_top of
+        u[L], project, form the parent right-hand sides, solve the root,
+        prolongate the corrections and smooth on levels L-1..1 (top-level
+        smoothing is left to the caller)."""
+        L = self.L
+        u = list(u)
+        g = [None] * (L + 1)
+        g[L] = f
+        ubar = [None] * (L + 1)
+        r = r_top
+        for l in range(L, 0, -1):
+            if l < L:
+                u[l] = self.smooth(l, u[l], g[l], self.s1)
+                r = self.residual(l, u[l], g[l])
+            u[l - 1] = self.tr[l].project(u[l])
+            ubar[l - 1] = u[l - 1].copy()
+            g[l - 1] = self.A(l - 1, u[l - 1]) + self.tr[l].restrict(r)
+        u[0] = self.root_solve(g[0])
+        for l in range(1, L + 1):
+            u[l] = u[l] + self.tr[l].interpolate(u[l - 1] - ubar[l - 1])
+            if l < L:
+                u[l] = self.smooth(l, u[l], g[l], self.s2)
+        return u
+
+    def fas_vcycle(self, u, f):
+        """Alg. 2 on the list u (one vector per level, root first); f is the top
+        RHS.  Returns (u, |r_top|) with r_top the top residual after pre-smoothing."""
+        L = self.L
+        u = [x.copy() for x in u]
+        u[L] = self.smooth(L, u[L], f, self.s1)
+        r = self.residual(L, u[L], f)
+        u = self._down_up(u, f, r)
+        u[L] = self.smooth(L, u[L], f, self.s2)
+        return u, np.linalg.norm(r)
+
+    def cs_vcycle(self, u_top, f_top):
+        """Alg. 1."""
+        s1, s2 = self.s1, self.s2
+        L = self.L
+        u = [None] * (L + 1)
+        f = [None] * (L + 1)
+        u[L], f[L] = u_top.copy(), f_top
+        for l in range(L, 0, -1):
+            u[l] = self.smooth(l, u[l], f[l], s1)
+            u[l - 1] = np.zeros(self.ops[l - 1].ndof)
+            f[l - 1] = self.tr[l].restrict(f[l] - self.A(l, u[l]))
+        u[0] = self.root_solve(f[0])
+        for l in range(1, L + 1):
+            u[l] = u[l] + self.tr[l].interpolate(u[l - 1])
+            u[l] = self.smooth(l, u[l], f[l], s2)
+        return u[L]
+
+    def zero_levels(self, u_top):
+        return [np.zeros(o.ndof) for o in self.ops[:-1]] + [u_top.copy()]
+
+    def solve(self, u_top, f, rtol=1e-10, max_cycles=50):
+        """V-cycles with crossover smoothing; returns (u_top, history of r_2).
+
+        n_s1 top sweeps, then per cycle: top residual r (the stopping test
+        |r| <= rtol |r^0|), the down/up legs, and n_sc top sweeps."""
+        L = self.L
+        u = self.zero_levels(u_top)
+        hist = [np.linalg.norm(self.residual(L, u[L], f))]
+        u[L] = self.smooth(L, u[L], f, self.s1)
+        for k in range(max_cycles + 1):
+            r = self.residual(L, u[L], f)
+            if k > 0:
+                hist.append(np.linalg.norm(r))
+                if hist[-1] <= rtol * hist[0] or k == max_cycles:
+                    break
+            u = self._down_up(u, f, r)
+            u[L] = self.smooth(L, u[L], f, self.sc)
+        return u[L], hist
+
+    def scg(self, l, u, f, n, r_max):
+        """Alg. 6 (inexact PCG with one Schwarz sweep as preconditioner)."""
+        r = f - self.A(l, u)
+        p = r.copy()
+        r0 = None
+        gamma = None
+        for i in range(1, n + 1):
+            z = self.sw[l].correction(r)
+            if i > 1:
+                beta = z @ (r - r0) / gamma
+                p = beta * p + z
+            q = self.A(l, p)
+            gamma = z @ r
+            alpha = gamma / (p @ q)
+            r0 = r.copy()
+            r = r - alpha * q
+            u = u + alpha * p
+            if np.linalg.norm(r) <= r_max:
+                break
+        return u

@@ -1,0 +1,85 @@
+"""Transfer operators between consecutive levels (Sec. 3.2), FP64.
+
+* I (prolongation): embedded interpolation, the coarse polynomial evaluated at
+  the fine nodes.  p-refinement: same element; h-refinement: child octant
+  (c1,c2,c3) takes the parent reference coordinate (xi + (2c-1))/2.
+* R = I^T (restriction, the transpose of I, Sec. 3.2).
+* P (solution projection, embedded-interpolation variant): the fine
+  polynomial evaluated at the coarse nodes; for h-refinement each parent node
+  takes the value of the child that contains it, and parent nodes on a child
+  interface (only for even p, the middle GLL node) average the children that
+  share them.
+
+Pins (tests/test_oracle_transfer.py): P I = identity; I reproduces coarse
+polynomials at the fine nodes' physical positions; R equals the transpose of
+the assembled I; averaging happens only for even p.
+"""
+import numpy as np
+
+from .gll import gll, interp_matrix
+
+
+def _mode(A1, A2, A3, u):
+    """(A3 x A2 x A1) applied to u [ne, k, j, i]."""
+    y = np.einsum("ai,ekji->ekja", A1, u)
+    y = np.einsum("bj,ekja->ekba", A2, y)
+    return np.einsum("ck,ekba->ecba", A3, y)
+
+
+class Transfer:
+    """Transfers between coarse level `lc` and fine level `lf` (fine['parent'])."""
+
+    def __init__(self, lc, lf):
+        self.pc, self.pf = lc["p"], lf["p"]
+        self.Nc, self.Nf = self.pc + 1, self.pf + 1
+        self.nec, self.nef = lc["nbr"].shape[0], lf["nbr"].shape[0]
+        self.parent = lf["parent"]
+        self.octant = lf["octant"]
+        self.h = bool(np.all(self.octant >= 0))
+        xf, _ = gll(self.pf)
+        xc, _ = gll(self.pc)
+        if not self.h:
+            self.I1 = [interp_matrix(self.pc, xf)]          # [Nf, Nc]
+            self.P1 = [interp_matrix(self.pf, xc)]          # [Nc, Nf]
+        else:
+            assert self.pc == self.pf
+            self.I1 = [interp_matrix(self.pc, (xf + s) / 2.0) for s in (-1.0, 1.0)]
+            self.P1 = []
+            for s, inside in ((-1.0, xc <= 0.0), (1.0, xc >= 0.0)):
+                wgt = np.where(inside, np.where(xc == 0.0, 0.5, 1.0), 0.0)
+                xchild = np.clip(2.0 * xc - s, -1.0, 1.0)
+                self.P1.append(wgt[:, None] * interp_matrix(self.pf, xchild))
+
+    def _oct(self, e):
+        o = self.octant[e]
+        return (0, 0, 0) if o < 0 else (o & 1, (o >> 1) & 1, (o >> 2) & 1)
+
+    def interpolate(self, uc):
+        """u_f = I u_c on every fine element."""
+        uc = np.asarray(uc).reshape(self.nec, self.Nc, self.Nc, self.Nc)
+        uf = np.zeros((self.nef, self.Nf, self.Nf, self.Nf))
+        for e in range(self.nef):
+            o = self._oct(e)
+            A = [self.I1[o[d]] for d in range(3)] if self.h else [self.I1[0]] * 3
+            uf[e] = _mode(A[0], A[1], A[2], uc[self.parent[e]][None])[0]
+        return uf.reshape(-1)
+
+    def restrict(self, rf):
+        """r_c = R r_f = I^T r_f."""
+        rf = np.asarray(rf).reshape(self.nef, self.Nf, self.Nf, self.Nf)
+        rc = np.zeros((self.nec, self.Nc, self.Nc, self.Nc))
+        for e in range(self.nef):
+            o = self._oct(e)
+            A = [self.I1[o[d]] for d in range(3)] if self.h else [self.I1[0]] * 3
+            rc[self.parent[e]] += _mode(A[0].T, A[1].T, A[2].T, rf[e][None])[0]
+        return rc.reshape(-1)
+
+    def project(self, uf):
+        """u_c = P u_f (embedded interpolation with averaging at shared nodes)."""
+        uf = np.asarray(uf).reshape(self.nef, self.Nf, self.Nf, self.Nf)
+        uc = np.zeros((self.nec, self.Nc, self.Nc, self.Nc))
+        for e in range(self.nef):
+            o = self._oct(e)
+            A = [self.P1[o[d]] for d in range(3)] if self.h else [self.P1[0]] * 3
+            uc[self.parent[e]] += _mode(A[0], A[1], A[2], uf[e][None])[0]
+        return uc.reshape(-1)

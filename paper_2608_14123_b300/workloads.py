@@ -1,0 +1,271 @@
+"""Seeded synthetic inputs shared by the CUDA path and the oracle.
+
+This module holds mesh *topology and coordinates* and the manufactured
+right-hand-side functions only.  It contains none of the method's arithmetic
+(no basis, quadrature, operator, smoother or transfer): both the oracle and the
+CUDA library derive every discrete quantity from these inputs on their own.
+
+Meshes are multilevel hexahedral meshes in the sense of Sec. 3.1: a list of
+levels from the root (index 0) to the top, each level a conforming hex mesh
+with one polynomial degree.  Consecutive levels are related either by
+p-refinement (same elements, higher degree) or by regular h-refinement (each
+element split into 8 children).
+
+Per level (all numpy arrays, element index e in lexicographic x-fastest order):
+  p        polynomial degree of the level
+  corners  float64 [ne, 8, 3]   corner c = cx + 2*cy + 4*cz of the trilinear map
+  nbr      int32   [ne, 6]      face f in (-x,+x,-y,+y,-z,+z): neighbour element,
+                                or -1 = Dirichlet boundary, -2 = Neumann boundary
+  nbr27    int32   [ne, 27]     element at offset (ox,oy,oz) in {-1,0,1}^3,
+                                slot (ox+1) + 3*(oy+1) + 9*(oz+1); -1 = none
+  parent   int32   [ne]         element of the next coarser level (-1 on the root)
+  octant   int32   [ne]         child octant cx+2cy+4cz for h-refinement, -1 for
+                                p-refinement (parent is the same element)
+  cls      int8    [ne]         0 = leaf, 1 = twig, 2 = frozen (Sec. 3.1)
+All neighbouring elements share aligned local axes (structured topology).
+"""
+import numpy as np
+
+SEED_BASE = 20261202
+
+LEAF, TWIG, FROZEN = 0, 1, 2
+
+_FACE_OFF = ((-1, 0, 0), (1, 0, 0), (0, -1, 0), (0, 1, 0), (0, 0, -1), (0, 0, 1))
+
+
+def uniform_vertices(nx, ny=None, nz=None, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0)):
+    """Vertex grid [nx+1, ny+1, nz+1, 3] of an axis-aligned box."""
+    ny = nx if ny is None else ny
+    nz = nx if nz is None else nz
+    xs = np.linspace(lo[0], hi[0], nx + 1)
+    ys = np.linspace(lo[1], hi[1], ny + 1)
+    zs = np.linspace(lo[2], hi[2], nz + 1)
+    V = np.zeros((nx + 1, ny + 1, nz + 1, 3))
+    V[..., 0] = xs[:, None, None]
+    V[..., 1] = ys[None, :, None]
+    V[..., 2] = zs[None, None, :]
+    return V
+
+
+def corner_jacobians_positive(V):
+    """Input validation: the triple product of the three edges at every corner of
+    every cell of the vertex grid is positive (no folded cells)."""
+    ok = True
+    for cx in (0, 1):
+        for cy in (0, 1):
+            for cz in (0, 1):
+                sx, sy, sz = 1 - 2 * cx, 1 - 2 * cy, 1 - 2 * cz
+                def at(dx, dy, dz):
+                    return V[cx + dx: V.shape[0] - 1 + cx + dx,
+                             cy + dy: V.shape[1] - 1 + cy + dy,
+                             cz + dz: V.shape[2] - 1 + cz + dz]
+                o = at(0, 0, 0)
+                ex = (at(sx, 0, 0) - o) * sx
+                ey = (at(0, sy, 0) - o) * sy
+                ez = (at(0, 0, sz) - o) * sz
+                trip = np.einsum("...a,...a->...", ex, np.cross(ey, ez))
+                ok = ok and bool(np.all(trip > 0))
+    return ok
+
+
+def perturbed_vertices(n, amp, rng, graded_ratio_z=None, max_draws=100):
+    """As `_perturbed_vertices_once`, redrawn until every cell is unfolded."""
+    for _ in range(max_draws):
+        V = _perturbed_vertices_once(n, amp, rng, graded_ratio_z)
+        if corner_jacobians_positive(V):
+            return V
+    raise RuntimeError("no valid perturbed mesh drawn")
+
+
+def _perturbed_vertices_once(n, amp, rng, graded_ratio_z=None):
+    """Vertex grid of [0,1]^3 with n^3 cells; interior vertices are moved by
+    U(-amp, amp) cells per coordinate in logical space, boundary vertices stay
+    on the cube faces.  If graded_ratio_z is given, the logical z coordinate s
+    is mapped by the geometric grading Z(s) = (r^s - 1) / (r^n - 1)."""
+    idx = np.arange(n + 1, dtype=np.float64)
+    L = np.zeros((n + 1, n + 1, n + 1, 3))
+    L[..., 0] = idx[:, None, None]
+    L[..., 1] = idx[None, :, None]
+    L[..., 2] = idx[None, None, :]
+    interior = np.zeros((n + 1, n + 1, n + 1), dtype=bool)
+    interior[1:-1, 1:-1, 1:-1] = True
+    eps = rng.uniform(-amp, amp, size=L.shape)
+    L = L + eps * interior[..., None]
+    V = L / n
+    if graded_ratio_z is not None:
+        r = graded_ratio_z
+        V[..., 2] = (r ** L[..., 2] - 1.0) / (r ** n - 1.0)
+    return V
+
+
+def grading_ratio(n, total_over_min):
+    """Ratio r with sum_{k<n} r^k = total_over_min (bisection)."""
+    lo, hi = 1.0 + 1e-12, 4.0
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        s = (mid ** n - 1.0) / (mid - 1.0)
+        if s < total_over_min:
+            lo = mid
+        else:
+            hi = mid
+    return 0.5 * (lo + hi)
+
+
+def level_from_vertices(V, p, boundary=-1):
+    """Conforming structured level from a vertex grid V [nx+1, ny+1, nz+1, 3]."""
+    nx, ny, nz = V.shape[0] - 1, V.shape[1] - 1, V.shape[2] - 1
+    ne = nx * ny * nz
+    x, y, z = np.meshgrid(np.arange(nx), np.arange(ny), np.arange(nz), indexing="ij")
+    # lexicographic, x fastest
+    x = x.transpose(2, 1, 0).reshape(-1)
+    y = y.transpose(2, 1, 0).reshape(-1)
+    z = z.transpose(2, 1, 0).reshape(-1)
+    corners = np.zeros((ne, 8, 3))
+    for c in range(8):
+        cx, cy, cz = c & 1, (c >> 1) & 1, (c >> 2) & 1
+        corners[:, c, :] = V[x + cx, y + cy, z + cz]
+
+    def eid(ix, iy, iz):
+        ok = (ix >= 0) & (ix < nx) & (iy >= 0) & (iy < ny) & (iz >= 0) & (iz < nz)
+        return np.where(ok, ix + nx * (iy + ny * iz), -1), ok
+
+    nbr = np.zeros((ne, 6), dtype=np.int32)
+    for f, (ox, oy, oz) in enumerate(_FACE_OFF):
+        idn, ok = eid(x + ox, y + oy, z + oz)
+        nbr[:, f] = np.where(ok, idn, boundary)
+    nbr27 = np.zeros((ne, 27), dtype=np.int32)
+    for oz in (-1, 0, 1):
+        for oy in (-1, 0, 1):
+            for ox in (-1, 0, 1):
+                idn, _ = eid(x + ox, y + oy, z + oz)
+                nbr27[:, (ox + 1) + 3 * (oy + 1) + 9 * (oz + 1)] = idn
+    return dict(p=int(p), shape=(nx, ny, nz), corners=corners, nbr=nbr, nbr27=nbr27,
+                parent=np.full(ne, -1, np.int32), octant=np.full(ne, -1, np.int32),
+                cls=np.full(ne, LEAF, np.int8), ijk=np.stack([x, y, z], 1).astype(np.int32))
+
+
+def hierarchy(V_top, p_levels, h_root=None, boundary=-1):
+    """Multilevel mesh with global refinement (all non-top elements are twigs).
+
+    p_levels: degrees of the p-levels on the top mesh, finest first, e.g. [8,4,2,1].
+    h_root:   if given, the last p-level mesh is h-coarsened (every other
+              vertex kept) down to h_root cells per direction.
+    Returns the list of levels, root first.
+    """
+    levels_fine_first = []
+    for p in p_levels:
+        levels_fine_first.append(level_from_vertices(V_top, p, boundary))
+    V = V_top
+    if h_root is not None:
+        n = V.shape[0] - 1
+        while n > h_root:
+            assert n % 2 == 0 and all(s - 1 == n for s in V.shape[:3])
+            V = V[::2, ::2, ::2]
+            n //= 2
+            levels_fine_first.append(level_from_vertices(V, p_levels[-1], boundary))
+    levels = levels_fine_first[::-1]
+    for l in range(1, len(levels)):
+        fine, coarse = levels[l], levels[l - 1]
+        ne = fine["corners"].shape[0]
+        if fine["shape"] == coarse["shape"]:
+            fine["parent"] = np.arange(ne, dtype=np.int32)
+            fine["octant"] = np.full(ne, -1, np.int32)
+        else:
+            ijk = fine["ijk"]
+            cnx, cny, _ = coarse["shape"]
+            pi = ijk // 2
+            fine["parent"] = (pi[:, 0] + cnx * (pi[:, 1] + cny * pi[:, 2])).astype(np.int32)
+            o = ijk % 2
+            fine["octant"] = (o[:, 0] + 2 * o[:, 1] + 4 * o[:, 2]).astype(np.int32)
+    for l in range(len(levels) - 1):
+        levels[l]["cls"] = np.full(levels[l]["corners"].shape[0], TWIG, np.int8)
+    return levels
+
+
+# ---------------------------------------------------------------- right-hand sides
+def sine_rhs_spec(k=1.0):
+    """u = sin(k pi x) sin(k pi y) sin(k pi z), -lap u = 3 (k pi)^2 u."""
+    return dict(kind="sine", k=float(k))
+
+
+def modes_rhs_spec(rng, n_modes=16, kmax=8):
+    """f = sum_m a_m prod_d sin(k_md pi x_d); exact u = sum_m a_m prod sin / (pi^2 |k_m|^2)."""
+    k = rng.integers(1, kmax + 1, size=(n_modes, 3))
+    a = rng.standard_normal(n_modes)
+    return dict(kind="modes", k=k.astype(np.float64), a=a)
+
+
+def eval_f(spec, xyz):
+    """Source f(x) at points xyz [..., 3] (the manufactured input)."""
+    x, y, z = xyz[..., 0], xyz[..., 1], xyz[..., 2]
+    if spec["kind"] == "sine":
+        kp = spec["k"] * np.pi
+        return 3.0 * kp * kp * np.sin(kp * x) * np.sin(kp * y) * np.sin(kp * z)
+    out = np.zeros_like(x)
+    for (kx, ky, kz), a in zip(spec["k"], spec["a"]):
+        out += a * np.sin(kx * np.pi * x) * np.sin(ky * np.pi * y) * np.sin(kz * np.pi * z)
+    return out
+
+
+def eval_u(spec, xyz):
+    """Exact solution u(x) at points xyz [..., 3]."""
+    x, y, z = xyz[..., 0], xyz[..., 1], xyz[..., 2]
+    if spec["kind"] == "sine":
+        kp = spec["k"] * np.pi
+        return np.sin(kp * x) * np.sin(kp * y) * np.sin(kp * z)
+    out = np.zeros_like(x)
+    for (kx, ky, kz), a in zip(spec["k"], spec["a"]):
+        out += (a / (np.pi ** 2 * (kx * kx + ky * ky + kz * kz))
+                * np.sin(kx * np.pi * x) * np.sin(ky * np.pi * y) * np.sin(kz * np.pi * z))
+    return out
+
+
+def random_start(rng, n):
+    """Start vector uniform in [-1, 1] (Sec. 6.1)."""
+    return rng.uniform(-1.0, 1.0, size=n)
+
+
+# ---------------------------------------------------------------- the configurations
+def config(cid, small=False):
+    """Workload `cid` in 1..5 (config 4 is built by adaptive.py).
+
+    Returns dict(levels, rhs, u0, params) with params the solver parameters
+    (mu_star, delta, s1, s2, sc).  `small` shrinks configs 2/3/5 to a mesh the
+    oracle handles in seconds while keeping the structure (degree, hierarchy
+    shape, perturbation, grading).
+    """
+    rng = np.random.default_rng(SEED_BASE + cid)
+    if cid == 1:
+        V = uniform_vertices(4)
+        levels = hierarchy(V, [4, 2, 1])
+        rhs = sine_rhs_spec()
+        prm = dict(mu_star=2.0, delta=0.08, s1=2, s2=2, sc=4)
+    elif cid == 2:
+        n = 4 if small else 32
+        V = uniform_vertices(n)
+        levels = hierarchy(V, [8, 4, 2, 1], h_root=min(4, n))
+        rhs = modes_rhs_spec(rng)
+        prm = dict(mu_star=5.0, delta=0.08, s1=2, s2=2, sc=4)
+    elif cid == 3:
+        # small: 4^3 cells, grading to aspect ratio 4 (AR 16 on four cells folds)
+        n = 4 if small else 16
+        r = grading_ratio(n, (4.0 if small else 16.0) * n)
+        V = perturbed_vertices(n, 0.25, rng, graded_ratio_z=r)
+        levels = hierarchy(V, [7, 3, 1], h_root=min(4, n))
+        rhs = modes_rhs_spec(rng)
+        # mu_star = 5 leaves this SIP operator indefinite on perturbed cells;
+        # 10 (upper end of the paper's tested range) keeps it SPD
+        prm = dict(mu_star=10.0, delta=0.08, s1=2, s2=2, sc=4)
+    elif cid == 5:
+        n = 8 if small else 64
+        V = perturbed_vertices(n, 0.15, rng)
+        levels = hierarchy(V, [7, 3, 1], h_root=4)
+        rhs = modes_rhs_spec(rng)
+        prm = dict(mu_star=5.0, delta=0.08, s1=2, s2=2, sc=4)
+    else:
+        raise ValueError(f"unknown config {cid}")
+    top = levels[-1]
+    N = top["p"] + 1
+    ndof = top["corners"].shape[0] * N ** 3
+    u0 = random_start(rng, ndof)
+    return dict(levels=levels, rhs=rhs, u0=u0, params=prm, cid=cid)
