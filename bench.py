@@ -1,0 +1,346 @@
+#!/usr/bin/env python
+"""Benchmark of the FAS multigrid hot path on one B300 (or N replicas).
+
+Workload (one "step" = one FAS V-cycle over the whole hierarchy, Alg. 2):
+Poisson on [0,1]^3, Dirichlet, uniform Cartesian 32^3 elements, p = 8
+(23.9M DoF), p-coarsening 8 -> 4 -> 2 -> 1 then h-coarsening to 4^3, V(2,2)
+with the weighted additive Schwarz / fast-diagonalization smoother, seeded
+16-mode right-hand side.  Headline: the FP32 smoother with FP64 residual,
+tau, restriction and root solve; the plain FP64 path is measured beside it.
+
+Prints one JSON line.  `--impl reference` times the FP64 CPU oracle instead
+(on a bounded sample of the same workload).
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2608_14123_b300 import workloads as wl  # noqa: E402
+
+METRIC = "DoF/s per FAS V-cycle and time-to-1e-10 residual, mixed+learned vs FP64, 1 B300"
+UNIT = "DoF/s"
+L2_BYTES = 126 * 2 ** 20
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            d = json.load(fh)
+        return dict(hbm=float(d.get("hbm_gbs", 6400.0)), src="measured", raw=d)
+    return dict(hbm=6400.0, src="fallback", raw=None)
+
+
+def apply_flops_per_dof(N, box=True):
+    """Algorithmic FP64 flops per DoF of the sum-factorized SIP apply (Eq. (2)):
+    volume: 3 reference derivatives and 3 transposed ones, N FMA each, plus the
+    metric; faces: 6 N^2 face nodes per element, each with the own and the
+    neighbour's normal derivative (N FMA each), the flux and the lifting."""
+    vol = 2 * 6 * N + (6 if box else 18)
+    face = 6 * N * N * (2 * 2 * N + 12) / N ** 3
+    return vol + face
+
+
+def fd_flops_per_dof(N, m):
+    ns = N + 2 * m
+    return 12.0 * ns ** 4 / N ** 3
+
+
+def start_clock_log():
+    try:
+        fh = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        p = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                              "-lms", "200"], stdout=fh, stderr=subprocess.DEVNULL)
+        return p, fh
+    except Exception:
+        return None, None
+
+
+def stop_clock_log(p, fh, dev_index=0):
+    if p is None:
+        return None
+    p.terminate()
+    try:
+        p.wait(timeout=5)
+    except Exception:
+        p.kill()
+    fh.flush()
+    fh.seek(0)
+    sm, mx, reasons = [], [], set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for line in fh:
+        parts = [x.strip() for x in line.split(",")]
+        if len(parts) < 9 or parts[0] != str(dev_index):
+            continue
+        try:
+            sm.append(float(parts[1]))
+            mx.append(float(parts[2]))
+        except ValueError:
+            continue
+        for nm, v in zip(names, parts[5:9]):
+            if v.lower() == "active":
+                reasons.add(nm)
+    os.unlink(fh.name)
+    if not sm:
+        return None
+    return dict(sm_mhz=float(np.median(sm)), sm_max_mhz=float(max(mx)), reasons=sorted(reasons),
+                samples=len(sm))
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ------------------------------------------------------------------ CPU oracle arm
+def oracle_sample_rate(cores_note=True, n_sample=8, cycles=1):
+    """DoF/s per V-cycle of the FP64 oracle on a bounded sample of the workload:
+    the same degree, hierarchy shape and smoother on n_sample^3 elements."""
+    from oracle import fas, sip
+    V = wl.uniform_vertices(n_sample)
+    levels = wl.hierarchy(V, [8, 4, 2, 1], h_root=4)
+    rng = np.random.default_rng(wl.SEED_BASE + 2)
+    spec = wl.modes_rhs_spec(rng)
+    H = fas.Hierarchy(levels, 5.0, 0.08, 2, 2, 4)
+    top = H.ops[-1]
+    X = top.geo["x"]
+    b = sip.rhs(top, wl.eval_f(spec, X), np.zeros(X.shape[:-1])).reshape(-1)
+    u = H.zero_levels(wl.random_start(rng, top.ndof))
+    t0 = time.perf_counter()
+    for _ in range(cycles):
+        u, _ = H.fas_vcycle(u, b)
+    dt = time.perf_counter() - t0
+    return top.ndof * cycles / dt, dt, top.ndof
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count()
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    n_sample = 8
+    rates = []
+    t_all = time.perf_counter()
+    for _ in range(args.warmup):
+        oracle_sample_rate(n_sample=n_sample)
+    for _ in range(args.steps):
+        r, dt, ndof = oracle_sample_rate(n_sample=n_sample)
+        rates.append(r)
+    value = float(np.mean(rates))
+    threads = int(os.environ.get("OMP_NUM_THREADS", host_cores()))
+    out = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ndof / value * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "cartesian-32^3-p8-dirichlet-poisson (sampled at 8^3 elements)",
+                   "global_batch": 1, "seq_len": 0, "parallelism": "replicas",
+                   "sample_dof": ndof},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": f"one FP64 oracle V-cycle on {n_sample}^3 elements p=8 "
+                                   f"({ndof} DoF) per step"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "wall_s": time.perf_counter() - t_all,
+    }
+    print(json.dumps(out), flush=True)
+
+
+# ------------------------------------------------------------------ GPU arm
+def run_gpu(args):
+    import torch
+    from paper_2608_14123_b300 import dgfas
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    cfg = wl.config(2)
+    pr = cfg["params"]
+    levels = cfg["levels"]
+    top = levels[-1]
+    N = top["p"] + 1
+    prec = dgfas.DGFAS_FP32 if args.precision == "fp32" else dgfas.DGFAS_FP64
+    S = dgfas.Solver(levels, pr["mu_star"], pr["delta"], pr["s1"], pr["s2"], pr["sc"],
+                     precision=prec)
+    S.dgfas_use_graph(True)
+    ndof = S.ndof(-1)
+    xyz = S.node_coords(-1)
+    f_nod = torch.from_numpy(wl.eval_f(cfg["rhs"], xyz.cpu().numpy())).to(dev)
+    del xyz
+    b = torch.empty_like(f_nod)
+    S.dgfas_assemble_rhs(f_nod, None, b)
+    del f_nod
+    u0 = torch.from_numpy(cfg["u0"]).to(dev)
+    u = u0.clone()
+
+    for _ in range(args.warmup):
+        S.dgfas_fas_vcycle(u, b, want_norm=False)
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    clk_p, clk_fh = start_clock_log()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        S.dgfas_fas_vcycle(u, b, want_norm=False)
+    e1.record()
+    torch.cuda.synchronize()
+    clocks = stop_clock_log(clk_p, clk_fh, local)
+    ms = e0.elapsed_time(e1) / args.steps
+    if ws > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+        torch.distributed.barrier()
+    value = ndof * ws / (ms * 1e-3)
+
+    # ---- end to end through the public API with host buffers
+    u_host = torch.from_numpy(cfg["u0"]).pin_memory()
+    b_host = b.cpu().pin_memory()
+    u_back = torch.empty_like(u_host).pin_memory()
+    ud = torch.empty_like(u0)
+    bd = torch.empty_like(b)
+    steps_e2e = max(2, min(args.steps, 5))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps_e2e):
+        ud.copy_(u_host, non_blocking=True)
+        bd.copy_(b_host, non_blocking=True)
+        S.dgfas_fas_vcycle(ud, bd, want_norm=False)
+        u_back.copy_(ud, non_blocking=True)
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / steps_e2e
+    e2e = {"value": ndof / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 2 * ndof * 8,
+           "d2h_bytes_per_step": ndof * 8}
+
+    # ---- per-kernel timing of the top-level smoother and the roofline
+    L = S.n_levels - 1
+    uk = u0.clone()
+    prof = S.dgfas_profile_sweep(L, uk, b, 5)
+    fp64_tf, fp32_tf = dgfas.dgfas_fma_peak()
+    pk = peaks()
+    m = 2
+    ns = N + 2 * m
+    sweeps = pr["s1"] + pr["s2"]
+    kernels = {
+        "residual_fp64": dict(count=1, ms=prof["residual_fp64"], bound="alu",
+                              flops=apply_flops_per_dof(N) * ndof, peak=fp64_tf, unit="TFLOP/s"),
+        "residual_smoother": dict(count=sweeps, ms=prof["residual_smoother"], bound="alu",
+                                  flops=apply_flops_per_dof(N) * ndof,
+                                  peak=fp32_tf if prec else fp64_tf, unit="TFLOP/s"),
+        "fd": dict(count=sweeps, ms=prof["fd"], bound="alu", flops=fd_flops_per_dof(N, m) * ndof,
+                   peak=fp32_tf if prec else fp64_tf, unit="TFLOP/s"),
+        "combine": dict(count=sweeps, ms=prof["combine"], bound="hbm",
+                        bytes=ndof * 16.0, peak=pk["hbm"], unit="GB/s"),
+    }
+    dom = max(kernels, key=lambda k: kernels[k]["count"] * kernels[k]["ms"])
+    kd = kernels[dom]
+    if kd["bound"] == "hbm":
+        achieved = kd["bytes"] / (kd["ms"] * 1e-3) / 1e9
+    else:
+        achieved = kd["flops"] / (kd["ms"] * 1e-3) / 1e12
+    roofline = {"bound": kd["bound"], "kernel": dom, "achieved": achieved, "peak": kd["peak"],
+                "unit": kd["unit"], "frac": achieved / kd["peak"], "traffic": None,
+                "peak_source": ("measured FMA microbenchmark (dgfas_fma_peak)" if kd["bound"] == "alu"
+                                else f"{pk['src']} HBM copy")}
+    shares = {k: v["count"] * v["ms"] for k, v in kernels.items()}
+
+    # ---- time to 1e-10 (mixed and plain FP64)
+    tts = {}
+    for name, pmode in (("mixed_fp32", dgfas.DGFAS_FP32), ("fp64", dgfas.DGFAS_FP64)):
+        if args.skip_fp64 and pmode == dgfas.DGFAS_FP64:
+            continue
+        S2 = S if pmode == prec else dgfas.Solver(levels, pr["mu_star"], pr["delta"], pr["s1"],
+                                                   pr["s2"], pr["sc"], precision=pmode)
+        S2.dgfas_use_graph(True)
+        us = u0.clone()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        info = S2.dgfas_solve(us, b, 1e-10, 40, raise_on_fail=False)
+        torch.cuda.synchronize()
+        tts[name] = {"seconds": time.perf_counter() - t0, "cycles": info["cycles"],
+                     "rel_residual": info["r_final"] / info["r0"], "code": info["code"]}
+        if S2 is not S:
+            S2.close()
+
+    # ---- CPU baseline (rank 0, N = 1 only)
+    cpu = None
+    if rank == 0 and ws == 1 and not args.skip_cpu:
+        rate, dt, sdof = oracle_sample_rate(n_sample=8)
+        cpu = {"value": rate, "unit": UNIT, "cores": int(os.environ.get("OMP_NUM_THREADS",
+                                                                          host_cores())),
+               "kind": "oracle",
+               "sample": f"one FP64 oracle V-cycle on 8^3 elements p=8 ({sdof} DoF), {dt:.1f} s"}
+
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64" if prec else "f64", "data": "synthetic",
+            "config": {"workload": "cartesian-32^3-p8-dirichlet-poisson", "elements": top["corners"].shape[0],
+                       "p": top["p"], "dof": ndof, "levels": [lv["p"] for lv in levels],
+                       "smoother": f"WAS V({pr['s1']},{pr['s2']}) delta={pr['delta']}",
+                       "precision": args.precision, "global_batch": 1, "seq_len": 0,
+                       "parallelism": "replicas" if ws > 1 else "single",
+                       "l2": "inputs larger than L2 (top vector 191 MB > 126 MB)"},
+            "gpu_launches": None,
+            "roofline": roofline,
+            "kernel_ms": {k: v["ms"] for k, v in kernels.items()},
+            "kernel_share_ms_per_cycle": shares,
+            "peaks": {"fp64_tflops": fp64_tf, "fp32_tflops": fp32_tf, "hbm_gbs": pk["hbm"],
+                      "hbm_source": pk["src"]},
+            "time_to_1e-10": tts,
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+            "clocks": clocks,
+        }
+        print(json.dumps(out), flush=True)
+    S.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="dgfas", choices=["dgfas", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--skip-fp64", action="store_true")
+    ap.add_argument("--skip-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

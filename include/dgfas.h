@@ -1,0 +1,188 @@
+/*
+ * dgfas.h - C ABI of the B300 FAS multigrid hot path for SIP DG-SEM elliptic
+ * problems (Stiller, "Adaptive multigrid for high-order discontinuous Galerkin
+ * methods based on the full approximation scheme").
+ *
+ * Problem (Sec. 2.1, Eq. (1)):  kappa u - div(nu grad u) = f in Omega, u = u_D
+ * on Dirichlet faces, nu du/dn = q_N on Neumann faces; constant kappa >= 0 and
+ * nu > 0.  Discretization (Sec. 2.2, Eq. (2)): symmetric interior penalty DG on
+ * hexahedra with a GLL nodal basis of degree p per element and GLL collocation
+ * quadrature; the algebraic system is A u = f (Eq. (3)).
+ *
+ * Conventions shared by every call
+ * - Vectors are FP64, element-major: u[e][k][j][i] with i fastest, (p+1)^3
+ *   nodes per element, e the element index of the level.
+ * - Vector pointers passed to the calls below are DEVICE pointers owned by the
+ *   caller unless stated otherwise; mesh arrays in dgfas_level are HOST
+ *   pointers, copied during setup (the caller may free them afterwards).
+ * - Every call is ordered on the CUDA stream given at setup and is
+ *   asynchronous, except where a host output (rnorm_out, info) forces a
+ *   synchronization.
+ * - Return codes: DGFAS_OK (0) or a negative DGFAS_ERR_* code; nothing throws
+ *   across the ABI.  dgfas_strerror() gives a static message for a code, and
+ *   dgfas_last_error() the detail of the last failure in this thread.
+ */
+#ifndef DGFAS_H
+#define DGFAS_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DGFAS_OK 0
+#define DGFAS_ERR_INVALID -1        /* bad argument or inconsistent mesh arrays */
+#define DGFAS_ERR_OOM -2            /* device allocation failed */
+#define DGFAS_ERR_CUDA -3           /* a CUDA runtime call failed */
+#define DGFAS_ERR_MESH -4           /* non-positive Jacobian at a GLL node */
+#define DGFAS_ERR_NOT_CONVERGED -5  /* max_cycles reached before rtol */
+#define DGFAS_ERR_DIVERGED -6       /* NaN/Inf or residual growth > 1e3 x r_0 */
+#define DGFAS_ERR_UNSUPPORTED -7    /* p > 10, subdomain width > 16, ... */
+
+/* element classes of Sec. 3.1 */
+#define DGFAS_LEAF 0
+#define DGFAS_TWIG 1
+#define DGFAS_FROZEN 2
+
+/* smoother-internal precision (the V-cycle residual, tau, restriction and
+   root solve are always FP64) */
+#define DGFAS_FP64 0
+#define DGFAS_FP32 1
+
+/* smoother (Sec. 4.3): weighted additive Schwarz (Alg. 5) or Schwarz-
+   preconditioned inexact CG (Alg. 6) */
+#define DGFAS_WAS 0
+#define DGFAS_SCG 1
+
+/* One level of the multilevel mesh (Sec. 3.1): a conforming hexahedral mesh
+   with one polynomial degree.  All arrays are host arrays of n_elem rows. */
+typedef struct {
+  int p;                     /* polynomial degree, 1 <= p <= 10 */
+  int n_elem;
+  const double* corners;     /* [n_elem][8][3] trilinear map corners,
+                                corner c = cx + 2 cy + 4 cz */
+  const int* nbr;            /* [n_elem][6] face (-x,+x,-y,+y,-z,+z): neighbour
+                                element, -1 Dirichlet, -2 Neumann; neighbours
+                                share aligned local axes */
+  const int* nbr27;          /* [n_elem][27] element at offset (ox,oy,oz) in
+                                {-1,0,1}^3, slot (ox+1)+3(oy+1)+9(oz+1), -1 none
+                                (overlap layers of the Schwarz subdomains) */
+  const int* parent;         /* [n_elem] element of level l-1; ignored on root */
+  const int* octant;         /* [n_elem] h-child octant cx+2cy+4cz, or -1 when
+                                the parent is the same element (p-refinement) */
+  const signed char* cls;    /* [n_elem] DGFAS_LEAF / TWIG / FROZEN */
+} dgfas_level;
+
+typedef struct {
+  int n_levels;              /* >= 1, root first */
+  const dgfas_level* levels;
+  double nu;                 /* diffusivity (constant) */
+  double kappa;              /* reaction coefficient (constant, >= 0) */
+} dgfas_mesh;
+
+typedef struct {
+  double mu_star;            /* penalty scaling mu_* > 1 (Sec. 2.2) */
+  double delta;              /* Schwarz overlap 0 < delta < 0.5 (Sec. 4.3.1) */
+  int s1, s2, sc;            /* pre-, post-, crossover smoothing steps */
+  int precision;             /* DGFAS_FP64 or DGFAS_FP32 smoother */
+  int smoother;              /* DGFAS_WAS or DGFAS_SCG */
+  int max_cycles;            /* default cap for dgfas_solve when <= 0 is passed */
+} dgfas_params;
+
+typedef struct {
+  int cycles;                /* V-cycles run */
+  double r0;                 /* initial residual r_2^0 */
+  double r_final;            /* final residual r_2 */
+  double seconds;            /* wall time of the cycles (host clock) */
+  double history[128];       /* r_2 after each cycle (first 128) */
+} dgfas_info;
+
+/* Builds all device state of the hierarchy: geometry factors, penalties, the
+   nine 1D fast-diagonalization variants per level (Sec. 4.3.1), the geometric
+   surrogate widths per element, transfer matrices (Sec. 3.2) and the factorized
+   root operator.  `cuda_stream` is a cudaStream_t (NULL = legacy default).
+   Errors: INVALID (arrays inconsistent), UNSUPPORTED, MESH, OOM, CUDA. */
+int dgfas_setup_levels(const dgfas_mesh* mesh, const dgfas_params* prm,
+                       void* cuda_stream, void** out_ctx);
+
+void dgfas_destroy(void* ctx);
+
+/* DoF count (n_elem (p+1)^3) of level `level` (0 = root), or a negative code. */
+long long dgfas_level_ndof(void* ctx, int level);
+
+/* Physical coordinates of the GLL nodes of `level` into xyz [ndof][3] (device).
+   Used to sample manufactured data f(x), u_D(x). */
+int dgfas_node_coords(void* ctx, int level, double* xyz);
+
+/* Right-hand side of Eq. (2) on the top level: b = int v f + Dirichlet terms
+   (2 mu nu v u_D - nu dv/dn u_D), from nodal f and u_D (both [ndof], device;
+   uD may be NULL for u_D = 0). */
+int dgfas_assemble_rhs(void* ctx, const double* f_nodal, const double* uD_nodal,
+                       double* b);
+
+/* Operator application of Eq. (2) on `level`: out = A u, or out = g - A u when
+   g != NULL (the residual; rows of frozen elements are 0, Eq. (4d)).  u, g, out
+   [ndof] device; out must not alias u. */
+int dgfas_apply_op(void* ctx, int level, const double* u, const double* g, double* out);
+
+/* n sweeps of the level smoother (Alg. 5 WAS, or Alg. 6 SCG if selected) on
+   A u = g: each WAS sweep computes r = g - A u and adds the weighted Schwarz
+   correction sum_e R_s^T W^e (A~_s^e)^-1 R_s r of Eq. (11); frozen entries of u
+   are unchanged.  u updated in place. */
+int dgfas_schwarz_smooth(void* ctx, int level, double* u, const double* g, int nsweeps);
+
+/* One FAS V-cycle (Alg. 2) on the hierarchy: s1 pre-smoothing sweeps on the
+   top level, residual, projection, parent RHS (tau), ..., root solve,
+   correction prolongation, s2 post-smoothing.  u_top [ndof_top] updated in
+   place, f_top the top RHS.  If rnorm_out != NULL the Euclidean norm of the
+   top residual after pre-smoothing is written there (synchronizes). */
+int dgfas_fas_vcycle(void* ctx, double* u_top, const double* f_top, double* rnorm_out);
+
+/* V-cycles with crossover smoothing (Sec. 6.1) until r_2 <= rtol * r_2^0 or
+   max_cycles: s1 top sweeps, then per cycle the stopping test on the top
+   residual, the FAS down/up legs and sc top sweeps.  Synchronizes every cycle
+   for the stopping test.  Returns OK, NOT_CONVERGED or DIVERGED. */
+int dgfas_solve(void* ctx, double* u_top, const double* f_top, double rtol, int max_cycles,
+                dgfas_info* info);
+
+/* Euclidean norm of v [ndof of level] (deterministic two-pass reduction). */
+int dgfas_norm(void* ctx, int level, const double* v, double* out_host);
+
+/* Replaces the per-element surrogate coefficients g0..g3 of Eq. (10) on
+   `level` (default: the geometric surrogate of Sec. 4.3.1) by g [n_elem][4]
+   (device, FP64), e.g. the output of the learned surrogate. */
+int dgfas_set_surrogate(void* ctx, int level, const double* g);
+
+/* Copies the current surrogate coefficients of `level` to g [n_elem][4] (device). */
+int dgfas_get_surrogate(void* ctx, int level, double* g);
+
+/* Enables (1) or disables (0) CUDA-graph replay of the V-cycle body in
+   dgfas_fas_vcycle / dgfas_solve (captured on first use per (u, f) pair). */
+int dgfas_use_graph(void* ctx, int enable);
+
+/* Per-kernel timing of `reps` smoother sweeps on `level` (level >= 1) with CUDA
+   events on the context's stream.  ms_out [4] (host) receives the average
+   duration in ms of: the smoother-precision residual, the FD kernel (gather,
+   fast diagonalization, weighting), the combine kernel, and the FP64 residual
+   apply of the V-cycle.  u is updated by the sweeps. */
+int dgfas_profile_sweep(void* ctx, int level, double* u, const double* g, int reps,
+                        double* ms_out);
+
+/* Measured FMA throughput of the current device in TFLOP/s (FP64 and FP32):
+   the denominators of the roofline of ALU-bound kernels. */
+int dgfas_fma_peak(double* tflops_fp64, double* tflops_fp32);
+
+/* Host-only (no device work): the fast-diagonalization data of one side variant
+   (variant = 3*left + right with 0 = interior, 1 = Dirichlet, 2 = Neumann) for
+   degree p, overlap delta and penalty mu_star (Sec. 4.3.1): subdomain width n,
+   S [n][n] (row = node, column = mode; S^T M S = I, S^T L S = diag(lambda)),
+   lambda [n] and the weights W [n].  Buffers of at least 16*16 / 16 doubles. */
+int dgfas_host_fd_variant(int p, double delta, double mu_star, int variant, double* S,
+                          double* lam, double* W, int* n_out);
+
+const char* dgfas_strerror(int code);
+const char* dgfas_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DGFAS_H */

@@ -1,0 +1,115 @@
+// Internal structures shared by the host setup, the kernels and the driver.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/dgfas.h"
+
+#define DGFAS_MAX_N 11     // p <= 10
+#define DGFAS_MAX_NS 16    // subdomain width per direction
+
+// Per-level device view passed by value to kernels.
+template <typename T>
+struct LevelView {
+  int ne, N, m, nsm;          // elements, nodes per direction, overlap layers, max subdomain width
+  int box;                    // 1: every element is an axis-aligned box (factors from h)
+  T nu, kappa;
+  const int* nbr;             // [ne][6]
+  const int* nbr27;           // [ne][27]
+  const signed char* cls;     // [ne]
+  const T* h;                 // [ne][3] box widths (box levels)
+  const T* G;                 // [ne][6][N^3] volume metric (general levels)
+  const T* fW;                // [ne][6][N^2] face quadrature weights (general)
+  const T* fc;                // [ne][6][3][N^2] W n . grad xi_t (general)
+  const T* mu;                // [ne][6] face penalty
+  const T* mass;              // [ne][N^3] lumped mass (kappa != 0, general) or null
+  const T* D;                 // [N][N]
+  const T* w;                 // [N] GLL weights
+  const T* x;                 // [N] GLL nodes
+  // Schwarz
+  const unsigned char* var;   // [ne][3] variant index 0..8 per direction
+  const T* g;                 // [ne][4] surrogate coefficients g0..g3
+  const T* S;                 // [9][nsm][nsm]  S[v][row][col]
+  const T* lam;               // [9][nsm]
+  const T* W;                 // [9][nsm]
+};
+
+struct TransferView {
+  int nef, nec, Nf, Nc, h;    // h: 1 for h-refinement (8 children)
+  const int* parent;          // [nef]
+  const int* octant;          // [nef]
+  const int* children;        // [nec][8] (-1 none); p-refinement: children[E][0] = E
+  const signed char* clsf;    // [nef] fine classes
+  const double* I;            // [2][Nf][Nc]
+  const double* P;            // [2][Nc][Nf]
+};
+
+struct LevelHost {
+  int p, N, ne, m, nsm, box;
+  long long ndof;
+  std::vector<int> nbr, nbr27, parent, octant;
+  std::vector<signed char> cls;
+  std::vector<double> corners;
+  // device arrays (FP64 and FP32 copies of the geometry / tables)
+  int *d_nbr = nullptr, *d_nbr27 = nullptr, *d_parent = nullptr, *d_octant = nullptr,
+      *d_children = nullptr;
+  signed char* d_cls = nullptr;
+  unsigned char* d_var = nullptr;
+  double *d_h = nullptr, *d_G = nullptr, *d_fW = nullptr, *d_fc = nullptr, *d_mu = nullptr,
+         *d_mass = nullptr, *d_D = nullptr, *d_w = nullptr, *d_g = nullptr, *d_S = nullptr,
+         *d_lam = nullptr, *d_W = nullptr, *d_x = nullptr;
+  float *f_h = nullptr, *f_G = nullptr, *f_fW = nullptr, *f_fc = nullptr, *f_mu = nullptr,
+        *f_mass = nullptr, *f_D = nullptr, *f_w = nullptr, *f_g = nullptr, *f_S = nullptr,
+        *f_lam = nullptr, *f_W = nullptr, *f_x = nullptr;
+  double *d_I = nullptr, *d_P = nullptr;   // transfer from level-1 to this level
+  // work vectors
+  double *u = nullptr, *gv = nullptr, *r = nullptr, *ubar = nullptr, *t = nullptr;
+  LevelView<double> v64;
+  LevelView<float> v32;
+  TransferView tr;
+};
+
+struct Ctx {
+  cudaStream_t stream = nullptr;
+  dgfas_params prm{};
+  double nu = 1.0, kappa = 0.0;
+  std::vector<LevelHost> lv;
+  // scratch
+  void* patch = nullptr;        // Schwarz patch buffer (max over levels)
+  size_t patch_bytes = 0;
+  float* r32 = nullptr;         // smoother residual (FP32 mode)
+  double* red = nullptr;        // reduction partials
+  double* red_host = nullptr;   // pinned
+  double* scg_buf = nullptr;    // SCG vectors (p, q, z, r0) for the largest level
+  double* dscal = nullptr;      // device scalars of the SCG recurrences
+  double* Ainv = nullptr;       // root inverse
+  int n_root = 0;
+  // graphs
+  int use_graph = 0;
+  cudaGraphExec_t gexec = nullptr;
+  const double* g_u = nullptr;
+  const double* g_f = nullptr;
+  int g_kind = -1;
+};
+
+// kernels.cu
+int launch_apply(Ctx& c, int l, int prec, const double* u, const double* b, void* out,
+                 double alpha);
+int launch_fd(Ctx& c, int l, int prec, const void* r);
+int launch_combine(Ctx& c, int l, int prec, double* u, double scale);
+int launch_combine_to(Ctx& c, int l, int prec, double* z);
+int launch_project(Ctx& c, int l, const double* uf);   // lv[l-1].u = ubar = P uf
+int launch_restrict(Ctx& c, int l, const double* rf, double* rc);
+int launch_prolong(Ctx& c, int l, double* uf);         // uf += I (lv[l-1].u - ubar)
+int launch_root(Ctx& c);
+int launch_sumsq(Ctx& c, const double* v, long long n, double* partial_out);
+int launch_dot(Ctx& c, const double* a, const double* b, long long n, double* partial_out);
+int launch_axpy(Ctx& c, long long n, double alpha, const double* x, double* y);
+int launch_node_coords(Ctx& c, int l, double* xyz);
+int launch_rhs(Ctx& c, const double* f, const double* uD, double* b);
+int launch_to_float(Ctx& c, const double* x, float* y, long long n);
+extern int g_red_blocks;
+
+void set_error(const std::string& s);

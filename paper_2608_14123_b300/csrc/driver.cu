@@ -1,0 +1,817 @@
+// C ABI of the hot path: level setup, operator, smoother, FAS V-cycle (Alg. 2)
+// and solve with crossover smoothing; CUDA-graph replay of the cycle body.
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "dgfas_internal.h"
+#include "setup_host.h"
+
+static thread_local std::string g_err;
+void set_error(const std::string& s) { g_err = s; }
+
+#define CK(x)                                                                 \
+  do {                                                                        \
+    cudaError_t e_ = (x);                                                     \
+    if (e_ != cudaSuccess) {                                                  \
+      set_error(std::string("CUDA: ") + cudaGetErrorString(e_) + " at " #x); \
+      return DGFAS_ERR_CUDA;                                                  \
+    }                                                                         \
+  } while (0)
+#define RET(x)                    \
+  do {                            \
+    int rc_ = (x);                \
+    if (rc_ != DGFAS_OK) return rc_; \
+  } while (0)
+
+template <typename T>
+static int upload(T** dst, const std::vector<T>& v) {
+  if (v.empty()) { *dst = nullptr; return DGFAS_OK; }
+  if (cudaMalloc((void**)dst, v.size() * sizeof(T)) != cudaSuccess) {
+    set_error("cudaMalloc failed in setup");
+    return DGFAS_ERR_OOM;
+  }
+  CK(cudaMemcpy(*dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+  return DGFAS_OK;
+}
+
+template <typename T>
+static int upload_f(float** dst, const std::vector<T>& v) {
+  std::vector<float> f(v.begin(), v.end());
+  return upload(dst, f);
+}
+
+static int dalloc(double** p, size_t n) {
+  if (n == 0) { *p = nullptr; return DGFAS_OK; }
+  if (cudaMalloc((void**)p, n * sizeof(double)) != cudaSuccess) {
+    set_error("cudaMalloc failed");
+    return DGFAS_ERR_OOM;
+  }
+  CK(cudaMemset(*p, 0, n * sizeof(double)));
+  return DGFAS_OK;
+}
+
+static char side_char(int nb) { return nb >= 0 ? 'i' : (nb == -1 ? 'd' : 'n'); }
+static int side_idx(int nb) { return nb >= 0 ? 0 : (nb == -1 ? 1 : 2); }
+
+// ---------------------------------------------------------------- one level
+static int build_level(Ctx& c, const dgfas_level& in, const dgfas_params& prm, LevelHost& H) {
+  const int p = in.p, N = p + 1, ne = in.n_elem;
+  if (p < 1 || p > 10 || ne <= 0) {
+    set_error("level: need 1 <= p <= 10 and n_elem > 0");
+    return DGFAS_ERR_UNSUPPORTED;
+  }
+  H.p = p; H.N = N; H.ne = ne;
+  H.ndof = (long long)ne * N * N * N;
+  H.nbr.assign(in.nbr, in.nbr + 6 * (size_t)ne);
+  H.nbr27.assign(in.nbr27, in.nbr27 + 27 * (size_t)ne);
+  H.cls.assign(in.cls, in.cls + ne);
+  H.corners.assign(in.corners, in.corners + 24 * (size_t)ne);
+  H.parent.assign(in.parent, in.parent + ne);
+  H.octant.assign(in.octant, in.octant + ne);
+  for (int e = 0; e < ne; ++e)
+    for (int f = 0; f < 6; ++f) {
+      int nb = H.nbr[6 * e + f];
+      if (nb >= ne || nb < -2) { set_error("nbr out of range"); return DGFAS_ERR_INVALID; }
+    }
+  for (size_t q = 0; q < H.nbr27.size(); ++q)
+    if (H.nbr27[q] >= ne || H.nbr27[q] < -1) { set_error("nbr27 out of range"); return DGFAS_ERR_INVALID; }
+  std::vector<double> x, w;
+  host::gll(p, x, w);
+  std::vector<double> D = host::diff_matrix(x);
+  const int N2 = N * N, N3 = N2 * N;
+  // box detection
+  H.box = 1;
+  std::vector<double> hbox(3 * (size_t)ne);
+  for (int e = 0; e < ne && H.box; ++e) H.box = host::is_box(&H.corners[24 * e], &hbox[3 * e]);
+  const double nu = c.nu;
+  std::vector<double> G, fW, fc, mass, mu(6 * (size_t)ne), hp(6 * (size_t)ne);
+  if (H.box) {
+    for (int e = 0; e < ne; ++e)
+      for (int f = 0; f < 6; ++f) hp[6 * e + f] = hbox[3 * e + f / 2];
+  } else {
+    G.assign((size_t)ne * 6 * N3, 0.0);
+    fW.assign((size_t)ne * 6 * N2, 0.0);
+    fc.assign((size_t)ne * 6 * 3 * N2, 0.0);
+    mass.assign((size_t)ne * N3, 0.0);
+    std::vector<double> Gi((size_t)N3 * 9), dJ(N3);
+    for (int e = 0; e < ne; ++e) {
+      const double* cr = &H.corners[24 * e];
+      double vol = 0.0;
+      for (int k = 0; k < N; ++k)
+        for (int j = 0; j < N; ++j)
+          for (int i = 0; i < N; ++i) {
+            const int n = (k * N + j) * N + i;
+            double X[3], J[9];
+            host::trilinear(cr, x[i], x[j], x[k], X, J);
+            double det = J[0] * (J[4] * J[8] - J[5] * J[7]) - J[1] * (J[3] * J[8] - J[5] * J[6]) +
+                         J[2] * (J[3] * J[7] - J[4] * J[6]);
+            if (!(det > 0)) {
+              set_error("non-positive Jacobian at a GLL node of element " + std::to_string(e));
+              return DGFAS_ERR_MESH;
+            }
+            double* gi = &Gi[(size_t)n * 9];
+            gi[0] = (J[4] * J[8] - J[5] * J[7]) / det;
+            gi[1] = (J[2] * J[7] - J[1] * J[8]) / det;
+            gi[2] = (J[1] * J[5] - J[2] * J[4]) / det;
+            gi[3] = (J[5] * J[6] - J[3] * J[8]) / det;
+            gi[4] = (J[0] * J[8] - J[2] * J[6]) / det;
+            gi[5] = (J[2] * J[3] - J[0] * J[5]) / det;
+            gi[6] = (J[3] * J[7] - J[4] * J[6]) / det;
+            gi[7] = (J[1] * J[6] - J[0] * J[7]) / det;
+            gi[8] = (J[0] * J[4] - J[1] * J[3]) / det;
+            dJ[n] = det;
+            const double wq = w[i] * w[j] * w[k];
+            vol += wq * det;
+            mass[(size_t)e * N3 + n] = wq * det;
+            // G_df = nu w J grad xi_d . grad xi_f ; rows of gi are grad xi_b
+            auto dot = [&](int d1, int d2) {
+              return gi[3 * d1] * gi[3 * d2] + gi[3 * d1 + 1] * gi[3 * d2 + 1] + gi[3 * d1 + 2] * gi[3 * d2 + 2];
+            };
+            const double s = nu * wq * det;
+            double* Ge = &G[(size_t)e * 6 * N3 + n];
+            Ge[0] = s * dot(0, 0);
+            Ge[N3] = s * dot(1, 1);
+            Ge[2 * N3] = s * dot(2, 2);
+            Ge[3 * N3] = s * dot(0, 1);
+            Ge[4 * N3] = s * dot(0, 2);
+            Ge[5 * N3] = s * dot(1, 2);
+          }
+      for (int f = 0; f < 6; ++f) {
+        const int d = f / 2, side = f % 2, end = side ? N - 1 : 0;
+        const double sg = side ? 1.0 : -1.0;
+        double area = 0.0;
+        for (int b = 0; b < N; ++b)
+          for (int a = 0; a < N; ++a) {
+            int i, j, k;
+            if (d == 0) { i = end; j = a; k = b; }
+            else if (d == 1) { i = a; j = end; k = b; }
+            else { i = a; j = b; k = end; }
+            const int n = (k * N + j) * N + i;
+            const double* gi = &Gi[(size_t)n * 9];
+            const double gd2 = gi[3 * d] * gi[3 * d] + gi[3 * d + 1] * gi[3 * d + 1] + gi[3 * d + 2] * gi[3 * d + 2];
+            const double wab = w[a] * w[b];
+            const double Wq = wab * dJ[n] * std::sqrt(gd2);
+            fW[((size_t)e * 6 + f) * N2 + b * N + a] = Wq;
+            area += Wq;
+            for (int t = 0; t < 3; ++t) {
+              const double gdt = gi[3 * d] * gi[3 * t] + gi[3 * d + 1] * gi[3 * t + 1] + gi[3 * d + 2] * gi[3 * t + 2];
+              fc[(((size_t)e * 6 + f) * 3 + t) * N2 + b * N + a] = sg * nu * wab * dJ[n] * gdt;
+            }
+          }
+        hp[6 * e + f] = vol / area;
+      }
+    }
+  }
+  for (int e = 0; e < ne; ++e)
+    for (int f = 0; f < 6; ++f) {
+      const int nb = H.nbr[6 * e + f];
+      const double own = p * (p + 1) / (2.0 * hp[6 * e + f]);
+      if (nb >= 0) {
+        const double oth = p * (p + 1) / (2.0 * hp[6 * nb + (f ^ 1)]);
+        mu[6 * e + f] = prm.mu_star * 0.5 * (own + oth);
+      } else {
+        mu[6 * e + f] = prm.mu_star * own;
+      }
+    }
+  // ---- Schwarz tables
+  H.m = host::overlap_layers(p, prm.delta);
+  if (H.m < 1 || H.m >= N) { set_error("overlap layers must satisfy 1 <= m < p+1"); return DGFAS_ERR_UNSUPPORTED; }
+  H.nsm = N + 2 * H.m;
+  if (H.nsm > DGFAS_MAX_NS) { set_error("subdomain width > 16"); return DGFAS_ERR_UNSUPPORTED; }
+  const int nsm = H.nsm;
+  std::vector<double> S(9 * (size_t)nsm * nsm, 0.0), lam(9 * (size_t)nsm, 0.0), Wt(9 * (size_t)nsm, 0.0);
+  const char sc[3] = {'i', 'd', 'n'};
+  for (int v = 0; v < 9; ++v) {
+    std::vector<double> Sv, lv, wv;
+    host::fd_variant(p, H.m, prm.mu_star, prm.delta, sc[v / 3], sc[v % 3], Sv, lv, wv);
+    const int n = (int)lv.size();
+    for (int r = 0; r < n; ++r) {
+      for (int q = 0; q < n; ++q) S[((size_t)v * nsm + r) * nsm + q] = Sv[r * n + q];
+      lam[v * nsm + r] = lv[r];
+      Wt[v * nsm + r] = wv[r];
+    }
+    for (int r = n; r < nsm; ++r) lam[v * nsm + r] = 1.0;   // padding, never read as divisor
+  }
+  std::vector<unsigned char> var(3 * (size_t)ne);
+  std::vector<double> g(4 * (size_t)ne);
+  for (int e = 0; e < ne; ++e) {
+    for (int d = 0; d < 3; ++d)
+      var[3 * e + d] = (unsigned char)(3 * side_idx(H.nbr[6 * e + 2 * d]) + side_idx(H.nbr[6 * e + 2 * d + 1]));
+    double dx[3];
+    host::surrogate_widths(&H.corners[24 * e], dx);
+    g[4 * e] = c.kappa * dx[0] * dx[1] * dx[2] / 8.0;
+    for (int i = 0; i < 3; ++i) g[4 * e + 1 + i] = nu * dx[(i + 1) % 3] * dx[(i + 2) % 3] / (2.0 * dx[i]);
+  }
+  (void)side_char;
+  // ---- uploads
+  RET(upload(&H.d_nbr, H.nbr));
+  RET(upload(&H.d_nbr27, H.nbr27));
+  RET(upload(&H.d_cls, H.cls));
+  RET(upload(&H.d_var, var));
+  RET(upload(&H.d_D, D));
+  RET(upload(&H.d_w, w));
+  RET(upload(&H.d_x, x));
+  RET(upload(&H.d_mu, mu));
+  RET(upload(&H.d_g, g));
+  RET(upload(&H.d_S, S));
+  RET(upload(&H.d_lam, lam));
+  RET(upload(&H.d_W, Wt));
+  RET(upload_f(&H.f_D, D));
+  RET(upload_f(&H.f_w, w));
+  RET(upload_f(&H.f_x, x));
+  RET(upload_f(&H.f_mu, mu));
+  RET(upload_f(&H.f_g, g));
+  RET(upload_f(&H.f_S, S));
+  RET(upload_f(&H.f_lam, lam));
+  RET(upload_f(&H.f_W, Wt));
+  if (H.box) {
+    RET(upload(&H.d_h, hbox));
+    RET(upload_f(&H.f_h, hbox));
+  } else {
+    RET(upload(&H.d_G, G));
+    RET(upload(&H.d_fW, fW));
+    RET(upload(&H.d_fc, fc));
+    RET(upload(&H.d_mass, mass));
+    RET(upload_f(&H.f_G, G));
+    RET(upload_f(&H.f_fW, fW));
+    RET(upload_f(&H.f_fc, fc));
+    RET(upload_f(&H.f_mass, mass));
+  }
+  auto fill = [&](auto& V, auto* h, auto* G_, auto* fW_, auto* fc_, auto* mu_, auto* mass_, auto* D_,
+                  auto* w_, auto* x_, auto* g_, auto* S_, auto* lam_, auto* W_) {
+    V.ne = ne; V.N = N; V.m = H.m; V.nsm = nsm; V.box = H.box;
+    V.nu = nu; V.kappa = c.kappa;
+    V.nbr = H.d_nbr; V.nbr27 = H.d_nbr27; V.cls = H.d_cls; V.var = H.d_var;
+    V.h = h; V.G = G_; V.fW = fW_; V.fc = fc_; V.mu = mu_; V.mass = mass_; V.D = D_; V.w = w_;
+    V.x = x_; V.g = g_; V.S = S_; V.lam = lam_; V.W = W_;
+  };
+  fill(H.v64, H.d_h, H.d_G, H.d_fW, H.d_fc, H.d_mu, H.d_mass, H.d_D, H.d_w, H.d_x, H.d_g, H.d_S,
+       H.d_lam, H.d_W);
+  fill(H.v32, H.f_h, H.f_G, H.f_fW, H.f_fc, H.f_mu, H.f_mass, H.f_D, H.f_w, H.f_x, H.f_g, H.f_S,
+       H.f_lam, H.f_W);
+  return DGFAS_OK;
+}
+
+// transfer matrices from level C (coarse) to level F (fine)
+static int build_transfer(LevelHost& C, LevelHost& F) {
+  const int Nf = F.N, Nc = C.N;
+  bool h = true, pref = true;
+  for (int e = 0; e < F.ne; ++e) {
+    if (F.octant[e] < 0) h = false; else pref = false;
+    if (F.parent[e] < 0 || F.parent[e] >= C.ne) { set_error("parent out of range"); return DGFAS_ERR_INVALID; }
+  }
+  if (!h && !pref) { set_error("a level mixes h- and p-children"); return DGFAS_ERR_INVALID; }
+  if (h && Nf != Nc) { set_error("h-refinement must keep the degree"); return DGFAS_ERR_INVALID; }
+  std::vector<double> xf, wf, xc, wc;
+  host::gll(F.p, xf, wf);
+  host::gll(C.p, xc, wc);
+  std::vector<double> I(2 * (size_t)Nf * Nc, 0.0), P(2 * (size_t)Nc * Nf, 0.0);
+  for (int s = 0; s < 2; ++s) {
+    std::vector<double> y(Nf);
+    for (int i = 0; i < Nf; ++i) y[i] = h ? 0.5 * (xf[i] + (s ? 1.0 : -1.0)) : xf[i];
+    std::vector<double> Ls = host::interp(xc, y);   // [Nf][Nc]
+    std::copy(Ls.begin(), Ls.end(), I.begin() + (size_t)s * Nf * Nc);
+    std::vector<double> yc(Nc), wgt(Nc);
+    for (int i = 0; i < Nc; ++i) {
+      if (!h) { yc[i] = xc[i]; wgt[i] = 1.0; continue; }
+      const bool inside = s ? xc[i] >= 0.0 : xc[i] <= 0.0;
+      wgt[i] = inside ? (xc[i] == 0.0 ? 0.5 : 1.0) : 0.0;
+      double t = 2.0 * xc[i] - (s ? 1.0 : -1.0);
+      yc[i] = std::min(1.0, std::max(-1.0, t));
+    }
+    std::vector<double> Lp = host::interp(xf, yc);  // [Nc][Nf]
+    for (int i = 0; i < Nc; ++i)
+      for (int j = 0; j < Nf; ++j) P[((size_t)s * Nc + i) * Nf + j] = wgt[i] * Lp[i * Nf + j];
+  }
+  std::vector<int> children(8 * (size_t)C.ne, -1);
+  for (int e = 0; e < F.ne; ++e) {
+    int slot = h ? F.octant[e] : 0;
+    if (slot < 0 || slot > 7) { set_error("octant out of range"); return DGFAS_ERR_INVALID; }
+    children[8 * (size_t)F.parent[e] + slot] = e;
+  }
+  RET(upload(&F.d_I, I));
+  RET(upload(&F.d_P, P));
+  RET(upload(&F.d_children, children));
+  RET(upload(&F.d_parent, F.parent));
+  RET(upload(&F.d_octant, F.octant));
+  F.tr.nef = F.ne; F.tr.nec = C.ne; F.tr.Nf = Nf; F.tr.Nc = Nc; F.tr.h = h ? 1 : 0;
+  F.tr.parent = F.d_parent; F.tr.octant = F.d_octant; F.tr.children = F.d_children;
+  F.tr.clsf = F.d_cls; F.tr.I = F.d_I; F.tr.P = F.d_P;
+  return DGFAS_OK;
+}
+
+// explicit inverse of the (SPD) root operator: columns A e_i by the apply kernel,
+// Cholesky factorization and inversion on the host
+static int build_root(Ctx& c) {
+  LevelHost& R = c.lv[0];
+  const int n = (int)R.ndof;
+  if (n > 4096) { set_error("root level larger than 4096 DoF"); return DGFAS_ERR_UNSUPPORTED; }
+  c.n_root = n;
+  double *E = nullptr, *Acol = nullptr;
+  RET(dalloc(&E, (size_t)n * n));
+  RET(dalloc(&Acol, (size_t)n * n));
+  std::vector<double> eye((size_t)n * n, 0.0);
+  for (int i = 0; i < n; ++i) eye[(size_t)i * n + i] = 1.0;
+  CK(cudaMemcpy(E, eye.data(), eye.size() * sizeof(double), cudaMemcpyHostToDevice));
+  for (int i = 0; i < n; ++i)
+    RET(launch_apply(c, 0, DGFAS_FP64, E + (size_t)i * n, nullptr, Acol + (size_t)i * n, 1.0));
+  CK(cudaStreamSynchronize(c.stream));
+  std::vector<double> A((size_t)n * n);
+  CK(cudaMemcpy(A.data(), Acol, A.size() * sizeof(double), cudaMemcpyDeviceToHost));
+  cudaFree(E);
+  cudaFree(Acol);
+  // symmetrize (row i of Acol = A e_i = column i), Cholesky A = L L^T (lower in place)
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < i; ++j) {
+      double s = 0.5 * (A[(size_t)i * n + j] + A[(size_t)j * n + i]);
+      A[(size_t)i * n + j] = A[(size_t)j * n + i] = s;
+    }
+  for (int j = 0; j < n; ++j) {
+    double s = A[(size_t)j * n + j];
+    for (int k = 0; k < j; ++k) s -= A[(size_t)j * n + k] * A[(size_t)j * n + k];
+    if (!(s > 0)) { set_error("root operator not positive definite"); return DGFAS_ERR_MESH; }
+    const double d = std::sqrt(s);
+    A[(size_t)j * n + j] = d;
+    for (int i = j + 1; i < n; ++i) {
+      double t = A[(size_t)i * n + j];
+      for (int k = 0; k < j; ++k) t -= A[(size_t)i * n + k] * A[(size_t)j * n + k];
+      A[(size_t)i * n + j] = t / d;
+    }
+  }
+  // inverse = L^-T L^-1, column by column
+  std::vector<double> inv((size_t)n * n), y(n);
+  for (int col = 0; col < n; ++col) {
+    for (int i = 0; i < n; ++i) {
+      double t = (i == col) ? 1.0 : 0.0;
+      for (int k = 0; k < i; ++k) t -= A[(size_t)i * n + k] * y[k];
+      y[i] = t / A[(size_t)i * n + i];
+    }
+    for (int i = n - 1; i >= 0; --i) {
+      double t = y[i];
+      for (int k = i + 1; k < n; ++k) t -= A[(size_t)k * n + i] * y[k];
+      y[i] = t / A[(size_t)i * n + i];
+    }
+    for (int i = 0; i < n; ++i) inv[(size_t)i * n + col] = y[i];
+  }
+  RET(upload(&c.Ainv, inv));
+  return DGFAS_OK;
+}
+
+static void free_level(LevelHost& H) {
+  void* ptrs[] = {H.d_nbr, H.d_nbr27, H.d_parent, H.d_octant, H.d_children, H.d_cls, H.d_var,
+                  H.d_h, H.d_G, H.d_fW, H.d_fc, H.d_mu, H.d_mass, H.d_D, H.d_w, H.d_g, H.d_S,
+                  H.d_lam, H.d_W, H.d_x, H.f_h, H.f_G, H.f_fW, H.f_fc, H.f_mu, H.f_mass, H.f_D,
+                  H.f_w, H.f_g, H.f_S, H.f_lam, H.f_W, H.f_x, H.d_I, H.d_P, H.u, H.gv, H.r,
+                  H.ubar, H.t};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+}
+
+extern "C" void dgfas_destroy(void* vctx) {
+  if (!vctx) return;
+  Ctx* c = (Ctx*)vctx;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  if (c->gexec) cudaGraphExecDestroy(c->gexec);
+  for (auto& H : c->lv) free_level(H);
+  void* ptrs[] = {c->patch, c->r32, c->red, c->scg_buf, c->dscal, c->Ainv};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  if (c->red_host) cudaFreeHost(c->red_host);
+  delete c;
+}
+
+extern "C" int dgfas_setup_levels(const dgfas_mesh* mesh, const dgfas_params* prm,
+                                  void* stream, void** out) {
+  if (!mesh || !prm || !out || mesh->n_levels < 1 || !mesh->levels) {
+    set_error("setup: null argument or no levels");
+    return DGFAS_ERR_INVALID;
+  }
+  if (!(prm->delta > 0 && prm->delta < 0.5) || !(prm->mu_star > 0) || prm->s1 < 0 ||
+      prm->s2 < 0 || prm->sc < 0 || !(mesh->nu > 0) || mesh->kappa < 0) {
+    set_error("setup: parameter out of range");
+    return DGFAS_ERR_INVALID;
+  }
+  if (prm->precision != DGFAS_FP64 && prm->precision != DGFAS_FP32) {
+    set_error("setup: unknown precision");
+    return DGFAS_ERR_INVALID;
+  }
+  Ctx* c = new Ctx();
+  c->stream = (cudaStream_t)stream;
+  c->prm = *prm;
+  c->nu = mesh->nu;
+  c->kappa = mesh->kappa;
+  c->lv.resize(mesh->n_levels);
+  int rc = DGFAS_OK;
+  size_t patch = 0, maxdof = 0;
+  for (int l = 0; l < mesh->n_levels && rc == DGFAS_OK; ++l) {
+    const dgfas_level& in = mesh->levels[l];
+    if (!in.corners || !in.nbr || !in.nbr27 || !in.cls || (l > 0 && (!in.parent || !in.octant))) {
+      set_error("setup: level arrays missing");
+      rc = DGFAS_ERR_INVALID;
+      break;
+    }
+    rc = build_level(*c, in, *prm, c->lv[l]);
+    if (rc != DGFAS_OK) break;
+    LevelHost& H = c->lv[l];
+    patch = std::max(patch, (size_t)H.ne * H.nsm * H.nsm * H.nsm * sizeof(double));
+    maxdof = std::max(maxdof, (size_t)H.ndof);
+    if (l > 0) rc = build_transfer(c->lv[l - 1], H);
+    if (rc != DGFAS_OK) break;
+    const bool top = l == mesh->n_levels - 1;
+    if (!top) {
+      rc = dalloc(&H.u, H.ndof);
+      if (!rc) rc = dalloc(&H.gv, H.ndof);
+      if (!rc) rc = dalloc(&H.ubar, H.ndof);
+      if (!rc) rc = dalloc(&H.t, H.ndof);
+    }
+    if (!rc) rc = dalloc(&H.r, H.ndof);
+  }
+  if (rc == DGFAS_OK) {
+    if (cudaMalloc(&c->patch, patch) != cudaSuccess) { set_error("patch buffer"); rc = DGFAS_ERR_OOM; }
+    c->patch_bytes = patch;
+  }
+  if (rc == DGFAS_OK && cudaMalloc((void**)&c->r32, maxdof * sizeof(float)) != cudaSuccess) {
+    set_error("r32 buffer");
+    rc = DGFAS_ERR_OOM;
+  }
+  if (rc == DGFAS_OK) rc = dalloc(&c->red, g_red_blocks + 64);
+  if (rc == DGFAS_OK && cudaMallocHost((void**)&c->red_host, (g_red_blocks + 64) * sizeof(double)) != cudaSuccess) {
+    set_error("pinned host buffer");
+    rc = DGFAS_ERR_OOM;
+  }
+  if (rc == DGFAS_OK && prm->smoother == DGFAS_SCG) rc = dalloc(&c->scg_buf, 5 * maxdof);
+  if (rc == DGFAS_OK) rc = dalloc(&c->dscal, 64);
+  if (rc == DGFAS_OK) rc = build_root(*c);
+  if (rc != DGFAS_OK) {
+    dgfas_destroy(c);
+    return rc;
+  }
+  *out = c;
+  return DGFAS_OK;
+}
+
+// ---------------------------------------------------------------- reductions
+static int norm_dev(Ctx& c, const double* v, long long n, double* out) {
+  RET(launch_sumsq(c, v, n, c.red));
+  CK(cudaMemcpyAsync(c.red_host, c.red, g_red_blocks * sizeof(double), cudaMemcpyDeviceToHost,
+                     c.stream));
+  CK(cudaStreamSynchronize(c.stream));
+  double s = 0.0;
+  for (int i = 0; i < g_red_blocks; ++i) s += c.red_host[i];
+  *out = std::sqrt(s);
+  return DGFAS_OK;
+}
+
+static int dot_dev(Ctx& c, const double* a, const double* b, long long n, double* out) {
+  RET(launch_dot(c, a, b, n, c.red));
+  CK(cudaMemcpyAsync(c.red_host, c.red, g_red_blocks * sizeof(double), cudaMemcpyDeviceToHost,
+                     c.stream));
+  CK(cudaStreamSynchronize(c.stream));
+  double s = 0.0;
+  for (int i = 0; i < g_red_blocks; ++i) s += c.red_host[i];
+  *out = s;
+  return DGFAS_OK;
+}
+
+// ---------------------------------------------------------------- smoothers
+// Schwarz correction z = sum_e R_s^T W (A~)^-1 R_s r of the residual in
+// lv[l].r (FP64) or c.r32 (FP32), added to u (add) or written to u.
+static int schwarz_correction(Ctx& c, int l, double* u, bool add) {
+  const int prec = c.prm.precision;
+  const void* r = prec == DGFAS_FP64 ? (const void*)c.lv[l].r : (const void*)c.r32;
+  RET(launch_fd(c, l, prec, r));
+  return add ? launch_combine(c, l, prec, u, 1.0) : launch_combine_to(c, l, prec, u);
+}
+
+static int residual_smoother(Ctx& c, int l, const double* u, const double* g) {
+  if (c.prm.precision == DGFAS_FP64) return launch_apply(c, l, DGFAS_FP64, u, g, c.lv[l].r, -1.0);
+  return launch_apply(c, l, DGFAS_FP32, u, g, c.r32, -1.0);
+}
+
+// Alg. 5
+static int was(Ctx& c, int l, double* u, const double* g, int n) {
+  for (int s = 0; s < n; ++s) {
+    RET(residual_smoother(c, l, u, g));
+    RET(schwarz_correction(c, l, u, true));
+  }
+  return DGFAS_OK;
+}
+
+// Alg. 6 with n iterations (FP64 recurrences; the Schwarz sweep in the
+// smoother precision).  Synchronizes for the scalar products.
+static int scg(Ctx& c, int l, double* u, const double* g, int n) {
+  LevelHost& H = c.lv[l];
+  const long long nd = H.ndof;
+  double *r = H.r, *p = c.scg_buf, *q = p + nd, *z = q + nd, *r0 = z + nd;
+  RET(launch_apply(c, l, DGFAS_FP64, u, g, r, -1.0));
+  double gamma = 0.0;
+  for (int i = 1; i <= n; ++i) {
+    if (c.prm.precision == DGFAS_FP32) RET(launch_to_float(c, r, c.r32, nd));
+    RET(schwarz_correction(c, l, z, false));
+    if (i > 1) {
+      CK(cudaMemcpyAsync(q, r, nd * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
+      RET(launch_axpy(c, nd, -1.0, r0, q));   // q = r - r0
+      double num;
+      RET(dot_dev(c, z, q, nd, &num));
+      const double beta = num / gamma;
+      // p = beta p + z
+      RET(launch_axpy(c, nd, beta - 1.0, p, p));
+      RET(launch_axpy(c, nd, 1.0, z, p));
+    } else {
+      CK(cudaMemcpyAsync(p, z, nd * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
+    }
+    RET(launch_apply(c, l, DGFAS_FP64, p, nullptr, q, 1.0));
+    RET(dot_dev(c, z, r, nd, &gamma));
+    double pq;
+    RET(dot_dev(c, p, q, nd, &pq));
+    const double alpha = gamma / pq;
+    CK(cudaMemcpyAsync(r0, r, nd * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
+    RET(launch_axpy(c, nd, -alpha, q, r));
+    RET(launch_axpy(c, nd, alpha, p, u));
+  }
+  return DGFAS_OK;
+}
+
+static int smooth(Ctx& c, int l, double* u, const double* g, int n) {
+  if (n <= 0) return DGFAS_OK;
+  if (c.prm.smoother == DGFAS_SCG) return scg(c, l, u, g, n);
+  return was(c, l, u, g, n);
+}
+
+// ---------------------------------------------------------------- FAS V-cycle
+// Alg. 2 below the top pre-smoothing: lv[L].r holds the top residual of uL.
+static int down_up(Ctx& c, double* uL, const double* fL) {
+  const int L = (int)c.lv.size() - 1;
+  for (int l = L; l >= 1; --l) {
+    double* ul = l == L ? uL : c.lv[l].u;
+    const double* gl = l == L ? fL : c.lv[l].gv;
+    if (l < L) {
+      RET(smooth(c, l, ul, gl, c.prm.s1));
+      RET(launch_apply(c, l, DGFAS_FP64, ul, gl, c.lv[l].r, -1.0));
+    }
+    RET(launch_project(c, l, ul));                                   // u_{l-1} = P u_l
+    RET(launch_restrict(c, l, c.lv[l].r, c.lv[l - 1].t));           // R r_l
+    RET(launch_apply(c, l - 1, DGFAS_FP64, c.lv[l - 1].u, c.lv[l - 1].t, c.lv[l - 1].gv, 1.0));
+  }
+  RET(launch_root(c));
+  for (int l = 1; l <= L; ++l) {
+    double* ul = l == L ? uL : c.lv[l].u;
+    const double* gl = l == L ? fL : c.lv[l].gv;
+    RET(launch_prolong(c, l, ul));
+    if (l < L) RET(smooth(c, l, ul, gl, c.prm.s2));
+  }
+  return DGFAS_OK;
+}
+
+static int vcycle_body(Ctx& c, double* u, const double* f) {
+  const int L = (int)c.lv.size() - 1;
+  RET(smooth(c, L, u, f, c.prm.s1));
+  RET(launch_apply(c, L, DGFAS_FP64, u, f, c.lv[L].r, -1.0));
+  RET(launch_sumsq(c, c.lv[L].r, c.lv[L].ndof, c.red));
+  if (L == 0) return DGFAS_OK;
+  RET(down_up(c, u, f));
+  return smooth(c, L, u, f, c.prm.s2);
+}
+
+static int solve_cycle_body(Ctx& c, double* u, const double* f) {
+  const int L = (int)c.lv.size() - 1;
+  RET(down_up(c, u, f));
+  RET(smooth(c, L, u, f, c.prm.sc));
+  RET(launch_apply(c, L, DGFAS_FP64, u, f, c.lv[L].r, -1.0));
+  return launch_sumsq(c, c.lv[L].r, c.lv[L].ndof, c.red);
+}
+
+static bool graph_ok(Ctx& c) { return c.use_graph && c.prm.smoother == DGFAS_WAS; }
+
+static int run_body(Ctx& c, int kind, double* u, const double* f) {
+  if (!graph_ok(c)) return kind == 0 ? vcycle_body(c, u, f) : solve_cycle_body(c, u, f);
+  if (!(c.gexec && c.g_u == u && c.g_f == f && c.g_kind == kind)) {
+    if (c.gexec) { cudaGraphExecDestroy(c.gexec); c.gexec = nullptr; }
+    // one uncaptured run sets the kernels' attributes; then capture
+    RET(kind == 0 ? vcycle_body(c, u, f) : solve_cycle_body(c, u, f));
+    CK(cudaStreamSynchronize(c.stream));
+    cudaGraph_t g;
+    CK(cudaStreamBeginCapture(c.stream, cudaStreamCaptureModeRelaxed));
+    int rc = kind == 0 ? vcycle_body(c, u, f) : solve_cycle_body(c, u, f);
+    cudaError_t ce = cudaStreamEndCapture(c.stream, &g);
+    if (rc != DGFAS_OK) return rc;
+    if (ce != cudaSuccess) { set_error("graph capture failed"); return DGFAS_ERR_CUDA; }
+    CK(cudaGraphInstantiate(&c.gexec, g, 0));
+    cudaGraphDestroy(g);
+    c.g_u = u; c.g_f = f; c.g_kind = kind;
+    return DGFAS_OK;   // this call's cycle already ran uncaptured
+  }
+  CK(cudaGraphLaunch(c.gexec, c.stream));
+  return DGFAS_OK;
+}
+
+static double host_norm(Ctx& c) {
+  double s = 0.0;
+  for (int i = 0; i < g_red_blocks; ++i) s += c.red_host[i];
+  return std::sqrt(s);
+}
+
+// ---------------------------------------------------------------- ABI
+extern "C" long long dgfas_level_ndof(void* ctx, int level) {
+  Ctx* c = (Ctx*)ctx;
+  if (!c || level < 0 || level >= (int)c->lv.size()) return DGFAS_ERR_INVALID;
+  return c->lv[level].ndof;
+}
+
+extern "C" int dgfas_node_coords(void* ctx, int level, double* xyz) {
+  Ctx* c = (Ctx*)ctx;
+  if (!c || !xyz || level < 0 || level >= (int)c->lv.size()) return DGFAS_ERR_INVALID;
+  return launch_node_coords(*c, level, xyz);
+}
+
+extern "C" int dgfas_assemble_rhs(void* ctx, const double* f, const double* uD, double* b) {
+  Ctx* c = (Ctx*)ctx;
+  if (!c || !f || !b) return DGFAS_ERR_INVALID;
+  return launch_rhs(*c, f, uD, b);
+}
+
+extern "C" int dgfas_apply_op(void* ctx, int level, const double* u, const double* g, double* out) {
+  Ctx* c = (Ctx*)ctx;
+  if (!c || !u || !out || u == out || level < 0 || level >= (int)c->lv.size()) {
+    set_error("apply_op: invalid argument");
+    return DGFAS_ERR_INVALID;
+  }
+  return g ? launch_apply(*c, level, DGFAS_FP64, u, g, out, -1.0)
+           : launch_apply(*c, level, DGFAS_FP64, u, nullptr, out, 1.0);
+}
+
+extern "C" int dgfas_schwarz_smooth(void* ctx, int level, double* u, const double* g, int n) {
+  Ctx* c = (Ctx*)ctx;
+  if (!c || !u || !g || n < 0 || level < 1 || level >= (int)c->lv.size()) {
+    set_error("schwarz_smooth: invalid argument (levels >= 1 have a smoother)");
+    return DGFAS_ERR_INVALID;
+  }
+  return smooth(*c, level, u, g, n);
+}
+
+extern "C" int dgfas_norm(void* ctx, int level, const double* v, double* out) {
+  Ctx* c = (Ctx*)ctx;
+  if (!c || !v || !out || level < 0 || level >= (int)c->lv.size()) return DGFAS_ERR_INVALID;
+  return norm_dev(*c, v, c->lv[level].ndof, out);
+}
+
+extern "C" int dgfas_fas_vcycle(void* ctx, double* u, const double* f, double* rnorm) {
+  Ctx* c = (Ctx*)ctx;
+  if (!c || !u || !f) return DGFAS_ERR_INVALID;
+  RET(run_body(*c, 0, u, f));
+  if (rnorm) {
+    CK(cudaMemcpyAsync(c->red_host, c->red, g_red_blocks * sizeof(double), cudaMemcpyDeviceToHost,
+                       c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    *rnorm = host_norm(*c);
+  }
+  return DGFAS_OK;
+}
+
+extern "C" int dgfas_solve(void* ctx, double* u, const double* f, double rtol, int max_cycles,
+                           dgfas_info* info) {
+  Ctx* c = (Ctx*)ctx;
+  if (!c || !u || !f || !(rtol > 0)) return DGFAS_ERR_INVALID;
+  if (max_cycles <= 0) max_cycles = c->prm.max_cycles > 0 ? c->prm.max_cycles : 50;
+  const int L = (int)c->lv.size() - 1;
+  auto t0 = std::chrono::steady_clock::now();
+  double r0;
+  RET(launch_apply(*c, L, DGFAS_FP64, u, f, c->lv[L].r, -1.0));
+  RET(norm_dev(*c, c->lv[L].r, c->lv[L].ndof, &r0));
+  RET(smooth(*c, L, u, f, c->prm.s1));
+  RET(launch_apply(*c, L, DGFAS_FP64, u, f, c->lv[L].r, -1.0));
+  int cycles = 0, rc = DGFAS_ERR_NOT_CONVERGED;
+  double r = r0;
+  if (info) { info->r0 = r0; memset(info->history, 0, sizeof(info->history)); }
+  if (!(r0 > 0)) rc = (r0 == 0) ? DGFAS_OK : DGFAS_ERR_DIVERGED;
+  while (rc == DGFAS_ERR_NOT_CONVERGED && cycles < max_cycles && L > 0) {
+    RET(run_body(*c, 1, u, f));
+    CK(cudaMemcpyAsync(c->red_host, c->red, g_red_blocks * sizeof(double), cudaMemcpyDeviceToHost,
+                       c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    r = host_norm(*c);
+    if (info && cycles < 128) info->history[cycles] = r;
+    ++cycles;
+    if (!std::isfinite(r) || r > 1e3 * r0) rc = DGFAS_ERR_DIVERGED;
+    else if (r <= rtol * r0) rc = DGFAS_OK;
+  }
+  auto t1 = std::chrono::steady_clock::now();
+  if (info) {
+    info->cycles = cycles;
+    info->r_final = r;
+    info->seconds = std::chrono::duration<double>(t1 - t0).count();
+  }
+  return rc;
+}
+
+extern "C" int dgfas_set_surrogate(void* ctx, int level, const double* g) {
+  Ctx* c = (Ctx*)ctx;
+  if (!c || !g || level < 0 || level >= (int)c->lv.size()) return DGFAS_ERR_INVALID;
+  LevelHost& H = c->lv[level];
+  const size_t n = 4 * (size_t)H.ne;
+  CK(cudaMemcpyAsync(H.d_g, g, n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+  std::vector<double> tmp(n);
+  CK(cudaMemcpyAsync(tmp.data(), H.d_g, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  std::vector<float> f(tmp.begin(), tmp.end());
+  CK(cudaMemcpy(H.f_g, f.data(), n * sizeof(float), cudaMemcpyHostToDevice));
+  return DGFAS_OK;
+}
+
+extern "C" int dgfas_get_surrogate(void* ctx, int level, double* g) {
+  Ctx* c = (Ctx*)ctx;
+  if (!c || !g || level < 0 || level >= (int)c->lv.size()) return DGFAS_ERR_INVALID;
+  LevelHost& H = c->lv[level];
+  CK(cudaMemcpyAsync(g, H.d_g, 4 * (size_t)H.ne * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+  return DGFAS_OK;
+}
+
+extern "C" int dgfas_use_graph(void* ctx, int enable) {
+  Ctx* c = (Ctx*)ctx;
+  if (!c) return DGFAS_ERR_INVALID;
+  c->use_graph = enable ? 1 : 0;
+  if (!enable && c->gexec) { cudaGraphExecDestroy(c->gexec); c->gexec = nullptr; }
+  return DGFAS_OK;
+}
+
+extern "C" const char* dgfas_strerror(int code) {
+  switch (code) {
+    case DGFAS_OK: return "ok";
+    case DGFAS_ERR_INVALID: return "invalid argument";
+    case DGFAS_ERR_OOM: return "device out of memory";
+    case DGFAS_ERR_CUDA: return "CUDA runtime error";
+    case DGFAS_ERR_MESH: return "invalid mesh (non-positive Jacobian or indefinite root)";
+    case DGFAS_ERR_NOT_CONVERGED: return "not converged within max_cycles";
+    case DGFAS_ERR_DIVERGED: return "diverged (NaN/Inf or residual growth)";
+    case DGFAS_ERR_UNSUPPORTED: return "unsupported configuration";
+  }
+  return "unknown error";
+}
+
+extern "C" const char* dgfas_last_error(void) { return g_err.c_str(); }
+
+// Host-only view of one fast-diagonalization variant (no device work): the
+// subdomain width n, S [n][n] (row = node, column = mode), lambda [n], W [n].
+extern "C" int dgfas_host_fd_variant(int p, double delta, double mu_star, int variant, double* S,
+                                     double* lam, double* W, int* n_out) {
+  if (p < 1 || p > 10 || variant < 0 || variant > 8 || !S || !lam || !W || !n_out ||
+      !(delta > 0 && delta < 0.5))
+    return DGFAS_ERR_INVALID;
+  const int m = host::overlap_layers(p, delta);
+  const char sc[3] = {'i', 'd', 'n'};
+  std::vector<double> Sv, lv, wv;
+  host::fd_variant(p, m, mu_star, delta, sc[variant / 3], sc[variant % 3], Sv, lv, wv);
+  const int n = (int)lv.size();
+  *n_out = n;
+  for (int i = 0; i < n * n; ++i) S[i] = Sv[i];
+  for (int i = 0; i < n; ++i) { lam[i] = lv[i]; W[i] = wv[i]; }
+  return DGFAS_OK;
+}
+
+// Per-kernel timing of the smoother on `level` with CUDA events on the
+// context's stream: `reps` sweeps; ms_out[0..3] = average duration of the
+// smoother-precision residual, the FD kernel, the combine kernel and the FP64
+// residual apply.  u is updated by the sweeps.
+extern "C" int dgfas_profile_sweep(void* ctx, int level, double* u, const double* g, int reps,
+                                   double* ms_out) {
+  Ctx* c = (Ctx*)ctx;
+  if (!c || !u || !g || !ms_out || reps <= 0 || level < 1 || level >= (int)c->lv.size())
+    return DGFAS_ERR_INVALID;
+  cudaEvent_t ev[5];
+  for (auto& e : ev) CK(cudaEventCreate(&e));
+  double acc[4] = {0, 0, 0, 0};
+  for (int r = 0; r < reps; ++r) {
+    CK(cudaEventRecord(ev[0], c->stream));
+    RET(residual_smoother(*c, level, u, g));
+    CK(cudaEventRecord(ev[1], c->stream));
+    const int prec = c->prm.precision;
+    const void* rr = prec == DGFAS_FP64 ? (const void*)c->lv[level].r : (const void*)c->r32;
+    RET(launch_fd(*c, level, prec, rr));
+    CK(cudaEventRecord(ev[2], c->stream));
+    RET(launch_combine(*c, level, prec, u, 1.0));
+    CK(cudaEventRecord(ev[3], c->stream));
+    RET(launch_apply(*c, level, DGFAS_FP64, u, g, c->lv[level].r, -1.0));
+    CK(cudaEventRecord(ev[4], c->stream));
+    CK(cudaEventSynchronize(ev[4]));
+    for (int k = 0; k < 4; ++k) {
+      float ms;
+      CK(cudaEventElapsedTime(&ms, ev[k], ev[k + 1]));
+      acc[k] += ms;
+    }
+  }
+  for (int k = 0; k < 4; ++k) ms_out[k] = acc[k] / reps;
+  for (auto& e : ev) cudaEventDestroy(e);
+  return DGFAS_OK;
+}
+
+int launch_fma_peak(cudaStream_t st, int fp64, int iters, double* tflops);
+
+// Measured FMA throughput (TFLOP/s) of this GPU in FP64 and FP32: the ALU roofline.
+extern "C" int dgfas_fma_peak(double* tflops_fp64, double* tflops_fp32) {
+  if (!tflops_fp64 || !tflops_fp32) return DGFAS_ERR_INVALID;
+  RET(launch_fma_peak(nullptr, 1, 4096, tflops_fp64));
+  return launch_fma_peak(nullptr, 0, 65536, tflops_fp32);
+}

@@ -1,0 +1,854 @@
+// sm_103a kernels of the hot path:
+//  k_apply    SIP operator / residual by sum factorization (Sec. 2.2, Eq. (2))
+//  k_fd       Schwarz gather + fast-diagonalization solve + weighting (Eqs. (9)-(11))
+//  k_combine  deterministic pull of the weighted subdomain corrections (Eq. (11))
+//  k_project / k_restrict / k_prolong   FAS transfers (Sec. 3.2, Alg. 2)
+//  k_root     dense root solve (inverse times vector)
+//  reductions, axpy, coordinates, right-hand side
+#include <cstdio>
+
+#include "dgfas_internal.h"
+
+int g_red_blocks = 592;   // 4 x 148 SMs
+
+#define CK(x)                                                                 \
+  do {                                                                        \
+    cudaError_t e_ = (x);                                                     \
+    if (e_ != cudaSuccess) {                                                  \
+      set_error(std::string("CUDA: ") + cudaGetErrorString(e_) + " at " #x); \
+      return DGFAS_ERR_CUDA;                                                  \
+    }                                                                         \
+  } while (0)
+
+template <typename T> __device__ __forceinline__ T ld(const T* p) { return __ldg(p); }
+
+// ============================================================================ apply
+// Team of N*N threads (tx, ty) per element, looping over k; EPB teams per CTA.
+// Shared memory per team: u, neighbour buffer, F1, F2, F3, face-flux R (6 N^3).
+// out = b + alpha * A u   (b may be null); rows of frozen elements are 0.
+template <int N, typename T, typename TU, typename TO, bool BOX>
+__global__ void k_apply(const LevelView<T> L, const TU* __restrict__ u,
+                        const TU* __restrict__ b, TO* __restrict__ out, T alpha) {
+  constexpr int N2 = N * N, N3 = N * N * N;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sD = reinterpret_cast<T*>(smem_raw);
+  T* sw = sD + N2;
+  T* base = sw + 16;
+  const int team = threadIdx.y;
+  T* us = base + team * 6 * N3;
+  T* nb = us + N3;
+  T* F1 = nb + N3;
+  T* F2 = F1 + N3;
+  T* F3 = F2 + N3;
+  T* Rf = F3 + N3;
+  const int tx = threadIdx.x % N, ty = threadIdx.x / N;
+  const int e = blockIdx.x * blockDim.y + team;
+  const bool valid = e < L.ne;
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x, nth = blockDim.x * blockDim.y;
+  for (int t = tid; t < N2; t += nth) sD[t] = L.D[t];
+  for (int t = tid; t < N; t += nth) sw[t] = L.w[t];
+  const size_t eo = (size_t)e * N3;
+  if (valid)
+    for (int k = 0; k < N; ++k) us[(k * N + ty) * N + tx] = (T)u[eo + (k * N + ty) * N + tx];
+  __syncthreads();
+  T hx = 0, hy = 0, hz = 0, g0 = 0, g1 = 0, g2 = 0;
+  if (BOX && valid) {
+    hx = L.h[3 * e];
+    hy = L.h[3 * e + 1];
+    hz = L.h[3 * e + 2];
+    g0 = L.nu * hy * hz / (T(2) * hx);
+    g1 = L.nu * hx * hz / (T(2) * hy);
+    g2 = L.nu * hx * hy / (T(2) * hz);
+  }
+  // ---- volume term: F = G grad_xi u
+  if (valid) {
+    for (int k = 0; k < N; ++k) {
+      const int n = (k * N + ty) * N + tx;
+      T d0 = 0, d1 = 0, d2 = 0;
+#pragma unroll
+      for (int l = 0; l < N; ++l) {
+        d0 += sD[tx * N + l] * us[(k * N + ty) * N + l];
+        d1 += sD[ty * N + l] * us[(k * N + l) * N + tx];
+        d2 += sD[k * N + l] * us[(l * N + ty) * N + tx];
+      }
+      T mass_u = 0;
+      if (BOX) {
+        const T w3 = sw[tx] * sw[ty] * sw[k];
+        F1[n] = g0 * w3 * d0;
+        F2[n] = g1 * w3 * d1;
+        F3[n] = g2 * w3 * d2;
+        if (L.kappa != T(0)) mass_u = L.kappa * w3 * hx * hy * hz * T(0.125) * us[n];
+      } else {
+        const T* G = L.G + (size_t)e * 6 * N3 + n;
+        const T G00 = ld(G), G11 = ld(G + N3), G22 = ld(G + 2 * N3), G01 = ld(G + 3 * N3),
+                G02 = ld(G + 4 * N3), G12 = ld(G + 5 * N3);
+        F1[n] = G00 * d0 + G01 * d1 + G02 * d2;
+        F2[n] = G01 * d0 + G11 * d1 + G12 * d2;
+        F3[n] = G02 * d0 + G12 * d1 + G22 * d2;
+        if (L.kappa != T(0)) mass_u = L.kappa * ld(L.mass + eo + n) * us[n];
+      }
+      Rf[n] = mass_u;
+    }
+  }
+  __syncthreads();
+  // ---- face terms, one face per pass (edge/corner nodes belong to several faces)
+  for (int f = 0; f < 6; ++f) {
+    const int d = f >> 1, side = f & 1;
+    const int nbid = valid ? L.nbr[6 * e + f] : -2;
+    if (nbid >= 0) {
+      const size_t no = (size_t)nbid * N3;
+      for (int k = 0; k < N; ++k) nb[(k * N + ty) * N + tx] = (T)u[no + (k * N + ty) * N + tx];
+    }
+    __syncthreads();
+    if (valid && nbid != -2) {
+      const int a = tx, bb = ty;
+      const int end = side ? N - 1 : 0, endp = N - 1 - end;
+      int i, j, k, ip, jp, kp;
+      if (d == 0) { i = end; j = a; k = bb; ip = endp; jp = a; kp = bb; }
+      else if (d == 1) { i = a; j = end; k = bb; ip = a; jp = endp; kp = bb; }
+      else { i = a; j = bb; k = end; ip = a; jp = bb; kp = endp; }
+      const int n = (k * N + j) * N + i;
+      const T um = us[n];
+      T c0, c1, c2, W, mu;
+      mu = L.mu[6 * e + f];
+      if (BOX) {
+        const T sgn = side ? T(1) : T(-1);
+        const T wab = sw[a] * sw[bb];
+        const T gd = d == 0 ? g0 : (d == 1 ? g1 : g2);
+        const T hd = d == 0 ? hx : (d == 1 ? hy : hz);
+        W = L.nu * wab * (hx * hy * hz / hd) * T(0.25);   // nu * surface weight
+        c0 = d == 0 ? sgn * gd * wab : T(0);
+        c1 = d == 1 ? sgn * gd * wab : T(0);
+        c2 = d == 2 ? sgn * gd * wab : T(0);
+      } else {
+        const size_t fo = ((size_t)e * 6 + f) * N2 + bb * N + a;
+        W = L.nu * ld(L.fW + fo);
+        const T* fc = L.fc + ((size_t)e * 6 + f) * 3 * N2 + bb * N + a;
+        c0 = ld(fc);
+        c1 = ld(fc + N2);
+        c2 = ld(fc + 2 * N2);
+      }
+      // own normal flux q- = sum_t c_t du/dxi_t
+      T qm = 0;
+      {
+        T d0 = 0, d1 = 0, d2 = 0;
+        if (!BOX || d == 0)
+          for (int l = 0; l < N; ++l) d0 += sD[i * N + l] * us[(k * N + j) * N + l];
+        if (!BOX || d == 1)
+          for (int l = 0; l < N; ++l) d1 += sD[j * N + l] * us[(k * N + l) * N + i];
+        if (!BOX || d == 2)
+          for (int l = 0; l < N; ++l) d2 += sD[k * N + l] * us[(l * N + j) * N + i];
+        qm = c0 * d0 + c1 * d1 + c2 * d2;
+      }
+      T flux, lift;
+      if (nbid >= 0) {
+        const int np = (kp * N + jp) * N + ip;
+        const T up = nb[np];
+        T cp0, cp1, cp2;
+        if (BOX) {
+          const T sgn = side ? T(-1) : T(1);
+          const T wab = sw[a] * sw[bb];
+          const T phx = L.h[3 * nbid], phy = L.h[3 * nbid + 1], phz = L.h[3 * nbid + 2];
+          const T gp = d == 0 ? L.nu * phy * phz / (T(2) * phx)
+                              : (d == 1 ? L.nu * phx * phz / (T(2) * phy)
+                                        : L.nu * phx * phy / (T(2) * phz));
+          cp0 = d == 0 ? sgn * gp * wab : T(0);
+          cp1 = d == 1 ? sgn * gp * wab : T(0);
+          cp2 = d == 2 ? sgn * gp * wab : T(0);
+        } else {
+          const T* fc = L.fc + ((size_t)nbid * 6 + (f ^ 1)) * 3 * N2 + bb * N + a;
+          cp0 = ld(fc);
+          cp1 = ld(fc + N2);
+          cp2 = ld(fc + 2 * N2);
+        }
+        T d0 = 0, d1 = 0, d2 = 0;
+        if (!BOX || d == 0)
+          for (int l = 0; l < N; ++l) d0 += sD[ip * N + l] * nb[(kp * N + jp) * N + l];
+        if (!BOX || d == 1)
+          for (int l = 0; l < N; ++l) d1 += sD[jp * N + l] * nb[(kp * N + l) * N + ip];
+        if (!BOX || d == 2)
+          for (int l = 0; l < N; ++l) d2 += sD[kp * N + l] * nb[(l * N + jp) * N + ip];
+        const T qp = cp0 * d0 + cp1 * d1 + cp2 * d2;
+        const T jump = um - up;
+        flux = mu * W * jump - T(0.5) * (qm - qp);
+        lift = T(-0.5) * jump;
+      } else {   // Dirichlet
+        flux = T(2) * mu * W * um - qm;
+        lift = -um;
+      }
+      Rf[n] += flux;
+      F1[n] += c0 * lift;
+      F2[n] += c1 * lift;
+      F3[n] += c2 * lift;
+    }
+    __syncthreads();
+  }
+  // ---- transposed reference gradient
+  if (!valid) return;
+  const bool frozen = L.cls[e] == DGFAS_FROZEN;
+  for (int k = 0; k < N; ++k) {
+    const int n = (k * N + ty) * N + tx;
+    T r = Rf[n];
+#pragma unroll
+    for (int l = 0; l < N; ++l) {
+      r += sD[l * N + tx] * F1[(k * N + ty) * N + l];
+      r += sD[l * N + ty] * F2[(k * N + l) * N + tx];
+      r += sD[l * N + k] * F3[(l * N + ty) * N + tx];
+    }
+    T o = alpha * r;
+    if (b) o += (T)b[eo + n];
+    out[eo + n] = frozen ? TO(0) : (TO)o;
+  }
+}
+
+template <int N, typename T, typename TU, typename TO>
+static int apply_N(const LevelView<T>& L, const TU* u, const TU* b, TO* out, T alpha,
+                   cudaStream_t st) {
+  constexpr int N2 = N * N, N3 = N * N * N;
+  int epb = (128 + N2 - 1) / N2;
+  size_t smem = (N2 + 16 + (size_t)6 * N3 * epb) * sizeof(T);
+  while (epb > 1 && smem > 100 * 1024) {
+    --epb;
+    smem = (N2 + 16 + (size_t)6 * N3 * epb) * sizeof(T);
+  }
+  dim3 blk(N2, epb), grd((L.ne + epb - 1) / epb);
+  if (L.box) {
+    auto kf = k_apply<N, T, TU, TO, true>;
+    CK(cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    kf<<<grd, blk, smem, st>>>(L, u, b, out, alpha);
+  } else {
+    auto kf = k_apply<N, T, TU, TO, false>;
+    CK(cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    kf<<<grd, blk, smem, st>>>(L, u, b, out, alpha);
+  }
+  CK(cudaGetLastError());
+  return DGFAS_OK;
+}
+
+template <typename T, typename TU, typename TO>
+static int apply_disp(const LevelView<T>& L, const TU* u, const TU* b, TO* out, T alpha,
+                      cudaStream_t st) {
+  switch (L.N) {
+    case 2: return apply_N<2>(L, u, b, out, alpha, st);
+    case 3: return apply_N<3>(L, u, b, out, alpha, st);
+    case 4: return apply_N<4>(L, u, b, out, alpha, st);
+    case 5: return apply_N<5>(L, u, b, out, alpha, st);
+    case 6: return apply_N<6>(L, u, b, out, alpha, st);
+    case 7: return apply_N<7>(L, u, b, out, alpha, st);
+    case 8: return apply_N<8>(L, u, b, out, alpha, st);
+    case 9: return apply_N<9>(L, u, b, out, alpha, st);
+    case 10: return apply_N<10>(L, u, b, out, alpha, st);
+    case 11: return apply_N<11>(L, u, b, out, alpha, st);
+  }
+  set_error("apply: unsupported N");
+  return DGFAS_ERR_UNSUPPORTED;
+}
+
+// prec 0: FP64 in/out; prec 1: FP32 arithmetic on FP64 u/b, FP32 out
+int launch_apply(Ctx& c, int l, int prec, const double* u, const double* b, void* out,
+                 double alpha) {
+  LevelHost& H = c.lv[l];
+  if (prec == DGFAS_FP64)
+    return apply_disp<double, double, double>(H.v64, u, b, (double*)out, alpha, c.stream);
+  return apply_disp<float, double, float>(H.v32, u, b, (float*)out, (float)alpha, c.stream);
+}
+
+// ============================================================================ FD
+// One team of NS*NS threads (a, b) per element, looping over c.  Gathers the
+// residual patch R_s r (zero outside the mesh and on frozen elements), applies
+// (S3 x S2 x S1) D^-1 (S3^T x S2^T x S1^T), multiplies by W and writes the
+// weighted correction patch to `patch` [ne][NS^3] (row stride NS).
+__device__ __forceinline__ void side_map(int v, int a, int N, int m, int& off, int& idx) {
+  // v: 0..8 = ii,id,in,di,dd,dn,ni,nd,nn ; left interior iff v < 3
+  const int left_i = v < 3;
+  if (left_i) {
+    if (a < m) { off = -1; idx = N - m + a; return; }
+    a -= m;
+  }
+  if (a < N) { off = 0; idx = a; return; }
+  off = 1;
+  idx = a - N;
+}
+
+__host__ __device__ __forceinline__ int var_size(int v, int N, int m) {
+  const int li = v < 3, ri = (v % 3) == 0;
+  return N + m * (li + ri);
+}
+
+template <int NS, typename T, typename TR>
+__global__ void k_fd(const LevelView<T> L, const TR* __restrict__ r, T* __restrict__ patch) {
+  constexpr int NS2 = NS * NS, NS3 = NS * NS * NS;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int team = threadIdx.y;
+  T* X = reinterpret_cast<T*>(smem_raw) + team * (2 * NS3 + 3 * NS2 + 6 * NS);
+  T* Y = X + NS3;
+  T* S1 = Y + NS3;
+  T* S2 = S1 + NS2;
+  T* S3 = S2 + NS2;
+  T* l1 = S3 + NS2;
+  T* l2 = l1 + NS;
+  T* l3 = l2 + NS;
+  T* w1 = l3 + NS;
+  T* w2 = w1 + NS;
+  T* w3 = w2 + NS;
+  const int a = threadIdx.x % NS, b = threadIdx.x / NS;
+  const int e0 = blockIdx.x * blockDim.y + team;
+  const bool valid = e0 < L.ne;          // every thread reaches every barrier below
+  const int e = valid ? e0 : L.ne - 1;
+  const bool active = valid && L.cls[e] != DGFAS_FROZEN;
+  const int N = L.N, m = L.m, N3 = N * N * N;
+  const int v1 = L.var[3 * e], v2 = L.var[3 * e + 1], v3 = L.var[3 * e + 2];
+  const int n1 = var_size(v1, N, m), n2 = var_size(v2, N, m);
+  const int n3 = valid ? var_size(v3, N, m) : 0;
+  const int nsm = L.nsm;
+  // tables (sizes follow the level's nsm <= NS)
+  for (int t = threadIdx.x; t < nsm * nsm; t += NS2) {
+    const int rr = t / nsm, cc = t % nsm;
+    S1[rr * NS + cc] = L.S[((size_t)v1 * nsm + rr) * nsm + cc];
+    S2[rr * NS + cc] = L.S[((size_t)v2 * nsm + rr) * nsm + cc];
+    S3[rr * NS + cc] = L.S[((size_t)v3 * nsm + rr) * nsm + cc];
+  }
+  if (threadIdx.x < nsm) {
+    const int t = threadIdx.x;
+    l1[t] = L.lam[v1 * nsm + t]; l2[t] = L.lam[v2 * nsm + t]; l3[t] = L.lam[v3 * nsm + t];
+    w1[t] = L.W[v1 * nsm + t];   w2[t] = L.W[v2 * nsm + t];   w3[t] = L.W[v3 * nsm + t];
+  }
+  // gather
+  const bool in_ab = a < n1 && b < n2;
+  if (in_ab && active) {
+    int ox, ix, oy, iy;
+    side_map(v1, a, N, m, ox, ix);
+    side_map(v2, b, N, m, oy, iy);
+    for (int c = 0; c < n3; ++c) {
+      int oz, iz;
+      side_map(v3, c, N, m, oz, iz);
+      const int src = L.nbr27[27 * e + (ox + 1) + 3 * (oy + 1) + 9 * (oz + 1)];
+      T val = T(0);
+      if (src >= 0) val = (T)r[(size_t)src * N3 + (iz * N + iy) * N + ix];
+      X[(c * NS + b) * NS + a] = val;
+    }
+  }
+  // (teams are independent: a CTA holds whole teams and all threads reach the barriers)
+  __syncthreads();
+  // S1^T along a : Y[c][b][a] = sum_a' S1[a'][a] X[c][b][a']
+  if (in_ab)
+    for (int c = 0; c < n3; ++c) {
+      T s = 0;
+      for (int q = 0; q < n1; ++q) s += S1[q * NS + a] * X[(c * NS + b) * NS + q];
+      Y[(c * NS + b) * NS + a] = s;
+    }
+  __syncthreads();
+  // S2^T along b
+  if (in_ab)
+    for (int c = 0; c < n3; ++c) {
+      T s = 0;
+      for (int q = 0; q < n2; ++q) s += S2[q * NS + b] * Y[(c * NS + q) * NS + a];
+      X[(c * NS + b) * NS + a] = s;
+    }
+  __syncthreads();
+  // S3^T along c, scale by D^-1, S3 along c (the column stays in registers)
+  const T g0 = L.g[4 * e], g1 = L.g[4 * e + 1], g2 = L.g[4 * e + 2], g3 = L.g[4 * e + 3];
+  if (in_ab) {
+    T col[NS], tmp[NS];
+#pragma unroll
+    for (int c = 0; c < NS; ++c) col[c] = c < n3 ? X[(c * NS + b) * NS + a] : T(0);
+#pragma unroll
+    for (int c = 0; c < NS; ++c) {
+      T s = 0;
+#pragma unroll
+      for (int q = 0; q < NS; ++q) s += S3[q * NS + c] * col[q];
+      tmp[c] = c < n3 ? s / (g0 + g1 * l1[a] + g2 * l2[b] + g3 * l3[c]) : T(0);
+    }
+#pragma unroll
+    for (int c = 0; c < NS; ++c) {
+      T s = 0;
+#pragma unroll
+      for (int q = 0; q < NS; ++q) s += S3[c * NS + q] * tmp[q];
+      if (c < n3) Y[(c * NS + b) * NS + a] = s;
+    }
+  }
+  __syncthreads();
+  // S2 along b
+  if (in_ab)
+    for (int c = 0; c < n3; ++c) {
+      T s = 0;
+      for (int q = 0; q < n2; ++q) s += S2[b * NS + q] * Y[(c * NS + q) * NS + a];
+      X[(c * NS + b) * NS + a] = s;
+    }
+  __syncthreads();
+  // S1 along a, weight, write
+  if (in_ab && valid) {
+    T* P = patch + (size_t)e * NS3;
+    for (int c = 0; c < n3; ++c) {
+      T s = 0;
+      for (int q = 0; q < n1; ++q) s += S1[a * NS + q] * X[(c * NS + b) * NS + q];
+      P[(c * NS + b) * NS + a] = active ? s * w1[a] * w2[b] * w3[c] : T(0);
+    }
+  }
+}
+
+template <int NS, typename T, typename TR>
+static int fd_NS(const LevelView<T>& L, const TR* r, T* patch, cudaStream_t st) {
+  constexpr int NS2 = NS * NS, NS3 = NS2 * NS;
+  int epb = (128 + NS2 - 1) / NS2;
+  size_t per = (2 * NS3 + 3 * NS2 + 6 * NS) * sizeof(T);
+  while (epb > 1 && per * epb > 96 * 1024) --epb;
+  size_t smem = per * epb;
+  auto kf = k_fd<NS, T, TR>;
+  CK(cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  dim3 blk(NS2, epb), grd((L.ne + epb - 1) / epb);
+  kf<<<grd, blk, smem, st>>>(L, r, patch);
+  CK(cudaGetLastError());
+  return DGFAS_OK;
+}
+
+template <typename T, typename TR>
+static int fd_disp(const LevelView<T>& L, const TR* r, T* patch, cudaStream_t st) {
+  // the patch stride is the level's nsm; instantiate NS == nsm exactly
+  switch (L.nsm) {
+    case 2: return fd_NS<2>(L, r, patch, st);
+    case 3: return fd_NS<3>(L, r, patch, st);
+    case 4: return fd_NS<4>(L, r, patch, st);
+    case 5: return fd_NS<5>(L, r, patch, st);
+    case 6: return fd_NS<6>(L, r, patch, st);
+    case 7: return fd_NS<7>(L, r, patch, st);
+    case 8: return fd_NS<8>(L, r, patch, st);
+    case 9: return fd_NS<9>(L, r, patch, st);
+    case 10: return fd_NS<10>(L, r, patch, st);
+    case 11: return fd_NS<11>(L, r, patch, st);
+    case 12: return fd_NS<12>(L, r, patch, st);
+    case 13: return fd_NS<13>(L, r, patch, st);
+    case 14: return fd_NS<14>(L, r, patch, st);
+    case 15: return fd_NS<15>(L, r, patch, st);
+    case 16: return fd_NS<16>(L, r, patch, st);
+  }
+  set_error("fd: unsupported subdomain width");
+  return DGFAS_ERR_UNSUPPORTED;
+}
+
+int launch_fd(Ctx& c, int l, int prec, const void* r) {
+  LevelHost& H = c.lv[l];
+  if (prec == DGFAS_FP64)
+    return fd_disp<double, double>(H.v64, (const double*)r, (double*)c.patch, c.stream);
+  return fd_disp<float, float>(H.v32, (const float*)r, (float*)c.patch, c.stream);
+}
+
+// ============================================================================ combine
+// One thread per node of the level: u[e][n] = scale_u * u + sum of the weighted
+// patch entries of every subdomain that covers the node (own element and the up
+// to 26 neighbours whose overlap layers reach it).  Frozen entries untouched.
+template <typename T, bool ADD>
+__global__ void k_combine(const LevelView<T> L, const T* __restrict__ patch,
+                          double* __restrict__ u) {
+  const int N = L.N, N3 = N * N * N, m = L.m, nsm = L.nsm;
+  const size_t NS3 = (size_t)nsm * nsm * nsm;
+  const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid >= (long long)L.ne * N3) return;
+  const int e = (int)(gid / N3), n = (int)(gid % N3);
+  if (L.cls[e] == DGFAS_FROZEN) {
+    if (!ADD) u[gid] = 0.0;
+    return;
+  }
+  const int i = n % N, j = (n / N) % N, k = n / (N * N);
+  const int idx[3] = {i, j, k};
+  // per direction: candidate offsets (own always; -1 if i < m; +1 if i >= N - m)
+  int lo[3], hi[3];
+  for (int d = 0; d < 3; ++d) {
+    lo[d] = idx[d] < m ? -1 : 0;
+    hi[d] = idx[d] >= N - m ? 1 : 0;
+  }
+  double s = 0.0;
+  for (int oz = lo[2]; oz <= hi[2]; ++oz)
+    for (int oy = lo[1]; oy <= hi[1]; ++oy)
+      for (int ox = lo[0]; ox <= hi[0]; ++ox) {
+        const int src = L.nbr27[27 * e + (ox + 1) + 3 * (oy + 1) + 9 * (oz + 1)];
+        if (src < 0 || L.cls[src] == DGFAS_FROZEN) continue;
+        const int o[3] = {ox, oy, oz};
+        int pidx[3];
+        for (int d = 0; d < 3; ++d) {
+          const int v = L.var[3 * src + d];
+          const int mL = v < 3 ? m : 0;
+          pidx[d] = o[d] == 0 ? idx[d] + mL : (o[d] < 0 ? mL + N + idx[d] : idx[d] - (N - m));
+        }
+        s += (double)patch[(size_t)src * NS3 + ((size_t)pidx[2] * nsm + pidx[1]) * nsm + pidx[0]];
+      }
+  if (ADD) u[gid] += s;
+  else u[gid] = s;
+}
+
+int launch_combine(Ctx& c, int l, int prec, double* u, double) {
+  LevelHost& H = c.lv[l];
+  const long long n = H.ndof;
+  const int bs = 256;
+  const unsigned grd = (unsigned)((n + bs - 1) / bs);
+  if (prec == DGFAS_FP64)
+    k_combine<double, true><<<grd, bs, 0, c.stream>>>(H.v64, (const double*)c.patch, u);
+  else
+    k_combine<float, true><<<grd, bs, 0, c.stream>>>(H.v32, (const float*)c.patch, u);
+  CK(cudaGetLastError());
+  return DGFAS_OK;
+}
+
+int launch_combine_to(Ctx& c, int l, int prec, double* z) {
+  LevelHost& H = c.lv[l];
+  const long long n = H.ndof;
+  const int bs = 256;
+  const unsigned grd = (unsigned)((n + bs - 1) / bs);
+  if (prec == DGFAS_FP64)
+    k_combine<double, false><<<grd, bs, 0, c.stream>>>(H.v64, (const double*)c.patch, z);
+  else
+    k_combine<float, false><<<grd, bs, 0, c.stream>>>(H.v32, (const float*)c.patch, z);
+  CK(cudaGetLastError());
+  return DGFAS_OK;
+}
+
+// ============================================================================ transfers
+// Tensor-product application Y = (A3 x A2 x A1) X on one element, A_d [no][ni]
+// row-major, by three passes through shared memory.  Team-wide (all threads of
+// the CTA), sizes <= 11.
+__device__ void tensor3(const double* A1, const double* A2, const double* A3, int no, int ni,
+                        const double* X, double* T1, double* T2, double* Y, int tid, int nth) {
+  for (int t = tid; t < ni * ni * no; t += nth) {   // T1[k][j][a]
+    const int a = t % no, j = (t / no) % ni, k = t / (no * ni);
+    double s = 0;
+    for (int i = 0; i < ni; ++i) s += A1[a * ni + i] * X[(k * ni + j) * ni + i];
+    T1[(k * ni + j) * no + a] = s;
+  }
+  __syncthreads();
+  for (int t = tid; t < ni * no * no; t += nth) {   // T2[k][b][a]
+    const int a = t % no, bq = (t / no) % no, k = t / (no * no);
+    double s = 0;
+    for (int j = 0; j < ni; ++j) s += A2[bq * ni + j] * T1[(k * ni + j) * no + a];
+    T2[(k * no + bq) * no + a] = s;
+  }
+  __syncthreads();
+  for (int t = tid; t < no * no * no; t += nth) {   // Y[c][b][a]
+    const int a = t % no, bq = (t / no) % no, cq = t / (no * no);
+    double s = 0;
+    for (int k = 0; k < ni; ++k) s += A3[cq * ni + k] * T2[(k * no + bq) * no + a];
+    Y[(cq * no + bq) * no + a] = s;
+  }
+  __syncthreads();
+}
+
+#define TMAX (DGFAS_MAX_N * DGFAS_MAX_N * DGFAS_MAX_N)
+
+// P (fine -> coarse projection) or R (= I^T) gathered over the active children
+// of each coarse element: one CTA per coarse element.
+template <bool RESTRICT>
+__global__ void k_gather_children(const TransferView T, const double* __restrict__ xf,
+                                  double* __restrict__ xc, double* __restrict__ xcopy) {
+  __shared__ double X[TMAX], T1[TMAX], T2[TMAX], Y[TMAX], A[3][DGFAS_MAX_N * DGFAS_MAX_N];
+  const int E = blockIdx.x, tid = threadIdx.x, nth = blockDim.x;
+  const int Nf = T.Nf, Nc = T.Nc, Nf3 = Nf * Nf * Nf, Nc3 = Nc * Nc * Nc;
+  double acc[8];
+  for (int q = 0; q < 8; ++q) acc[q] = 0.0;
+  int any = 0;
+  for (int s = 0; s < (T.h ? 8 : 1); ++s) {
+    const int ch = T.children[8 * E + s];
+    if (ch < 0 || T.clsf[ch] == DGFAS_FROZEN) continue;
+    any = 1;
+    const int oct = T.octant[ch];
+    for (int t = tid; t < Nf3; t += nth) X[t] = xf[(size_t)ch * Nf3 + t];
+    for (int d = 0; d < 3; ++d) {
+      const int side = oct < 0 ? 0 : ((oct >> d) & 1);
+      for (int t = tid; t < Nc * Nf; t += nth) {
+        const int rr = t / Nf, cc = t % Nf;   // output (coarse) row rr, input (fine) col cc
+        A[d][t] = RESTRICT ? T.I[((size_t)side * Nf + cc) * Nc + rr]   // (I^T)[rr][cc]
+                           : T.P[((size_t)side * Nc + rr) * Nf + cc];
+      }
+    }
+    __syncthreads();
+    tensor3(A[0], A[1], A[2], Nc, Nf, X, T1, T2, Y, tid, nth);
+    for (int q = 0, t = tid; t < Nc3; t += nth, ++q) acc[q] += Y[t];
+    __syncthreads();
+  }
+  if (!any) return;
+  for (int q = 0, t = tid; t < Nc3; t += nth, ++q) {
+    xc[(size_t)E * Nc3 + t] = acc[q];
+    if (xcopy) xcopy[(size_t)E * Nc3 + t] = acc[q];
+  }
+}
+
+// u_f += I (u_c - ubar_c) on active fine elements; frozen fine elements take
+// u_f = I u_c (frozen update, Alg. 2).  One CTA per fine element.
+__global__ void k_prolong(const TransferView T, const double* __restrict__ uc,
+                          const double* __restrict__ ubar, double* __restrict__ uf) {
+  __shared__ double X[TMAX], T1[TMAX], T2[TMAX], Y[TMAX], A[3][DGFAS_MAX_N * DGFAS_MAX_N];
+  const int e = blockIdx.x, tid = threadIdx.x, nth = blockDim.x;
+  const int Nf = T.Nf, Nc = T.Nc, Nf3 = Nf * Nf * Nf, Nc3 = Nc * Nc * Nc;
+  const int par = T.parent[e], oct = T.octant[e];
+  const bool frozen = T.clsf[e] == DGFAS_FROZEN;
+  for (int t = tid; t < Nc3; t += nth)
+    X[t] = uc[(size_t)par * Nc3 + t] - (frozen ? 0.0 : ubar[(size_t)par * Nc3 + t]);
+  for (int d = 0; d < 3; ++d) {
+    const int side = oct < 0 ? 0 : ((oct >> d) & 1);
+    for (int t = tid; t < Nf * Nc; t += nth) A[d][t] = T.I[(size_t)side * Nf * Nc + t];
+  }
+  __syncthreads();
+  tensor3(A[0], A[1], A[2], Nf, Nc, X, T1, T2, Y, tid, nth);
+  for (int t = tid; t < Nf3; t += nth) {
+    const size_t g = (size_t)e * Nf3 + t;
+    uf[g] = frozen ? Y[t] : uf[g] + Y[t];
+  }
+}
+
+int launch_project(Ctx& c, int l, const double* uf) {
+  LevelHost& F = c.lv[l];
+  LevelHost& C = c.lv[l - 1];
+  k_gather_children<false><<<C.ne, 256, 0, c.stream>>>(F.tr, uf, C.u, C.ubar);
+  CK(cudaGetLastError());
+  return DGFAS_OK;
+}
+
+int launch_restrict(Ctx& c, int l, const double* rf, double* rc) {
+  LevelHost& F = c.lv[l];
+  LevelHost& C = c.lv[l - 1];
+  k_gather_children<true><<<C.ne, 256, 0, c.stream>>>(F.tr, rf, rc, nullptr);
+  CK(cudaGetLastError());
+  return DGFAS_OK;
+}
+
+int launch_prolong(Ctx& c, int l, double* uf) {
+  LevelHost& F = c.lv[l];
+  LevelHost& C = c.lv[l - 1];
+  k_prolong<<<F.ne, 128, 0, c.stream>>>(F.tr, C.u, C.ubar, uf);
+  CK(cudaGetLastError());
+  return DGFAS_OK;
+}
+
+// ============================================================================ root
+// u_0 = A_0^-1 g_0 with the precomputed inverse: one warp per row.
+__global__ void k_root(const double* __restrict__ Ainv, const double* __restrict__ g,
+                       double* __restrict__ u, int n) {
+  const int row = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32, lane = threadIdx.x % 32;
+  if (row >= n) return;
+  double s = 0.0;
+  for (int j = lane; j < n; j += 32) s += Ainv[(size_t)row * n + j] * g[j];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if (lane == 0) u[row] = s;
+}
+
+int launch_root(Ctx& c) {
+  const int n = c.n_root;
+  k_root<<<(n + 7) / 8, 256, 0, c.stream>>>(c.Ainv, c.lv[0].gv, c.lv[0].u, n);
+  CK(cudaGetLastError());
+  return DGFAS_OK;
+}
+
+// ============================================================================ reductions
+// Deterministic: fixed grid, per-block tree sums in a fixed order; the host (or a
+// final kernel) adds the g_red_blocks partials in index order.
+template <bool DOT>
+__global__ void k_partial(const double* __restrict__ a, const double* __restrict__ b,
+                          long long n, double* __restrict__ part) {
+  __shared__ double sh[256];
+  double s = 0.0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    s += DOT ? a[i] * b[i] : a[i] * a[i];
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+}
+
+int launch_sumsq(Ctx& c, const double* v, long long n, double* part) {
+  k_partial<false><<<g_red_blocks, 256, 0, c.stream>>>(v, nullptr, n, part);
+  CK(cudaGetLastError());
+  return DGFAS_OK;
+}
+
+int launch_dot(Ctx& c, const double* a, const double* b, long long n, double* part) {
+  k_partial<true><<<g_red_blocks, 256, 0, c.stream>>>(a, b, n, part);
+  CK(cudaGetLastError());
+  return DGFAS_OK;
+}
+
+__global__ void k_axpy(long long n, double alpha, const double* __restrict__ x,
+                       double* __restrict__ y) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] += alpha * x[i];
+}
+
+int launch_axpy(Ctx& c, long long n, double alpha, const double* x, double* y) {
+  k_axpy<<<(unsigned)((n + 255) / 256), 256, 0, c.stream>>>(n, alpha, x, y);
+  CK(cudaGetLastError());
+  return DGFAS_OK;
+}
+
+__global__ void k_to_float(const double* __restrict__ x, float* __restrict__ y, long long n) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] = (float)x[i];
+}
+
+int launch_to_float(Ctx& c, const double* x, float* y, long long n) {
+  k_to_float<<<(unsigned)((n + 255) / 256), 256, 0, c.stream>>>(x, y, n);
+  CK(cudaGetLastError());
+  return DGFAS_OK;
+}
+
+// ============================================================================ coordinates
+__global__ void k_coords(const LevelView<double> L, const double* __restrict__ corners,
+                         double* __restrict__ xyz) {
+  const int N = L.N, N3 = N * N * N;
+  const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid >= (long long)L.ne * N3) return;
+  const int e = (int)(gid / N3), n = (int)(gid % N3);
+  const double xi[3] = {L.x[n % N], L.x[(n / N) % N], L.x[n / (N * N)]};
+  double X[3] = {0, 0, 0};
+  for (int c = 0; c < 8; ++c) {
+    double f = 1.0;
+    for (int d = 0; d < 3; ++d) f *= 0.5 * (1.0 + (((c >> d) & 1) ? 1.0 : -1.0) * xi[d]);
+    for (int a = 0; a < 3; ++a) X[a] += f * corners[(size_t)e * 24 + c * 3 + a];
+  }
+  for (int a = 0; a < 3; ++a) xyz[gid * 3 + a] = X[a];
+}
+
+int launch_node_coords(Ctx& c, int l, double* xyz) {
+  LevelHost& H = c.lv[l];
+  double* dcorn = nullptr;
+  CK(cudaMallocAsync(&dcorn, H.corners.size() * sizeof(double), c.stream));
+  CK(cudaMemcpyAsync(dcorn, H.corners.data(), H.corners.size() * sizeof(double),
+                     cudaMemcpyHostToDevice, c.stream));
+  k_coords<<<(unsigned)((H.ndof + 255) / 256), 256, 0, c.stream>>>(H.v64, dcorn, xyz);
+  CK(cudaGetLastError());
+  CK(cudaFreeAsync(dcorn, c.stream));
+  return DGFAS_OK;
+}
+
+// ============================================================================ RHS
+// b = M f + Dirichlet terms of Eq. (2): 2 mu nu W u_D at face nodes and the
+// lifting -nu (dv/dn) u_D through the transposed reference gradient.
+template <int N, bool BOX>
+__global__ void k_rhs(const LevelView<double> L, const double* __restrict__ f,
+                      const double* __restrict__ uD, double* __restrict__ b) {
+  constexpr int N2 = N * N, N3 = N2 * N;
+  __shared__ double sD[N2], sw[N], F1[N3], F2[N3], F3[N3], R[N3];
+  const int e = blockIdx.x, tx = threadIdx.x % N, ty = threadIdx.x / N;
+  for (int t = threadIdx.x; t < N2; t += N2) sD[t] = L.D[t];
+  if (threadIdx.x < N) sw[threadIdx.x] = L.w[threadIdx.x];
+  __syncthreads();
+  double hx = 0, hy = 0, hz = 0;
+  if (BOX) { hx = L.h[3 * e]; hy = L.h[3 * e + 1]; hz = L.h[3 * e + 2]; }
+  const size_t eo = (size_t)e * N3;
+  for (int k = 0; k < N; ++k) {
+    const int n = (k * N + ty) * N + tx;
+    const double mass = BOX ? sw[tx] * sw[ty] * sw[k] * hx * hy * hz * 0.125 : L.mass[eo + n];
+    R[n] = mass * f[eo + n];
+    F1[n] = F2[n] = F3[n] = 0.0;
+  }
+  __syncthreads();
+  for (int fc = 0; fc < 6; ++fc) {
+    if (uD && L.nbr[6 * e + fc] == -1) {
+      const int d = fc >> 1, side = fc & 1, end = side ? N - 1 : 0, a = tx, bb = ty;
+      int i, j, k;
+      if (d == 0) { i = end; j = a; k = bb; }
+      else if (d == 1) { i = a; j = end; k = bb; }
+      else { i = a; j = bb; k = end; }
+      const int n = (k * N + j) * N + i;
+      double W, c0, c1, c2;
+      if (BOX) {
+        const double wab = sw[a] * sw[bb], sgn = side ? 1.0 : -1.0;
+        const double hd = d == 0 ? hx : (d == 1 ? hy : hz);
+        const double gd = L.nu * (hx * hy * hz / hd) / (2.0 * hd);
+        W = L.nu * wab * (hx * hy * hz / hd) * 0.25;
+        c0 = d == 0 ? sgn * gd * wab : 0.0;
+        c1 = d == 1 ? sgn * gd * wab : 0.0;
+        c2 = d == 2 ? sgn * gd * wab : 0.0;
+      } else {
+        W = L.nu * L.fW[((size_t)e * 6 + fc) * N2 + bb * N + a];
+        const double* cc = L.fc + ((size_t)e * 6 + fc) * 3 * N2 + bb * N + a;
+        c0 = cc[0]; c1 = cc[N2]; c2 = cc[2 * N2];
+      }
+      const double ud = uD[eo + n];
+      R[n] += 2.0 * L.mu[6 * e + fc] * W * ud;
+      F1[n] -= c0 * ud;
+      F2[n] -= c1 * ud;
+      F3[n] -= c2 * ud;
+    }
+    __syncthreads();
+  }
+  for (int k = 0; k < N; ++k) {
+    const int n = (k * N + ty) * N + tx;
+    double r = R[n];
+    for (int l = 0; l < N; ++l) {
+      r += sD[l * N + tx] * F1[(k * N + ty) * N + l];
+      r += sD[l * N + ty] * F2[(k * N + l) * N + tx];
+      r += sD[l * N + k] * F3[(l * N + ty) * N + tx];
+    }
+    b[eo + n] = r;
+  }
+}
+
+template <int N>
+static int rhs_N(Ctx& c, const double* f, const double* uD, double* b) {
+  LevelHost& H = c.lv.back();
+  if (H.box) k_rhs<N, true><<<H.ne, N * N, 0, c.stream>>>(H.v64, f, uD, b);
+  else k_rhs<N, false><<<H.ne, N * N, 0, c.stream>>>(H.v64, f, uD, b);
+  CK(cudaGetLastError());
+  return DGFAS_OK;
+}
+
+int launch_rhs(Ctx& c, const double* f, const double* uD, double* b) {
+  switch (c.lv.back().N) {
+    case 2: return rhs_N<2>(c, f, uD, b);
+    case 3: return rhs_N<3>(c, f, uD, b);
+    case 4: return rhs_N<4>(c, f, uD, b);
+    case 5: return rhs_N<5>(c, f, uD, b);
+    case 6: return rhs_N<6>(c, f, uD, b);
+    case 7: return rhs_N<7>(c, f, uD, b);
+    case 8: return rhs_N<8>(c, f, uD, b);
+    case 9: return rhs_N<9>(c, f, uD, b);
+    case 10: return rhs_N<10>(c, f, uD, b);
+    case 11: return rhs_N<11>(c, f, uD, b);
+  }
+  return DGFAS_ERR_UNSUPPORTED;
+}
+
+// ============================================================================ FMA peak
+// Roofline denominator for the ALU-bound kernels: independent FMA chains
+// (8 per thread) in FP64 or FP32, grid of 16 CTAs x 256 threads per SM.
+template <typename T>
+__global__ void k_fma_peak(T* out, int iters, T a, T b) {
+  T x[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) x[q] = (T)(threadIdx.x + q);
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) x[q] = fma(x[q], a, b);
+  }
+  T s = 0;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) s += x[q];
+  if (s == (T)12345.678) out[0] = s;   // keeps the chains alive
+}
+
+int launch_fma_peak(cudaStream_t st, int fp64, int iters, double* tflops) {
+  int dev, nsm;
+  CK(cudaGetDevice(&dev));
+  CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  void* out;
+  CK(cudaMalloc(&out, 16));
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  const int grid = nsm * 16, blk = 256;
+  for (int rep = 0; rep < 2; ++rep) {   // first run warms up
+    CK(cudaEventRecord(e0, st));
+    if (fp64) k_fma_peak<double><<<grid, blk, 0, st>>>((double*)out, iters, 0.999999, 1e-7);
+    else k_fma_peak<float><<<grid, blk, 0, st>>>((float*)out, iters, 0.999999f, 1e-7f);
+    CK(cudaEventRecord(e1, st));
+    CK(cudaEventSynchronize(e1));
+  }
+  float ms;
+  CK(cudaEventElapsedTime(&ms, e0, e1));
+  *tflops = 2.0 * 8.0 * iters * (double)grid * blk / (ms * 1e-3) / 1e12;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(out);
+  return DGFAS_OK;
+}

@@ -1,0 +1,243 @@
+"""Thin ctypes binding of the dgfas C ABI (include/dgfas.h).
+
+Argument marshalling only: every step of the hot path runs in the sm_103a
+kernels of libdgfas.so.  Device vectors are torch CUDA tensors (FP64,
+contiguous); their data pointers and the current torch stream are passed to
+the library.  The binding raises if the library is missing: there is no
+fallback path.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libdgfas.so")
+
+DGFAS_FP64, DGFAS_FP32 = 0, 1
+DGFAS_WAS, DGFAS_SCG = 0, 1
+ERRORS = {0: "ok", -1: "INVALID", -2: "OOM", -3: "CUDA", -4: "MESH", -5: "NOT_CONVERGED",
+          -6: "DIVERGED", -7: "UNSUPPORTED"}
+
+
+class DgfasError(RuntimeError):
+    def __init__(self, code, where, detail=""):
+        self.code = code
+        super().__init__(f"{where}: {ERRORS.get(code, code)} {detail}")
+
+
+class dgfas_level(ctypes.Structure):
+    _fields_ = [("p", ctypes.c_int), ("n_elem", ctypes.c_int),
+                ("corners", ctypes.POINTER(ctypes.c_double)),
+                ("nbr", ctypes.POINTER(ctypes.c_int)), ("nbr27", ctypes.POINTER(ctypes.c_int)),
+                ("parent", ctypes.POINTER(ctypes.c_int)), ("octant", ctypes.POINTER(ctypes.c_int)),
+                ("cls", ctypes.POINTER(ctypes.c_byte))]
+
+
+class dgfas_mesh(ctypes.Structure):
+    _fields_ = [("n_levels", ctypes.c_int), ("levels", ctypes.POINTER(dgfas_level)),
+                ("nu", ctypes.c_double), ("kappa", ctypes.c_double)]
+
+
+class dgfas_params(ctypes.Structure):
+    _fields_ = [("mu_star", ctypes.c_double), ("delta", ctypes.c_double),
+                ("s1", ctypes.c_int), ("s2", ctypes.c_int), ("sc", ctypes.c_int),
+                ("precision", ctypes.c_int), ("smoother", ctypes.c_int),
+                ("max_cycles", ctypes.c_int)]
+
+
+class dgfas_info(ctypes.Structure):
+    _fields_ = [("cycles", ctypes.c_int), ("r0", ctypes.c_double), ("r_final", ctypes.c_double),
+                ("seconds", ctypes.c_double), ("history", ctypes.c_double * 128)]
+
+
+SYMBOLS = ["dgfas_setup_levels", "dgfas_destroy", "dgfas_level_ndof", "dgfas_node_coords",
+           "dgfas_assemble_rhs", "dgfas_apply_op", "dgfas_schwarz_smooth", "dgfas_fas_vcycle",
+           "dgfas_solve", "dgfas_norm", "dgfas_set_surrogate", "dgfas_get_surrogate",
+           "dgfas_use_graph", "dgfas_profile_sweep", "dgfas_fma_peak", "dgfas_host_fd_variant", "dgfas_strerror", "dgfas_last_error"]
+
+_lib = None
+
+
+def load():
+    """Loads libdgfas.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} missing: run paper_2608_14123_b300/build.py")
+    lib = ctypes.CDLL(LIB_PATH)
+    P, I, D, LL = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_longlong
+    sig = {
+        "dgfas_setup_levels": (I, [ctypes.POINTER(dgfas_mesh), ctypes.POINTER(dgfas_params), P,
+                                   ctypes.POINTER(P)]),
+        "dgfas_destroy": (None, [P]),
+        "dgfas_level_ndof": (LL, [P, I]),
+        "dgfas_node_coords": (I, [P, I, P]),
+        "dgfas_assemble_rhs": (I, [P, P, P, P]),
+        "dgfas_apply_op": (I, [P, I, P, P, P]),
+        "dgfas_schwarz_smooth": (I, [P, I, P, P, I]),
+        "dgfas_fas_vcycle": (I, [P, P, P, ctypes.POINTER(D)]),
+        "dgfas_solve": (I, [P, P, P, D, I, ctypes.POINTER(dgfas_info)]),
+        "dgfas_norm": (I, [P, I, P, ctypes.POINTER(D)]),
+        "dgfas_set_surrogate": (I, [P, I, P]),
+        "dgfas_get_surrogate": (I, [P, I, P]),
+        "dgfas_use_graph": (I, [P, I]),
+        "dgfas_host_fd_variant": (I, [I, D, D, I, P, P, P, ctypes.POINTER(I)]),
+        "dgfas_profile_sweep": (I, [P, I, P, P, I, P]),
+        "dgfas_fma_peak": (I, [ctypes.POINTER(D), ctypes.POINTER(D)]),
+        "dgfas_strerror": (ctypes.c_char_p, [I]),
+        "dgfas_last_error": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(code, where):
+    if code != 0:
+        raise DgfasError(code, where, load().dgfas_last_error().decode())
+    return code
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    assert t.is_cuda and t.is_contiguous(), "device tensors must be contiguous CUDA tensors"
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream():
+    import torch
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+class Solver:
+    """Owns one dgfas context: the hierarchy `levels` (root first, as produced by
+    paper_2608_14123_b300.workloads) and the solver parameters."""
+
+    def __init__(self, levels, mu_star, delta, s1=2, s2=2, sc=4, precision=DGFAS_FP64,
+                 smoother=DGFAS_WAS, nu=1.0, kappa=0.0, max_cycles=50):
+        lib = load()
+        self._keep = []
+        arr = (dgfas_level * len(levels))()
+        for i, lv in enumerate(levels):
+            ne = lv["nbr"].shape[0]
+            corners = np.ascontiguousarray(lv["corners"], dtype=np.float64)
+            nbr = np.ascontiguousarray(lv["nbr"], dtype=np.int32)
+            nbr27 = np.ascontiguousarray(lv["nbr27"], dtype=np.int32)
+            parent = np.ascontiguousarray(lv["parent"], dtype=np.int32)
+            octant = np.ascontiguousarray(lv["octant"], dtype=np.int32)
+            cls = np.ascontiguousarray(lv["cls"], dtype=np.int8)
+            self._keep += [corners, nbr, nbr27, parent, octant, cls]
+            arr[i] = dgfas_level(lv["p"], ne,
+                                 corners.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                 nbr.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                                 nbr27.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                                 parent.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                                 octant.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                                 cls.ctypes.data_as(ctypes.POINTER(ctypes.c_byte)))
+        mesh = dgfas_mesh(len(levels), arr, nu, kappa)
+        prm = dgfas_params(mu_star, delta, s1, s2, sc, precision, smoother, max_cycles)
+        ctx = ctypes.c_void_p()
+        _check(lib.dgfas_setup_levels(ctypes.byref(mesh), ctypes.byref(prm), _stream(),
+                                      ctypes.byref(ctx)), "dgfas_setup_levels")
+        self.ctx = ctx
+        self.n_levels = len(levels)
+        self.levels = levels
+        self._keep = None
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            load().dgfas_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- ABI calls (same names, marshalling only)
+    def ndof(self, level=-1):
+        level = level % self.n_levels
+        return int(load().dgfas_level_ndof(self.ctx, level))
+
+    def dgfas_node_coords(self, level, xyz):
+        _check(load().dgfas_node_coords(self.ctx, level % self.n_levels, _ptr(xyz)), "node_coords")
+
+    def dgfas_assemble_rhs(self, f, uD, b):
+        _check(load().dgfas_assemble_rhs(self.ctx, _ptr(f), _ptr(uD), _ptr(b)), "assemble_rhs")
+
+    def dgfas_apply_op(self, level, u, g, out):
+        _check(load().dgfas_apply_op(self.ctx, level % self.n_levels, _ptr(u), _ptr(g), _ptr(out)),
+               "apply_op")
+
+    def dgfas_schwarz_smooth(self, level, u, g, n):
+        _check(load().dgfas_schwarz_smooth(self.ctx, level % self.n_levels, _ptr(u), _ptr(g), n),
+               "schwarz_smooth")
+
+    def dgfas_fas_vcycle(self, u, f, want_norm=True):
+        r = ctypes.c_double(0.0)
+        _check(load().dgfas_fas_vcycle(self.ctx, _ptr(u), _ptr(f),
+                                       ctypes.byref(r) if want_norm else None), "fas_vcycle")
+        return r.value
+
+    def dgfas_solve(self, u, f, rtol=1e-10, max_cycles=50, raise_on_fail=True):
+        info = dgfas_info()
+        code = load().dgfas_solve(self.ctx, _ptr(u), _ptr(f), rtol, max_cycles, ctypes.byref(info))
+        if raise_on_fail:
+            _check(code, "solve")
+        hist = [info.r0] + list(info.history[:min(info.cycles, 128)])
+        return dict(code=code, cycles=info.cycles, r0=info.r0, r_final=info.r_final,
+                    seconds=info.seconds, history=hist)
+
+    def dgfas_norm(self, level, v):
+        r = ctypes.c_double(0.0)
+        _check(load().dgfas_norm(self.ctx, level % self.n_levels, _ptr(v), ctypes.byref(r)), "norm")
+        return r.value
+
+    def dgfas_set_surrogate(self, level, g):
+        _check(load().dgfas_set_surrogate(self.ctx, level % self.n_levels, _ptr(g)), "set_surrogate")
+
+    def dgfas_get_surrogate(self, level, g):
+        _check(load().dgfas_get_surrogate(self.ctx, level % self.n_levels, _ptr(g)), "get_surrogate")
+
+    def dgfas_use_graph(self, enable):
+        _check(load().dgfas_use_graph(self.ctx, 1 if enable else 0), "use_graph")
+
+    def dgfas_profile_sweep(self, level, u, g, reps):
+        ms = np.zeros(4)
+        _check(load().dgfas_profile_sweep(self.ctx, level % self.n_levels, _ptr(u), _ptr(g), reps,
+                                          ms.ctypes.data_as(ctypes.c_void_p)), "profile_sweep")
+        return dict(residual_smoother=ms[0], fd=ms[1], combine=ms[2], residual_fp64=ms[3])
+
+    # ---- conveniences built from the calls above
+    def node_coords(self, level=-1):
+        import torch
+        xyz = torch.empty((self.ndof(level), 3), dtype=torch.float64, device="cuda")
+        self.dgfas_node_coords(level, xyz)
+        return xyz
+
+
+def dgfas_host_fd_variant(p, delta, mu_star, variant):
+    """Host-side FD tables of one side variant: (S [n, n], lam [n], W [n])."""
+    S = np.zeros(256)
+    lam = np.zeros(16)
+    W = np.zeros(16)
+    n = ctypes.c_int(0)
+    dp = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+    _check(load().dgfas_host_fd_variant(p, delta, mu_star, variant, dp(S), dp(lam), dp(W),
+                                        ctypes.byref(n)), "host_fd_variant")
+    k = n.value
+    return S[:k * k].reshape(k, k), lam[:k], W[:k]
+
+
+def dgfas_fma_peak():
+    """Measured FP64 and FP32 FMA throughput (TFLOP/s) of the current device."""
+    a, b = ctypes.c_double(0), ctypes.c_double(0)
+    _check(load().dgfas_fma_peak(ctypes.byref(a), ctypes.byref(b)), "fma_peak")
+    return a.value, b.value
