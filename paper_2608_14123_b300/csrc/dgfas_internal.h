@@ -66,6 +66,7 @@ struct LevelHost {
   double *d_I = nullptr, *d_P = nullptr;   // transfer from level-1 to this level
   // work vectors
   double *u = nullptr, *gv = nullptr, *r = nullptr, *ubar = nullptr, *t = nullptr;
+  double* delta = nullptr;   // smoother correction (FP64 or FP32 storage)
   LevelView<double> v64;
   LevelView<float> v32;
   TransferView tr;
@@ -79,7 +80,9 @@ struct Ctx {
   // scratch
   void* patch = nullptr;        // Schwarz patch buffer (max over levels)
   size_t patch_bytes = 0;
-  float* r32 = nullptr;         // smoother residual (FP32 mode)
+  void* rw = nullptr;           // smoother working residual (smoother precision)
+  cudaStream_t cap = nullptr;   // internal stream for graph capture / replay
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
   double* red = nullptr;        // reduction partials
   double* red_host = nullptr;   // pinned
   double* scg_buf = nullptr;    // SCG vectors (p, q, z, r0) for the largest level
@@ -97,12 +100,15 @@ struct Ctx {
 // kernels.cu
 int launch_apply(Ctx& c, int l, int prec, const double* u, const double* b, void* out,
                  double alpha);
+int launch_apply_corr(Ctx& c, int l, int prec, const void* delta, const double* b, void* out,
+                      int out_fp64);
 int launch_fd(Ctx& c, int l, int prec, const void* r);
-int launch_combine(Ctx& c, int l, int prec, double* u, double scale);
+int launch_combine(Ctx& c, int l, int prec, void* delta);
+int launch_add_delta(Ctx& c, long long n, int prec, const void* d, double* u);
 int launch_combine_to(Ctx& c, int l, int prec, double* z);
 int launch_project(Ctx& c, int l, const double* uf);   // lv[l-1].u = ubar = P uf
 int launch_restrict(Ctx& c, int l, const double* rf, double* rc);
-int launch_prolong(Ctx& c, int l, double* uf);         // uf += I (lv[l-1].u - ubar)
+int launch_prolong(Ctx& c, int l, double* uf, int prec, void* delta);  // delta = I (u_c - ubar)
 int launch_root(Ctx& c);
 int launch_sumsq(Ctx& c, const double* v, long long n, double* partial_out);
 int launch_dot(Ctx& c, const double* a, const double* b, long long n, double* partial_out);

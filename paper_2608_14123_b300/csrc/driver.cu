@@ -365,7 +365,7 @@ static void free_level(LevelHost& H) {
                   H.d_h, H.d_G, H.d_fW, H.d_fc, H.d_mu, H.d_mass, H.d_D, H.d_w, H.d_g, H.d_S,
                   H.d_lam, H.d_W, H.d_x, H.f_h, H.f_G, H.f_fW, H.f_fc, H.f_mu, H.f_mass, H.f_D,
                   H.f_w, H.f_g, H.f_S, H.f_lam, H.f_W, H.f_x, H.d_I, H.d_P, H.u, H.gv, H.r,
-                  H.ubar, H.t};
+                  H.ubar, H.t, H.delta};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -375,8 +375,11 @@ extern "C" void dgfas_destroy(void* vctx) {
   Ctx* c = (Ctx*)vctx;
   if (c->stream) cudaStreamSynchronize(c->stream);
   if (c->gexec) cudaGraphExecDestroy(c->gexec);
+  if (c->cap) cudaStreamDestroy(c->cap);
+  if (c->ev_in) cudaEventDestroy(c->ev_in);
+  if (c->ev_out) cudaEventDestroy(c->ev_out);
   for (auto& H : c->lv) free_level(H);
-  void* ptrs[] = {c->patch, c->r32, c->red, c->scg_buf, c->dscal, c->Ainv};
+  void* ptrs[] = {c->patch, c->rw, c->red, c->scg_buf, c->dscal, c->Ainv};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->red_host) cudaFreeHost(c->red_host);
@@ -428,14 +431,21 @@ extern "C" int dgfas_setup_levels(const dgfas_mesh* mesh, const dgfas_params* pr
       if (!rc) rc = dalloc(&H.t, H.ndof);
     }
     if (!rc) rc = dalloc(&H.r, H.ndof);
+    if (!rc) rc = dalloc(&H.delta, H.ndof);
   }
   if (rc == DGFAS_OK) {
     if (cudaMalloc(&c->patch, patch) != cudaSuccess) { set_error("patch buffer"); rc = DGFAS_ERR_OOM; }
     c->patch_bytes = patch;
   }
-  if (rc == DGFAS_OK && cudaMalloc((void**)&c->r32, maxdof * sizeof(float)) != cudaSuccess) {
-    set_error("r32 buffer");
+  if (rc == DGFAS_OK && cudaMalloc(&c->rw, maxdof * sizeof(double)) != cudaSuccess) {
+    set_error("smoother residual buffer");
     rc = DGFAS_ERR_OOM;
+  }
+  if (rc == DGFAS_OK && (cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess ||
+                         cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+                         cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming) != cudaSuccess)) {
+    set_error("stream/event creation");
+    rc = DGFAS_ERR_CUDA;
   }
   if (rc == DGFAS_OK) rc = dalloc(&c->red, g_red_blocks + 64);
   if (rc == DGFAS_OK && cudaMallocHost((void**)&c->red_host, (g_red_blocks + 64) * sizeof(double)) != cudaSuccess) {
@@ -477,49 +487,67 @@ static int dot_dev(Ctx& c, const double* a, const double* b, long long n, double
 }
 
 // ---------------------------------------------------------------- smoothers
-// Schwarz correction z = sum_e R_s^T W (A~)^-1 R_s r of the residual in
-// lv[l].r (FP64) or c.r32 (FP32), added to u (add) or written to u.
-static int schwarz_correction(Ctx& c, int l, double* u, bool add) {
+// Schwarz correction of the smoother-precision residual in c.rw: delta += z.
+static int schwarz_into_delta(Ctx& c, int l) {
   const int prec = c.prm.precision;
-  const void* r = prec == DGFAS_FP64 ? (const void*)c.lv[l].r : (const void*)c.r32;
-  RET(launch_fd(c, l, prec, r));
-  return add ? launch_combine(c, l, prec, u, 1.0) : launch_combine_to(c, l, prec, u);
+  RET(launch_fd(c, l, prec, c.rw));
+  return launch_combine(c, l, prec, c.lv[l].delta);
 }
 
-static int residual_smoother(Ctx& c, int l, const double* u, const double* g) {
-  if (c.prm.precision == DGFAS_FP64) return launch_apply(c, l, DGFAS_FP64, u, g, c.lv[l].r, -1.0);
-  return launch_apply(c, l, DGFAS_FP32, u, g, c.r32, -1.0);
-}
-
-// Alg. 5
-static int was(Ctx& c, int l, double* u, const double* g, int n) {
+// One smoothing block of n WAS sweeps (Alg. 5) in correction form.  lv[l].r
+// holds the FP64 residual r = g - A u of the current u; the sweeps solve
+// A delta = r approximately in the smoother precision, starting from delta = 0
+// (zero_start) or from the prolongated correction already in lv[l].delta, and
+// finally u += delta.  Each sweep: w = r - A delta, delta += sum_e R^T W A~^-1 R w.
+// With want_res, lv[l].r becomes the residual r - A delta of the new u.  In
+// exact arithmetic this equals n sweeps of Alg. 5 on A u = g; in mixed precision
+// every residual the smoother sees is a correction-sized quantity, so the outer
+// FP64 residual drives the iteration (iterative refinement).
+static int was_block(Ctx& c, int l, double* u, int n, bool zero_start, bool want_res) {
+  LevelHost& H = c.lv[l];
+  const int prec = c.prm.precision;
+  const size_t esz = prec == DGFAS_FP64 ? sizeof(double) : sizeof(float);
+  if (zero_start) CK(cudaMemsetAsync(H.delta, 0, H.ndof * esz, c.stream));
   for (int s = 0; s < n; ++s) {
-    RET(residual_smoother(c, l, u, g));
-    RET(schwarz_correction(c, l, u, true));
+    if (s == 0 && zero_start) {
+      if (prec == DGFAS_FP64) {
+        CK(cudaMemcpyAsync(c.rw, H.r, H.ndof * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
+      } else {
+        RET(launch_to_float(c, H.r, (float*)c.rw, H.ndof));
+      }
+    } else {
+      RET(launch_apply_corr(c, l, prec, H.delta, H.r, c.rw, 0));
+    }
+    RET(schwarz_into_delta(c, l));
   }
-  return DGFAS_OK;
+  if (want_res) RET(launch_apply_corr(c, l, prec, H.delta, H.r, H.r, 1));
+  return launch_add_delta(c, H.ndof, prec, H.delta, u);
 }
 
-// Alg. 6 with n iterations (FP64 recurrences; the Schwarz sweep in the
-// smoother precision).  Synchronizes for the scalar products.
-static int scg(Ctx& c, int l, double* u, const double* g, int n) {
+// Alg. 6 with n iterations: FP64 recurrences and operator, the Schwarz sweep
+// in the smoother precision.  Starts from the FP64 residual in lv[l].r; u
+// updated in place; lv[l].r ends as the CG residual.  Synchronizes for the
+// scalar products.
+static int scg_block(Ctx& c, int l, double* u, const double* g, int n) {
   LevelHost& H = c.lv[l];
   const long long nd = H.ndof;
+  const int prec = c.prm.precision;
   double *r = H.r, *p = c.scg_buf, *q = p + nd, *z = q + nd, *r0 = z + nd;
-  RET(launch_apply(c, l, DGFAS_FP64, u, g, r, -1.0));
+  (void)g;
   double gamma = 0.0;
   for (int i = 1; i <= n; ++i) {
-    if (c.prm.precision == DGFAS_FP32) RET(launch_to_float(c, r, c.r32, nd));
-    RET(schwarz_correction(c, l, z, false));
+    if (prec == DGFAS_FP32) RET(launch_to_float(c, r, (float*)c.rw, nd));
+    else CK(cudaMemcpyAsync(c.rw, r, nd * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
+    RET(launch_fd(c, l, prec, c.rw));
+    RET(launch_combine_to(c, l, prec, z));
     if (i > 1) {
       CK(cudaMemcpyAsync(q, r, nd * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
       RET(launch_axpy(c, nd, -1.0, r0, q));   // q = r - r0
       double num;
       RET(dot_dev(c, z, q, nd, &num));
       const double beta = num / gamma;
-      // p = beta p + z
-      RET(launch_axpy(c, nd, beta - 1.0, p, p));
-      RET(launch_axpy(c, nd, 1.0, z, p));
+      RET(launch_axpy(c, nd, beta - 1.0, p, p));   // p = beta p
+      RET(launch_axpy(c, nd, 1.0, z, p));          // p += z
     } else {
       CK(cudaMemcpyAsync(p, z, nd * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
     }
@@ -535,22 +563,41 @@ static int scg(Ctx& c, int l, double* u, const double* g, int n) {
   return DGFAS_OK;
 }
 
-static int smooth(Ctx& c, int l, double* u, const double* g, int n) {
-  if (n <= 0) return DGFAS_OK;
-  if (c.prm.smoother == DGFAS_SCG) return scg(c, l, u, g, n);
-  return was(c, l, u, g, n);
+// Smoothing of A u = g on level l with lv[l].r = g - A u on entry.  With
+// want_res, lv[l].r = g - A u of the smoothed u on exit.  zero_start = false
+// means lv[l].delta holds a prolongated correction not yet added to u.
+static int smooth(Ctx& c, int l, double* u, const double* g, int n, bool zero_start,
+                  bool want_res) {
+  if (c.prm.smoother == DGFAS_SCG) {
+    if (!zero_start) {   // add the pending correction, then recompute the residual
+      RET(launch_add_delta(c, c.lv[l].ndof, c.prm.precision, c.lv[l].delta, u));
+      RET(launch_apply(c, l, DGFAS_FP64, u, g, c.lv[l].r, -1.0));
+    }
+    RET(scg_block(c, l, u, g, n));
+    if (want_res) RET(launch_apply(c, l, DGFAS_FP64, u, g, c.lv[l].r, -1.0));
+    return DGFAS_OK;
+  }
+  if (n <= 0) {
+    if (!zero_start) RET(launch_add_delta(c, c.lv[l].ndof, c.prm.precision, c.lv[l].delta, u));
+    if (want_res && !zero_start) RET(launch_apply(c, l, DGFAS_FP64, u, g, c.lv[l].r, -1.0));
+    return DGFAS_OK;
+  }
+  return was_block(c, l, u, n, zero_start, want_res);
 }
 
 // ---------------------------------------------------------------- FAS V-cycle
-// Alg. 2 below the top pre-smoothing: lv[L].r holds the top residual of uL.
+// Alg. 2 below the top level: lv[L].r holds the top residual of uL (after the
+// top pre-smoothing).  Ends with the top correction I (u_{L-1} - P u_L) in
+// lv[L].delta, not yet added to uL (the caller's top smoothing adds it).
 static int down_up(Ctx& c, double* uL, const double* fL) {
   const int L = (int)c.lv.size() - 1;
+  const int prec = c.prm.precision;
   for (int l = L; l >= 1; --l) {
     double* ul = l == L ? uL : c.lv[l].u;
     const double* gl = l == L ? fL : c.lv[l].gv;
     if (l < L) {
-      RET(smooth(c, l, ul, gl, c.prm.s1));
       RET(launch_apply(c, l, DGFAS_FP64, ul, gl, c.lv[l].r, -1.0));
+      RET(smooth(c, l, ul, gl, c.prm.s1, true, true));
     }
     RET(launch_project(c, l, ul));                                   // u_{l-1} = P u_l
     RET(launch_restrict(c, l, c.lv[l].r, c.lv[l - 1].t));           // R r_l
@@ -560,52 +607,82 @@ static int down_up(Ctx& c, double* uL, const double* fL) {
   for (int l = 1; l <= L; ++l) {
     double* ul = l == L ? uL : c.lv[l].u;
     const double* gl = l == L ? fL : c.lv[l].gv;
-    RET(launch_prolong(c, l, ul));
-    if (l < L) RET(smooth(c, l, ul, gl, c.prm.s2));
+    RET(launch_prolong(c, l, ul, prec, c.lv[l].delta));             // delta_l = I (u_{l-1} - ubar)
+    if (l < L) {
+      // the post-smoothing starts from the residual of the pre-smoothed u_l,
+      // which is still in lv[l].r (restriction only read it)
+      RET(smooth(c, l, ul, gl, c.prm.s2, false, false));
+    }
   }
   return DGFAS_OK;
 }
 
+// Alg. 2 on the top level: residual, s1 pre-sweeps, down/up legs, s2 post-sweeps.
+// c.red receives the partial sums of |r|^2 of the residual after pre-smoothing.
 static int vcycle_body(Ctx& c, double* u, const double* f) {
   const int L = (int)c.lv.size() - 1;
-  RET(smooth(c, L, u, f, c.prm.s1));
   RET(launch_apply(c, L, DGFAS_FP64, u, f, c.lv[L].r, -1.0));
+  RET(smooth(c, L, u, f, c.prm.s1, true, true));
   RET(launch_sumsq(c, c.lv[L].r, c.lv[L].ndof, c.red));
   if (L == 0) return DGFAS_OK;
   RET(down_up(c, u, f));
-  return smooth(c, L, u, f, c.prm.s2);
+  return smooth(c, L, u, f, c.prm.s2, false, false);
 }
 
+// One cycle of the crossover solve: down/up legs from the top residual in
+// lv[L].r, n_sc top sweeps starting from the prolongated correction, FP64
+// top residual and its partial sums (the stopping test of the next cycle).
 static int solve_cycle_body(Ctx& c, double* u, const double* f) {
   const int L = (int)c.lv.size() - 1;
   RET(down_up(c, u, f));
-  RET(smooth(c, L, u, f, c.prm.sc));
+  RET(smooth(c, L, u, f, c.prm.sc, false, false));
   RET(launch_apply(c, L, DGFAS_FP64, u, f, c.lv[L].r, -1.0));
   return launch_sumsq(c, c.lv[L].r, c.lv[L].ndof, c.red);
 }
 
 static bool graph_ok(Ctx& c) { return c.use_graph && c.prm.smoother == DGFAS_WAS; }
 
+// Runs one cycle body on the caller's stream, or replays it as a CUDA graph
+// captured on the context's internal stream (ordered after and before the
+// caller's stream by events).
 static int run_body(Ctx& c, int kind, double* u, const double* f) {
   if (!graph_ok(c)) return kind == 0 ? vcycle_body(c, u, f) : solve_cycle_body(c, u, f);
+  cudaStream_t user = c.stream;
+  CK(cudaEventRecord(c.ev_in, user));
+  CK(cudaStreamWaitEvent(c.cap, c.ev_in, 0));
+  c.stream = c.cap;
+  int rc = DGFAS_OK;
   if (!(c.gexec && c.g_u == u && c.g_f == f && c.g_kind == kind)) {
     if (c.gexec) { cudaGraphExecDestroy(c.gexec); c.gexec = nullptr; }
-    // one uncaptured run sets the kernels' attributes; then capture
-    RET(kind == 0 ? vcycle_body(c, u, f) : solve_cycle_body(c, u, f));
-    CK(cudaStreamSynchronize(c.stream));
-    cudaGraph_t g;
-    CK(cudaStreamBeginCapture(c.stream, cudaStreamCaptureModeRelaxed));
-    int rc = kind == 0 ? vcycle_body(c, u, f) : solve_cycle_body(c, u, f);
-    cudaError_t ce = cudaStreamEndCapture(c.stream, &g);
-    if (rc != DGFAS_OK) return rc;
-    if (ce != cudaSuccess) { set_error("graph capture failed"); return DGFAS_ERR_CUDA; }
-    CK(cudaGraphInstantiate(&c.gexec, g, 0));
-    cudaGraphDestroy(g);
-    c.g_u = u; c.g_f = f; c.g_kind = kind;
-    return DGFAS_OK;   // this call's cycle already ran uncaptured
+    // this call's cycle runs uncaptured (it also sets the kernels' attributes) ...
+    rc = kind == 0 ? vcycle_body(c, u, f) : solve_cycle_body(c, u, f);
+    if (rc == DGFAS_OK && cudaStreamSynchronize(c.cap) != cudaSuccess) rc = DGFAS_ERR_CUDA;
+    // ... then the same launches are captured for the following calls
+    if (rc == DGFAS_OK) {
+      cudaGraph_t g = nullptr;
+      if (cudaStreamBeginCapture(c.cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        rc = DGFAS_ERR_CUDA;
+      } else {
+        int rc2 = kind == 0 ? vcycle_body(c, u, f) : solve_cycle_body(c, u, f);
+        cudaError_t ce = cudaStreamEndCapture(c.cap, &g);
+        if (rc2 != DGFAS_OK) rc = rc2;
+        else if (ce != cudaSuccess || cudaGraphInstantiate(&c.gexec, g, 0) != cudaSuccess) {
+          set_error("graph capture/instantiate failed");
+          rc = DGFAS_ERR_CUDA;
+          c.gexec = nullptr;
+        }
+        if (g) cudaGraphDestroy(g);
+        if (rc == DGFAS_OK) { c.g_u = u; c.g_f = f; c.g_kind = kind; }
+      }
+    }
+  } else if (cudaGraphLaunch(c.gexec, c.cap) != cudaSuccess) {
+    set_error("graph launch failed");
+    rc = DGFAS_ERR_CUDA;
   }
-  CK(cudaGraphLaunch(c.gexec, c.stream));
-  return DGFAS_OK;
+  c.stream = user;
+  CK(cudaEventRecord(c.ev_out, c.cap));
+  CK(cudaStreamWaitEvent(user, c.ev_out, 0));
+  return rc;
 }
 
 static double host_norm(Ctx& c) {
@@ -649,7 +726,8 @@ extern "C" int dgfas_schwarz_smooth(void* ctx, int level, double* u, const doubl
     set_error("schwarz_smooth: invalid argument (levels >= 1 have a smoother)");
     return DGFAS_ERR_INVALID;
   }
-  return smooth(*c, level, u, g, n);
+  RET(launch_apply(*c, level, DGFAS_FP64, u, g, c->lv[level].r, -1.0));
+  return smooth(*c, level, u, g, n, true, false);
 }
 
 extern "C" int dgfas_norm(void* ctx, int level, const double* v, double* out) {
@@ -681,7 +759,7 @@ extern "C" int dgfas_solve(void* ctx, double* u, const double* f, double rtol, i
   double r0;
   RET(launch_apply(*c, L, DGFAS_FP64, u, f, c->lv[L].r, -1.0));
   RET(norm_dev(*c, c->lv[L].r, c->lv[L].ndof, &r0));
-  RET(smooth(*c, L, u, f, c->prm.s1));
+  RET(smooth(*c, L, u, f, c->prm.s1, true, false));
   RET(launch_apply(*c, L, DGFAS_FP64, u, f, c->lv[L].r, -1.0));
   int cycles = 0, rc = DGFAS_ERR_NOT_CONVERGED;
   double r = r0;
@@ -773,27 +851,30 @@ extern "C" int dgfas_host_fd_variant(int p, double delta, double mu_star, int va
 
 // Per-kernel timing of the smoother on `level` with CUDA events on the
 // context's stream: `reps` sweeps; ms_out[0..3] = average duration of the
-// smoother-precision residual, the FD kernel, the combine kernel and the FP64
-// residual apply.  u is updated by the sweeps.
+// smoother-precision residual of the correction, the FD kernel, the combine
+// kernel and the FP64 residual apply.  u is not modified.
 extern "C" int dgfas_profile_sweep(void* ctx, int level, double* u, const double* g, int reps,
                                    double* ms_out) {
   Ctx* c = (Ctx*)ctx;
   if (!c || !u || !g || !ms_out || reps <= 0 || level < 1 || level >= (int)c->lv.size())
     return DGFAS_ERR_INVALID;
+  LevelHost& H = c->lv[level];
+  const int prec = c->prm.precision;
+  const size_t esz = prec == DGFAS_FP64 ? sizeof(double) : sizeof(float);
   cudaEvent_t ev[5];
   for (auto& e : ev) CK(cudaEventCreate(&e));
   double acc[4] = {0, 0, 0, 0};
+  RET(launch_apply(*c, level, DGFAS_FP64, u, g, H.r, -1.0));
+  CK(cudaMemsetAsync(H.delta, 0, H.ndof * esz, c->stream));
   for (int r = 0; r < reps; ++r) {
     CK(cudaEventRecord(ev[0], c->stream));
-    RET(residual_smoother(*c, level, u, g));
+    RET(launch_apply_corr(*c, level, prec, H.delta, H.r, c->rw, 0));
     CK(cudaEventRecord(ev[1], c->stream));
-    const int prec = c->prm.precision;
-    const void* rr = prec == DGFAS_FP64 ? (const void*)c->lv[level].r : (const void*)c->r32;
-    RET(launch_fd(*c, level, prec, rr));
+    RET(launch_fd(*c, level, prec, c->rw));
     CK(cudaEventRecord(ev[2], c->stream));
-    RET(launch_combine(*c, level, prec, u, 1.0));
+    RET(launch_combine(*c, level, prec, H.delta));
     CK(cudaEventRecord(ev[3], c->stream));
-    RET(launch_apply(*c, level, DGFAS_FP64, u, g, c->lv[level].r, -1.0));
+    RET(launch_apply(*c, level, DGFAS_FP64, u, g, c->lv[level].t ? c->lv[level].t : H.r, -1.0));
     CK(cudaEventRecord(ev[4], c->stream));
     CK(cudaEventSynchronize(ev[4]));
     for (int k = 0; k < 4; ++k) {

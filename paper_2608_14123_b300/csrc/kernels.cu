@@ -26,9 +26,9 @@ template <typename T> __device__ __forceinline__ T ld(const T* p) { return __ldg
 // Team of N*N threads (tx, ty) per element, looping over k; EPB teams per CTA.
 // Shared memory per team: u, neighbour buffer, F1, F2, F3, face-flux R (6 N^3).
 // out = b + alpha * A u   (b may be null); rows of frozen elements are 0.
-template <int N, typename T, typename TU, typename TO, bool BOX>
+template <int N, typename T, typename TU, typename TB, typename TO, bool BOX>
 __global__ void k_apply(const LevelView<T> L, const TU* __restrict__ u,
-                        const TU* __restrict__ b, TO* __restrict__ out, T alpha) {
+                        const TB* __restrict__ b, TO* __restrict__ out, T alpha) {
   constexpr int N2 = N * N, N3 = N * N * N;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sD = reinterpret_cast<T*>(smem_raw);
@@ -201,8 +201,8 @@ __global__ void k_apply(const LevelView<T> L, const TU* __restrict__ u,
   }
 }
 
-template <int N, typename T, typename TU, typename TO>
-static int apply_N(const LevelView<T>& L, const TU* u, const TU* b, TO* out, T alpha,
+template <int N, typename T, typename TU, typename TB, typename TO>
+static int apply_N(const LevelView<T>& L, const TU* u, const TB* b, TO* out, T alpha,
                    cudaStream_t st) {
   constexpr int N2 = N * N, N3 = N * N * N;
   int epb = (128 + N2 - 1) / N2;
@@ -212,45 +212,69 @@ static int apply_N(const LevelView<T>& L, const TU* u, const TU* b, TO* out, T a
     smem = (N2 + 16 + (size_t)6 * N3 * epb) * sizeof(T);
   }
   dim3 blk(N2, epb), grd((L.ne + epb - 1) / epb);
+  // the attribute is set once per instantiation (never inside a graph capture)
   if (L.box) {
-    auto kf = k_apply<N, T, TU, TO, true>;
-    CK(cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    auto kf = k_apply<N, T, TU, TB, TO, true>;
+    static bool attr = false;
+    if (!attr) {
+      CK(cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024));
+      attr = true;
+    }
     kf<<<grd, blk, smem, st>>>(L, u, b, out, alpha);
   } else {
-    auto kf = k_apply<N, T, TU, TO, false>;
-    CK(cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    auto kf = k_apply<N, T, TU, TB, TO, false>;
+    static bool attr = false;
+    if (!attr) {
+      CK(cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024));
+      attr = true;
+    }
     kf<<<grd, blk, smem, st>>>(L, u, b, out, alpha);
   }
   CK(cudaGetLastError());
   return DGFAS_OK;
 }
 
-template <typename T, typename TU, typename TO>
-static int apply_disp(const LevelView<T>& L, const TU* u, const TU* b, TO* out, T alpha,
+template <typename T, typename TU, typename TB, typename TO>
+static int apply_disp(const LevelView<T>& L, const TU* u, const TB* b, TO* out, T alpha,
                       cudaStream_t st) {
   switch (L.N) {
-    case 2: return apply_N<2>(L, u, b, out, alpha, st);
-    case 3: return apply_N<3>(L, u, b, out, alpha, st);
-    case 4: return apply_N<4>(L, u, b, out, alpha, st);
-    case 5: return apply_N<5>(L, u, b, out, alpha, st);
-    case 6: return apply_N<6>(L, u, b, out, alpha, st);
-    case 7: return apply_N<7>(L, u, b, out, alpha, st);
-    case 8: return apply_N<8>(L, u, b, out, alpha, st);
-    case 9: return apply_N<9>(L, u, b, out, alpha, st);
-    case 10: return apply_N<10>(L, u, b, out, alpha, st);
-    case 11: return apply_N<11>(L, u, b, out, alpha, st);
+    case 2: return apply_N<2, T, TU, TB, TO>(L, u, b, out, alpha, st);
+    case 3: return apply_N<3, T, TU, TB, TO>(L, u, b, out, alpha, st);
+    case 4: return apply_N<4, T, TU, TB, TO>(L, u, b, out, alpha, st);
+    case 5: return apply_N<5, T, TU, TB, TO>(L, u, b, out, alpha, st);
+    case 6: return apply_N<6, T, TU, TB, TO>(L, u, b, out, alpha, st);
+    case 7: return apply_N<7, T, TU, TB, TO>(L, u, b, out, alpha, st);
+    case 8: return apply_N<8, T, TU, TB, TO>(L, u, b, out, alpha, st);
+    case 9: return apply_N<9, T, TU, TB, TO>(L, u, b, out, alpha, st);
+    case 10: return apply_N<10, T, TU, TB, TO>(L, u, b, out, alpha, st);
+    case 11: return apply_N<11, T, TU, TB, TO>(L, u, b, out, alpha, st);
   }
   set_error("apply: unsupported N");
   return DGFAS_ERR_UNSUPPORTED;
 }
 
-// prec 0: FP64 in/out; prec 1: FP32 arithmetic on FP64 u/b, FP32 out
+// FP64 operator: out = b + alpha A u, everything FP64.
 int launch_apply(Ctx& c, int l, int prec, const double* u, const double* b, void* out,
                  double alpha) {
+  (void)prec;
+  return apply_disp<double, double, double, double>(c.lv[l].v64, u, b, (double*)out, alpha,
+                                                    c.stream);
+}
+
+// Smoother-precision operator on a correction: out = b - A delta with b FP64,
+// delta and the arithmetic in the smoother precision, out in the smoother
+// precision (out_fp64 = 0) or FP64 (out_fp64 = 1).
+int launch_apply_corr(Ctx& c, int l, int prec, const void* delta, const double* b, void* out,
+                      int out_fp64) {
   LevelHost& H = c.lv[l];
   if (prec == DGFAS_FP64)
-    return apply_disp<double, double, double>(H.v64, u, b, (double*)out, alpha, c.stream);
-  return apply_disp<float, double, float>(H.v32, u, b, (float*)out, (float)alpha, c.stream);
+    return apply_disp<double, double, double, double>(H.v64, (const double*)delta, b,
+                                                      (double*)out, -1.0, c.stream);
+  if (out_fp64)
+    return apply_disp<float, float, double, double>(H.v32, (const float*)delta, b, (double*)out,
+                                                    -1.0f, c.stream);
+  return apply_disp<float, float, double, float>(H.v32, (const float*)delta, b, (float*)out,
+                                                 -1.0f, c.stream);
 }
 
 // ============================================================================ FD
@@ -395,7 +419,11 @@ static int fd_NS(const LevelView<T>& L, const TR* r, T* patch, cudaStream_t st) 
   while (epb > 1 && per * epb > 96 * 1024) --epb;
   size_t smem = per * epb;
   auto kf = k_fd<NS, T, TR>;
-  CK(cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  static bool attr = false;
+  if (!attr) {
+    CK(cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024));
+    attr = true;
+  }
   dim3 blk(NS2, epb), grd((L.ne + epb - 1) / epb);
   kf<<<grd, blk, smem, st>>>(L, r, patch);
   CK(cudaGetLastError());
@@ -437,16 +465,16 @@ int launch_fd(Ctx& c, int l, int prec, const void* r) {
 // One thread per node of the level: u[e][n] = scale_u * u + sum of the weighted
 // patch entries of every subdomain that covers the node (own element and the up
 // to 26 neighbours whose overlap layers reach it).  Frozen entries untouched.
-template <typename T, bool ADD>
+template <typename T, bool ADD, typename TO>
 __global__ void k_combine(const LevelView<T> L, const T* __restrict__ patch,
-                          double* __restrict__ u) {
+                          TO* __restrict__ u) {
   const int N = L.N, N3 = N * N * N, m = L.m, nsm = L.nsm;
   const size_t NS3 = (size_t)nsm * nsm * nsm;
   const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (gid >= (long long)L.ne * N3) return;
   const int e = (int)(gid / N3), n = (int)(gid % N3);
   if (L.cls[e] == DGFAS_FROZEN) {
-    if (!ADD) u[gid] = 0.0;
+    if (!ADD) u[gid] = TO(0);
     return;
   }
   const int i = n % N, j = (n / N) % N, k = n / (N * N);
@@ -472,32 +500,36 @@ __global__ void k_combine(const LevelView<T> L, const T* __restrict__ patch,
         }
         s += (double)patch[(size_t)src * NS3 + ((size_t)pidx[2] * nsm + pidx[1]) * nsm + pidx[0]];
       }
-  if (ADD) u[gid] += s;
-  else u[gid] = s;
+  if (ADD) u[gid] += (TO)s;
+  else u[gid] = (TO)s;
 }
 
-int launch_combine(Ctx& c, int l, int prec, double* u, double) {
+// delta += sum of the weighted patches (delta in the smoother precision)
+int launch_combine(Ctx& c, int l, int prec, void* delta) {
   LevelHost& H = c.lv[l];
   const long long n = H.ndof;
   const int bs = 256;
   const unsigned grd = (unsigned)((n + bs - 1) / bs);
   if (prec == DGFAS_FP64)
-    k_combine<double, true><<<grd, bs, 0, c.stream>>>(H.v64, (const double*)c.patch, u);
+    k_combine<double, true, double><<<grd, bs, 0, c.stream>>>(H.v64, (const double*)c.patch,
+                                                              (double*)delta);
   else
-    k_combine<float, true><<<grd, bs, 0, c.stream>>>(H.v32, (const float*)c.patch, u);
+    k_combine<float, true, float><<<grd, bs, 0, c.stream>>>(H.v32, (const float*)c.patch,
+                                                            (float*)delta);
   CK(cudaGetLastError());
   return DGFAS_OK;
 }
 
+// z = sum of the weighted patches (FP64 output, SCG preconditioner)
 int launch_combine_to(Ctx& c, int l, int prec, double* z) {
   LevelHost& H = c.lv[l];
   const long long n = H.ndof;
   const int bs = 256;
   const unsigned grd = (unsigned)((n + bs - 1) / bs);
   if (prec == DGFAS_FP64)
-    k_combine<double, false><<<grd, bs, 0, c.stream>>>(H.v64, (const double*)c.patch, z);
+    k_combine<double, false, double><<<grd, bs, 0, c.stream>>>(H.v64, (const double*)c.patch, z);
   else
-    k_combine<float, false><<<grd, bs, 0, c.stream>>>(H.v32, (const float*)c.patch, z);
+    k_combine<float, false, double><<<grd, bs, 0, c.stream>>>(H.v32, (const float*)c.patch, z);
   CK(cudaGetLastError());
   return DGFAS_OK;
 }
@@ -570,10 +602,14 @@ __global__ void k_gather_children(const TransferView T, const double* __restrict
   }
 }
 
-// u_f += I (u_c - ubar_c) on active fine elements; frozen fine elements take
-// u_f = I u_c (frozen update, Alg. 2).  One CTA per fine element.
+// Correction prolongation of Alg. 2: on active fine elements the correction
+// I (u_c - ubar_c) is written to delta (the smoother then starts from it and
+// adds delta to u); frozen fine elements take u_f = I u_c (frozen update) and
+// delta = 0.  One CTA per fine element.
+template <typename TD>
 __global__ void k_prolong(const TransferView T, const double* __restrict__ uc,
-                          const double* __restrict__ ubar, double* __restrict__ uf) {
+                          const double* __restrict__ ubar, double* __restrict__ uf,
+                          TD* __restrict__ delta) {
   __shared__ double X[TMAX], T1[TMAX], T2[TMAX], Y[TMAX], A[3][DGFAS_MAX_N * DGFAS_MAX_N];
   const int e = blockIdx.x, tid = threadIdx.x, nth = blockDim.x;
   const int Nf = T.Nf, Nc = T.Nc, Nf3 = Nf * Nf * Nf, Nc3 = Nc * Nc * Nc;
@@ -589,7 +625,12 @@ __global__ void k_prolong(const TransferView T, const double* __restrict__ uc,
   tensor3(A[0], A[1], A[2], Nf, Nc, X, T1, T2, Y, tid, nth);
   for (int t = tid; t < Nf3; t += nth) {
     const size_t g = (size_t)e * Nf3 + t;
-    uf[g] = frozen ? Y[t] : uf[g] + Y[t];
+    if (frozen) {
+      uf[g] = Y[t];
+      delta[g] = TD(0);
+    } else {
+      delta[g] = (TD)Y[t];
+    }
   }
 }
 
@@ -609,10 +650,13 @@ int launch_restrict(Ctx& c, int l, const double* rf, double* rc) {
   return DGFAS_OK;
 }
 
-int launch_prolong(Ctx& c, int l, double* uf) {
+int launch_prolong(Ctx& c, int l, double* uf, int prec, void* delta) {
   LevelHost& F = c.lv[l];
   LevelHost& C = c.lv[l - 1];
-  k_prolong<<<F.ne, 128, 0, c.stream>>>(F.tr, C.u, C.ubar, uf);
+  if (prec == DGFAS_FP64)
+    k_prolong<double><<<F.ne, 128, 0, c.stream>>>(F.tr, C.u, C.ubar, uf, (double*)delta);
+  else
+    k_prolong<float><<<F.ne, 128, 0, c.stream>>>(F.tr, C.u, C.ubar, uf, (float*)delta);
   CK(cudaGetLastError());
   return DGFAS_OK;
 }
@@ -676,6 +720,20 @@ __global__ void k_axpy(long long n, double alpha, const double* __restrict__ x,
 
 int launch_axpy(Ctx& c, long long n, double alpha, const double* x, double* y) {
   k_axpy<<<(unsigned)((n + 255) / 256), 256, 0, c.stream>>>(n, alpha, x, y);
+  CK(cudaGetLastError());
+  return DGFAS_OK;
+}
+
+template <typename TD>
+__global__ void k_add_delta(long long n, const TD* __restrict__ d, double* __restrict__ u) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) u[i] += (double)d[i];
+}
+
+int launch_add_delta(Ctx& c, long long n, int prec, const void* d, double* u) {
+  const unsigned g = (unsigned)((n + 255) / 256);
+  if (prec == DGFAS_FP64) k_add_delta<double><<<g, 256, 0, c.stream>>>(n, (const double*)d, u);
+  else k_add_delta<float><<<g, 256, 0, c.stream>>>(n, (const float*)d, u);
   CK(cudaGetLastError());
   return DGFAS_OK;
 }

@@ -108,3 +108,22 @@ def test_solve_reaches_1e10(cid, small, prec):
     else:
         assert info["cycles"] <= len(hist) - 1 + 2
         assert rel(u.cpu().numpy(), uo) < 1e-8
+
+
+def test_graph_replay_matches_direct_launches():
+    cfg = wl.config(1)
+    torch = torch_cuda()
+    S1, S2 = make_solver(cfg, precision=1), make_solver(cfg, precision=1)
+    S2.dgfas_use_graph(True)
+    H = make_oracle(cfg)
+    b, _ = rhs_both(cfg, S1, H)
+    u1 = torch.from_numpy(cfg["u0"].copy()).cuda()
+    u2 = u1.clone()
+    for _ in range(3):
+        r1 = S1.dgfas_fas_vcycle(u1, b)
+        r2 = S2.dgfas_fas_vcycle(u2, b)
+    assert r1 == r2
+    assert torch.equal(u1, u2)
+    i1 = S1.dgfas_solve(u1.clone(), b, 1e-10, 30)
+    i2 = S2.dgfas_solve(u2.clone(), b, 1e-10, 30)
+    assert i1["cycles"] == i2["cycles"] and i1["history"] == i2["history"]
