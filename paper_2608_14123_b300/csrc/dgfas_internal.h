@@ -20,6 +20,8 @@ struct LevelView {
   const int* nbr27;           // [ne][27]
   const signed char* cls;     // [ne]
   const T* h;                 // [ne][3] box widths (box levels)
+  const T* bx;                // [ne][6] box factors g_d, a_d (box levels)
+  const T* Lhat;              // [N][N] D^T W D
   const T* G;                 // [ne][6][N^3] volume metric (general levels)
   const T* fW;                // [ne][6][N^2] face quadrature weights (general)
   const T* fc;                // [ne][6][3][N^2] W n . grad xi_t (general)
@@ -57,6 +59,8 @@ struct LevelHost {
       *d_children = nullptr;
   signed char* d_cls = nullptr;
   unsigned char* d_var = nullptr;
+  double *d_bx = nullptr, *d_Lhat = nullptr;
+  float *f_bx = nullptr, *f_Lhat = nullptr;
   double *d_h = nullptr, *d_G = nullptr, *d_fW = nullptr, *d_fc = nullptr, *d_mu = nullptr,
          *d_mass = nullptr, *d_D = nullptr, *d_w = nullptr, *d_g = nullptr, *d_S = nullptr,
          *d_lam = nullptr, *d_W = nullptr, *d_x = nullptr;

@@ -227,9 +227,26 @@ static int build_level(Ctx& c, const dgfas_level& in, const dgfas_params& prm, L
   RET(upload_f(&H.f_S, S));
   RET(upload_f(&H.f_lam, lam));
   RET(upload_f(&H.f_W, Wt));
+  {
+    std::vector<double> Lh((size_t)N * N, 0.0);
+    for (int i = 0; i < N; ++i)
+      for (int j = 0; j < N; ++j)
+        for (int q = 0; q < N; ++q) Lh[i * N + j] += D[q * N + i] * w[q] * D[q * N + j];
+    RET(upload(&H.d_Lhat, Lh));
+    RET(upload_f(&H.f_Lhat, Lh));
+  }
   if (H.box) {
     RET(upload(&H.d_h, hbox));
     RET(upload_f(&H.f_h, hbox));
+    std::vector<double> bx(6 * (size_t)ne);
+    for (int e = 0; e < ne; ++e)
+      for (int dd = 0; dd < 3; ++dd) {
+        const double hj = hbox[3 * e + (dd + 1) % 3], hk = hbox[3 * e + (dd + 2) % 3];
+        bx[6 * e + dd] = nu * hj * hk / (2.0 * hbox[3 * e + dd]);
+        bx[6 * e + 3 + dd] = nu * hj * hk / 4.0;
+      }
+    RET(upload(&H.d_bx, bx));
+    RET(upload_f(&H.f_bx, bx));
   } else {
     RET(upload(&H.d_G, G));
     RET(upload(&H.d_fW, fW));
@@ -240,17 +257,17 @@ static int build_level(Ctx& c, const dgfas_level& in, const dgfas_params& prm, L
     RET(upload_f(&H.f_fc, fc));
     RET(upload_f(&H.f_mass, mass));
   }
-  auto fill = [&](auto& V, auto* h, auto* G_, auto* fW_, auto* fc_, auto* mu_, auto* mass_, auto* D_,
+  auto fill = [&](auto& V, auto* bx_, auto* Lh_, auto* h, auto* G_, auto* fW_, auto* fc_, auto* mu_, auto* mass_, auto* D_,
                   auto* w_, auto* x_, auto* g_, auto* S_, auto* lam_, auto* W_) {
     V.ne = ne; V.N = N; V.m = H.m; V.nsm = nsm; V.box = H.box;
     V.nu = nu; V.kappa = c.kappa;
     V.nbr = H.d_nbr; V.nbr27 = H.d_nbr27; V.cls = H.d_cls; V.var = H.d_var;
-    V.h = h; V.G = G_; V.fW = fW_; V.fc = fc_; V.mu = mu_; V.mass = mass_; V.D = D_; V.w = w_;
+    V.bx = bx_; V.Lhat = Lh_; V.h = h; V.G = G_; V.fW = fW_; V.fc = fc_; V.mu = mu_; V.mass = mass_; V.D = D_; V.w = w_;
     V.x = x_; V.g = g_; V.S = S_; V.lam = lam_; V.W = W_;
   };
-  fill(H.v64, H.d_h, H.d_G, H.d_fW, H.d_fc, H.d_mu, H.d_mass, H.d_D, H.d_w, H.d_x, H.d_g, H.d_S,
+  fill(H.v64, H.d_bx, H.d_Lhat, H.d_h, H.d_G, H.d_fW, H.d_fc, H.d_mu, H.d_mass, H.d_D, H.d_w, H.d_x, H.d_g, H.d_S,
        H.d_lam, H.d_W);
-  fill(H.v32, H.f_h, H.f_G, H.f_fW, H.f_fc, H.f_mu, H.f_mass, H.f_D, H.f_w, H.f_x, H.f_g, H.f_S,
+  fill(H.v32, H.f_bx, H.f_Lhat, H.f_h, H.f_G, H.f_fW, H.f_fc, H.f_mu, H.f_mass, H.f_D, H.f_w, H.f_x, H.f_g, H.f_S,
        H.f_lam, H.f_W);
   return DGFAS_OK;
 }
@@ -361,7 +378,7 @@ static int build_root(Ctx& c) {
 }
 
 static void free_level(LevelHost& H) {
-  void* ptrs[] = {H.d_nbr, H.d_nbr27, H.d_parent, H.d_octant, H.d_children, H.d_cls, H.d_var,
+  void* ptrs[] = {H.d_bx, H.d_Lhat, H.f_bx, H.f_Lhat, H.d_nbr, H.d_nbr27, H.d_parent, H.d_octant, H.d_children, H.d_cls, H.d_var,
                   H.d_h, H.d_G, H.d_fW, H.d_fc, H.d_mu, H.d_mass, H.d_D, H.d_w, H.d_g, H.d_S,
                   H.d_lam, H.d_W, H.d_x, H.f_h, H.f_G, H.f_fW, H.f_fc, H.f_mu, H.f_mass, H.f_D,
                   H.f_w, H.f_g, H.f_S, H.f_lam, H.f_W, H.f_x, H.d_I, H.d_P, H.u, H.gv, H.r,

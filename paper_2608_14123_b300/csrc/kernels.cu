@@ -201,6 +201,118 @@ __global__ void k_apply(const LevelView<T> L, const TU* __restrict__ u,
   }
 }
 
+// Axis-aligned box elements: the volume term is the Kronecker form
+// sum_d g_d (W x W x Lhat_d) u with Lhat = D^T W D (exact for boxes), so each
+// node costs 3N FMA instead of the 6N of gradient plus transposed gradient.
+// Faces add the flux at the face node and the lifting -c [[u]]/2 (or -c u_D)
+// along the node's normal line through the Lhat-free derivative row D.
+// bx[e] = {g_1, g_2, g_3, nu*|face_1|/4-factor a_1, a_2, a_3} with
+// g_d = nu h_j h_k / (2 h_d) and a_d = nu h_j h_k / 4.
+template <int N, typename T, typename TU, typename TB, typename TO>
+__global__ void k_apply_box(const LevelView<T> L, const T* __restrict__ bx,
+                            const T* __restrict__ Lhat, const TU* __restrict__ u,
+                            const TB* __restrict__ b, TO* __restrict__ out, T alpha) {
+  constexpr int N2 = N * N, N3 = N * N * N;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sD = reinterpret_cast<T*>(smem_raw);
+  T* sL = sD + N2;
+  T* sw = sL + N2;
+  T* base = sw + 16;
+  const int team = threadIdx.y;
+  T* us = base + team * 3 * N3;
+  T* nb = us + N3;
+  T* R = nb + N3;
+  const int tx = threadIdx.x % N, ty = threadIdx.x / N;
+  const int e = blockIdx.x * blockDim.y + team;
+  const bool valid = e < L.ne;
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x, nth = blockDim.x * blockDim.y;
+  for (int t = tid; t < N2; t += nth) {
+    sD[t] = L.D[t];
+    sL[t] = Lhat[t];
+  }
+  for (int t = tid; t < N; t += nth) sw[t] = L.w[t];
+  const size_t eo = (size_t)e * N3;
+  if (valid)
+    for (int k = 0; k < N; ++k) us[(k * N + ty) * N + tx] = (T)u[eo + (k * N + ty) * N + tx];
+  __syncthreads();
+  T g[3] = {0, 0, 0}, af[3] = {0, 0, 0};
+  if (valid) {
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      g[d] = bx[6 * e + d];
+      af[d] = bx[6 * e + 3 + d];
+    }
+    const T kap = L.kappa * T(0.125) * L.h[3 * e] * L.h[3 * e + 1] * L.h[3 * e + 2];
+    for (int k = 0; k < N; ++k) {
+      T s0 = 0, s1 = 0, s2 = 0;
+#pragma unroll
+      for (int l = 0; l < N; ++l) {
+        s0 += sL[tx * N + l] * us[(k * N + ty) * N + l];
+        s1 += sL[ty * N + l] * us[(k * N + l) * N + tx];
+        s2 += sL[k * N + l] * us[(l * N + ty) * N + tx];
+      }
+      const int n = (k * N + ty) * N + tx;
+      const T wi = sw[tx], wj = sw[ty], wk = sw[k];
+      R[n] = g[0] * wj * wk * s0 + g[1] * wi * wk * s1 + g[2] * wi * wj * s2 +
+             kap * wi * wj * wk * us[n];
+    }
+  }
+  __syncthreads();
+  for (int f = 0; f < 6; ++f) {
+    const int d = f >> 1, side = f & 1;
+    const int nbid = valid ? L.nbr[6 * e + f] : -2;
+    if (nbid >= 0) {
+      const size_t no = (size_t)nbid * N3;
+      for (int k = 0; k < N; ++k) nb[(k * N + ty) * N + tx] = (T)u[no + (k * N + ty) * N + tx];
+    }
+    __syncthreads();
+    if (valid && nbid != -2) {
+      const int a = tx, bb = ty;
+      const int end = side ? N - 1 : 0, endp = N - 1 - end;
+      // strides of the normal line and the face node offset
+      const int st = d == 0 ? 1 : (d == 1 ? N : N2);
+      const int fo = d == 0 ? (bb * N + a) * N : (d == 1 ? bb * N2 + a : bb * N + a);
+      const T wab = sw[a] * sw[bb];
+      const T sgn = side ? T(1) : T(-1);
+      const T cn = sgn * g[d] * wab;            // W n . grad xi_d (times nu)
+      const T W = af[d] * wab;                  // nu * surface weight
+      const T mu = L.mu[6 * e + f];
+      T dm = 0, dp = 0;
+#pragma unroll
+      for (int l = 0; l < N; ++l) {
+        dm += sD[end * N + l] * us[fo + l * st];
+        dp += sD[endp * N + l] * nb[fo + l * st];
+      }
+      const T um = us[fo + end * st];
+      const T qm = cn * dm;
+      T flux, lift;
+      if (nbid >= 0) {
+        const T gp = bx[6 * nbid + d];
+        const T qp = -sgn * gp * wab * dp;
+        const T jump = um - nb[fo + endp * st];
+        flux = mu * W * jump - T(0.5) * (qm - qp);
+        lift = T(-0.5) * jump * cn;
+      } else {
+        flux = T(2) * mu * W * um - qm;
+        lift = -um * cn;
+      }
+      R[fo + end * st] += flux;
+      // lifting: sum over the normal line of D[end][l] * lift
+#pragma unroll
+      for (int l = 0; l < N; ++l) R[fo + l * st] += sD[end * N + l] * lift;
+    }
+    __syncthreads();
+  }
+  if (!valid) return;
+  const bool frozen = L.cls[e] == DGFAS_FROZEN;
+  for (int k = 0; k < N; ++k) {
+    const int n = (k * N + ty) * N + tx;
+    T o = alpha * R[n];
+    if (b) o += (T)b[eo + n];
+    out[eo + n] = frozen ? TO(0) : (TO)o;
+  }
+}
+
 template <int N, typename T, typename TU, typename TB, typename TO>
 static int apply_N(const LevelView<T>& L, const TU* u, const TB* b, TO* out, T alpha,
                    cudaStream_t st) {
@@ -214,13 +326,20 @@ static int apply_N(const LevelView<T>& L, const TU* u, const TB* b, TO* out, T a
   dim3 blk(N2, epb), grd((L.ne + epb - 1) / epb);
   // the attribute is set once per instantiation (never inside a graph capture)
   if (L.box) {
-    auto kf = k_apply<N, T, TU, TB, TO, true>;
+    int epb2 = (128 + N2 - 1) / N2;
+    size_t smem2 = (2 * N2 + 16 + (size_t)3 * N3 * epb2) * sizeof(T);
+    while (epb2 > 1 && smem2 > 100 * 1024) {
+      --epb2;
+      smem2 = (2 * N2 + 16 + (size_t)3 * N3 * epb2) * sizeof(T);
+    }
+    auto kf = k_apply_box<N, T, TU, TB, TO>;
     static bool attr = false;
     if (!attr) {
       CK(cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024));
       attr = true;
     }
-    kf<<<grd, blk, smem, st>>>(L, u, b, out, alpha);
+    dim3 blk2(N2, epb2), grd2((L.ne + epb2 - 1) / epb2);
+    kf<<<grd2, blk2, smem2, st>>>(L, L.bx, L.Lhat, u, b, out, alpha);
   } else {
     auto kf = k_apply<N, T, TU, TB, TO, false>;
     static bool attr = false;
@@ -337,6 +456,12 @@ __global__ void k_fd(const LevelView<T> L, const TR* __restrict__ r, T* __restri
     l1[t] = L.lam[v1 * nsm + t]; l2[t] = L.lam[v2 * nsm + t]; l3[t] = L.lam[v3 * nsm + t];
     w1[t] = L.W[v1 * nsm + t];   w2[t] = L.W[v2 * nsm + t];   w3[t] = L.W[v3 * nsm + t];
   }
+  // zero both buffers: the unrolled products below read the padding (times zero)
+  for (int t = threadIdx.x; t < NS3; t += NS2) {
+    X[t] = T(0);
+    Y[t] = T(0);
+  }
+  __syncthreads();
   // gather
   const bool in_ab = a < n1 && b < n2;
   if (in_ab && active) {
@@ -354,21 +479,31 @@ __global__ void k_fd(const LevelView<T> L, const TR* __restrict__ r, T* __restri
   }
   // (teams are independent: a CTA holds whole teams and all threads reach the barriers)
   __syncthreads();
-  // S1^T along a : Y[c][b][a] = sum_a' S1[a'][a] X[c][b][a']
-  if (in_ab)
+  // S1^T along a : Y[c][b][a] = sum_a' S1[a'][a] X[c][b][a']; the thread's
+  // column of S1 stays in registers (zero beyond the variant's size)
+  T sr[NS];
+  if (in_ab) {
+#pragma unroll
+    for (int q = 0; q < NS; ++q) sr[q] = q < n1 ? S1[q * NS + a] : T(0);
     for (int c = 0; c < n3; ++c) {
       T s = 0;
-      for (int q = 0; q < n1; ++q) s += S1[q * NS + a] * X[(c * NS + b) * NS + q];
+#pragma unroll
+      for (int q = 0; q < NS; ++q) s += sr[q] * X[(c * NS + b) * NS + q];
       Y[(c * NS + b) * NS + a] = s;
     }
+  }
   __syncthreads();
   // S2^T along b
-  if (in_ab)
+  if (in_ab) {
+#pragma unroll
+    for (int q = 0; q < NS; ++q) sr[q] = q < n2 ? S2[q * NS + b] : T(0);
     for (int c = 0; c < n3; ++c) {
       T s = 0;
-      for (int q = 0; q < n2; ++q) s += S2[q * NS + b] * Y[(c * NS + q) * NS + a];
+#pragma unroll
+      for (int q = 0; q < NS; ++q) s += sr[q] * Y[(c * NS + q) * NS + a];
       X[(c * NS + b) * NS + a] = s;
     }
+  }
   __syncthreads();
   // S3^T along c, scale by D^-1, S3 along c (the column stays in registers)
   const T g0 = L.g[4 * e], g1 = L.g[4 * e + 1], g2 = L.g[4 * e + 2], g3 = L.g[4 * e + 3];
@@ -393,20 +528,28 @@ __global__ void k_fd(const LevelView<T> L, const TR* __restrict__ r, T* __restri
   }
   __syncthreads();
   // S2 along b
-  if (in_ab)
+  if (in_ab) {
+#pragma unroll
+    for (int q = 0; q < NS; ++q) sr[q] = q < n2 ? S2[b * NS + q] : T(0);
     for (int c = 0; c < n3; ++c) {
       T s = 0;
-      for (int q = 0; q < n2; ++q) s += S2[b * NS + q] * Y[(c * NS + q) * NS + a];
+#pragma unroll
+      for (int q = 0; q < NS; ++q) s += sr[q] * Y[(c * NS + q) * NS + a];
       X[(c * NS + b) * NS + a] = s;
     }
+  }
   __syncthreads();
   // S1 along a, weight, write
   if (in_ab && valid) {
+#pragma unroll
+    for (int q = 0; q < NS; ++q) sr[q] = q < n1 ? S1[a * NS + q] : T(0);
     T* P = patch + (size_t)e * NS3;
+    const T wab = w1[a] * w2[b];
     for (int c = 0; c < n3; ++c) {
       T s = 0;
-      for (int q = 0; q < n1; ++q) s += S1[a * NS + q] * X[(c * NS + b) * NS + q];
-      P[(c * NS + b) * NS + a] = active ? s * w1[a] * w2[b] * w3[c] : T(0);
+#pragma unroll
+      for (int q = 0; q < NS; ++q) s += sr[q] * X[(c * NS + b) * NS + q];
+      P[(c * NS + b) * NS + a] = active ? s * wab * w3[c] : T(0);
     }
   }
 }
@@ -462,54 +605,66 @@ int launch_fd(Ctx& c, int l, int prec, const void* r) {
 }
 
 // ============================================================================ combine
-// One thread per node of the level: u[e][n] = scale_u * u + sum of the weighted
-// patch entries of every subdomain that covers the node (own element and the up
-// to 26 neighbours whose overlap layers reach it).  Frozen entries untouched.
+// One CTA per element (deterministic pull, no atomics): each own node sums the
+// weighted patch entries of every subdomain that covers it, i.e. its own
+// element's and those of the up to 26 neighbours whose overlap layers reach it
+// (at most 2 candidates per direction, 8 in all).  The neighbour ids and their
+// left-side flags are staged in shared memory once per element.  Frozen
+// elements are left untouched (ADD) or zeroed (!ADD).
 template <typename T, bool ADD, typename TO>
 __global__ void k_combine(const LevelView<T> L, const T* __restrict__ patch,
                           TO* __restrict__ u) {
+  __shared__ int s_nb[27];
+  __shared__ unsigned char s_ml[27][3];
+  const int e = blockIdx.x;
   const int N = L.N, N3 = N * N * N, m = L.m, nsm = L.nsm;
   const size_t NS3 = (size_t)nsm * nsm * nsm;
-  const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (gid >= (long long)L.ne * N3) return;
-  const int e = (int)(gid / N3), n = (int)(gid % N3);
-  if (L.cls[e] == DGFAS_FROZEN) {
-    if (!ADD) u[gid] = TO(0);
-    return;
+  const bool frozen = L.cls[e] == DGFAS_FROZEN;
+  if (threadIdx.x < 27) {
+    int src = L.nbr27[27 * e + threadIdx.x];
+    if (src >= 0 && L.cls[src] == DGFAS_FROZEN) src = -1;
+    s_nb[threadIdx.x] = src;
+    for (int d = 0; d < 3; ++d)
+      s_ml[threadIdx.x][d] = (src >= 0 && L.var[3 * src + d] < 3) ? (unsigned char)m : 0;
   }
-  const int i = n % N, j = (n / N) % N, k = n / (N * N);
-  const int idx[3] = {i, j, k};
-  // per direction: candidate offsets (own always; -1 if i < m; +1 if i >= N - m)
-  int lo[3], hi[3];
-  for (int d = 0; d < 3; ++d) {
-    lo[d] = idx[d] < m ? -1 : 0;
-    hi[d] = idx[d] >= N - m ? 1 : 0;
-  }
-  double s = 0.0;
-  for (int oz = lo[2]; oz <= hi[2]; ++oz)
-    for (int oy = lo[1]; oy <= hi[1]; ++oy)
-      for (int ox = lo[0]; ox <= hi[0]; ++ox) {
-        const int src = L.nbr27[27 * e + (ox + 1) + 3 * (oy + 1) + 9 * (oz + 1)];
-        if (src < 0 || L.cls[src] == DGFAS_FROZEN) continue;
-        const int o[3] = {ox, oy, oz};
-        int pidx[3];
-        for (int d = 0; d < 3; ++d) {
-          const int v = L.var[3 * src + d];
-          const int mL = v < 3 ? m : 0;
-          pidx[d] = o[d] == 0 ? idx[d] + mL : (o[d] < 0 ? mL + N + idx[d] : idx[d] - (N - m));
+  __syncthreads();
+  const size_t eo = (size_t)e * N3;
+  for (int n = threadIdx.x; n < N3; n += blockDim.x) {
+    if (frozen) {
+      if (!ADD) u[eo + n] = TO(0);
+      continue;
+    }
+    const int i = n % N, j = (n / N) % N, k = n / (N * N);
+    const int lx = i < m ? -1 : 0, hx = i >= N - m ? 1 : 0;
+    const int ly = j < m ? -1 : 0, hy = j >= N - m ? 1 : 0;
+    const int lz = k < m ? -1 : 0, hz = k >= N - m ? 1 : 0;
+    double s = 0.0;
+    for (int oz = lz; oz <= hz; ++oz)
+      for (int oy = ly; oy <= hy; ++oy)
+        for (int ox = lx; ox <= hx; ++ox) {
+          const int slot = (ox + 1) + 3 * (oy + 1) + 9 * (oz + 1);
+          const int src = s_nb[slot];
+          if (src < 0) continue;
+          const int px = ox == 0 ? i + s_ml[slot][0] : (ox < 0 ? s_ml[slot][0] + N + i : i - (N - m));
+          const int py = oy == 0 ? j + s_ml[slot][1] : (oy < 0 ? s_ml[slot][1] + N + j : j - (N - m));
+          const int pz = oz == 0 ? k + s_ml[slot][2] : (oz < 0 ? s_ml[slot][2] + N + k : k - (N - m));
+          s += (double)patch[(size_t)src * NS3 + ((size_t)pz * nsm + py) * nsm + px];
         }
-        s += (double)patch[(size_t)src * NS3 + ((size_t)pidx[2] * nsm + pidx[1]) * nsm + pidx[0]];
-      }
-  if (ADD) u[gid] += (TO)s;
-  else u[gid] = (TO)s;
+    if (ADD) u[eo + n] += (TO)s;
+    else u[eo + n] = (TO)s;
+  }
+}
+
+static int combine_threads(int N) {
+  const int N3 = N * N * N;
+  return N3 >= 256 ? 256 : ((N3 + 31) / 32) * 32;
 }
 
 // delta += sum of the weighted patches (delta in the smoother precision)
 int launch_combine(Ctx& c, int l, int prec, void* delta) {
   LevelHost& H = c.lv[l];
-  const long long n = H.ndof;
-  const int bs = 256;
-  const unsigned grd = (unsigned)((n + bs - 1) / bs);
+  const int bs = combine_threads(H.N);
+  const unsigned grd = (unsigned)H.ne;
   if (prec == DGFAS_FP64)
     k_combine<double, true, double><<<grd, bs, 0, c.stream>>>(H.v64, (const double*)c.patch,
                                                               (double*)delta);
@@ -523,9 +678,8 @@ int launch_combine(Ctx& c, int l, int prec, void* delta) {
 // z = sum of the weighted patches (FP64 output, SCG preconditioner)
 int launch_combine_to(Ctx& c, int l, int prec, double* z) {
   LevelHost& H = c.lv[l];
-  const long long n = H.ndof;
-  const int bs = 256;
-  const unsigned grd = (unsigned)((n + bs - 1) / bs);
+  const int bs = combine_threads(H.N);
+  const unsigned grd = (unsigned)H.ne;
   if (prec == DGFAS_FP64)
     k_combine<double, false, double><<<grd, bs, 0, c.stream>>>(H.v64, (const double*)c.patch, z);
   else
