@@ -179,6 +179,22 @@ int dgfas_fma_peak(double* tflops_fp64, double* tflops_fp32);
 int dgfas_host_fd_variant(int p, double delta, double mu_star, int variant, double* S,
                           double* lam, double* W, int* n_out);
 
+/* Allocation-free Schwarz correction (the paper has no counterpart; it exists
+   for callers that cannot allocate device memory when they smooth, e.g. code
+   running inside its own stream capture or under an allocator that owns all
+   device memory).  Adds to u [ndof] the FP64 weighted Schwarz correction
+   sum_e R_s^T W^e (A~_s^e)^-1 R_s r of the residual r [ndof] on `level` (>= 1),
+   i.e. the update of one sweep of Alg. 5 given its residual.  Both are device
+   pointers; u is updated in place, r is read only.
+   Scratch: a fixed 16 MiB device array inside the library (2^21 FP64 patch
+   entries) replaces the context's patch buffer; levels needing more, i.e.
+   n_elem (p+1+2m)^3 > 2^21, are rejected with DGFAS_ERR_UNSUPPORTED.  The call
+   makes no device allocation of any kind.  Its first call on a device looks up
+   the array's device address (cudaGetSymbolAddress), so make that first call
+   before any stream capture.  All calls share the one array: calls whose work
+   overlaps on the GPU (different streams, or several contexts) race on it. */
+int dgfas_schwarz_correct_static(void* ctx, int level, const double* r, double* u);
+
 const char* dgfas_strerror(int code);
 const char* dgfas_last_error(void);
 

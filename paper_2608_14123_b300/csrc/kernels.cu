@@ -1064,3 +1064,17 @@ int launch_fma_peak(cudaStream_t st, int fp64, int iters, double* tflops) {
   cudaFree(out);
   return DGFAS_OK;
 }
+
+// FP64 FD step and combine with a caller-chosen patch buffer (used by the
+// allocation-free entry point; the smoother itself uses the context's buffer).
+int launch_fd_patch(Ctx& c, int l, const double* r, double* patch) {
+  return fd_disp<double, double>(c.lv[l].v64, r, patch, c.stream);
+}
+
+int launch_combine_patch(Ctx& c, int l, const double* patch, double* u) {
+  LevelHost& H = c.lv[l];
+  k_combine<double, true, double><<<(unsigned)H.ne, combine_threads(H.N), 0, c.stream>>>(
+      H.v64, patch, u);
+  CK(cudaGetLastError());
+  return DGFAS_OK;
+}

@@ -54,7 +54,7 @@ class dgfas_info(ctypes.Structure):
 SYMBOLS = ["dgfas_setup_levels", "dgfas_destroy", "dgfas_level_ndof", "dgfas_node_coords",
            "dgfas_assemble_rhs", "dgfas_apply_op", "dgfas_schwarz_smooth", "dgfas_fas_vcycle",
            "dgfas_solve", "dgfas_norm", "dgfas_set_surrogate", "dgfas_get_surrogate",
-           "dgfas_use_graph", "dgfas_profile_sweep", "dgfas_fma_peak", "dgfas_host_fd_variant", "dgfas_strerror", "dgfas_last_error"]
+           "dgfas_use_graph", "dgfas_profile_sweep", "dgfas_fma_peak", "dgfas_schwarz_correct_static", "dgfas_host_fd_variant", "dgfas_strerror", "dgfas_last_error"]
 
 _lib = None
 
@@ -86,6 +86,7 @@ def load():
         "dgfas_host_fd_variant": (I, [I, D, D, I, P, P, P, ctypes.POINTER(I)]),
         "dgfas_profile_sweep": (I, [P, I, P, P, I, P]),
         "dgfas_fma_peak": (I, [ctypes.POINTER(D), ctypes.POINTER(D)]),
+        "dgfas_schwarz_correct_static": (I, [P, I, P, P]),
         "dgfas_strerror": (ctypes.c_char_p, [I]),
         "dgfas_last_error": (ctypes.c_char_p, []),
     }
@@ -214,6 +215,12 @@ class Solver:
         _check(load().dgfas_profile_sweep(self.ctx, level % self.n_levels, _ptr(u), _ptr(g), reps,
                                           ms.ctypes.data_as(ctypes.c_void_p)), "profile_sweep")
         return dict(residual_smoother=ms[0], fd=ms[1], combine=ms[2], residual_fp64=ms[3])
+
+    def dgfas_schwarz_correct_static(self, level, r, u):
+        """u += weighted Schwarz correction of r, using the library's static
+        scratch array (no device allocation in the call)."""
+        _check(load().dgfas_schwarz_correct_static(self.ctx, level % self.n_levels, _ptr(r), _ptr(u)),
+               "schwarz_correct_static")
 
     # ---- conveniences built from the calls above
     def node_coords(self, level=-1):
