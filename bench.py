@@ -205,10 +205,14 @@ def run_gpu(args):
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push("timed")
+    k_before = dgfas.dgfas_kernel_launches()
     e0.record()
     for _ in range(args.steps):
         S.dgfas_fas_vcycle(u, b, want_norm=False)
     e1.record()
+    torch.cuda.nvtx.range_pop()
+    gpu_launches = dgfas.dgfas_kernel_launches() - k_before
     torch.cuda.synchronize()
     clocks = stop_clock_log(clk_p, clk_fh, local)
     ms = e0.elapsed_time(e1) / args.steps
@@ -309,7 +313,7 @@ def run_gpu(args):
                        "precision": args.precision, "global_batch": 1, "seq_len": 0,
                        "parallelism": "replicas" if ws > 1 else "single",
                        "l2": "inputs larger than L2 (top vector 191 MB > 126 MB)"},
-            "gpu_launches": None,
+            "gpu_launches": gpu_launches,
             "roofline": roofline,
             "kernel_ms": {k: v["ms"] for k, v in kernels.items()},
             "kernel_share_ms_per_cycle": shares,

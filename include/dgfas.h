@@ -179,6 +179,10 @@ int dgfas_fma_peak(double* tflops_fp64, double* tflops_fp32);
 int dgfas_host_fd_variant(int p, double delta, double mu_star, int variant, double* S,
                           double* lam, double* W, int* n_out);
 
+/* Number of kernels the library has launched in this process (including the
+   kernel nodes of replayed CUDA graphs). */
+long long dgfas_kernel_launches(void);
+
 /* Allocation-free Schwarz correction (the paper has no counterpart; it exists
    for callers that cannot allocate device memory when they smooth, e.g. code
    running inside its own stream capture or under an allocator that owns all

@@ -1,6 +1,7 @@
 // Internal structures shared by the host setup, the kernels and the driver.
 #pragma once
 #include <cuda_runtime.h>
+#include <atomic>
 #include <cstdint>
 #include <string>
 #include <vector>
@@ -99,6 +100,7 @@ struct Ctx {
   const double* g_u = nullptr;
   const double* g_f = nullptr;
   int g_kind = -1;
+  long long graph_kernels = 0;   // kernel nodes of the captured graph
 };
 
 // kernels.cu
@@ -121,5 +123,6 @@ int launch_node_coords(Ctx& c, int l, double* xyz);
 int launch_rhs(Ctx& c, const double* f, const double* uD, double* b);
 int launch_to_float(Ctx& c, const double* x, float* y, long long n);
 extern int g_red_blocks;
+extern std::atomic<long long> g_kernels;   // kernels launched (graph replays included)
 
 void set_error(const std::string& s);

@@ -680,8 +680,11 @@ static int run_body(Ctx& c, int kind, double* u, const double* f) {
       if (cudaStreamBeginCapture(c.cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
         rc = DGFAS_ERR_CUDA;
       } else {
+        const long long k0 = g_kernels.load();
         int rc2 = kind == 0 ? vcycle_body(c, u, f) : solve_cycle_body(c, u, f);
         cudaError_t ce = cudaStreamEndCapture(c.cap, &g);
+        c.graph_kernels = g_kernels.load() - k0;   // captured, not executed
+        g_kernels -= c.graph_kernels;
         if (rc2 != DGFAS_OK) rc = rc2;
         else if (ce != cudaSuccess || cudaGraphInstantiate(&c.gexec, g, 0) != cudaSuccess) {
           set_error("graph capture/instantiate failed");
@@ -695,6 +698,8 @@ static int run_body(Ctx& c, int kind, double* u, const double* f) {
   } else if (cudaGraphLaunch(c.gexec, c.cap) != cudaSuccess) {
     set_error("graph launch failed");
     rc = DGFAS_ERR_CUDA;
+  } else {
+    g_kernels += c.graph_kernels;
   }
   c.stream = user;
   CK(cudaEventRecord(c.ev_out, c.cap));
@@ -913,3 +918,7 @@ extern "C" int dgfas_fma_peak(double* tflops_fp64, double* tflops_fp32) {
   RET(launch_fma_peak(nullptr, 1, 4096, tflops_fp64));
   return launch_fma_peak(nullptr, 0, 65536, tflops_fp32);
 }
+
+// Number of kernels this library has launched in the process so far, the
+// kernel nodes of replayed CUDA graphs included.
+extern "C" long long dgfas_kernel_launches(void) { return g_kernels.load(); }

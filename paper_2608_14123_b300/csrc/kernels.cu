@@ -5,11 +5,13 @@
 //  k_project / k_restrict / k_prolong   FAS transfers (Sec. 3.2, Alg. 2)
 //  k_root     dense root solve (inverse times vector)
 //  reductions, axpy, coordinates, right-hand side
+#include <atomic>
 #include <cstdio>
 
 #include "dgfas_internal.h"
 
 int g_red_blocks = 592;   // 4 x 148 SMs
+std::atomic<long long> g_kernels{0};   // kernels launched through the library
 
 #define CK(x)                                                                 \
   do {                                                                        \
@@ -349,6 +351,7 @@ static int apply_N(const LevelView<T>& L, const TU* u, const TB* b, TO* out, T a
     }
     kf<<<grd, blk, smem, st>>>(L, u, b, out, alpha);
   }
+  ++g_kernels;
   CK(cudaGetLastError());
   return DGFAS_OK;
 }
@@ -505,41 +508,52 @@ __global__ void k_fd(const LevelView<T> L, const TR* __restrict__ r, T* __restri
     }
   }
   __syncthreads();
-  // S3^T along c, scale by D^-1, S3 along c (the column stays in registers)
-  const T g0 = L.g[4 * e], g1 = L.g[4 * e + 1], g2 = L.g[4 * e + 2], g3 = L.g[4 * e + 3];
-  if (in_ab) {
-    T col[NS], tmp[NS];
+  // S3^T along c: thread (a, c') of the NS x NS team, S3 column c' in registers,
+  // loop over b:  Y[c'][b][a] = sum_c S3[c][c'] X[c][b][a]
+  const int cq = b;   // second thread index reused as the c index
+  const bool in_ac = a < n1 && cq < n3;
+  if (in_ac) {
 #pragma unroll
-    for (int c = 0; c < NS; ++c) col[c] = c < n3 ? X[(c * NS + b) * NS + a] : T(0);
-#pragma unroll
-    for (int c = 0; c < NS; ++c) {
+    for (int q = 0; q < NS; ++q) sr[q] = q < n3 ? S3[q * NS + cq] : T(0);
+    for (int bb = 0; bb < n2; ++bb) {
       T s = 0;
 #pragma unroll
-      for (int q = 0; q < NS; ++q) s += S3[q * NS + c] * col[q];
-      tmp[c] = c < n3 ? s / (g0 + g1 * l1[a] + g2 * l2[b] + g3 * l3[c]) : T(0);
-    }
-#pragma unroll
-    for (int c = 0; c < NS; ++c) {
-      T s = 0;
-#pragma unroll
-      for (int q = 0; q < NS; ++q) s += S3[c * NS + q] * tmp[q];
-      if (c < n3) Y[(c * NS + b) * NS + a] = s;
+      for (int q = 0; q < NS; ++q) s += sr[q] * X[(q * NS + bb) * NS + a];
+      Y[(cq * NS + bb) * NS + a] = s;
     }
   }
   __syncthreads();
-  // S2 along b
+  // scale by D^-1 = 1 / (g0 + g1 lam1_a + g2 lam2_b + g3 lam3_c)
+  const T g0 = L.g[4 * e], g1 = L.g[4 * e + 1], g2 = L.g[4 * e + 2], g3 = L.g[4 * e + 3];
+  if (in_ab)
+    for (int c = 0; c < n3; ++c)
+      Y[(c * NS + b) * NS + a] /= (g0 + g1 * l1[a] + g2 * l2[b] + g3 * l3[c]);
+  __syncthreads();
+  // S3 along c: X[c][b][a] = sum_c' S3[c][c'] Y[c'][b][a], thread (a, c)
+  if (in_ac) {
+#pragma unroll
+    for (int q = 0; q < NS; ++q) sr[q] = q < n3 ? S3[cq * NS + q] : T(0);
+    for (int bb = 0; bb < n2; ++bb) {
+      T s = 0;
+#pragma unroll
+      for (int q = 0; q < NS; ++q) s += sr[q] * Y[(q * NS + bb) * NS + a];
+      X[(cq * NS + bb) * NS + a] = s;
+    }
+  }
+  __syncthreads();
+  // S2 along b: Y[c][b][a] = sum_b' S2[b][b'] X[c][b'][a]
   if (in_ab) {
 #pragma unroll
     for (int q = 0; q < NS; ++q) sr[q] = q < n2 ? S2[b * NS + q] : T(0);
     for (int c = 0; c < n3; ++c) {
       T s = 0;
 #pragma unroll
-      for (int q = 0; q < NS; ++q) s += sr[q] * Y[(c * NS + q) * NS + a];
-      X[(c * NS + b) * NS + a] = s;
+      for (int q = 0; q < NS; ++q) s += sr[q] * X[(c * NS + q) * NS + a];
+      Y[(c * NS + b) * NS + a] = s;
     }
   }
   __syncthreads();
-  // S1 along a, weight, write
+  // S1 along a, weight, write: P[c][b][a] = W sum_a' S1[a][a'] Y[c][b][a']
   if (in_ab && valid) {
 #pragma unroll
     for (int q = 0; q < NS; ++q) sr[q] = q < n1 ? S1[a * NS + q] : T(0);
@@ -548,12 +562,11 @@ __global__ void k_fd(const LevelView<T> L, const TR* __restrict__ r, T* __restri
     for (int c = 0; c < n3; ++c) {
       T s = 0;
 #pragma unroll
-      for (int q = 0; q < NS; ++q) s += sr[q] * X[(c * NS + b) * NS + q];
+      for (int q = 0; q < NS; ++q) s += sr[q] * Y[(c * NS + b) * NS + q];
       P[(c * NS + b) * NS + a] = active ? s * wab * w3[c] : T(0);
     }
   }
 }
-
 template <int NS, typename T, typename TR>
 static int fd_NS(const LevelView<T>& L, const TR* r, T* patch, cudaStream_t st) {
   constexpr int NS2 = NS * NS, NS3 = NS2 * NS;
@@ -569,6 +582,7 @@ static int fd_NS(const LevelView<T>& L, const TR* r, T* patch, cudaStream_t st) 
   }
   dim3 blk(NS2, epb), grd((L.ne + epb - 1) / epb);
   kf<<<grd, blk, smem, st>>>(L, r, patch);
+  ++g_kernels;
   CK(cudaGetLastError());
   return DGFAS_OK;
 }
@@ -638,7 +652,7 @@ __global__ void k_combine(const LevelView<T> L, const T* __restrict__ patch,
     const int lx = i < m ? -1 : 0, hx = i >= N - m ? 1 : 0;
     const int ly = j < m ? -1 : 0, hy = j >= N - m ? 1 : 0;
     const int lz = k < m ? -1 : 0, hz = k >= N - m ? 1 : 0;
-    double s = 0.0;
+    T s = T(0);   // accumulated in the smoother precision
     for (int oz = lz; oz <= hz; ++oz)
       for (int oy = ly; oy <= hy; ++oy)
         for (int ox = lx; ox <= hx; ++ox) {
@@ -648,7 +662,7 @@ __global__ void k_combine(const LevelView<T> L, const T* __restrict__ patch,
           const int px = ox == 0 ? i + s_ml[slot][0] : (ox < 0 ? s_ml[slot][0] + N + i : i - (N - m));
           const int py = oy == 0 ? j + s_ml[slot][1] : (oy < 0 ? s_ml[slot][1] + N + j : j - (N - m));
           const int pz = oz == 0 ? k + s_ml[slot][2] : (oz < 0 ? s_ml[slot][2] + N + k : k - (N - m));
-          s += (double)patch[(size_t)src * NS3 + ((size_t)pz * nsm + py) * nsm + px];
+          s += patch[(size_t)src * NS3 + ((size_t)pz * nsm + py) * nsm + px];
         }
     if (ADD) u[eo + n] += (TO)s;
     else u[eo + n] = (TO)s;
@@ -671,6 +685,7 @@ int launch_combine(Ctx& c, int l, int prec, void* delta) {
   else
     k_combine<float, true, float><<<grd, bs, 0, c.stream>>>(H.v32, (const float*)c.patch,
                                                             (float*)delta);
+  ++g_kernels;
   CK(cudaGetLastError());
   return DGFAS_OK;
 }
@@ -684,6 +699,7 @@ int launch_combine_to(Ctx& c, int l, int prec, double* z) {
     k_combine<double, false, double><<<grd, bs, 0, c.stream>>>(H.v64, (const double*)c.patch, z);
   else
     k_combine<float, false, double><<<grd, bs, 0, c.stream>>>(H.v32, (const float*)c.patch, z);
+  ++g_kernels;
   CK(cudaGetLastError());
   return DGFAS_OK;
 }
@@ -792,6 +808,7 @@ int launch_project(Ctx& c, int l, const double* uf) {
   LevelHost& F = c.lv[l];
   LevelHost& C = c.lv[l - 1];
   k_gather_children<false><<<C.ne, 256, 0, c.stream>>>(F.tr, uf, C.u, C.ubar);
+  ++g_kernels;
   CK(cudaGetLastError());
   return DGFAS_OK;
 }
@@ -800,6 +817,7 @@ int launch_restrict(Ctx& c, int l, const double* rf, double* rc) {
   LevelHost& F = c.lv[l];
   LevelHost& C = c.lv[l - 1];
   k_gather_children<true><<<C.ne, 256, 0, c.stream>>>(F.tr, rf, rc, nullptr);
+  ++g_kernels;
   CK(cudaGetLastError());
   return DGFAS_OK;
 }
@@ -811,6 +829,7 @@ int launch_prolong(Ctx& c, int l, double* uf, int prec, void* delta) {
     k_prolong<double><<<F.ne, 128, 0, c.stream>>>(F.tr, C.u, C.ubar, uf, (double*)delta);
   else
     k_prolong<float><<<F.ne, 128, 0, c.stream>>>(F.tr, C.u, C.ubar, uf, (float*)delta);
+  ++g_kernels;
   CK(cudaGetLastError());
   return DGFAS_OK;
 }
@@ -830,6 +849,7 @@ __global__ void k_root(const double* __restrict__ Ainv, const double* __restrict
 int launch_root(Ctx& c) {
   const int n = c.n_root;
   k_root<<<(n + 7) / 8, 256, 0, c.stream>>>(c.Ainv, c.lv[0].gv, c.lv[0].u, n);
+  ++g_kernels;
   CK(cudaGetLastError());
   return DGFAS_OK;
 }
@@ -856,12 +876,14 @@ __global__ void k_partial(const double* __restrict__ a, const double* __restrict
 
 int launch_sumsq(Ctx& c, const double* v, long long n, double* part) {
   k_partial<false><<<g_red_blocks, 256, 0, c.stream>>>(v, nullptr, n, part);
+  ++g_kernels;
   CK(cudaGetLastError());
   return DGFAS_OK;
 }
 
 int launch_dot(Ctx& c, const double* a, const double* b, long long n, double* part) {
   k_partial<true><<<g_red_blocks, 256, 0, c.stream>>>(a, b, n, part);
+  ++g_kernels;
   CK(cudaGetLastError());
   return DGFAS_OK;
 }
@@ -874,6 +896,7 @@ __global__ void k_axpy(long long n, double alpha, const double* __restrict__ x,
 
 int launch_axpy(Ctx& c, long long n, double alpha, const double* x, double* y) {
   k_axpy<<<(unsigned)((n + 255) / 256), 256, 0, c.stream>>>(n, alpha, x, y);
+  ++g_kernels;
   CK(cudaGetLastError());
   return DGFAS_OK;
 }
@@ -888,6 +911,7 @@ int launch_add_delta(Ctx& c, long long n, int prec, const void* d, double* u) {
   const unsigned g = (unsigned)((n + 255) / 256);
   if (prec == DGFAS_FP64) k_add_delta<double><<<g, 256, 0, c.stream>>>(n, (const double*)d, u);
   else k_add_delta<float><<<g, 256, 0, c.stream>>>(n, (const float*)d, u);
+  ++g_kernels;
   CK(cudaGetLastError());
   return DGFAS_OK;
 }
@@ -899,6 +923,7 @@ __global__ void k_to_float(const double* __restrict__ x, float* __restrict__ y, 
 
 int launch_to_float(Ctx& c, const double* x, float* y, long long n) {
   k_to_float<<<(unsigned)((n + 255) / 256), 256, 0, c.stream>>>(x, y, n);
+  ++g_kernels;
   CK(cudaGetLastError());
   return DGFAS_OK;
 }
@@ -927,6 +952,7 @@ int launch_node_coords(Ctx& c, int l, double* xyz) {
   CK(cudaMemcpyAsync(dcorn, H.corners.data(), H.corners.size() * sizeof(double),
                      cudaMemcpyHostToDevice, c.stream));
   k_coords<<<(unsigned)((H.ndof + 255) / 256), 256, 0, c.stream>>>(H.v64, dcorn, xyz);
+  ++g_kernels;
   CK(cudaGetLastError());
   CK(cudaFreeAsync(dcorn, c.stream));
   return DGFAS_OK;
@@ -1001,6 +1027,7 @@ static int rhs_N(Ctx& c, const double* f, const double* uD, double* b) {
   LevelHost& H = c.lv.back();
   if (H.box) k_rhs<N, true><<<H.ne, N * N, 0, c.stream>>>(H.v64, f, uD, b);
   else k_rhs<N, false><<<H.ne, N * N, 0, c.stream>>>(H.v64, f, uD, b);
+  ++g_kernels;
   CK(cudaGetLastError());
   return DGFAS_OK;
 }
@@ -1075,6 +1102,7 @@ int launch_combine_patch(Ctx& c, int l, const double* patch, double* u) {
   LevelHost& H = c.lv[l];
   k_combine<double, true, double><<<(unsigned)H.ne, combine_threads(H.N), 0, c.stream>>>(
       H.v64, patch, u);
+  ++g_kernels;
   CK(cudaGetLastError());
   return DGFAS_OK;
 }

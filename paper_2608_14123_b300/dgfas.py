@@ -54,7 +54,7 @@ class dgfas_info(ctypes.Structure):
 SYMBOLS = ["dgfas_setup_levels", "dgfas_destroy", "dgfas_level_ndof", "dgfas_node_coords",
            "dgfas_assemble_rhs", "dgfas_apply_op", "dgfas_schwarz_smooth", "dgfas_fas_vcycle",
            "dgfas_solve", "dgfas_norm", "dgfas_set_surrogate", "dgfas_get_surrogate",
-           "dgfas_use_graph", "dgfas_profile_sweep", "dgfas_fma_peak", "dgfas_schwarz_correct_static", "dgfas_host_fd_variant", "dgfas_strerror", "dgfas_last_error"]
+           "dgfas_use_graph", "dgfas_profile_sweep", "dgfas_fma_peak", "dgfas_schwarz_correct_static", "dgfas_kernel_launches", "dgfas_host_fd_variant", "dgfas_strerror", "dgfas_last_error"]
 
 _lib = None
 
@@ -87,6 +87,7 @@ def load():
         "dgfas_profile_sweep": (I, [P, I, P, P, I, P]),
         "dgfas_fma_peak": (I, [ctypes.POINTER(D), ctypes.POINTER(D)]),
         "dgfas_schwarz_correct_static": (I, [P, I, P, P]),
+        "dgfas_kernel_launches": (LL, []),
         "dgfas_strerror": (ctypes.c_char_p, [I]),
         "dgfas_last_error": (ctypes.c_char_p, []),
     }
@@ -248,3 +249,8 @@ def dgfas_fma_peak():
     a, b = ctypes.c_double(0), ctypes.c_double(0)
     _check(load().dgfas_fma_peak(ctypes.byref(a), ctypes.byref(b)), "fma_peak")
     return a.value, b.value
+
+
+def dgfas_kernel_launches():
+    """Kernels launched by the library so far in this process (graph nodes included)."""
+    return int(load().dgfas_kernel_launches())
