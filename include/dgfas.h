@@ -179,6 +179,39 @@ int dgfas_fma_peak(double* tflops_fp64, double* tflops_fp32);
 int dgfas_host_fd_variant(int p, double delta, double mu_star, int variant, double* S,
                           double* lam, double* W, int* n_out);
 
+/* ---- learned surrogate (the paper has no learned part; this is the
+   network that predicts the surrogate coefficients of Eq. (10) from an
+   element's corners).  MLP 24 -> 64 -> 64 -> 6, tanh hidden layers, linear
+   output, FP32; parameters in one flat device array of
+   dgfas_mlp_param_count() floats: W1[64][24] b1[64] W2[64][64] b2[64]
+   W3[6][64] b3[6].  Inputs X [n][24]: corner coordinates minus the centroid,
+   divided by V^(1/3); outputs [n][6]: log(dx_i / V^(1/3)), log(s_i). */
+int dgfas_mlp_param_count(void);
+
+/* out [n][6] = MLP(params, X) (device pointers; synchronizes `stream`). */
+int dgfas_mlp_forward(const float* params, const float* X, int n, float* out, void* stream);
+
+/* grad [param_count] = d/dparams of the mean squared error of MLP(X) - Y over
+   all n samples and 6 outputs (device pointers; synchronizes). */
+int dgfas_mlp_grad(const float* params, const float* X, const float* Y, int n, float* grad,
+                   void* stream);
+
+/* Adam training (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected) with
+   minibatches of `batch` samples drawn by a per-epoch permutation from `seed`.
+   params, m, v [param_count] device, updated in place (m = v = 0 and t0 = 0 at
+   the start); X [n][24], Y [n][6] device.  loss_out (host, may be NULL)
+   receives the full-data loss after every epoch.  Synchronizes. */
+int dgfas_mlp_train(float* params, float* m, float* v, const float* X, const float* Y, int n,
+                    int epochs, int batch, float lr, unsigned long long seed, int t0,
+                    float* loss_out, void* stream);
+
+/* Sets the surrogate coefficients of `level` from the network's prediction:
+   g_i = s_i nu dx_j dx_k / (2 dx_i), g_0 = kappa dx_1 dx_2 dx_3 / 8.  Elements
+   whose predicted |log s_i| exceeds max_log_scaling (or is not finite) keep
+   their geometric coefficients; their count goes to *n_fallback (host). */
+int dgfas_learned_surrogate(void* ctx, int level, const float* params, double max_log_scaling,
+                            int* n_fallback);
+
 /* Number of kernels the library has launched in this process (including the
    kernel nodes of replayed CUDA graphs). */
 long long dgfas_kernel_launches(void);

@@ -54,7 +54,8 @@ class dgfas_info(ctypes.Structure):
 SYMBOLS = ["dgfas_setup_levels", "dgfas_destroy", "dgfas_level_ndof", "dgfas_node_coords",
            "dgfas_assemble_rhs", "dgfas_apply_op", "dgfas_schwarz_smooth", "dgfas_fas_vcycle",
            "dgfas_solve", "dgfas_norm", "dgfas_set_surrogate", "dgfas_get_surrogate",
-           "dgfas_use_graph", "dgfas_profile_sweep", "dgfas_fma_peak", "dgfas_schwarz_correct_static", "dgfas_kernel_launches", "dgfas_host_fd_variant", "dgfas_strerror", "dgfas_last_error"]
+           "dgfas_use_graph", "dgfas_profile_sweep", "dgfas_fma_peak", "dgfas_schwarz_correct_static", "dgfas_kernel_launches", "dgfas_mlp_param_count",
+           "dgfas_mlp_forward", "dgfas_mlp_grad", "dgfas_mlp_train", "dgfas_learned_surrogate", "dgfas_host_fd_variant", "dgfas_strerror", "dgfas_last_error"]
 
 _lib = None
 
@@ -88,6 +89,11 @@ def load():
         "dgfas_fma_peak": (I, [ctypes.POINTER(D), ctypes.POINTER(D)]),
         "dgfas_schwarz_correct_static": (I, [P, I, P, P]),
         "dgfas_kernel_launches": (LL, []),
+        "dgfas_mlp_param_count": (I, []),
+        "dgfas_mlp_forward": (I, [P, P, I, P, P]),
+        "dgfas_mlp_grad": (I, [P, P, P, I, P, P]),
+        "dgfas_mlp_train": (I, [P, P, P, P, P, I, I, I, ctypes.c_float, ctypes.c_ulonglong, I, P, P]),
+        "dgfas_learned_surrogate": (I, [P, I, P, D, ctypes.POINTER(I)]),
         "dgfas_strerror": (ctypes.c_char_p, [I]),
         "dgfas_last_error": (ctypes.c_char_p, []),
     }
@@ -222,6 +228,14 @@ class Solver:
         scratch array (no device allocation in the call)."""
         _check(load().dgfas_schwarz_correct_static(self.ctx, level % self.n_levels, _ptr(r), _ptr(u)),
                "schwarz_correct_static")
+
+    def dgfas_learned_surrogate(self, level, params, max_log_scaling=2.5):
+        """Surrogate coefficients of `level` from the MLP; returns the number of
+        elements that kept their geometric coefficients."""
+        nf = ctypes.c_int(0)
+        _check(load().dgfas_learned_surrogate(self.ctx, level % self.n_levels, _ptr(params),
+                                              max_log_scaling, ctypes.byref(nf)), "learned_surrogate")
+        return nf.value
 
     # ---- conveniences built from the calls above
     def node_coords(self, level=-1):
