@@ -119,6 +119,24 @@ int dgfas_node_coords(void* ctx, int level, double* xyz);
 int dgfas_assemble_rhs(void* ctx, const double* f_nodal, const double* uD_nodal,
                        double* b);
 
+/* Right-hand side of Eq. (2) on any level (as dgfas_assemble_rhs); with local
+   refinement the leaves of every level need their own RHS. */
+int dgfas_assemble_rhs_level(void* ctx, int level, const double* f_nodal,
+                             const double* uD_nodal, double* b);
+
+/* Sets the RHS f_l [ndof of level] (device) kept on the leaf elements of a
+   level below the top (Eq. (4c): leaves replicate the original RHS).  Levels
+   without leaves ignore it. */
+int dgfas_set_level_rhs(void* ctx, int level, const double* f);
+
+/* r_2 of Sec. 6.1: the Euclidean norm of the residual over the leaf elements
+   of all levels (the top level's from u_top, f_top; the others from the
+   context's level solutions and their leaf RHS).  Synchronizes. */
+int dgfas_composite_residual(void* ctx, double* u_top, const double* f_top, double* out);
+
+/* Copies the context's current solution of a level below the top into u. */
+int dgfas_get_level_solution(void* ctx, int level, double* u);
+
 /* Operator application of Eq. (2) on `level`: out = A u, or out = g - A u when
    g != NULL (the residual; rows of frozen elements are 0, Eq. (4d)).  u, g, out
    [ndof] device; out must not alias u. */
@@ -172,7 +190,9 @@ int dgfas_profile_sweep(void* ctx, int level, double* u, const double* g, int re
 int dgfas_fma_peak(double* tflops_fp64, double* tflops_fp32);
 
 /* Host-only (no device work): the fast-diagonalization data of one side variant
-   (variant = 3*left + right with 0 = interior, 1 = Dirichlet, 2 = Neumann) for
+   (variant = 4*left + right with side types 0 = interior, 1 = Dirichlet,
+   2 = Neumann, 3 = interior face whose neighbour is frozen, which contributes
+   no overlap layers) for
    degree p, overlap delta and penalty mu_star (Sec. 4.3.1): subdomain width n,
    S [n][n] (row = node, column = mode; S^T M S = I, S^T L S = diag(lambda)),
    lambda [n] and the weights W [n].  Buffers of at least 16*16 / 16 doubles. */

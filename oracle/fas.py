@@ -38,6 +38,10 @@ class Hierarchy:
                                     None if gcoefs is None else gcoefs[l])
                             for l, lv in enumerate(levels) if l > 0]
         self.tr = [None] + [Transfer(levels[l - 1], levels[l]) for l in range(1, len(levels))]
+        self.cls = [np.asarray(lv["cls"]) for lv in levels]
+        self.active = [c != 2 for c in self.cls]
+        self.local = any(np.any(c == 2) for c in self.cls) or any(
+            np.any(c == 0) for c in self.cls[:-1])
         A0 = assemble(self.ops[0]).toarray()
         self.root_chol = sla.cho_factor(A0)
 
@@ -46,7 +50,8 @@ class Hierarchy:
         return len(self.levels) - 1
 
     def A(self, l, u):
-        return apply(self.ops[l], u).reshape(-1)
+        """A_l u with frozen rows set to zero (Eq. (4d): r^f = 0)."""
+        return apply(self.ops[l], u, rows_mask=self.active[l]).reshape(-1)
 
     def residual(self, l, u, g):
         return g - self.A(l, u)
@@ -162,3 +167,79 @@ class Hierarchy:
             if np.linalg.norm(r) <= r_max:
                 break
         return u
+
+
+class LocalHierarchy(Hierarchy):
+    """FAS for locally refined multilevel meshes (Sec. 3.1, 3.3, Alg. 2):
+    twigs, leaves and frozen elements on every level; f is a list of per-level
+    right-hand sides (used on leaves), u a list of per-level vectors."""
+
+    def leaf_mask(self, l):
+        N3 = self.ops[l].N ** 3
+        return np.repeat(self.cls[l] == 0, N3)
+
+    def composite_residual(self, u, f):
+        """r_2 of Sec. 6.1: Euclidean norm of the leaf residuals of all levels,
+        evaluated on the composite solution: the twigs of each level first take
+        the projection of the finer level (top down, Eq. (6b)), the frozen
+        elements keep their interpolated values."""
+        u = list(u)
+        for l in range(self.L, 0, -1):
+            u[l - 1], _ = self.tr[l].project_active(u[l], u[l - 1], self.cls[l])
+        s = 0.0
+        for l in range(self.L + 1):
+            m = self.leaf_mask(l)
+            if np.any(m):
+                r = f[l] - self.A(l, u[l])
+                s += np.sum(r[m] ** 2)
+        return np.sqrt(s)
+
+    def _down_up_local(self, u, f, r_top):
+        L = self.L
+        u = list(u)
+        g = [None] * (L + 1)
+        g[L] = f[L]
+        ubar = [None] * (L + 1)
+        r = r_top
+        for l in range(L, 0, -1):
+            if l < L:
+                u[l] = self.smooth(l, u[l], g[l], self.s1)
+                r = self.residual(l, u[l], g[l])
+            u[l - 1], _ = self.tr[l].project_active(u[l], u[l - 1], self.cls[l])
+            ubar[l - 1] = u[l - 1].copy()
+            t = self.tr[l].restrict_active(r, self.cls[l])
+            gl = self.A(l - 1, u[l - 1]) + t
+            leaf = self.leaf_mask(l - 1)
+            gl[leaf] = f[l - 1][leaf]
+            g[l - 1] = gl
+        u[0] = self.root_solve(g[0])
+        for l in range(1, L + 1):
+            u[l] = self.tr[l].prolong_fas(u[l], u[l - 1], ubar[l - 1], self.cls[l])
+            if l < L:
+                u[l] = self.smooth(l, u[l], g[l], self.s2)
+        return u
+
+    def fas_vcycle_local(self, u, f):
+        """Alg. 2 on all levels of a locally refined hierarchy; returns (u, |r_top|)."""
+        L = self.L
+        u = [x.copy() for x in u]
+        u[L] = self.smooth(L, u[L], f[L], self.s1)
+        r = self.residual(L, u[L], f[L])
+        u = self._down_up_local(u, f, r)
+        u[L] = self.smooth(L, u[L], f[L], self.s2)
+        return u, np.linalg.norm(r)
+
+    def solve_local(self, u, f, rtol=1e-10, max_cycles=50):
+        """Crossover solve on the composite problem; returns (u, history of r_2)."""
+        L = self.L
+        u = [x.copy() for x in u]
+        hist = [self.composite_residual(u, f)]
+        u[L] = self.smooth(L, u[L], f[L], self.s1)
+        for k in range(max_cycles):
+            r = self.residual(L, u[L], f[L])
+            u = self._down_up_local(u, f, r)
+            u[L] = self.smooth(L, u[L], f[L], self.sc)
+            hist.append(self.composite_residual(u, f))
+            if hist[-1] <= rtol * hist[0]:
+                break
+        return u, hist

@@ -33,6 +33,11 @@ from .gll import gll, diff_matrix
 
 SIDE = {-1: "d", -2: "n"}
 VARIANTS = ("ii", "id", "in", "di", "dd", "dn", "ni", "nd", "nn")
+# with local refinement a fourth side type appears: "f", an interior face
+# whose neighbour is frozen (its values are fixed, so the subdomain takes no
+# layers from it; the face's own-side terms stay in the local operator)
+SIDES4 = ("i", "d", "n", "f")
+VARIANTS16 = tuple(a + b for a in SIDES4 for b in SIDES4)
 
 
 def overlap_layers(p, delta):
@@ -40,8 +45,10 @@ def overlap_layers(p, delta):
     return int(np.sum((1.0 + x) / 2.0 <= delta + 1e-14))
 
 
-def side_of(nb):
-    return "i" if nb >= 0 else SIDE[int(nb)]
+def side_of(nb, cls=None):
+    if nb >= 0:
+        return "f" if cls is not None and cls[nb] == 2 else "i"
+    return SIDE[int(nb)]
 
 
 def sip_1d_three_cells(p, mu_star, left, right):
@@ -55,7 +62,7 @@ def sip_1d_three_cells(p, mu_star, left, right):
     mu = mu_star * p * (p + 1) / 4.0
     L = np.zeros((3 * N, 3 * N))
     mass = np.zeros(3 * N)
-    cells = [0 if left == "i" else None, 1, 2 if right == "i" else None]
+    cells = [0 if left in "if" else None, 1, 2 if right in "if" else None]
     for c in cells:
         if c is None:
             continue
@@ -148,7 +155,7 @@ class FDTables:
         self.p, self.delta, self.mu_star = p, delta, mu_star
         self.m = overlap_layers(p, delta)
         self.tab = {}
-        for v in VARIANTS:
+        for v in VARIANTS16:
             M, L = subdomain_1d(p, self.m, mu_star, v[0], v[1])
             S, lam = fd_eigen(M, L)
             W = weights_1d(p, self.m, delta, v[0], v[1])
@@ -199,8 +206,9 @@ class Schwarz:
         self.m = self.tables.m
         nbr = level["nbr"]
         self.ne = nbr.shape[0]
-        self.var = [[side_of(nbr[e, 2 * d]) + side_of(nbr[e, 2 * d + 1]) for d in range(3)]
-                    for e in range(self.ne)]
+        cls = level["cls"]
+        self.var = [[side_of(nbr[e, 2 * d], cls) + side_of(nbr[e, 2 * d + 1], cls)
+                     for d in range(3)] for e in range(self.ne)]
         if gcoef is None:
             gcoef = np.array([surrogate_coeffs(surrogate_widths(level["corners"][e]), nu, kappa)
                               for e in range(self.ne)])

@@ -54,6 +54,43 @@ class Transfer:
         o = self.octant[e]
         return (0, 0, 0) if o < 0 else (o & 1, (o >> 1) & 1, (o >> 2) & 1)
 
+    def active_children(self, lf_cls):
+        """Mask of fine elements that take part in P and R (active children)."""
+        return np.asarray(lf_cls) != 2
+
+    def project_active(self, uf, uc_old, fine_cls):
+        """u_c^t = P^{t,a} u_f^a: only active children contribute and only their
+        parents (twigs) receive a result; other coarse entries keep uc_old."""
+        act = self.active_children(fine_cls)
+        uf = np.asarray(uf).reshape(self.nef, self.Nf, self.Nf, self.Nf)
+        out = np.asarray(uc_old).reshape(self.nec, self.Nc, self.Nc, self.Nc).copy()
+        recv = np.zeros(self.nec, bool)
+        recv[self.parent[act]] = True
+        out[recv] = 0.0
+        for e in np.nonzero(act)[0]:
+            o = self._oct(e)
+            A = [self.P1[o[d]] for d in range(3)] if self.h else [self.P1[0]] * 3
+            out[self.parent[e]] += _mode(A[0], A[1], A[2], uf[e][None])[0]
+        return out.reshape(-1), recv
+
+    def restrict_active(self, rf, fine_cls):
+        """R^{t,a} r_f^a: only active children contribute."""
+        act = self.active_children(fine_cls)
+        rf = np.asarray(rf).reshape(self.nef, self.Nf, self.Nf, self.Nf).copy()
+        rf[~act] = 0.0
+        return self.restrict(rf)
+
+    def prolong_fas(self, uf, uc, ubar, fine_cls):
+        """Frozen update u_f^f = I u_c (parents are leaves) and correction
+        prolongation u_f^a += I (u_c - ubar) on active children (Alg. 2)."""
+        fr = np.asarray(fine_cls) == 2
+        uf = np.asarray(uf).reshape(self.nef, self.Nf, self.Nf, self.Nf).copy()
+        full = self.interpolate(uc).reshape(uf.shape)
+        corr = self.interpolate(np.asarray(uc) - np.asarray(ubar)).reshape(uf.shape)
+        uf[fr] = full[fr]
+        uf[~fr] += corr[~fr]
+        return uf.reshape(-1)
+
     def interpolate(self, uc):
         """u_f = I u_c on every fine element."""
         uc = np.asarray(uc).reshape(self.nec, self.Nc, self.Nc, self.Nc)

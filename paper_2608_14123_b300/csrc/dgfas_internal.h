@@ -32,11 +32,12 @@ struct LevelView {
   const T* w;                 // [N] GLL weights
   const T* x;                 // [N] GLL nodes
   // Schwarz
-  const unsigned char* var;   // [ne][3] variant index 0..8 per direction
+  const unsigned char* var;   // [ne][3] variant 4*left+right per direction (side types
+                              // 0 interior, 1 Dirichlet, 2 Neumann, 3 frozen neighbour)
   const T* g;                 // [ne][4] surrogate coefficients g0..g3
-  const T* S;                 // [9][nsm][nsm]  S[v][row][col]
-  const T* lam;               // [9][nsm]
-  const T* W;                 // [9][nsm]
+  const T* S;                 // [16][nsm][nsm]  S[v][row][col]
+  const T* lam;               // [16][nsm]
+  const T* W;                 // [16][nsm]
 };
 
 struct TransferView {
@@ -72,6 +73,8 @@ struct LevelHost {
   // work vectors
   double *u = nullptr, *gv = nullptr, *r = nullptr, *ubar = nullptr, *t = nullptr;
   double* delta = nullptr;   // smoother correction (FP64 or FP32 storage)
+  double* fl = nullptr;      // RHS of the leaf elements (levels below the top)
+  int has_leaf = 0, has_frozen = 0;
   LevelView<double> v64;
   LevelView<float> v32;
   TransferView tr;
@@ -101,6 +104,7 @@ struct Ctx {
   const double* g_f = nullptr;
   int g_kind = -1;
   long long graph_kernels = 0;   // kernel nodes of the captured graph
+  int local = 0;                 // leaves below the top or frozen elements exist
 };
 
 // kernels.cu
@@ -120,7 +124,9 @@ int launch_sumsq(Ctx& c, const double* v, long long n, double* partial_out);
 int launch_dot(Ctx& c, const double* a, const double* b, long long n, double* partial_out);
 int launch_axpy(Ctx& c, long long n, double alpha, const double* x, double* y);
 int launch_node_coords(Ctx& c, int l, double* xyz);
-int launch_rhs(Ctx& c, const double* f, const double* uD, double* b);
+int launch_rhs(Ctx& c, int l, const double* f, const double* uD, double* b);
+int launch_sumsq_leaf(Ctx& c, int l, const double* v, double* part);
+int launch_leaf_rhs(Ctx& c, int l, const double* f, double* g);
 int launch_to_float(Ctx& c, const double* x, float* y, long long n);
 extern int g_red_blocks;
 extern std::atomic<long long> g_kernels;   // kernels launched (graph replays included)

@@ -54,7 +54,12 @@ static int dalloc(double** p, size_t n) {
 }
 
 static char side_char(int nb) { return nb >= 0 ? 'i' : (nb == -1 ? 'd' : 'n'); }
-static int side_idx(int nb) { return nb >= 0 ? 0 : (nb == -1 ? 1 : 2); }
+// side type of a face: 0 interior, 1 Dirichlet, 2 Neumann, 3 interior face
+// whose neighbour is frozen (the subdomain takes no layers from it)
+static int side_idx(int nb, const std::vector<signed char>& cls) {
+  if (nb >= 0) return cls[nb] == DGFAS_FROZEN ? 3 : 0;
+  return nb == -1 ? 1 : 2;
+}
 
 // ---------------------------------------------------------------- one level
 static int build_level(Ctx& c, const dgfas_level& in, const dgfas_params& prm, LevelHost& H) {
@@ -182,11 +187,12 @@ static int build_level(Ctx& c, const dgfas_level& in, const dgfas_params& prm, L
   H.nsm = N + 2 * H.m;
   if (H.nsm > DGFAS_MAX_NS) { set_error("subdomain width > 16"); return DGFAS_ERR_UNSUPPORTED; }
   const int nsm = H.nsm;
-  std::vector<double> S(9 * (size_t)nsm * nsm, 0.0), lam(9 * (size_t)nsm, 0.0), Wt(9 * (size_t)nsm, 0.0);
-  const char sc[3] = {'i', 'd', 'n'};
-  for (int v = 0; v < 9; ++v) {
+  std::vector<double> S(16 * (size_t)nsm * nsm, 0.0), lam(16 * (size_t)nsm, 0.0),
+      Wt(16 * (size_t)nsm, 0.0);
+  const char sc[4] = {'i', 'd', 'n', 'f'};
+  for (int v = 0; v < 16; ++v) {
     std::vector<double> Sv, lv, wv;
-    host::fd_variant(p, H.m, prm.mu_star, prm.delta, sc[v / 3], sc[v % 3], Sv, lv, wv);
+    host::fd_variant(p, H.m, prm.mu_star, prm.delta, sc[v / 4], sc[v % 4], Sv, lv, wv);
     const int n = (int)lv.size();
     for (int r = 0; r < n; ++r) {
       for (int q = 0; q < n; ++q) S[((size_t)v * nsm + r) * nsm + q] = Sv[r * n + q];
@@ -199,7 +205,8 @@ static int build_level(Ctx& c, const dgfas_level& in, const dgfas_params& prm, L
   std::vector<double> g(4 * (size_t)ne);
   for (int e = 0; e < ne; ++e) {
     for (int d = 0; d < 3; ++d)
-      var[3 * e + d] = (unsigned char)(3 * side_idx(H.nbr[6 * e + 2 * d]) + side_idx(H.nbr[6 * e + 2 * d + 1]));
+      var[3 * e + d] = (unsigned char)(4 * side_idx(H.nbr[6 * e + 2 * d], H.cls) +
+                                       side_idx(H.nbr[6 * e + 2 * d + 1], H.cls));
     double dx[3];
     host::surrogate_widths(&H.corners[24 * e], dx);
     g[4 * e] = c.kappa * dx[0] * dx[1] * dx[2] / 8.0;
@@ -382,7 +389,7 @@ static void free_level(LevelHost& H) {
                   H.d_h, H.d_G, H.d_fW, H.d_fc, H.d_mu, H.d_mass, H.d_D, H.d_w, H.d_g, H.d_S,
                   H.d_lam, H.d_W, H.d_x, H.f_h, H.f_G, H.f_fW, H.f_fc, H.f_mu, H.f_mass, H.f_D,
                   H.f_w, H.f_g, H.f_S, H.f_lam, H.f_W, H.f_x, H.d_I, H.d_P, H.u, H.gv, H.r,
-                  H.ubar, H.t, H.delta};
+                  H.ubar, H.t, H.delta, H.fl};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -449,6 +456,12 @@ extern "C" int dgfas_setup_levels(const dgfas_mesh* mesh, const dgfas_params* pr
     }
     if (!rc) rc = dalloc(&H.r, H.ndof);
     if (!rc) rc = dalloc(&H.delta, H.ndof);
+    for (int e = 0; e < H.ne; ++e) {
+      H.has_leaf |= H.cls[e] == DGFAS_LEAF;
+      H.has_frozen |= H.cls[e] == DGFAS_FROZEN;
+    }
+    if (!rc && !top && H.has_leaf) rc = dalloc(&H.fl, H.ndof);
+    if ((!top && H.has_leaf) || H.has_frozen) c->local = 1;
   }
   if (rc == DGFAS_OK) {
     if (cudaMalloc(&c->patch, patch) != cudaSuccess) { set_error("patch buffer"); rc = DGFAS_ERR_OOM; }
@@ -619,6 +632,7 @@ static int down_up(Ctx& c, double* uL, const double* fL) {
     RET(launch_project(c, l, ul));                                   // u_{l-1} = P u_l
     RET(launch_restrict(c, l, c.lv[l].r, c.lv[l - 1].t));           // R r_l
     RET(launch_apply(c, l - 1, DGFAS_FP64, c.lv[l - 1].u, c.lv[l - 1].t, c.lv[l - 1].gv, 1.0));
+    if (c.lv[l - 1].has_leaf) RET(launch_leaf_rhs(c, l - 1, c.lv[l - 1].fl, c.lv[l - 1].gv));
   }
   RET(launch_root(c));
   for (int l = 1; l <= L; ++l) {
@@ -707,6 +721,31 @@ static int run_body(Ctx& c, int kind, double* u, const double* f) {
   return rc;
 }
 
+// r_2 of Sec. 6.1: Euclidean norm of the residual over the leaf elements of
+// all levels (synchronizes).  The top level's residual goes to lv[L].r.
+static int composite_norm(Ctx& c, double* u, const double* f, double* out) {
+  const int L = (int)c.lv.size() - 1;
+  double s = 0.0;
+  // the composite solution: twigs take the projection of the finer level
+  // (top down, Eq. (6b)); frozen elements keep their interpolated values
+  for (int l = L; l >= 1; --l) RET(launch_project(c, l, l == L ? u : c.lv[l].u));
+  for (int l = 0; l <= L; ++l) {
+    LevelHost& H = c.lv[l];
+    if (!H.has_leaf) continue;
+    const double* ul = l == L ? u : H.u;
+    const double* gl = l == L ? f : H.fl;
+    double* r = l == L ? H.r : H.t;
+    RET(launch_apply(c, l, DGFAS_FP64, ul, gl, r, -1.0));
+    RET(launch_sumsq_leaf(c, l, r, c.red));
+    CK(cudaMemcpyAsync(c.red_host, c.red, g_red_blocks * sizeof(double), cudaMemcpyDeviceToHost,
+                       c.stream));
+    CK(cudaStreamSynchronize(c.stream));
+    for (int i = 0; i < g_red_blocks; ++i) s += c.red_host[i];
+  }
+  *out = std::sqrt(s);
+  return DGFAS_OK;
+}
+
 static double host_norm(Ctx& c) {
   double s = 0.0;
   for (int i = 0; i < g_red_blocks; ++i) s += c.red_host[i];
@@ -729,7 +768,38 @@ extern "C" int dgfas_node_coords(void* ctx, int level, double* xyz) {
 extern "C" int dgfas_assemble_rhs(void* ctx, const double* f, const double* uD, double* b) {
   Ctx* c = (Ctx*)ctx;
   if (!c || !f || !b) return DGFAS_ERR_INVALID;
-  return launch_rhs(*c, f, uD, b);
+  return launch_rhs(*c, (int)c->lv.size() - 1, f, uD, b);
+}
+
+extern "C" int dgfas_assemble_rhs_level(void* ctx, int level, const double* f, const double* uD,
+                                        double* b) {
+  Ctx* c = (Ctx*)ctx;
+  if (!c || !f || !b || level < 0 || level >= (int)c->lv.size()) return DGFAS_ERR_INVALID;
+  return launch_rhs(*c, level, f, uD, b);
+}
+
+extern "C" int dgfas_set_level_rhs(void* ctx, int level, const double* f) {
+  Ctx* c = (Ctx*)ctx;
+  if (!c || !f || level < 0 || level >= (int)c->lv.size() - 1) return DGFAS_ERR_INVALID;
+  LevelHost& H = c->lv[level];
+  if (!H.fl) return DGFAS_OK;   // no leaf elements on this level: nothing to keep
+  CK(cudaMemcpyAsync(H.fl, f, H.ndof * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+  return DGFAS_OK;
+}
+
+extern "C" int dgfas_composite_residual(void* ctx, double* u_top, const double* f_top,
+                                        double* out) {
+  Ctx* c = (Ctx*)ctx;
+  if (!c || !u_top || !f_top || !out) return DGFAS_ERR_INVALID;
+  return composite_norm(*c, u_top, f_top, out);
+}
+
+extern "C" int dgfas_get_level_solution(void* ctx, int level, double* u) {
+  Ctx* c = (Ctx*)ctx;
+  if (!c || !u || level < 0 || level >= (int)c->lv.size() - 1) return DGFAS_ERR_INVALID;
+  CK(cudaMemcpyAsync(u, c->lv[level].u, c->lv[level].ndof * sizeof(double),
+                     cudaMemcpyDeviceToDevice, c->stream));
+  return DGFAS_OK;
 }
 
 extern "C" int dgfas_apply_op(void* ctx, int level, const double* u, const double* g, double* out) {
@@ -779,8 +849,12 @@ extern "C" int dgfas_solve(void* ctx, double* u, const double* f, double rtol, i
   const int L = (int)c->lv.size() - 1;
   auto t0 = std::chrono::steady_clock::now();
   double r0;
-  RET(launch_apply(*c, L, DGFAS_FP64, u, f, c->lv[L].r, -1.0));
-  RET(norm_dev(*c, c->lv[L].r, c->lv[L].ndof, &r0));
+  if (c->local) {
+    RET(composite_norm(*c, u, f, &r0));
+  } else {
+    RET(launch_apply(*c, L, DGFAS_FP64, u, f, c->lv[L].r, -1.0));
+    RET(norm_dev(*c, c->lv[L].r, c->lv[L].ndof, &r0));
+  }
   RET(smooth(*c, L, u, f, c->prm.s1, true, false));
   RET(launch_apply(*c, L, DGFAS_FP64, u, f, c->lv[L].r, -1.0));
   int cycles = 0, rc = DGFAS_ERR_NOT_CONVERGED;
@@ -789,10 +863,15 @@ extern "C" int dgfas_solve(void* ctx, double* u, const double* f, double rtol, i
   if (!(r0 > 0)) rc = (r0 == 0) ? DGFAS_OK : DGFAS_ERR_DIVERGED;
   while (rc == DGFAS_ERR_NOT_CONVERGED && cycles < max_cycles && L > 0) {
     RET(run_body(*c, 1, u, f));
-    CK(cudaMemcpyAsync(c->red_host, c->red, g_red_blocks * sizeof(double), cudaMemcpyDeviceToHost,
-                       c->stream));
-    CK(cudaStreamSynchronize(c->stream));
-    r = host_norm(*c);
+    if (c->local) {
+      RET(composite_norm(*c, u, f, &r));
+      // the next cycle starts from the top residual (composite_norm left it in lv[L].r)
+    } else {
+      CK(cudaMemcpyAsync(c->red_host, c->red, g_red_blocks * sizeof(double),
+                         cudaMemcpyDeviceToHost, c->stream));
+      CK(cudaStreamSynchronize(c->stream));
+      r = host_norm(*c);
+    }
     if (info && cycles < 128) info->history[cycles] = r;
     ++cycles;
     if (!std::isfinite(r) || r > 1e3 * r0) rc = DGFAS_ERR_DIVERGED;
@@ -857,13 +936,13 @@ extern "C" const char* dgfas_last_error(void) { return g_err.c_str(); }
 // subdomain width n, S [n][n] (row = node, column = mode), lambda [n], W [n].
 extern "C" int dgfas_host_fd_variant(int p, double delta, double mu_star, int variant, double* S,
                                      double* lam, double* W, int* n_out) {
-  if (p < 1 || p > 10 || variant < 0 || variant > 8 || !S || !lam || !W || !n_out ||
+  if (p < 1 || p > 10 || variant < 0 || variant > 15 || !S || !lam || !W || !n_out ||
       !(delta > 0 && delta < 0.5))
     return DGFAS_ERR_INVALID;
   const int m = host::overlap_layers(p, delta);
-  const char sc[3] = {'i', 'd', 'n'};
+  const char sc[4] = {'i', 'd', 'n', 'f'};
   std::vector<double> Sv, lv, wv;
-  host::fd_variant(p, m, mu_star, delta, sc[variant / 3], sc[variant % 3], Sv, lv, wv);
+  host::fd_variant(p, m, mu_star, delta, sc[variant / 4], sc[variant % 4], Sv, lv, wv);
   const int n = (int)lv.size();
   *n_out = n;
   for (int i = 0; i < n * n; ++i) S[i] = Sv[i];

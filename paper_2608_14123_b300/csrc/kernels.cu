@@ -404,9 +404,10 @@ int launch_apply_corr(Ctx& c, int l, int prec, const void* delta, const double* 
 // residual patch R_s r (zero outside the mesh and on frozen elements), applies
 // (S3 x S2 x S1) D^-1 (S3^T x S2^T x S1^T), multiplies by W and writes the
 // weighted correction patch to `patch` [ne][NS^3] (row stride NS).
+// Side types per direction: 0 interior, 1 Dirichlet, 2 Neumann, 3 interior
+// face with a frozen neighbour (no overlap layers); variant v = 4 left + right.
 __device__ __forceinline__ void side_map(int v, int a, int N, int m, int& off, int& idx) {
-  // v: 0..8 = ii,id,in,di,dd,dn,ni,nd,nn ; left interior iff v < 3
-  const int left_i = v < 3;
+  const int left_i = (v >> 2) == 0;
   if (left_i) {
     if (a < m) { off = -1; idx = N - m + a; return; }
     a -= m;
@@ -417,7 +418,7 @@ __device__ __forceinline__ void side_map(int v, int a, int N, int m, int& off, i
 }
 
 __host__ __device__ __forceinline__ int var_size(int v, int N, int m) {
-  const int li = v < 3, ri = (v % 3) == 0;
+  const int li = (v >> 2) == 0, ri = (v & 3) == 0;
   return N + m * (li + ri);
 }
 
@@ -638,8 +639,12 @@ __global__ void k_combine(const LevelView<T> L, const T* __restrict__ patch,
     int src = L.nbr27[27 * e + threadIdx.x];
     if (src >= 0 && L.cls[src] == DGFAS_FROZEN) src = -1;
     s_nb[threadIdx.x] = src;
-    for (int d = 0; d < 3; ++d)
-      s_ml[threadIdx.x][d] = (src >= 0 && L.var[3 * src + d] < 3) ? (unsigned char)m : 0;
+    for (int d = 0; d < 3; ++d) {
+      const int v = src >= 0 ? L.var[3 * src + d] : 0;
+      // bit 0..1: left-layer count flag, bit 2: left side interior, bit 3: right side interior
+      s_ml[threadIdx.x][d] = (unsigned char)(((v >> 2) == 0 ? m : 0) | (((v >> 2) == 0) << 6) |
+                                             (((v & 3) == 0) << 7));
+    }
   }
   __syncthreads();
   const size_t eo = (size_t)e * N3;
@@ -659,9 +664,15 @@ __global__ void k_combine(const LevelView<T> L, const T* __restrict__ patch,
           const int slot = (ox + 1) + 3 * (oy + 1) + 9 * (oz + 1);
           const int src = s_nb[slot];
           if (src < 0) continue;
-          const int px = ox == 0 ? i + s_ml[slot][0] : (ox < 0 ? s_ml[slot][0] + N + i : i - (N - m));
-          const int py = oy == 0 ? j + s_ml[slot][1] : (oy < 0 ? s_ml[slot][1] + N + j : j - (N - m));
-          const int pz = oz == 0 ? k + s_ml[slot][2] : (oz < 0 ? s_ml[slot][2] + N + k : k - (N - m));
+          const int fx = s_ml[slot][0], fy = s_ml[slot][1], fz = s_ml[slot][2];
+          // the neighbour's patch reaches this element only through interior sides
+          if ((ox < 0 && !(fx & 128)) || (ox > 0 && !(fx & 64)) || (oy < 0 && !(fy & 128)) ||
+              (oy > 0 && !(fy & 64)) || (oz < 0 && !(fz & 128)) || (oz > 0 && !(fz & 64)))
+            continue;
+          const int mx = fx & 63, my = fy & 63, mz = fz & 63;
+          const int px = ox == 0 ? i + mx : (ox < 0 ? mx + N + i : i - (N - m));
+          const int py = oy == 0 ? j + my : (oy < 0 ? my + N + j : j - (N - m));
+          const int pz = oz == 0 ? k + mz : (oz < 0 ? mz + N + k : k - (N - m));
           s += patch[(size_t)src * NS3 + ((size_t)pz * nsm + py) * nsm + px];
         }
     if (ADD) u[eo + n] += (TO)s;
@@ -874,6 +885,47 @@ __global__ void k_partial(const double* __restrict__ a, const double* __restrict
   if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
 }
 
+// partial sums of v^2 over the nodes of leaf elements only (composite residual)
+__global__ void k_partial_leaf(const double* __restrict__ v, const signed char* __restrict__ cls,
+                               int N3, long long n, double* __restrict__ part) {
+  __shared__ double sh[256];
+  double s = 0.0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    if (cls[i / N3] == DGFAS_LEAF) s += v[i] * v[i];
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+}
+
+int launch_sumsq_leaf(Ctx& c, int l, const double* v, double* part) {
+  LevelHost& H = c.lv[l];
+  k_partial_leaf<<<g_red_blocks, 256, 0, c.stream>>>(v, H.d_cls, H.N * H.N * H.N, H.ndof, part);
+  ++g_kernels;
+  CK(cudaGetLastError());
+  return DGFAS_OK;
+}
+
+// g = f on the nodes of leaf elements (the leaves keep the original RHS, Eq. (4c))
+__global__ void k_leaf_rhs(const double* __restrict__ f, const signed char* __restrict__ cls,
+                           int N3, long long n, double* __restrict__ g) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n && cls[i / N3] == DGFAS_LEAF) g[i] = f[i];
+}
+
+int launch_leaf_rhs(Ctx& c, int l, const double* f, double* g) {
+  LevelHost& H = c.lv[l];
+  k_leaf_rhs<<<(unsigned)((H.ndof + 255) / 256), 256, 0, c.stream>>>(f, H.d_cls, H.N * H.N * H.N,
+                                                                      H.ndof, g);
+  ++g_kernels;
+  CK(cudaGetLastError());
+  return DGFAS_OK;
+}
+
 int launch_sumsq(Ctx& c, const double* v, long long n, double* part) {
   k_partial<false><<<g_red_blocks, 256, 0, c.stream>>>(v, nullptr, n, part);
   ++g_kernels;
@@ -1023,8 +1075,8 @@ __global__ void k_rhs(const LevelView<double> L, const double* __restrict__ f,
 }
 
 template <int N>
-static int rhs_N(Ctx& c, const double* f, const double* uD, double* b) {
-  LevelHost& H = c.lv.back();
+static int rhs_N(Ctx& c, int l, const double* f, const double* uD, double* b) {
+  LevelHost& H = c.lv[l];
   if (H.box) k_rhs<N, true><<<H.ne, N * N, 0, c.stream>>>(H.v64, f, uD, b);
   else k_rhs<N, false><<<H.ne, N * N, 0, c.stream>>>(H.v64, f, uD, b);
   ++g_kernels;
@@ -1032,18 +1084,18 @@ static int rhs_N(Ctx& c, const double* f, const double* uD, double* b) {
   return DGFAS_OK;
 }
 
-int launch_rhs(Ctx& c, const double* f, const double* uD, double* b) {
-  switch (c.lv.back().N) {
-    case 2: return rhs_N<2>(c, f, uD, b);
-    case 3: return rhs_N<3>(c, f, uD, b);
-    case 4: return rhs_N<4>(c, f, uD, b);
-    case 5: return rhs_N<5>(c, f, uD, b);
-    case 6: return rhs_N<6>(c, f, uD, b);
-    case 7: return rhs_N<7>(c, f, uD, b);
-    case 8: return rhs_N<8>(c, f, uD, b);
-    case 9: return rhs_N<9>(c, f, uD, b);
-    case 10: return rhs_N<10>(c, f, uD, b);
-    case 11: return rhs_N<11>(c, f, uD, b);
+int launch_rhs(Ctx& c, int l, const double* f, const double* uD, double* b) {
+  switch (c.lv[l].N) {
+    case 2: return rhs_N<2>(c, l, f, uD, b);
+    case 3: return rhs_N<3>(c, l, f, uD, b);
+    case 4: return rhs_N<4>(c, l, f, uD, b);
+    case 5: return rhs_N<5>(c, l, f, uD, b);
+    case 6: return rhs_N<6>(c, l, f, uD, b);
+    case 7: return rhs_N<7>(c, l, f, uD, b);
+    case 8: return rhs_N<8>(c, l, f, uD, b);
+    case 9: return rhs_N<9>(c, l, f, uD, b);
+    case 10: return rhs_N<10>(c, l, f, uD, b);
+    case 11: return rhs_N<11>(c, l, f, uD, b);
   }
   return DGFAS_ERR_UNSUPPORTED;
 }

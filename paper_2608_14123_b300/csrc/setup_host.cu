@@ -233,7 +233,7 @@ void fd_variant(int p, int m, double mu_star, double delta, char left, char righ
   std::vector<double> D = diff_matrix(x);
   const double mu = mu_star * p * (p + 1) / 4.0;
   std::vector<double> L(n3 * n3, 0.0), mass(n3, 0.0);
-  bool cell[3] = {left == 'i', true, right == 'i'};
+  bool cell[3] = {left == 'i' || left == 'f', true, right == 'i' || right == 'f'};
   for (int c = 0; c < 3; ++c) {
     if (!cell[c]) continue;
     for (int i = 0; i < N; ++i) {

@@ -55,7 +55,9 @@ SYMBOLS = ["dgfas_setup_levels", "dgfas_destroy", "dgfas_level_ndof", "dgfas_nod
            "dgfas_assemble_rhs", "dgfas_apply_op", "dgfas_schwarz_smooth", "dgfas_fas_vcycle",
            "dgfas_solve", "dgfas_norm", "dgfas_set_surrogate", "dgfas_get_surrogate",
            "dgfas_use_graph", "dgfas_profile_sweep", "dgfas_fma_peak", "dgfas_schwarz_correct_static", "dgfas_kernel_launches", "dgfas_mlp_param_count",
-           "dgfas_mlp_forward", "dgfas_mlp_grad", "dgfas_mlp_train", "dgfas_learned_surrogate", "dgfas_host_fd_variant", "dgfas_strerror", "dgfas_last_error"]
+           "dgfas_mlp_forward", "dgfas_mlp_grad", "dgfas_mlp_train", "dgfas_learned_surrogate",
+           "dgfas_assemble_rhs_level", "dgfas_set_level_rhs", "dgfas_composite_residual",
+           "dgfas_get_level_solution", "dgfas_host_fd_variant", "dgfas_strerror", "dgfas_last_error"]
 
 _lib = None
 
@@ -94,6 +96,10 @@ def load():
         "dgfas_mlp_grad": (I, [P, P, P, I, P, P]),
         "dgfas_mlp_train": (I, [P, P, P, P, P, I, I, I, ctypes.c_float, ctypes.c_ulonglong, I, P, P]),
         "dgfas_learned_surrogate": (I, [P, I, P, D, ctypes.POINTER(I)]),
+        "dgfas_assemble_rhs_level": (I, [P, I, P, P, P]),
+        "dgfas_set_level_rhs": (I, [P, I, P]),
+        "dgfas_composite_residual": (I, [P, P, P, ctypes.POINTER(D)]),
+        "dgfas_get_level_solution": (I, [P, I, P]),
         "dgfas_strerror": (ctypes.c_char_p, [I]),
         "dgfas_last_error": (ctypes.c_char_p, []),
     }
@@ -236,6 +242,22 @@ class Solver:
         _check(load().dgfas_learned_surrogate(self.ctx, level % self.n_levels, _ptr(params),
                                               max_log_scaling, ctypes.byref(nf)), "learned_surrogate")
         return nf.value
+
+    def dgfas_assemble_rhs_level(self, level, f, uD, b):
+        _check(load().dgfas_assemble_rhs_level(self.ctx, level % self.n_levels, _ptr(f), _ptr(uD),
+                                               _ptr(b)), "assemble_rhs_level")
+
+    def dgfas_set_level_rhs(self, level, f):
+        _check(load().dgfas_set_level_rhs(self.ctx, level, _ptr(f)), "set_level_rhs")
+
+    def dgfas_composite_residual(self, u, f):
+        r = ctypes.c_double(0.0)
+        _check(load().dgfas_composite_residual(self.ctx, _ptr(u), _ptr(f), ctypes.byref(r)),
+               "composite_residual")
+        return r.value
+
+    def dgfas_get_level_solution(self, level, u):
+        _check(load().dgfas_get_level_solution(self.ctx, level, _ptr(u)), "get_level_solution")
 
     # ---- conveniences built from the calls above
     def node_coords(self, level=-1):

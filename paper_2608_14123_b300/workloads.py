@@ -269,3 +269,147 @@ def config(cid, small=False):
     ndof = top["corners"].shape[0] * N ** 3
     u0 = random_start(rng, ndof)
     return dict(levels=levels, rhs=rhs, u0=u0, params=prm, cid=cid)
+
+
+# ---------------------------------------------------------------- local refinement
+def front_spec(rng, alpha=50.0):
+    """Steep spherical front u = atan(alpha (|x - x0| - r0)): x0 = -U(0.05, 0.25)^3
+    (outside the domain), r0 uniform in the middle 60% between the nearest and
+    the farthest point of [0,1]^3 from x0."""
+    x0 = -rng.uniform(0.05, 0.25, size=3)
+    near = np.linalg.norm(x0)                   # nearest point is the origin corner
+    far = np.linalg.norm(1.0 - x0)
+    r0 = near + (far - near) * rng.uniform(0.2, 0.8)
+    return dict(kind="front", alpha=float(alpha), x0=x0, r0=float(r0))
+
+
+def _front_parts(spec, xyz):
+    d = xyz - spec["x0"]
+    rho = np.linalg.norm(d, axis=-1)
+    return rho, spec["alpha"] * (rho - spec["r0"])
+
+
+def eval_front_u(spec, xyz):
+    _, s = _front_parts(spec, xyz)
+    return np.arctan(s)
+
+
+def eval_front_f(spec, xyz):
+    """f = -lap u = -(u'' + 2 u' / rho) for u = atan(alpha (rho - r0))."""
+    rho, s = _front_parts(spec, xyz)
+    a = spec["alpha"]
+    up = a / (1.0 + s * s)
+    upp = -2.0 * a * a * s / (1.0 + s * s) ** 2
+    return -(upp + 2.0 * up / rho)
+
+
+def _cell_front_distance(spec, lo, h):
+    """Distance from the axis-aligned cells [lo, lo+h] to the sphere |x-x0| = r0."""
+    x0, r0 = spec["x0"], spec["r0"]
+    near = np.linalg.norm(np.clip(x0, lo, lo + h) - x0, axis=-1)
+    far = np.linalg.norm(np.maximum(np.abs(lo - x0), np.abs(lo + h - x0)), axis=-1)
+    return np.where(r0 < near, near - r0, np.where(r0 > far, r0 - far, 0.0))
+
+
+def refined_hierarchy(spec, n_base=8, p=3, n_ref=3, n_root=4, buffer=2.0):
+    """Multilevel mesh with local refinement towards the front (Sec. 3.1).
+
+    Levels: h-coarsened p=1 levels down to n_root^3 (root), the base n_base^3
+    at p=1 and at degree p (global), then n_ref refinement levels at degree p.
+    A cell of grid n (size h = 1/n) is marked for regular refinement when its
+    distance to the front is <= buffer * h; with buffer >= 2 every neighbour of
+    a marked cell lies in the active zone of its level, so marked cells are
+    nested and every frozen child has a leaf parent.  Level k+1 holds the
+    children of the marked cells of level k (active) and of their unmarked
+    face/edge/vertex neighbours (frozen).  Faces of frozen elements that leave
+    the level's zone are Neumann (-2); frozen rows are never evaluated.
+    """
+    levels = []
+    # global part: p=1 from n_root to n_base, then degree p on n_base
+    V = uniform_vertices(n_base)
+    glob = hierarchy(V, [p, 1], h_root=n_root)          # root first, ends at (n_base, p)
+    glob_shapes = [lv["shape"] for lv in glob]
+    assert glob_shapes[-1] == (n_base,) * 3
+    # cells (integer coordinates) per level from the base up
+    def mark(n, cells):
+        h = 1.0 / n
+        lo = cells * h
+        return _cell_front_distance(spec, lo, h) <= buffer * h
+
+    base_cells = glob[-1]["ijk"].astype(np.int64)
+    marked = mark(n_base, base_cells)
+    glob[-1]["cls"] = np.where(marked, TWIG, LEAF).astype(np.int8)
+    levels = glob
+    n = n_base
+    prev_cells, prev_marked = base_cells, marked
+    prev_index = {tuple(c): i for i, c in enumerate(base_cells)}
+    for k in range(n_ref):
+        n2 = 2 * n
+        mset = {tuple(c) for c in prev_cells[prev_marked]}
+        # unmarked neighbours of marked cells on the parent grid
+        nbrs = set()
+        for c in mset:
+            for oz in (-1, 0, 1):
+                for oy in (-1, 0, 1):
+                    for ox in (-1, 0, 1):
+                        q = (c[0] + ox, c[1] + oy, c[2] + oz)
+                        if q in mset or min(q) < 0 or max(q) >= n:
+                            continue
+                        nbrs.add(q)
+        assert all(q in prev_index for q in nbrs), "frozen parent outside the active zone"
+        children, cls_list, parent, octant = [], [], [], []
+        for group, cl in ((sorted(mset), None), (sorted(nbrs), FROZEN)):
+            for c in group:
+                for o in range(8):
+                    ox, oy, oz = o & 1, (o >> 1) & 1, (o >> 2) & 1
+                    children.append((2 * c[0] + ox, 2 * c[1] + oy, 2 * c[2] + oz))
+                    cls_list.append(cl)
+                    parent.append(prev_index[c])
+                    octant.append(o)
+        cells = np.array(children, dtype=np.int64)
+        ne = len(cells)
+        index = {tuple(c): i for i, c in enumerate(cells)}
+        last = k == n_ref - 1
+        m2 = np.zeros(ne, bool) if last else mark(n2, cells)
+        cls = np.array([FROZEN if cl == FROZEN else (TWIG if m2[i] else LEAF)
+                        for i, cl in enumerate(cls_list)], dtype=np.int8)
+        m2 &= cls != FROZEN
+        h2 = 1.0 / n2
+        corners = np.zeros((ne, 8, 3))
+        for cc in range(8):
+            off = np.array([cc & 1, (cc >> 1) & 1, (cc >> 2) & 1])
+            corners[:, cc, :] = (cells + off) * h2
+        nbr = np.zeros((ne, 6), np.int32)
+        for f, (ox, oy, oz) in enumerate(_FACE_OFF):
+            for i, c in enumerate(cells):
+                q = (c[0] + ox, c[1] + oy, c[2] + oz)
+                if min(q) < 0 or max(q) >= n2:
+                    nbr[i, f] = -1
+                else:
+                    nbr[i, f] = index.get(q, -2)
+        nbr27 = np.full((ne, 27), -1, np.int32)
+        for oz in (-1, 0, 1):
+            for oy in (-1, 0, 1):
+                for ox in (-1, 0, 1):
+                    s = (ox + 1) + 3 * (oy + 1) + 9 * (oz + 1)
+                    for i, c in enumerate(cells):
+                        nbr27[i, s] = index.get((c[0] + ox, c[1] + oy, c[2] + oz), -1)
+        levels.append(dict(p=int(p), shape=(n2, n2, n2), corners=corners, nbr=nbr, nbr27=nbr27,
+                           parent=np.array(parent, np.int32), octant=np.array(octant, np.int32),
+                           cls=cls, ijk=cells.astype(np.int32)))
+        n, prev_cells, prev_marked, prev_index = n2, cells, m2, index
+    return levels
+
+
+def config4(small=False):
+    """Config 4: steep front (alpha = 50) on [0,1]^3, base 8^3 at p = 3 with up
+    to 3 levels of local refinement towards the front (p = 3 on every level)."""
+    rng = np.random.default_rng(SEED_BASE + 4)
+    spec = front_spec(rng)
+    levels = refined_hierarchy(spec, n_base=4 if small else 8, n_ref=1 if small else 3,
+                               n_root=2 if small else 4)
+    top = levels[-1]
+    ndof = top["corners"].shape[0] * (top["p"] + 1) ** 3
+    u0 = random_start(rng, ndof)
+    return dict(levels=levels, rhs=spec, u0=u0, cid=4,
+                params=dict(mu_star=5.0, delta=0.08, s1=2, s2=2, sc=4))

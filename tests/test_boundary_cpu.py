@@ -43,7 +43,7 @@ def test_host_fd_tables_match_oracle(p, delta):
     mu = 5.0
     T = schwarz.FDTables(p, delta, mu)
     rng = np.random.default_rng(p)
-    for v, name in enumerate(schwarz.VARIANTS):
+    for v, name in enumerate(schwarz.VARIANTS16):
         S, lam, W = dgfas.dgfas_host_fd_variant(p, delta, mu, v)
         t = T.tab[name]
         assert S.shape == t["S"].shape
@@ -59,5 +59,7 @@ def test_host_fd_tables_match_oracle(p, delta):
 def test_host_fd_rejects_bad_arguments():
     with pytest.raises(dgfas.DgfasError):
         dgfas.dgfas_host_fd_variant(11, 0.08, 5.0, 0)
+    with pytest.raises(dgfas.DgfasError):
+        dgfas.dgfas_host_fd_variant(4, 0.08, 5.0, 16)
     with pytest.raises(dgfas.DgfasError):
         dgfas.dgfas_host_fd_variant(4, 0.6, 5.0, 0)
