@@ -639,6 +639,9 @@ static int down_up(Ctx& c, double* uL, const double* fL) {
     double* ul = l == L ? uL : c.lv[l].u;
     const double* gl = l == L ? fL : c.lv[l].gv;
     RET(launch_prolong(c, l, ul, prec, c.lv[l].delta));             // delta_l = I (u_{l-1} - ubar)
+    // the frozen update changed u^f, and with it the residual of the active rows:
+    // the smoothing that follows starts from the residual of the updated u
+    if (c.lv[l].has_frozen) RET(launch_apply(c, l, DGFAS_FP64, ul, gl, c.lv[l].r, -1.0));
     if (l < L) {
       // the post-smoothing starts from the residual of the pre-smoothed u_l,
       // which is still in lv[l].r (restriction only read it)
