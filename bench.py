@@ -165,6 +165,59 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
+# ------------------------------------------------------------------ other workloads
+def _solve_record(S, u, b, torch):
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    info = S.dgfas_solve(u, b, 1e-10, 40, raise_on_fail=False)
+    torch.cuda.synchronize()
+    return {"seconds": time.perf_counter() - t0, "cycles": info["cycles"],
+            "rel_residual": info["r_final"] / info["r0"], "code": info["code"]}
+
+
+def other_workloads(dgfas, torch):
+    """Time to 1e-10 on the locally refined front (config 4) and the large
+    curvilinear run (config 5), FP32 smoother vs FP64."""
+    out = {}
+    c4 = wl.config4()
+    pr = c4["params"]
+    leaf = sum(int(np.sum(lv["cls"] == 0)) * (lv["p"] + 1) ** 3 for lv in c4["levels"])
+    rec = {"leaf_dof": leaf, "levels": len(c4["levels"])}
+    for name, prec in (("mixed_fp32", dgfas.DGFAS_FP32), ("fp64", dgfas.DGFAS_FP64)):
+        S = dgfas.Solver(c4["levels"], pr["mu_star"], pr["delta"], pr["s1"], pr["s2"], pr["sc"],
+                         precision=prec)
+        L = S.n_levels - 1
+        for l in range(S.n_levels):
+            xyz = S.node_coords(l).cpu().numpy()
+            fn = torch.from_numpy(wl.eval_front_f(c4["rhs"], xyz)).cuda()
+            un = torch.from_numpy(wl.eval_front_u(c4["rhs"], xyz)).cuda()
+            b = torch.empty_like(fn)
+            S.dgfas_assemble_rhs_level(l, fn, un, b)
+            if l < L:
+                S.dgfas_set_level_rhs(l, b)
+        rec[name] = _solve_record(S, torch.from_numpy(c4["u0"]).cuda(), b, torch)
+        S.close()
+    out["config4_front_local_refinement_p3"] = rec
+    c5 = wl.config(5)
+    pr = c5["params"]
+    rec = {"dof": int(c5["u0"].size), "smoother": "SCG (Alg. 6)"}
+    for name, prec in (("mixed_fp32", dgfas.DGFAS_FP32), ("fp64", dgfas.DGFAS_FP64)):
+        S = dgfas.Solver(c5["levels"], pr["mu_star"], pr["delta"], pr["s1"], pr["s2"], pr["sc"],
+                         precision=prec, smoother=dgfas.DGFAS_SCG)
+        xyz = S.node_coords(-1)
+        f = torch.from_numpy(wl.eval_f(c5["rhs"], xyz.cpu().numpy())).cuda()
+        del xyz
+        b = torch.empty_like(f)
+        S.dgfas_assemble_rhs(f, None, b)
+        del f
+        rec[name] = _solve_record(S, torch.from_numpy(c5["u0"]).cuda(), b, torch)
+        S.close()
+        del b
+        torch.cuda.empty_cache()
+    out["config5_curvilinear64_p7"] = rec
+    return out
+
+
 # ------------------------------------------------------------------ GPU arm
 def run_gpu(args):
     import torch
@@ -292,6 +345,11 @@ def run_gpu(args):
         if S2 is not S:
             S2.close()
 
+    # ---- the other workloads: time to 1e-10 (mixed vs FP64), one solve each
+    others = {}
+    if not args.skip_others:
+        others = other_workloads(dgfas, torch)
+
     # ---- CPU baseline (rank 0, N = 1 only)
     cpu = None
     if rank == 0 and ws == 1 and not args.skip_cpu:
@@ -320,6 +378,7 @@ def run_gpu(args):
             "peaks": {"fp64_tflops": fp64_tf, "fp32_tflops": fp32_tf, "hbm_gbs": pk["hbm"],
                       "hbm_source": pk["src"]},
             "time_to_1e-10": tts,
+            "other_workloads": others,
             "e2e": e2e,
             "cpu_baseline": cpu,
             "clocks": clocks,
@@ -339,6 +398,7 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--skip-others", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
