@@ -232,6 +232,13 @@ int dgfas_mlp_train(float* params, float* m, float* v, const float* X, const flo
 int dgfas_learned_surrogate(void* ctx, int level, const float* params, double max_log_scaling,
                             int* n_fallback);
 
+/* Self-test of the tensor-core path (tcgen05.mma kind::f16, BF16 operands,
+   FP32 accumulation in TMEM): one CTA computes D[128][16] = A B^T with
+   A[r][k] = (r + 2k) % 7 - 3 and B[n][k] = (3n + k) % 5 - 2 (exact in BF16 and
+   FP32) into out_host [128*16]; *timeout_host = 1 if the completion wait ran
+   out (the kernel never waits unboundedly). */
+int dgfas_tc_selftest(float* out_host, int* timeout_host);
+
 /* Number of kernels the library has launched in this process (including the
    kernel nodes of replayed CUDA graphs). */
 long long dgfas_kernel_launches(void);

@@ -57,7 +57,7 @@ SYMBOLS = ["dgfas_setup_levels", "dgfas_destroy", "dgfas_level_ndof", "dgfas_nod
            "dgfas_use_graph", "dgfas_profile_sweep", "dgfas_fma_peak", "dgfas_schwarz_correct_static", "dgfas_kernel_launches", "dgfas_mlp_param_count",
            "dgfas_mlp_forward", "dgfas_mlp_grad", "dgfas_mlp_train", "dgfas_learned_surrogate",
            "dgfas_assemble_rhs_level", "dgfas_set_level_rhs", "dgfas_composite_residual",
-           "dgfas_get_level_solution", "dgfas_host_fd_variant", "dgfas_strerror", "dgfas_last_error"]
+           "dgfas_get_level_solution", "dgfas_tc_selftest", "dgfas_host_fd_variant", "dgfas_strerror", "dgfas_last_error"]
 
 _lib = None
 
@@ -100,6 +100,7 @@ def load():
         "dgfas_set_level_rhs": (I, [P, I, P]),
         "dgfas_composite_residual": (I, [P, P, P, ctypes.POINTER(D)]),
         "dgfas_get_level_solution": (I, [P, I, P]),
+        "dgfas_tc_selftest": (I, [P, ctypes.POINTER(I)]),
         "dgfas_strerror": (ctypes.c_char_p, [I]),
         "dgfas_last_error": (ctypes.c_char_p, []),
     }
@@ -290,3 +291,12 @@ def dgfas_fma_peak():
 def dgfas_kernel_launches():
     """Kernels launched by the library so far in this process (graph nodes included)."""
     return int(load().dgfas_kernel_launches())
+
+
+def dgfas_tc_selftest():
+    """Runs the tcgen05 self-test; returns (D [128, 16], timed_out)."""
+    out = np.zeros(128 * 16, dtype=np.float32)
+    to = ctypes.c_int(0)
+    _check(load().dgfas_tc_selftest(out.ctypes.data_as(ctypes.c_void_p), ctypes.byref(to)),
+           "tc_selftest")
+    return out.reshape(128, 16), bool(to.value)
