@@ -47,6 +47,9 @@ extern "C" {
    root solve are always FP64) */
 #define DGFAS_FP64 0
 #define DGFAS_FP32 1
+#define DGFAS_BF16 2   /* FP32 smoother residual and combine; FD mode products on
+                          the tensor cores (BF16 operands, FP32 accumulation, FP32
+                          scaling by the inverse eigenvalue sums) */
 
 /* smoother (Sec. 4.3): weighted additive Schwarz (Alg. 5) or Schwarz-
    preconditioned inexact CG (Alg. 6) */
@@ -83,7 +86,7 @@ typedef struct {
   double mu_star;            /* penalty scaling mu_* > 1 (Sec. 2.2) */
   double delta;              /* Schwarz overlap 0 < delta < 0.5 (Sec. 4.3.1) */
   int s1, s2, sc;            /* pre-, post-, crossover smoothing steps */
-  int precision;             /* DGFAS_FP64 or DGFAS_FP32 smoother */
+  int precision;             /* DGFAS_FP64, DGFAS_FP32 or DGFAS_BF16 smoother */
   int smoother;              /* DGFAS_WAS or DGFAS_SCG */
   int max_cycles;            /* default cap for dgfas_solve when <= 0 is passed */
 } dgfas_params;
@@ -231,6 +234,11 @@ int dgfas_mlp_train(float* params, float* m, float* v, const float* X, const flo
    their geometric coefficients; their count goes to *n_fallback (host). */
 int dgfas_learned_surrogate(void* ctx, int level, const float* params, double max_log_scaling,
                             int* n_fallback);
+
+/* 1 if a completion wait of the tensor-core FD kernel ran out since setup
+   (its bounded waits never hang; a timed-out sweep leaves an invalid patch),
+   0 otherwise, or a negative code. */
+int dgfas_tc_error(void* ctx);
 
 /* Self-test of the tensor-core path (tcgen05.mma kind::f16, BF16 operands,
    FP32 accumulation in TMEM): one CTA computes D[128][16] = A B^T with

@@ -95,6 +95,7 @@ struct Ctx {
   double* red_host = nullptr;   // pinned
   double* scg_buf = nullptr;    // SCG vectors (p, q, z, r0) for the largest level
   double* dscal = nullptr;      // device scalars of the SCG recurrences
+  int* tc_err = nullptr;        // set by the tensor-core FD kernel when a wait ran out
   double* Ainv = nullptr;       // root inverse
   int n_root = 0;
   // graphs
@@ -113,6 +114,7 @@ int launch_apply(Ctx& c, int l, int prec, const double* u, const double* b, void
 int launch_apply_corr(Ctx& c, int l, int prec, const void* delta, const double* b, void* out,
                       int out_fp64);
 int launch_fd(Ctx& c, int l, int prec, const void* r);
+int launch_fd_tc(Ctx& c, int l, const float* r);
 int launch_combine(Ctx& c, int l, int prec, void* delta);
 int launch_add_delta(Ctx& c, long long n, int prec, const void* d, double* u);
 int launch_combine_to(Ctx& c, int l, int prec, double* z);

@@ -403,7 +403,7 @@ extern "C" void dgfas_destroy(void* vctx) {
   if (c->ev_in) cudaEventDestroy(c->ev_in);
   if (c->ev_out) cudaEventDestroy(c->ev_out);
   for (auto& H : c->lv) free_level(H);
-  void* ptrs[] = {c->patch, c->rw, c->red, c->scg_buf, c->dscal, c->Ainv};
+  void* ptrs[] = {c->patch, c->rw, c->red, c->scg_buf, c->dscal, c->Ainv, c->tc_err};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->red_host) cudaFreeHost(c->red_host);
@@ -421,7 +421,8 @@ extern "C" int dgfas_setup_levels(const dgfas_mesh* mesh, const dgfas_params* pr
     set_error("setup: parameter out of range");
     return DGFAS_ERR_INVALID;
   }
-  if (prm->precision != DGFAS_FP64 && prm->precision != DGFAS_FP32) {
+  if (prm->precision != DGFAS_FP64 && prm->precision != DGFAS_FP32 &&
+      prm->precision != DGFAS_BF16) {
     set_error("setup: unknown precision");
     return DGFAS_ERR_INVALID;
   }
@@ -484,6 +485,13 @@ extern "C" int dgfas_setup_levels(const dgfas_mesh* mesh, const dgfas_params* pr
   }
   if (rc == DGFAS_OK && prm->smoother == DGFAS_SCG) rc = dalloc(&c->scg_buf, 5 * maxdof);
   if (rc == DGFAS_OK) rc = dalloc(&c->dscal, 64);
+  if (rc == DGFAS_OK) {
+    if (cudaMalloc((void**)&c->tc_err, sizeof(int)) != cudaSuccess ||
+        cudaMemset(c->tc_err, 0, sizeof(int)) != cudaSuccess) {
+      set_error("error flag");
+      rc = DGFAS_ERR_OOM;
+    }
+  }
   if (rc == DGFAS_OK) rc = build_root(*c);
   if (rc != DGFAS_OK) {
     dgfas_destroy(c);
@@ -887,6 +895,16 @@ extern "C" int dgfas_solve(void* ctx, double* u, const double* f, double rtol, i
     info->seconds = std::chrono::duration<double>(t1 - t0).count();
   }
   return rc;
+}
+
+// 1 if a tensor-core FD wait ran out since setup (then the patch is not valid)
+extern "C" int dgfas_tc_error(void* ctx) {
+  Ctx* c = (Ctx*)ctx;
+  if (!c) return DGFAS_ERR_INVALID;
+  int h = 0;
+  if (cudaMemcpy(&h, c->tc_err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return DGFAS_ERR_CUDA;
+  return h;
 }
 
 extern "C" int dgfas_set_surrogate(void* ctx, int level, const double* g) {

@@ -18,6 +18,7 @@
 #include <cuda_bf16.h>
 
 #include <atomic>
+#include <algorithm>
 #include <cstdint>
 
 #include "dgfas_internal.h"
@@ -184,5 +185,203 @@ extern "C" int dgfas_tc_selftest(float* out_host, int* timeout_host) {
   CK(cudaMemcpy(timeout_host, f, sizeof(int), cudaMemcpyDeviceToHost));
   cudaFree(d);
   cudaFree(f);
+  return DGFAS_OK;
+}
+
+// ---------------------------------------------------------------- FD on tensor cores
+struct FdTcSmem {
+  unsigned char A[2][2][128 * 16 * 2];   // ping-pong A operand, two M = 128 tiles each
+  unsigned char B[6][16 * 16 * 2];       // per direction: S^T (n = out, k = in) and S
+  float lam[3][16], W[3][16];
+  uint64_t mbar;
+  uint32_t tslot;
+};
+
+__device__ __forceinline__ void put_bf16(unsigned char* tile2, int row, int k, float v) {
+  // row in [0, 256): tile row / 128
+  *reinterpret_cast<__nv_bfloat16*>(tile2 + (row >> 7) * (128 * 16 * 2) + tile_off(row & 127, k)) =
+      __float2bfloat16(v);
+}
+
+// one mode product: D = A B^T for both M tiles; returns false on a timed-out wait
+__device__ __forceinline__ bool tc_step(FdTcSmem& s, int ain, int bsel, uint32_t tmem,
+                                        uint32_t& phase) {
+  fence_async_smem();
+  fence_before();
+  __syncthreads();
+  fence_after();
+  if (threadIdx.x == 0) {
+    const uint32_t idesc = idesc_bf16(128, 16);
+    const uint64_t bd = sdesc(smem_u32(s.B[bsel]), 128, 256);
+    mma_bf16(tmem, sdesc(smem_u32(s.A[ain][0]), 128, 256), bd, idesc, 0);
+    mma_bf16(tmem + 16, sdesc(smem_u32(s.A[ain][1]), 128, 256), bd, idesc, 0);
+    commit(smem_u32(&s.mbar));
+  }
+  const bool ok = mbar_wait(smem_u32(&s.mbar), phase);
+  phase ^= 1u;
+  fence_after();
+  return __syncthreads_and(ok ? 1 : 0) != 0;
+}
+
+// rows of this thread after a step: tile 0 row 32 w + lane and tile 1 row 128 + 32 w + lane
+__device__ __forceinline__ void tc_read(uint32_t tmem, float* v0, float* v1) {
+  const int warp = threadIdx.x >> 5;
+  const uint32_t base = tmem + ((uint32_t)(32 * warp) << 16);
+  tmem_ld16(base, v0);
+  tmem_ld16(base + 16, v1);
+}
+
+__global__ void __launch_bounds__(128) k_fd_tc(const LevelView<float> L, const float* __restrict__ r,
+                                               float* __restrict__ patch, int* __restrict__ err) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  FdTcSmem& s = *reinterpret_cast<FdTcSmem*>(smem_raw);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int N = L.N, m = L.m, nsm = L.nsm, N3 = N * N * N;
+  const size_t NS3 = (size_t)nsm * nsm * nsm;
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 32;" ::"r"(smem_u32(&s.tslot)));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    mbar_init(smem_u32(&s.mbar), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = s.tslot;
+  uint32_t phase = 0;
+  bool alive = true;
+  for (int e = blockIdx.x; e < L.ne && alive; e += gridDim.x) {
+    if (L.cls[e] == DGFAS_FROZEN) continue;
+    __syncthreads();   // the previous element's patch store has read s.W
+    const int v1 = L.var[3 * e], v2 = L.var[3 * e + 1], v3 = L.var[3 * e + 2];
+    const int vv[3] = {v1, v2, v3};
+    const int n1 = N + m * (((v1 >> 2) == 0) + ((v1 & 3) == 0));
+    const int n2 = N + m * (((v2 >> 2) == 0) + ((v2 & 3) == 0));
+    const int n3 = N + m * (((v3 >> 2) == 0) + ((v3 & 3) == 0));
+    const int nn[3] = {n1, n2, n3};
+    // B operands: B[2d] = S_d^T as (n = out index, k = in index) -> entry S[k][n];
+    // B[2d+1] = S_d -> entry S[n][k]; zero padded to 16 x 16
+    for (int t = tid; t < 3 * 256; t += 128) {
+      const int d = t / 256, n = (t / 16) % 16, k = t % 16;
+      const int v = vv[d], nd = nn[d];
+      const float* S = L.S + (size_t)v * nsm * nsm;
+      const bool in = n < nd && k < nd;
+      const float st = in ? S[k * nsm + n] : 0.0f;
+      const float sn = in ? S[n * nsm + k] : 0.0f;
+      *reinterpret_cast<__nv_bfloat16*>(s.B[2 * d] + tile_off(n, k)) = __float2bfloat16(st);
+      *reinterpret_cast<__nv_bfloat16*>(s.B[2 * d + 1] + tile_off(n, k)) = __float2bfloat16(sn);
+    }
+    if (tid < 48) {
+      const int d = tid / 16, q = tid % 16;
+      const bool in = q < nn[d];
+      s.lam[d][q] = in ? L.lam[vv[d] * nsm + q] : 1.0f;
+      s.W[d][q] = in ? L.W[vv[d] * nsm + q] : 0.0f;
+    }
+    // gather R_s r into A[0]: rows (c, b) = 16 c + b, K = a
+    for (int t = tid; t < 4096; t += 128) {
+      const int a = t & 15, b = (t >> 4) & 15, c = t >> 8;
+      float val = 0.0f;
+      if (a < n1 && b < n2 && c < n3) {
+        // side maps (left interior iff side type 0)
+        int ox, ix, oy, iy, oz, iz, aa = a, bq = b, cq = c;
+        if ((v1 >> 2) == 0) { if (aa < m) { ox = -1; ix = N - m + aa; } else { aa -= m; ox = aa < N ? 0 : 1; ix = aa < N ? aa : aa - N; } }
+        else { ox = aa < N ? 0 : 1; ix = aa < N ? aa : aa - N; }
+        if ((v2 >> 2) == 0) { if (bq < m) { oy = -1; iy = N - m + bq; } else { bq -= m; oy = bq < N ? 0 : 1; iy = bq < N ? bq : bq - N; } }
+        else { oy = bq < N ? 0 : 1; iy = bq < N ? bq : bq - N; }
+        if ((v3 >> 2) == 0) { if (cq < m) { oz = -1; iz = N - m + cq; } else { cq -= m; oz = cq < N ? 0 : 1; iz = cq < N ? cq : cq - N; } }
+        else { oz = cq < N ? 0 : 1; iz = cq < N ? cq : cq - N; }
+        const int src = L.nbr27[27 * e + (ox + 1) + 3 * (oy + 1) + 9 * (oz + 1)];
+        if (src >= 0) val = r[(size_t)src * N3 + (iz * N + iy) * N + ix];
+      }
+      put_bf16(s.A[0][0], 16 * c + b, a, val);
+    }
+    const float g0 = L.g[4 * e], g1 = L.g[4 * e + 1], g2 = L.g[4 * e + 2], g3 = L.g[4 * e + 3];
+    float x0[16], x1[16];
+    const int r0 = 32 * warp + lane, r1 = 128 + r0;
+    // 1: S1^T along a: rows (c, b) -> (c, b) x a'; write rows (c, a'), K = b
+    if (!(alive = tc_step(s, 0, 0, tmem, phase))) break;
+    tc_read(tmem, x0, x1);
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      put_bf16(s.A[1][0], 16 * (r0 >> 4) + q, r0 & 15, x0[q]);
+      put_bf16(s.A[1][0], 16 * (r1 >> 4) + q, r1 & 15, x1[q]);
+    }
+    // 2: S2^T along b: rows (c, a') -> x b'; write rows (a', b'), K = c
+    if (!(alive = tc_step(s, 1, 2, tmem, phase))) break;
+    tc_read(tmem, x0, x1);
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      put_bf16(s.A[0][0], 16 * (r0 & 15) + q, r0 >> 4, x0[q]);
+      put_bf16(s.A[0][0], 16 * (r1 & 15) + q, r1 >> 4, x1[q]);
+    }
+    // 3: S3^T along c: rows (a', b') -> x c'; scale by D^-1 in FP32; same rows, K = c'
+    if (!(alive = tc_step(s, 0, 4, tmem, phase))) break;
+    tc_read(tmem, x0, x1);
+    {
+      const int a0 = r0 >> 4, b0 = r0 & 15, a1 = r1 >> 4, b1 = r1 & 15;
+      const float d0 = g0 + g1 * s.lam[0][a0] + g2 * s.lam[1][b0];
+      const float d1 = g0 + g1 * s.lam[0][a1] + g2 * s.lam[1][b1];
+#pragma unroll
+      for (int q = 0; q < 16; ++q) {
+        put_bf16(s.A[1][0], r0, q, x0[q] / (d0 + g3 * s.lam[2][q]));
+        put_bf16(s.A[1][0], r1, q, x1[q] / (d1 + g3 * s.lam[2][q]));
+      }
+    }
+    // 4: S3 along c: rows (a', b') -> x c''; write rows (c'', a'), K = b'
+    if (!(alive = tc_step(s, 1, 5, tmem, phase))) break;
+    tc_read(tmem, x0, x1);
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      put_bf16(s.A[0][0], 16 * q + (r0 >> 4), r0 & 15, x0[q]);
+      put_bf16(s.A[0][0], 16 * q + (r1 >> 4), r1 & 15, x1[q]);
+    }
+    // 5: S2 along b: rows (c'', a') -> x b''; write rows (c'', b''), K = a'
+    if (!(alive = tc_step(s, 0, 3, tmem, phase))) break;
+    tc_read(tmem, x0, x1);
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      put_bf16(s.A[1][0], 16 * (r0 >> 4) + q, r0 & 15, x0[q]);
+      put_bf16(s.A[1][0], 16 * (r1 >> 4) + q, r1 & 15, x1[q]);
+    }
+    // 6: S1 along a: rows (c'', b'') -> x a''; weight and store the patch (FP32)
+    if (!(alive = tc_step(s, 1, 1, tmem, phase))) break;
+    tc_read(tmem, x0, x1);
+    {
+      float* P = patch + (size_t)e * NS3;
+      const int c0 = r0 >> 4, b0 = r0 & 15, c1 = r1 >> 4, b1 = r1 & 15;
+      if (c0 < n3 && b0 < n2) {
+        const float w = s.W[2][c0] * s.W[1][b0];
+        for (int q = 0; q < n1; ++q) P[((size_t)c0 * nsm + b0) * nsm + q] = x0[q] * w * s.W[0][q];
+      }
+      if (c1 < n3 && b1 < n2) {
+        const float w = s.W[2][c1] * s.W[1][b1];
+        for (int q = 0; q < n1; ++q) P[((size_t)c1 * nsm + b1) * nsm + q] = x1[q] * w * s.W[0][q];
+      }
+    }
+  }
+  if (!alive && tid == 0) atomicExch(err, 1);
+  fence_before();
+  __syncthreads();
+  fence_after();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 32;" ::"r"(tmem));
+}
+
+int launch_fd_tc(Ctx& c, int l, const float* r) {
+  LevelHost& H = c.lv[l];
+  static bool attr = false;
+  const int smem = (int)sizeof(FdTcSmem) + 1024;
+  if (!attr) {
+    CK(cudaFuncSetAttribute(k_fd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    attr = true;
+  }
+  int dev = 0, nsm = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const int grid = std::min(H.ne, nsm * 8);
+  k_fd_tc<<<grid, 128, smem, c.stream>>>(H.v32, r, (float*)c.patch, c.tc_err);
+  ++g_kernels;
+  CK(cudaGetLastError());
   return DGFAS_OK;
 }

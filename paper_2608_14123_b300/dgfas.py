@@ -14,7 +14,7 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libdgfas.so")
 
-DGFAS_FP64, DGFAS_FP32 = 0, 1
+DGFAS_FP64, DGFAS_FP32, DGFAS_BF16 = 0, 1, 2
 DGFAS_WAS, DGFAS_SCG = 0, 1
 ERRORS = {0: "ok", -1: "INVALID", -2: "OOM", -3: "CUDA", -4: "MESH", -5: "NOT_CONVERGED",
           -6: "DIVERGED", -7: "UNSUPPORTED"}
@@ -57,7 +57,7 @@ SYMBOLS = ["dgfas_setup_levels", "dgfas_destroy", "dgfas_level_ndof", "dgfas_nod
            "dgfas_use_graph", "dgfas_profile_sweep", "dgfas_fma_peak", "dgfas_schwarz_correct_static", "dgfas_kernel_launches", "dgfas_mlp_param_count",
            "dgfas_mlp_forward", "dgfas_mlp_grad", "dgfas_mlp_train", "dgfas_learned_surrogate",
            "dgfas_assemble_rhs_level", "dgfas_set_level_rhs", "dgfas_composite_residual",
-           "dgfas_get_level_solution", "dgfas_tc_selftest", "dgfas_host_fd_variant", "dgfas_strerror", "dgfas_last_error"]
+           "dgfas_get_level_solution", "dgfas_tc_selftest", "dgfas_tc_error", "dgfas_host_fd_variant", "dgfas_strerror", "dgfas_last_error"]
 
 _lib = None
 
@@ -101,6 +101,7 @@ def load():
         "dgfas_composite_residual": (I, [P, P, P, ctypes.POINTER(D)]),
         "dgfas_get_level_solution": (I, [P, I, P]),
         "dgfas_tc_selftest": (I, [P, ctypes.POINTER(I)]),
+        "dgfas_tc_error": (I, [P]),
         "dgfas_strerror": (ctypes.c_char_p, [I]),
         "dgfas_last_error": (ctypes.c_char_p, []),
     }
@@ -259,6 +260,9 @@ class Solver:
 
     def dgfas_get_level_solution(self, level, u):
         _check(load().dgfas_get_level_solution(self.ctx, level, _ptr(u)), "get_level_solution")
+
+    def dgfas_tc_error(self):
+        return int(load().dgfas_tc_error(self.ctx))
 
     # ---- conveniences built from the calls above
     def node_coords(self, level=-1):

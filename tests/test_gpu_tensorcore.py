@@ -16,3 +16,45 @@ def test_tcgen05_mma_selftest():
     n = np.arange(16)[:, None]
     B = ((3 * n + k) % 5 - 2).astype(np.float64)
     np.testing.assert_array_equal(D, A @ B.T)
+
+
+def _sweep(cfg, prec, level, seed=3):
+    from tests.gpu_helpers import make_solver, torch_cuda
+    torch = torch_cuda()
+    S = make_solver(cfg, precision=prec)
+    rng = np.random.default_rng(seed)
+    n = S.ndof(level)
+    u = torch.from_numpy(rng.uniform(-1, 1, n)).cuda()
+    g = torch.from_numpy(rng.uniform(-1, 1, n)).cuda()
+    u1 = u.clone()
+    S.dgfas_schwarz_smooth(level, u1, g, 1)
+    assert S.dgfas_tc_error() == 0
+    return (u1 - u).cpu().numpy()
+
+
+@pytest.mark.parametrize("cid,small", [(1, False), (2, True), (3, True)])
+def test_bf16_tensor_core_sweep_matches_fp32(cid, small):
+    """One Schwarz sweep with the tensor-core FD (BF16 operands, FP32
+    accumulation) against the FP32 SIMT FD: BF16 rounding of the six mode
+    products bounds the difference (~1e-2 of the correction)."""
+    from paper_2608_14123_b300 import workloads as wl
+    cfg = wl.config(cid, small=small)
+    for level in range(1, len(cfg["levels"])):
+        d32 = _sweep(cfg, dgfas.DGFAS_FP32, level)
+        d16 = _sweep(cfg, dgfas.DGFAS_BF16, level)
+        err = np.linalg.norm(d16 - d32) / np.linalg.norm(d32)
+        assert err < 3e-2, (level, err)
+
+
+@pytest.mark.parametrize("cid,small", [(1, False), (2, True)])
+def test_bf16_smoother_solve_reaches_1e10(cid, small):
+    from paper_2608_14123_b300 import workloads as wl
+    from tests.gpu_helpers import make_oracle, make_solver, rhs_both, torch_cuda
+    torch = torch_cuda()
+    cfg = wl.config(cid, small=small)
+    S, H = make_solver(cfg, precision=dgfas.DGFAS_BF16), make_oracle(cfg)
+    b, _ = rhs_both(cfg, S, H)
+    u = torch.from_numpy(cfg["u0"].copy()).cuda()
+    info = S.dgfas_solve(u, b, 1e-10, 40)
+    assert info["r_final"] <= 1e-10 * info["r0"]
+    assert S.dgfas_tc_error() == 0
