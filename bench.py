@@ -235,7 +235,7 @@ def run_gpu(args):
     levels = cfg["levels"]
     top = levels[-1]
     N = top["p"] + 1
-    prec = dgfas.DGFAS_FP32 if args.precision == "fp32" else dgfas.DGFAS_FP64
+    prec = {"fp32": dgfas.DGFAS_FP32, "bf16": dgfas.DGFAS_BF16, "fp64": dgfas.DGFAS_FP64}[args.precision]
     S = dgfas.Solver(levels, pr["mu_star"], pr["delta"], pr["s1"], pr["s2"], pr["sc"],
                      precision=prec)
     S.dgfas_use_graph(True)
@@ -310,8 +310,10 @@ def run_gpu(args):
         "residual_smoother": dict(count=sweeps, ms=prof["residual_smoother"], bound="alu",
                                   flops=apply_flops_per_dof(N) * ndof,
                                   peak=fp32_tf if prec else fp64_tf, unit="TFLOP/s"),
-        "fd": dict(count=sweeps, ms=prof["fd"], bound="alu", flops=fd_flops_per_dof(N, m) * ndof,
-                   peak=fp32_tf if prec else fp64_tf, unit="TFLOP/s"),
+        "fd": (dict(count=sweeps, ms=prof["fd"], bound="hbm", bytes=ndof * (4.0 + 4.0 * (ns / N) ** 3),
+                    peak=pk["hbm"], unit="GB/s") if prec == dgfas.DGFAS_BF16 else
+               dict(count=sweeps, ms=prof["fd"], bound="alu", flops=fd_flops_per_dof(N, m) * ndof,
+                    peak=fp32_tf if prec else fp64_tf, unit="TFLOP/s")),
         "combine": dict(count=sweeps, ms=prof["combine"], bound="hbm",
                         bytes=ndof * 16.0, peak=pk["hbm"], unit="GB/s"),
     }
@@ -329,7 +331,8 @@ def run_gpu(args):
 
     # ---- time to 1e-10 (mixed and plain FP64)
     tts = {}
-    for name, pmode in (("mixed_fp32", dgfas.DGFAS_FP32), ("fp64", dgfas.DGFAS_FP64)):
+    for name, pmode in (("mixed_fp32", dgfas.DGFAS_FP32), ("mixed_bf16", dgfas.DGFAS_BF16),
+                        ("fp64", dgfas.DGFAS_FP64)):
         if args.skip_fp64 and pmode == dgfas.DGFAS_FP64:
             continue
         S2 = S if pmode == prec else dgfas.Solver(levels, pr["mu_star"], pr["delta"], pr["s1"],
@@ -364,7 +367,7 @@ def run_gpu(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32+f64" if prec else "f64", "data": "synthetic",
+            "dtype": {0: "f64", 1: "f32+f64", 2: "bf16(tc)+f32+f64"}[prec], "data": "synthetic",
             "config": {"workload": "cartesian-32^3-p8-dirichlet-poisson", "elements": top["corners"].shape[0],
                        "p": top["p"], "dof": ndof, "levels": [lv["p"] for lv in levels],
                        "smoother": f"WAS V({pr['s1']},{pr['s2']}) delta={pr['delta']}",
@@ -395,7 +398,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="dgfas", choices=["dgfas", "reference"])
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "fp64"])
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-others", action="store_true")
