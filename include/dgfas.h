@@ -247,6 +247,12 @@ int dgfas_tc_error(void* ctx);
    out (the kernel never waits unboundedly). */
 int dgfas_tc_selftest(float* out_host, int* timeout_host);
 
+/* Self-test of an MN-major A operand (no swizzle) for tcgen05.mma: out_host
+   [2][128][16] holds D for the two assignments of the core-matrix strides to
+   the descriptor's leading / stride byte offsets ([1] is the layout the FD
+   kernel uses: leading = stride along K, stride = stride along M). */
+int dgfas_tc_selftest_mn(float* out_host, int* timeout_host);
+
 /* Number of kernels the library has launched in this process (including the
    kernel nodes of replayed CUDA graphs). */
 long long dgfas_kernel_launches(void);

@@ -198,23 +198,57 @@ struct FdTcSmem {
 };
 
 __device__ __forceinline__ void put_bf16(unsigned char* tile2, int row, int k, float v) {
-  // row in [0, 256): tile row / 128
+  // row in [0, 256): tile row / 128, K-major
   *reinterpret_cast<__nv_bfloat16*>(tile2 + (row >> 7) * (128 * 16 * 2) + tile_off(row & 127, k)) =
       __float2bfloat16(v);
 }
 
-// one mode product: D = A B^T for both M tiles; returns false on a timed-out wait
-__device__ __forceinline__ bool tc_step(FdTcSmem& s, int ain, int bsel, uint32_t tmem,
+__device__ __forceinline__ uint4 pack8(const float* v) {
+  uint4 o;
+  __nv_bfloat162 p0 = __floats2bfloat162_rn(v[0], v[1]), p1 = __floats2bfloat162_rn(v[2], v[3]),
+                  p2 = __floats2bfloat162_rn(v[4], v[5]), p3 = __floats2bfloat162_rn(v[6], v[7]);
+  o.x = *reinterpret_cast<uint32_t*>(&p0);
+  o.y = *reinterpret_cast<uint32_t*>(&p1);
+  o.z = *reinterpret_cast<uint32_t*>(&p2);
+  o.w = *reinterpret_cast<uint32_t*>(&p3);
+  return o;
+}
+
+// 16 values of rows m0..m0+15 (m0 % 16 == 0) at column k of an MN-major tile
+// pair: (m, k) at byte (m/8)*128 + (k/8)*2048 + (k%8)*16 + (m%8)*2 of tile m/128
+// (descriptor: leading byte offset 2048 = next core matrix along K, stride
+// byte offset 128 = next core matrix along M)
+__device__ __forceinline__ void st_mn(unsigned char* tile2, int m0, int k, const float* v) {
+  unsigned char* t = tile2 + (m0 >> 7) * (128 * 16 * 2);
+  const int ml = m0 & 127;
+  const uint32_t off = (uint32_t)((ml >> 3) * 128 + (k >> 3) * 2048 + (k & 7) * 16);
+  *reinterpret_cast<uint4*>(t + off) = pack8(v);
+  *reinterpret_cast<uint4*>(t + off + 128) = pack8(v + 8);
+}
+
+// 16 values k = 0..15 of row m of a K-major tile pair
+__device__ __forceinline__ void st_k(unsigned char* tile2, int m, const float* v) {
+  unsigned char* t = tile2 + (m >> 7) * (128 * 16 * 2);
+  const int ml = m & 127;
+  const uint32_t off = (uint32_t)((ml >> 3) * 256 + (ml & 7) * 16);
+  *reinterpret_cast<uint4*>(t + off) = pack8(v);
+  *reinterpret_cast<uint4*>(t + off + 128) = pack8(v + 8);
+}
+
+// one mode product: D = A B^T for both M tiles (A K-major or MN-major);
+// returns false on a timed-out wait
+__device__ __forceinline__ bool tc_step(FdTcSmem& s, int ain, int bsel, bool mn, uint32_t tmem,
                                         uint32_t& phase) {
   fence_async_smem();
   fence_before();
   __syncthreads();
   fence_after();
   if (threadIdx.x == 0) {
-    const uint32_t idesc = idesc_bf16(128, 16);
+    const uint32_t idesc = idesc_bf16(128, 16) | (mn ? (1u << 15) : 0u);
     const uint64_t bd = sdesc(smem_u32(s.B[bsel]), 128, 256);
-    mma_bf16(tmem, sdesc(smem_u32(s.A[ain][0]), 128, 256), bd, idesc, 0);
-    mma_bf16(tmem + 16, sdesc(smem_u32(s.A[ain][1]), 128, 256), bd, idesc, 0);
+    const uint32_t lbo = mn ? 2048 : 128, sbo = mn ? 128 : 256;
+    mma_bf16(tmem, sdesc(smem_u32(s.A[ain][0]), lbo, sbo), bd, idesc, 0);
+    mma_bf16(tmem + 16, sdesc(smem_u32(s.A[ain][1]), lbo, sbo), bd, idesc, 0);
     commit(smem_u32(&s.mbar));
   }
   const bool ok = mbar_wait(smem_u32(&s.mbar), phase);
@@ -223,16 +257,14 @@ __device__ __forceinline__ bool tc_step(FdTcSmem& s, int ain, int bsel, uint32_t
   return __syncthreads_and(ok ? 1 : 0) != 0;
 }
 
-// rows of this thread after a step: tile 0 row 32 w + lane and tile 1 row 128 + 32 w + lane
-__device__ __forceinline__ void tc_read(uint32_t tmem, float* v0, float* v1) {
+// this thread's TMEM row of tile `t` (row 128 t + 32 w + lane), 16 FP32 values
+__device__ __forceinline__ void tc_read1(uint32_t tmem, int t, float* v) {
   const int warp = threadIdx.x >> 5;
-  const uint32_t base = tmem + ((uint32_t)(32 * warp) << 16);
-  tmem_ld16(base, v0);
-  tmem_ld16(base + 16, v1);
+  tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + 16 * t, v);
 }
 
-__global__ void __launch_bounds__(128) k_fd_tc(const LevelView<float> L, const float* __restrict__ r,
-                                               float* __restrict__ patch, int* __restrict__ err) {
+__global__ void __launch_bounds__(128, 8) k_fd_tc(const LevelView<float> L, const float* __restrict__ r,
+                                                  float* __restrict__ patch, int* __restrict__ err) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   FdTcSmem& s = *reinterpret_cast<FdTcSmem*>(smem_raw);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -279,12 +311,11 @@ __global__ void __launch_bounds__(128) k_fd_tc(const LevelView<float> L, const f
       s.lam[d][q] = in ? L.lam[vv[d] * nsm + q] : 1.0f;
       s.W[d][q] = in ? L.W[vv[d] * nsm + q] : 0.0f;
     }
-    // gather R_s r into A[0]: rows (c, b) = 16 c + b, K = a
+    // gather R_s r into A[0] (K-major): rows (c, b) = 16 c + b, K = a
     for (int t = tid; t < 4096; t += 128) {
       const int a = t & 15, b = (t >> 4) & 15, c = t >> 8;
       float val = 0.0f;
       if (a < n1 && b < n2 && c < n3) {
-        // side maps (left interior iff side type 0)
         int ox, ix, oy, iy, oz, iz, aa = a, bq = b, cq = c;
         if ((v1 >> 2) == 0) { if (aa < m) { ox = -1; ix = N - m + aa; } else { aa -= m; ox = aa < N ? 0 : 1; ix = aa < N ? aa : aa - N; } }
         else { ox = aa < N ? 0 : 1; ix = aa < N ? aa : aa - N; }
@@ -298,66 +329,66 @@ __global__ void __launch_bounds__(128) k_fd_tc(const LevelView<float> L, const f
       put_bf16(s.A[0][0], 16 * c + b, a, val);
     }
     const float g0 = L.g[4 * e], g1 = L.g[4 * e + 1], g2 = L.g[4 * e + 2], g3 = L.g[4 * e + 3];
-    float x0[16], x1[16];
-    const int r0 = 32 * warp + lane, r1 = 128 + r0;
-    // 1: S1^T along a: rows (c, b) -> (c, b) x a'; write rows (c, a'), K = b
-    if (!(alive = tc_step(s, 0, 0, tmem, phase))) break;
-    tc_read(tmem, x0, x1);
+    float x[16];
+    // 1: S1^T along a (A K-major): rows (c, b) -> x a'; write rows (c, a'), K = b (MN-major)
+    if (!(alive = tc_step(s, 0, 0, false, tmem, phase))) break;
 #pragma unroll
-    for (int q = 0; q < 16; ++q) {
-      put_bf16(s.A[1][0], 16 * (r0 >> 4) + q, r0 & 15, x0[q]);
-      put_bf16(s.A[1][0], 16 * (r1 >> 4) + q, r1 & 15, x1[q]);
+    for (int t = 0; t < 2; ++t) {
+      const int rr = 128 * t + 32 * warp + lane;
+      tc_read1(tmem, t, x);
+      st_mn(s.A[1][0], 16 * (rr >> 4), rr & 15, x);
     }
-    // 2: S2^T along b: rows (c, a') -> x b'; write rows (a', b'), K = c
-    if (!(alive = tc_step(s, 1, 2, tmem, phase))) break;
-    tc_read(tmem, x0, x1);
+    // 2: S2^T along b: rows (c, a') -> x b'; write rows (a', b'), K = c (MN-major)
+    if (!(alive = tc_step(s, 1, 2, true, tmem, phase))) break;
 #pragma unroll
-    for (int q = 0; q < 16; ++q) {
-      put_bf16(s.A[0][0], 16 * (r0 & 15) + q, r0 >> 4, x0[q]);
-      put_bf16(s.A[0][0], 16 * (r1 & 15) + q, r1 >> 4, x1[q]);
+    for (int t = 0; t < 2; ++t) {
+      const int rr = 128 * t + 32 * warp + lane;
+      tc_read1(tmem, t, x);
+      st_mn(s.A[0][0], 16 * (rr & 15), rr >> 4, x);
     }
-    // 3: S3^T along c: rows (a', b') -> x c'; scale by D^-1 in FP32; same rows, K = c'
-    if (!(alive = tc_step(s, 0, 4, tmem, phase))) break;
-    tc_read(tmem, x0, x1);
-    {
-      const int a0 = r0 >> 4, b0 = r0 & 15, a1 = r1 >> 4, b1 = r1 & 15;
-      const float d0 = g0 + g1 * s.lam[0][a0] + g2 * s.lam[1][b0];
-      const float d1 = g0 + g1 * s.lam[0][a1] + g2 * s.lam[1][b1];
+    // 3: S3^T along c: rows (a', b') -> x c'; scale by D^-1 in FP32; same rows, K = c' (K-major)
+    if (!(alive = tc_step(s, 0, 4, true, tmem, phase))) break;
 #pragma unroll
-      for (int q = 0; q < 16; ++q) {
-        put_bf16(s.A[1][0], r0, q, x0[q] / (d0 + g3 * s.lam[2][q]));
-        put_bf16(s.A[1][0], r1, q, x1[q] / (d1 + g3 * s.lam[2][q]));
-      }
+    for (int t = 0; t < 2; ++t) {
+      const int rr = 128 * t + 32 * warp + lane;
+      tc_read1(tmem, t, x);
+      const float d0 = g0 + g1 * s.lam[0][rr >> 4] + g2 * s.lam[1][rr & 15];
+#pragma unroll
+      for (int q = 0; q < 16; ++q) x[q] = x[q] / (d0 + g3 * s.lam[2][q]);
+      st_k(s.A[1][0], rr, x);
     }
-    // 4: S3 along c: rows (a', b') -> x c''; write rows (c'', a'), K = b'
-    if (!(alive = tc_step(s, 1, 5, tmem, phase))) break;
-    tc_read(tmem, x0, x1);
+    // 4: S3 along c: rows (a', b') -> x c''; write rows (a', c''), K = b' (MN-major)
+    if (!(alive = tc_step(s, 1, 5, false, tmem, phase))) break;
 #pragma unroll
-    for (int q = 0; q < 16; ++q) {
-      put_bf16(s.A[0][0], 16 * q + (r0 >> 4), r0 & 15, x0[q]);
-      put_bf16(s.A[0][0], 16 * q + (r1 >> 4), r1 & 15, x1[q]);
+    for (int t = 0; t < 2; ++t) {
+      const int rr = 128 * t + 32 * warp + lane;
+      tc_read1(tmem, t, x);
+      st_mn(s.A[0][0], 16 * (rr >> 4), rr & 15, x);
     }
-    // 5: S2 along b: rows (c'', a') -> x b''; write rows (c'', b''), K = a'
-    if (!(alive = tc_step(s, 0, 3, tmem, phase))) break;
-    tc_read(tmem, x0, x1);
+    // 5: S2 along b: rows (a', c'') -> x b''; write rows (c'', b''), K = a' (MN-major)
+    if (!(alive = tc_step(s, 0, 3, true, tmem, phase))) break;
 #pragma unroll
-    for (int q = 0; q < 16; ++q) {
-      put_bf16(s.A[1][0], 16 * (r0 >> 4) + q, r0 & 15, x0[q]);
-      put_bf16(s.A[1][0], 16 * (r1 >> 4) + q, r1 & 15, x1[q]);
+    for (int t = 0; t < 2; ++t) {
+      const int rr = 128 * t + 32 * warp + lane;
+      tc_read1(tmem, t, x);
+      st_mn(s.A[1][0], 16 * (rr & 15), rr >> 4, x);
     }
     // 6: S1 along a: rows (c'', b'') -> x a''; weight and store the patch (FP32)
-    if (!(alive = tc_step(s, 1, 1, tmem, phase))) break;
-    tc_read(tmem, x0, x1);
+    if (!(alive = tc_step(s, 1, 1, true, tmem, phase))) break;
     {
       float* P = patch + (size_t)e * NS3;
-      const int c0 = r0 >> 4, b0 = r0 & 15, c1 = r1 >> 4, b1 = r1 & 15;
-      if (c0 < n3 && b0 < n2) {
-        const float w = s.W[2][c0] * s.W[1][b0];
-        for (int q = 0; q < n1; ++q) P[((size_t)c0 * nsm + b0) * nsm + q] = x0[q] * w * s.W[0][q];
-      }
-      if (c1 < n3 && b1 < n2) {
-        const float w = s.W[2][c1] * s.W[1][b1];
-        for (int q = 0; q < n1; ++q) P[((size_t)c1 * nsm + b1) * nsm + q] = x1[q] * w * s.W[0][q];
+#pragma unroll
+      for (int t = 0; t < 2; ++t) {
+        const int rr = 128 * t + 32 * warp + lane;
+        tc_read1(tmem, t, x);
+        const int cc = rr >> 4, bb = rr & 15;
+        if (cc < n3 && bb < n2) {
+          const float w = s.W[2][cc] * s.W[1][bb];
+          float* row = P + ((size_t)cc * nsm + bb) * nsm;
+#pragma unroll
+          for (int q = 0; q < 16; ++q)
+            if (q < n1) row[q] = x[q] * w * s.W[0][q];
+        }
       }
     }
   }
@@ -383,5 +414,85 @@ int launch_fd_tc(Ctx& c, int l, const float* r) {
   k_fd_tc<<<grid, 128, smem, c.stream>>>(H.v32, r, (float*)c.patch, c.tc_err);
   ++g_kernels;
   CK(cudaGetLastError());
+  return DGFAS_OK;
+}
+
+// Self-test of an MN-major A operand (no swizzle): element (m, k) of the
+// 128 x 16 tile at byte (m/8)*128 + (k/8)*2048 + (k%8)*16 + (m%8)*2 (core
+// matrices of 8 k-rows x 8 m-values).  Two MMAs read it with the two possible
+// assignments of the core-matrix strides to the descriptor's leading / stride
+// byte offsets (LBO = 128, SBO = 2048 and the swap); the buffer is sized so
+// that either reading stays inside it.  out [2][128][16].
+__global__ void k_tc_selftest_mn(float* __restrict__ out, int* __restrict__ flag) {
+  extern __shared__ __align__(1024) unsigned char dyn[];
+  unsigned char* sA = dyn;                 // 40 KB region, the tile in its first 4 KB
+  unsigned char* sB = dyn + 40 * 1024;     // 512 B
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t tslot;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  for (int t = tid; t < 40 * 1024 / 4; t += blockDim.x) reinterpret_cast<uint32_t*>(sA)[t] = 0u;
+  __syncthreads();
+  for (int t = tid; t < 128 * 16; t += blockDim.x) {
+    const int r = t / 16, k = t % 16;
+    const uint32_t off = (r >> 3) * 128 + (k >> 3) * 2048 + (k & 7) * 16 + (r & 7) * 2;
+    *reinterpret_cast<__nv_bfloat16*>(sA + off) = __float2bfloat16((float)((r + 2 * k) % 7 - 3));
+  }
+  for (int t = tid; t < 16 * 16; t += blockDim.x) {
+    const int n = t / 16, k = t % 16;
+    *reinterpret_cast<__nv_bfloat16*>(sB + tile_off(n, k)) = __float2bfloat16((float)((3 * n + k) % 5 - 2));
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 32;" ::"r"(smem_u32(&tslot)));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    mbar_init(smem_u32(&mbar), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  fence_async_smem();
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = tslot;
+  if (tid == 0) {
+    const uint32_t idesc = idesc_bf16(128, 16) | (1u << 15);   // A MN-major
+    const uint64_t bd = sdesc(smem_u32(sB), 128, 256);
+    mma_bf16(tmem, sdesc(smem_u32(sA), 128, 2048), bd, idesc, 0);
+    mma_bf16(tmem + 16, sdesc(smem_u32(sA), 2048, 128), bd, idesc, 0);
+    commit(smem_u32(&mbar));
+  }
+  const bool ok = mbar_wait(smem_u32(&mbar), 0);
+  fence_after();
+  if (!ok && lane == 0) atomicExch(flag, 1);
+  float v0[16], v1[16];
+  tc_read1(tmem, 0, v0);
+  tc_read1(tmem, 1, v1);
+  for (int q = 0; q < 16; ++q) {
+    out[(32 * warp + lane) * 16 + q] = ok ? v0[q] : 0.0f;
+    out[2048 + (32 * warp + lane) * 16 + q] = ok ? v1[q] : 0.0f;
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 32;" ::"r"(tmem));
+}
+
+extern "C" int dgfas_tc_selftest_mn(float* out_host, int* timeout_host) {
+  if (!out_host || !timeout_host) return DGFAS_ERR_INVALID;
+  float* d = nullptr;
+  int* f = nullptr;
+  const int smem = 40 * 1024 + 1024;
+  CK(cudaFuncSetAttribute(k_tc_selftest_mn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  CK(cudaMalloc(&d, 2 * 128 * 16 * sizeof(float)));
+  CK(cudaMalloc(&f, sizeof(int)));
+  CK(cudaMemset(f, 0, sizeof(int)));
+  k_tc_selftest_mn<<<1, 128, smem>>>(d, f);
+  ++g_kernels;
+  CK(cudaGetLastError());
+  CK(cudaDeviceSynchronize());
+  CK(cudaMemcpy(out_host, d, 2 * 128 * 16 * sizeof(float), cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(timeout_host, f, sizeof(int), cudaMemcpyDeviceToHost));
+  cudaFree(d);
+  cudaFree(f);
   return DGFAS_OK;
 }

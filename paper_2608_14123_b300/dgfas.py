@@ -57,7 +57,7 @@ SYMBOLS = ["dgfas_setup_levels", "dgfas_destroy", "dgfas_level_ndof", "dgfas_nod
            "dgfas_use_graph", "dgfas_profile_sweep", "dgfas_fma_peak", "dgfas_schwarz_correct_static", "dgfas_kernel_launches", "dgfas_mlp_param_count",
            "dgfas_mlp_forward", "dgfas_mlp_grad", "dgfas_mlp_train", "dgfas_learned_surrogate",
            "dgfas_assemble_rhs_level", "dgfas_set_level_rhs", "dgfas_composite_residual",
-           "dgfas_get_level_solution", "dgfas_tc_selftest", "dgfas_tc_error", "dgfas_host_fd_variant", "dgfas_strerror", "dgfas_last_error"]
+           "dgfas_get_level_solution", "dgfas_tc_selftest", "dgfas_tc_selftest_mn", "dgfas_tc_error", "dgfas_host_fd_variant", "dgfas_strerror", "dgfas_last_error"]
 
 _lib = None
 
@@ -102,6 +102,7 @@ def load():
         "dgfas_get_level_solution": (I, [P, I, P]),
         "dgfas_tc_selftest": (I, [P, ctypes.POINTER(I)]),
         "dgfas_tc_error": (I, [P]),
+        "dgfas_tc_selftest_mn": (I, [P, ctypes.POINTER(I)]),
         "dgfas_strerror": (ctypes.c_char_p, [I]),
         "dgfas_last_error": (ctypes.c_char_p, []),
     }

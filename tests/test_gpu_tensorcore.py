@@ -58,3 +58,21 @@ def test_bf16_smoother_solve_reaches_1e10(cid, small):
     info = S.dgfas_solve(u, b, 1e-10, 40)
     assert info["r_final"] <= 1e-10 * info["r0"]
     assert S.dgfas_tc_error() == 0
+
+
+def test_tcgen05_mn_major_operand_selftest():
+    """MN-major A operand (the layout the FD kernel writes without transposing
+    in shared memory): leading byte offset = core-matrix stride along K, stride
+    byte offset = core-matrix stride along M."""
+    import ctypes
+    lib = dgfas.load()
+    out = np.zeros(2 * 128 * 16, dtype=np.float32)
+    to = ctypes.c_int(0)
+    assert lib.dgfas_tc_selftest_mn(out.ctypes.data_as(ctypes.c_void_p), ctypes.byref(to)) == 0
+    assert to.value == 0
+    r = np.arange(128)[:, None]
+    k = np.arange(16)[None, :]
+    A = ((r + 2 * k) % 7 - 3).astype(np.float64)
+    n = np.arange(16)[:, None]
+    B = ((3 * n + k) % 5 - 2).astype(np.float64)
+    np.testing.assert_array_equal(out.reshape(2, 128, 16)[1], A @ B.T)
