@@ -311,22 +311,35 @@ __global__ void __launch_bounds__(128, 8) k_fd_tc(const LevelView<float> L, cons
       s.lam[d][q] = in ? L.lam[vv[d] * nsm + q] : 1.0f;
       s.W[d][q] = in ? L.W[vv[d] * nsm + q] : 0.0f;
     }
-    // gather R_s r into A[0] (K-major): rows (c, b) = 16 c + b, K = a
-    for (int t = tid; t < 4096; t += 128) {
-      const int a = t & 15, b = (t >> 4) & 15, c = t >> 8;
-      float val = 0.0f;
-      if (a < n1 && b < n2 && c < n3) {
-        int ox, ix, oy, iy, oz, iz, aa = a, bq = b, cq = c;
-        if ((v1 >> 2) == 0) { if (aa < m) { ox = -1; ix = N - m + aa; } else { aa -= m; ox = aa < N ? 0 : 1; ix = aa < N ? aa : aa - N; } }
-        else { ox = aa < N ? 0 : 1; ix = aa < N ? aa : aa - N; }
+    // gather R_s r into A[0] (K-major): rows (c, b) = 16 c + b, K = a; each task
+    // fills 8 consecutive a of one row with one 16-byte store
+    for (int task = tid; task < 512; task += 128) {
+      const int row = task >> 1, h = task & 1, c = row >> 4, b = row & 15;
+      float vals[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) vals[q] = 0.0f;
+      if (b < n2 && c < n3) {
+        int oy, iy, oz, iz, bq = b, cq = c;
         if ((v2 >> 2) == 0) { if (bq < m) { oy = -1; iy = N - m + bq; } else { bq -= m; oy = bq < N ? 0 : 1; iy = bq < N ? bq : bq - N; } }
         else { oy = bq < N ? 0 : 1; iy = bq < N ? bq : bq - N; }
         if ((v3 >> 2) == 0) { if (cq < m) { oz = -1; iz = N - m + cq; } else { cq -= m; oz = cq < N ? 0 : 1; iz = cq < N ? cq : cq - N; } }
         else { oz = cq < N ? 0 : 1; iz = cq < N ? cq : cq - N; }
-        const int src = L.nbr27[27 * e + (ox + 1) + 3 * (oy + 1) + 9 * (oz + 1)];
-        if (src >= 0) val = r[(size_t)src * N3 + (iz * N + iy) * N + ix];
+        const int* nb = L.nbr27 + 27 * e + 3 * (oy + 1) + 9 * (oz + 1);
+        const int line = (iz * N + iy) * N;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          int aa = 8 * h + q;
+          if (aa >= n1) break;
+          int ox, ix;
+          if ((v1 >> 2) == 0) { if (aa < m) { ox = -1; ix = N - m + aa; } else { aa -= m; ox = aa < N ? 0 : 1; ix = aa < N ? aa : aa - N; } }
+          else { ox = aa < N ? 0 : 1; ix = aa < N ? aa : aa - N; }
+          const int src = nb[ox + 1];
+          if (src >= 0) vals[q] = r[(size_t)src * N3 + line + ix];
+        }
       }
-      put_bf16(s.A[0][0], 16 * c + b, a, val);
+      unsigned char* t = s.A[0][0] + (row >> 7) * (128 * 16 * 2);
+      const int ml = row & 127;
+      *reinterpret_cast<uint4*>(t + (ml >> 3) * 256 + (ml & 7) * 16 + h * 128) = pack8(vals);
     }
     const float g0 = L.g[4 * e], g1 = L.g[4 * e + 1], g2 = L.g[4 * e + 2], g3 = L.g[4 * e + 3];
     float x[16];

@@ -614,7 +614,9 @@ static int fd_disp(const LevelView<T>& L, const TR* r, T* patch, cudaStream_t st
 
 int launch_fd(Ctx& c, int l, int prec, const void* r) {
   LevelHost& H = c.lv[l];
-  if (prec == DGFAS_BF16) return launch_fd_tc(c, l, (const float*)r);
+  // tensor cores pay off for wide subdomains only (operands are padded to
+  // 16^3); narrower levels keep the FP32 kernel in the BF16 mode
+  if (prec == DGFAS_BF16 && H.nsm >= 12) return launch_fd_tc(c, l, (const float*)r);
   if (prec == DGFAS_FP64)
     return fd_disp<double, double>(H.v64, (const double*)r, (double*)c.patch, c.stream);
   return fd_disp<float, float>(H.v32, (const float*)r, (float*)c.patch, c.stream);
