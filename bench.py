@@ -6,7 +6,9 @@ Poisson on [0,1]^3, Dirichlet, uniform Cartesian 32^3 elements, p = 8
 (23.9M DoF), p-coarsening 8 -> 4 -> 2 -> 1 then h-coarsening to 4^3, V(2,2)
 with the weighted additive Schwarz / fast-diagonalization smoother, seeded
 16-mode right-hand side.  Headline: the FP32 smoother with FP64 residual,
-tau, restriction and root solve; the plain FP64 path is measured beside it.
+tau, restriction and root solve, with the FD mode products of the top levels
+on the tensor cores (BF16 operands, FP32 accumulation); the FP32 and the
+plain FP64 paths are measured beside it.
 
 Prints one JSON line.  `--impl reference` times the FP64 CPU oracle instead
 (on a bounded sample of the same workload).
@@ -398,7 +400,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="dgfas", choices=["dgfas", "reference"])
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "fp64"])
+    ap.add_argument("--precision", default="bf16", choices=["fp32", "bf16", "fp64"])
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-others", action="store_true")
