@@ -101,6 +101,14 @@ def stop_clock_log(p, fh, dev_index=0):
                 samples=len(sm))
 
 
+def max_over_ranks(value, device):
+    """The largest per-rank value (the job's time is the slowest rank's)."""
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -272,9 +280,7 @@ def run_gpu(args):
     clocks = stop_clock_log(clk_p, clk_fh, local)
     ms = e0.elapsed_time(e1) / args.steps
     if ws > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+        ms = max_over_ranks(ms, dev)
         torch.distributed.barrier()
     value = ndof * ws / (ms * 1e-3)
 
