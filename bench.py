@@ -43,12 +43,17 @@ def peaks():
 
 
 def apply_flops_per_dof(N, box=True):
-    """Algorithmic FP64 flops per DoF of the sum-factorized SIP apply (Eq. (2)):
-    volume: 3 reference derivatives and 3 transposed ones, N FMA each, plus the
-    metric; faces: 6 N^2 face nodes per element, each with the own and the
-    neighbour's normal derivative (N FMA each), the flux and the lifting."""
-    vol = 2 * 6 * N + (6 if box else 18)
-    face = 6 * N * N * (2 * 2 * N + 12) / N ** 3
+    """Algorithmic FP64 flops per DoF of the SIP apply (Eq. (2)) as the kernels
+    evaluate it.  Box elements (Kronecker form): volume 3 N FMA plus 5
+    operations per node; faces: 6 N^2 face nodes per element, each with the own
+    and the neighbour's normal derivative and the lifting along the normal
+    line (3 N FMA) and about 12 operations of flux.  Curvilinear elements:
+    gradient and transposed gradient (6 N FMA) and the 3 x 3 metric."""
+    if box:
+        vol = 2 * 3 * N + 5
+    else:
+        vol = 2 * 6 * N + 18
+    face = 6 * N * N * (2 * 3 * N + 12) / N ** 3
     return vol + face
 
 

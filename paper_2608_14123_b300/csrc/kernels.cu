@@ -245,18 +245,29 @@ __global__ void k_apply_box(const LevelView<T> L, const T* __restrict__ bx,
       af[d] = bx[6 * e + 3 + d];
     }
     const T kap = L.kappa * T(0.125) * L.h[3 * e] * L.h[3 * e + 1] * L.h[3 * e + 2];
+    // per-thread constants of the k loop (the FP64 pipe is the bound: keep the
+    // per-node work at 3N FMA plus five operations)
+    const T wi = sw[tx], wj = sw[ty];
+    const T c0 = g[0] * wj, c1 = g[1] * wi, c2 = g[2] * wi * wj, ck = kap * wi * wj;
+    T lx[N], ly[N];
+#pragma unroll
+    for (int l = 0; l < N; ++l) {
+      lx[l] = sL[tx * N + l];
+      ly[l] = sL[ty * N + l];
+    }
     for (int k = 0; k < N; ++k) {
       T s0 = 0, s1 = 0, s2 = 0;
 #pragma unroll
       for (int l = 0; l < N; ++l) {
-        s0 += sL[tx * N + l] * us[(k * N + ty) * N + l];
-        s1 += sL[ty * N + l] * us[(k * N + l) * N + tx];
+        s0 += lx[l] * us[(k * N + ty) * N + l];
+        s1 += ly[l] * us[(k * N + l) * N + tx];
         s2 += sL[k * N + l] * us[(l * N + ty) * N + tx];
       }
       const int n = (k * N + ty) * N + tx;
-      const T wi = sw[tx], wj = sw[ty], wk = sw[k];
-      R[n] = g[0] * wj * wk * s0 + g[1] * wi * wk * s1 + g[2] * wi * wj * s2 +
-             kap * wi * wj * wk * us[n];
+      const T wk = sw[k];
+      T rv = (c0 * wk) * s0 + (c1 * wk) * s1 + c2 * s2;
+      if (kap != T(0)) rv += ck * wk * us[n];
+      R[n] = rv;
     }
   }
   __syncthreads();
@@ -754,9 +765,16 @@ __device__ void tensor3(const double* A1, const double* A2, const double* A3, in
 template <bool RESTRICT>
 __global__ void k_gather_children(const TransferView T, const double* __restrict__ xf,
                                   double* __restrict__ xc, double* __restrict__ xcopy) {
-  __shared__ double X[TMAX], T1[TMAX], T2[TMAX], Y[TMAX], A[3][DGFAS_MAX_N * DGFAS_MAX_N];
+  extern __shared__ __align__(16) double tsm[];
   const int E = blockIdx.x, tid = threadIdx.x, nth = blockDim.x;
   const int Nf = T.Nf, Nc = T.Nc, Nf3 = Nf * Nf * Nf, Nc3 = Nc * Nc * Nc;
+  // X [Nf^3], T1 [Nf^2 Nc], T2 [Nf Nc^2], Y [Nc^3], A [3][Nc Nf]: sized to the pair
+  double* X = tsm;
+  double* T1 = X + Nf3;
+  double* T2 = T1 + Nf * Nf * Nc;
+  double* Y = T2 + Nf * Nc * Nc;
+  double* Ab = Y + Nc3;
+  double* A[3] = {Ab, Ab + Nc * Nf, Ab + 2 * Nc * Nf};
   double acc[8];
   for (int q = 0; q < 8; ++q) acc[q] = 0.0;
   int any = 0;
@@ -794,9 +812,16 @@ template <typename TD>
 __global__ void k_prolong(const TransferView T, const double* __restrict__ uc,
                           const double* __restrict__ ubar, double* __restrict__ uf,
                           TD* __restrict__ delta) {
-  __shared__ double X[TMAX], T1[TMAX], T2[TMAX], Y[TMAX], A[3][DGFAS_MAX_N * DGFAS_MAX_N];
+  extern __shared__ __align__(16) double tsm[];
   const int e = blockIdx.x, tid = threadIdx.x, nth = blockDim.x;
   const int Nf = T.Nf, Nc = T.Nc, Nf3 = Nf * Nf * Nf, Nc3 = Nc * Nc * Nc;
+  // X [Nc^3], T1 [Nc^2 Nf], T2 [Nc Nf^2], Y [Nf^3], A [3][Nf Nc]
+  double* X = tsm;
+  double* T1 = X + Nc3;
+  double* T2 = T1 + Nc * Nc * Nf;
+  double* Y = T2 + Nc * Nf * Nf;
+  double* Ab = Y + Nf3;
+  double* A[3] = {Ab, Ab + Nf * Nc, Ab + 2 * Nf * Nc};
   const int par = T.parent[e], oct = T.octant[e];
   const bool frozen = T.clsf[e] == DGFAS_FROZEN;
   for (int t = tid; t < Nc3; t += nth)
@@ -818,10 +843,17 @@ __global__ void k_prolong(const TransferView T, const double* __restrict__ uc,
   }
 }
 
+// dynamic shared memory of the transfer kernels: both index orders fit
+static size_t transfer_smem(const TransferView& T) {
+  const size_t f = T.Nf, c = T.Nc;
+  const size_t n = f * f * f + f * f * c + f * c * c + c * c * c + 3 * f * c;
+  return n * sizeof(double);
+}
+
 int launch_project(Ctx& c, int l, const double* uf) {
   LevelHost& F = c.lv[l];
   LevelHost& C = c.lv[l - 1];
-  k_gather_children<false><<<C.ne, 256, 0, c.stream>>>(F.tr, uf, C.u, C.ubar);
+  k_gather_children<false><<<C.ne, 256, transfer_smem(F.tr), c.stream>>>(F.tr, uf, C.u, C.ubar);
   ++g_kernels;
   CK(cudaGetLastError());
   return DGFAS_OK;
@@ -830,7 +862,7 @@ int launch_project(Ctx& c, int l, const double* uf) {
 int launch_restrict(Ctx& c, int l, const double* rf, double* rc) {
   LevelHost& F = c.lv[l];
   LevelHost& C = c.lv[l - 1];
-  k_gather_children<true><<<C.ne, 256, 0, c.stream>>>(F.tr, rf, rc, nullptr);
+  k_gather_children<true><<<C.ne, 256, transfer_smem(F.tr), c.stream>>>(F.tr, rf, rc, nullptr);
   ++g_kernels;
   CK(cudaGetLastError());
   return DGFAS_OK;
@@ -840,9 +872,9 @@ int launch_prolong(Ctx& c, int l, double* uf, int prec, void* delta) {
   LevelHost& F = c.lv[l];
   LevelHost& C = c.lv[l - 1];
   if (prec == DGFAS_FP64)
-    k_prolong<double><<<F.ne, 128, 0, c.stream>>>(F.tr, C.u, C.ubar, uf, (double*)delta);
+    k_prolong<double><<<F.ne, 128, transfer_smem(F.tr), c.stream>>>(F.tr, C.u, C.ubar, uf, (double*)delta);
   else
-    k_prolong<float><<<F.ne, 128, 0, c.stream>>>(F.tr, C.u, C.ubar, uf, (float*)delta);
+    k_prolong<float><<<F.ne, 128, transfer_smem(F.tr), c.stream>>>(F.tr, C.u, C.ubar, uf, (float*)delta);
   ++g_kernels;
   CK(cudaGetLastError());
   return DGFAS_OK;
