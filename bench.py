@@ -19,6 +19,7 @@ import os
 import subprocess
 import sys
 import tempfile
+import threading
 import time
 
 import numpy as np
@@ -62,48 +63,108 @@ def fd_flops_per_dof(N, m):
     return 12.0 * ns ** 4 / N ** 3
 
 
-def start_clock_log():
-    try:
-        fh = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
-        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
-             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
-        p = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
-                              "-lms", "200"], stdout=fh, stderr=subprocess.DEVNULL)
-        return p, fh
-    except Exception:
-        return None, None
+class ClockSampler:
+    """SM clocks and clock-event reasons sampled DURING the timed region.
 
+    NVML is polled from a background thread every 5 ms (the timed region of the
+    default run is well under a second, too short for nvidia-smi's 200 ms
+    loop); nvidia-smi is the fallback when NVML cannot be loaded."""
+    # clock-event reason bits (nvml.h): sw power cap, hw slowdown,
+    # sw thermal slowdown, hw thermal slowdown
+    BITS = {"sw_power_cap": 0x4, "hw_slowdown": 0x8, "sw_thermal_slowdown": 0x20,
+            "hw_thermal_slowdown": 0x40}
 
-def stop_clock_log(p, fh, dev_index=0):
-    if p is None:
-        return None
-    p.terminate()
-    try:
-        p.wait(timeout=5)
-    except Exception:
-        p.kill()
-    fh.flush()
-    fh.seek(0)
-    sm, mx, reasons = [], [], set()
-    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-    for line in fh:
-        parts = [x.strip() for x in line.split(",")]
-        if len(parts) < 9 or parts[0] != str(dev_index):
-            continue
+    def __init__(self, device):
+        self.sm, self.mx, self.reasons = [], [], set()
+        self.stop_ev = threading.Event()
+        self.thread = self.proc = self.fh = None
+        self.err = None
         try:
-            sm.append(float(parts[1]))
-            mx.append(float(parts[2]))
-        except ValueError:
-            continue
-        for nm, v in zip(names, parts[5:9]):
-            if v.lower() == "active":
-                reasons.add(nm)
-    os.unlink(fh.name)
-    if not sm:
-        return None
-    return dict(sm_mhz=float(np.median(sm)), sm_max_mhz=float(max(mx)), reasons=sorted(reasons),
-                samples=len(sm))
+            import pynvml as nv
+            nv.nvmlInit()
+            self.nv = nv
+            import torch
+            h = None
+            try:
+                uuid = str(torch.cuda.get_device_properties(device).uuid)
+                h = nv.nvmlDeviceGetHandleByUUID(uuid if uuid.startswith("GPU-") else "GPU-" + uuid)
+            except Exception:
+                h = nv.nvmlDeviceGetHandleByIndex(device)
+            self.h = h
+            self.thread = threading.Thread(target=self._poll, daemon=True)
+            self.thread.start()
+        except Exception as ex:   # noqa: BLE001 - any NVML failure falls back to nvidia-smi
+            self.nv = None
+            self.err = f"{type(ex).__name__}: {ex}"[:200]
+            self._start_smi(device)
+
+    def _poll(self):
+        nv = self.nv
+        get_r = getattr(nv, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            nv.nvmlDeviceGetCurrentClocksThrottleReasons
+        mx = nv.nvmlDeviceGetMaxClockInfo(self.h, nv.NVML_CLOCK_SM)
+        while not self.stop_ev.is_set():
+            try:
+                self.sm.append(float(nv.nvmlDeviceGetClockInfo(self.h, nv.NVML_CLOCK_SM)))
+                self.mx.append(float(mx))
+                bits = get_r(self.h)
+                for nm, b in self.BITS.items():
+                    if bits & b:
+                        self.reasons.add(nm)
+            except Exception:
+                pass
+            self.stop_ev.wait(0.005)
+
+    def _start_smi(self, device):
+        try:
+            self.fh = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+            self.dev = device
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.thread is not None:
+            self.stop_ev.set()
+            self.thread.join(timeout=2)
+            src = "nvml, 5 ms"
+        elif self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.fh.flush()
+            self.fh.seek(0)
+            names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+            for line in self.fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9 or parts[0] != str(self.dev):
+                    continue
+                try:
+                    self.sm.append(float(parts[1]))
+                    self.mx.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        self.reasons.add(nm)
+            os.unlink(self.fh.name)
+            src = "nvidia-smi, 100 ms"
+        else:
+            return None
+        if not self.sm:
+            return None
+        out = dict(sm_mhz=float(np.median(self.sm)), sm_max_mhz=float(max(self.mx)),
+                   reasons=sorted(self.reasons), samples=len(self.sm), source=src)
+        if self.err:
+            out["nvml_error"] = self.err
+        return out
 
 
 def max_over_ranks(value, device):
@@ -269,7 +330,7 @@ def run_gpu(args):
     torch.cuda.synchronize()
     if ws > 1:
         torch.distributed.barrier()
-    clk_p, clk_fh = start_clock_log()
+    clk = ClockSampler(local)
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -282,7 +343,7 @@ def run_gpu(args):
     torch.cuda.nvtx.range_pop()
     gpu_launches = dgfas.dgfas_kernel_launches() - k_before
     torch.cuda.synchronize()
-    clocks = stop_clock_log(clk_p, clk_fh, local)
+    clocks = clk.stop()
     ms = e0.elapsed_time(e1) / args.steps
     if ws > 1:
         ms = max_over_ranks(ms, dev)

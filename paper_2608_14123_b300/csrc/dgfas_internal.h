@@ -38,6 +38,7 @@ struct LevelView {
   const T* S;                 // [16][nsm][nsm]  S[v][row][col]
   const T* lam;               // [16][nsm]
   const T* W;                 // [16][nsm]
+  const uint4* Btc;           // [16][2][32] BF16 operand tiles S^T and S (tensor-core FD)
 };
 
 struct TransferView {
@@ -69,6 +70,7 @@ struct LevelHost {
   float *f_h = nullptr, *f_G = nullptr, *f_fW = nullptr, *f_fc = nullptr, *f_mu = nullptr,
         *f_mass = nullptr, *f_D = nullptr, *f_w = nullptr, *f_g = nullptr, *f_S = nullptr,
         *f_lam = nullptr, *f_W = nullptr, *f_x = nullptr;
+  uint4* d_Btc = nullptr;                  // BF16 FD operand tiles per variant
   double *d_I = nullptr, *d_P = nullptr;   // transfer from level-1 to this level
   // work vectors
   double *u = nullptr, *gv = nullptr, *r = nullptr, *ubar = nullptr, *t = nullptr;

@@ -6,6 +6,8 @@
 #include <string>
 #include <vector>
 
+#include <cuda_bf16.h>
+
 #include "dgfas_internal.h"
 #include "setup_host.h"
 
@@ -271,7 +273,32 @@ static int build_level(Ctx& c, const dgfas_level& in, const dgfas_params& prm, L
     V.nbr = H.d_nbr; V.nbr27 = H.d_nbr27; V.cls = H.d_cls; V.var = H.d_var;
     V.bx = bx_; V.Lhat = Lh_; V.h = h; V.G = G_; V.fW = fW_; V.fc = fc_; V.mu = mu_; V.mass = mass_; V.D = D_; V.w = w_;
     V.x = x_; V.g = g_; V.S = S_; V.lam = lam_; V.W = W_;
+    V.Btc = H.d_Btc;
   };
+  {
+    // tensor-core FD operand tiles, one pair per variant: tile 0 holds S^T
+    // (entry (n, k) = S[k][n]), tile 1 holds S (entry (n, k) = S[n][k]), both
+    // zero padded to 16 x 16 BF16 in the K-major no-swizzle layout (byte
+    // (n/8) 256 + (k/8) 128 + (n%8) 16 + (k%8) 2)
+    std::vector<__nv_bfloat16> tiles(16 * 2 * 256, __float2bfloat16(0.0f));
+    for (int v = 0; v < 16; ++v) {
+      const int nv = H.N + H.m * (((v >> 2) == 0) + ((v & 3) == 0));
+      for (int n = 0; n < nv; ++n)
+        for (int k = 0; k < nv; ++k) {
+          const size_t o = (size_t)((n >> 3) * 128 + (k >> 3) * 64 + (n & 7) * 8 + (k & 7));
+          const float st = (float)S[((size_t)v * nsm + k) * nsm + n];
+          const float sn = (float)S[((size_t)v * nsm + n) * nsm + k];
+          tiles[(size_t)(2 * v) * 256 + o] = __float2bfloat16(st);
+          tiles[(size_t)(2 * v + 1) * 256 + o] = __float2bfloat16(sn);
+        }
+    }
+    if (cudaMalloc((void**)&H.d_Btc, tiles.size() * sizeof(__nv_bfloat16)) != cudaSuccess) {
+      set_error("cudaMalloc failed in setup");
+      return DGFAS_ERR_OOM;
+    }
+    CK(cudaMemcpy(H.d_Btc, tiles.data(), tiles.size() * sizeof(__nv_bfloat16),
+                  cudaMemcpyHostToDevice));
+  }
   fill(H.v64, H.d_bx, H.d_Lhat, H.d_h, H.d_G, H.d_fW, H.d_fc, H.d_mu, H.d_mass, H.d_D, H.d_w, H.d_x, H.d_g, H.d_S,
        H.d_lam, H.d_W);
   fill(H.v32, H.f_bx, H.f_Lhat, H.f_h, H.f_G, H.f_fW, H.f_fc, H.f_mu, H.f_mass, H.f_D, H.f_w, H.f_x, H.f_g, H.f_S,
@@ -385,7 +412,7 @@ static int build_root(Ctx& c) {
 }
 
 static void free_level(LevelHost& H) {
-  void* ptrs[] = {H.d_bx, H.d_Lhat, H.f_bx, H.f_Lhat, H.d_nbr, H.d_nbr27, H.d_parent, H.d_octant, H.d_children, H.d_cls, H.d_var,
+  void* ptrs[] = {H.d_Btc, H.d_bx, H.d_Lhat, H.f_bx, H.f_Lhat, H.d_nbr, H.d_nbr27, H.d_parent, H.d_octant, H.d_children, H.d_cls, H.d_var,
                   H.d_h, H.d_G, H.d_fW, H.d_fc, H.d_mu, H.d_mass, H.d_D, H.d_w, H.d_g, H.d_S,
                   H.d_lam, H.d_W, H.d_x, H.f_h, H.f_G, H.f_fW, H.f_fc, H.f_mu, H.f_mass, H.f_D,
                   H.f_w, H.f_g, H.f_S, H.f_lam, H.f_W, H.f_x, H.d_I, H.d_P, H.u, H.gv, H.r,

@@ -193,6 +193,7 @@ struct FdTcSmem {
   unsigned char A[2][2][128 * 16 * 2];   // ping-pong A operand, two M = 128 tiles each
   unsigned char B[6][16 * 16 * 2];       // per direction: S^T (n = out, k = in) and S
   float lam[3][16], W[3][16];
+  int gmap[3][16];                       // patch position -> (neighbour offset + 1) << 8 | node, or -1
   uint64_t mbar;
   uint32_t tslot;
 };
@@ -284,33 +285,49 @@ __global__ void __launch_bounds__(128, 8) k_fd_tc(const LevelView<float> L, cons
   const uint32_t tmem = s.tslot;
   uint32_t phase = 0;
   bool alive = true;
+  int prev = -1;   // variant triple of the tables currently in shared memory
   for (int e = blockIdx.x; e < L.ne && alive; e += gridDim.x) {
     if (L.cls[e] == DGFAS_FROZEN) continue;
     __syncthreads();   // the previous element's patch store has read s.W
     const int v1 = L.var[3 * e], v2 = L.var[3 * e + 1], v3 = L.var[3 * e + 2];
-    const int vv[3] = {v1, v2, v3};
+    const int key = v1 | (v2 << 4) | (v3 << 8);
+    if (key != prev) {
+      // the per-variant tables (B operands S_d^T and S_d from the setup-time
+      // BF16 tiles, eigenvalues, weights, gather map) change only with the
+      // element's side variants: reloaded when the triple differs from the
+      // previous element's (the same for the whole CTA)
+      const int vv[3] = {v1, v2, v3};
+      for (int t = tid; t < 6 * 32; t += 128) {
+        const int slot = t >> 5, q = t & 31, d = slot >> 1, which = slot & 1;
+        reinterpret_cast<uint4*>(s.B[slot])[q] = L.Btc[(vv[d] * 2 + which) * 32 + q];
+      }
+      if (tid < 48) {
+        const int d = tid / 16, q = tid % 16, v = vv[d];
+        const int nd = N + m * (((v >> 2) == 0) + ((v & 3) == 0));
+        const bool in = q < nd;
+        s.lam[d][q] = in ? L.lam[v * nsm + q] : 1.0f;
+        s.W[d][q] = in ? L.W[v * nsm + q] : 0.0f;
+        int code = -1;
+        if (in) {
+          int a = q, o, ix;
+          if ((v >> 2) == 0 && a < m) {
+            o = -1;
+            ix = N - m + a;
+          } else {
+            if ((v >> 2) == 0) a -= m;
+            o = a < N ? 0 : 1;
+            ix = a < N ? a : a - N;
+          }
+          code = ((o + 1) << 8) | ix;
+        }
+        s.gmap[d][q] = code;
+      }
+      prev = key;
+      __syncthreads();
+    }
     const int n1 = N + m * (((v1 >> 2) == 0) + ((v1 & 3) == 0));
     const int n2 = N + m * (((v2 >> 2) == 0) + ((v2 & 3) == 0));
     const int n3 = N + m * (((v3 >> 2) == 0) + ((v3 & 3) == 0));
-    const int nn[3] = {n1, n2, n3};
-    // B operands: B[2d] = S_d^T as (n = out index, k = in index) -> entry S[k][n];
-    // B[2d+1] = S_d -> entry S[n][k]; zero padded to 16 x 16
-    for (int t = tid; t < 3 * 256; t += 128) {
-      const int d = t / 256, n = (t / 16) % 16, k = t % 16;
-      const int v = vv[d], nd = nn[d];
-      const float* S = L.S + (size_t)v * nsm * nsm;
-      const bool in = n < nd && k < nd;
-      const float st = in ? S[k * nsm + n] : 0.0f;
-      const float sn = in ? S[n * nsm + k] : 0.0f;
-      *reinterpret_cast<__nv_bfloat16*>(s.B[2 * d] + tile_off(n, k)) = __float2bfloat16(st);
-      *reinterpret_cast<__nv_bfloat16*>(s.B[2 * d + 1] + tile_off(n, k)) = __float2bfloat16(sn);
-    }
-    if (tid < 48) {
-      const int d = tid / 16, q = tid % 16;
-      const bool in = q < nn[d];
-      s.lam[d][q] = in ? L.lam[vv[d] * nsm + q] : 1.0f;
-      s.W[d][q] = in ? L.W[vv[d] * nsm + q] : 0.0f;
-    }
     // gather R_s r into A[0] (K-major): rows (c, b) = 16 c + b, K = a; each task
     // fills 8 consecutive a of one row with one 16-byte store
     for (int task = tid; task < 512; task += 128) {
@@ -318,23 +335,18 @@ __global__ void __launch_bounds__(128, 8) k_fd_tc(const LevelView<float> L, cons
       float vals[8];
 #pragma unroll
       for (int q = 0; q < 8; ++q) vals[q] = 0.0f;
-      if (b < n2 && c < n3) {
-        int oy, iy, oz, iz, bq = b, cq = c;
-        if ((v2 >> 2) == 0) { if (bq < m) { oy = -1; iy = N - m + bq; } else { bq -= m; oy = bq < N ? 0 : 1; iy = bq < N ? bq : bq - N; } }
-        else { oy = bq < N ? 0 : 1; iy = bq < N ? bq : bq - N; }
-        if ((v3 >> 2) == 0) { if (cq < m) { oz = -1; iz = N - m + cq; } else { cq -= m; oz = cq < N ? 0 : 1; iz = cq < N ? cq : cq - N; } }
-        else { oz = cq < N ? 0 : 1; iz = cq < N ? cq : cq - N; }
-        const int* nb = L.nbr27 + 27 * e + 3 * (oy + 1) + 9 * (oz + 1);
-        const int line = (iz * N + iy) * N;
+      const int my = s.gmap[1][b], mz = s.gmap[2][c];
+      if (my >= 0 && mz >= 0) {
+        const int* nb = L.nbr27 + 27 * e + 3 * (my >> 8) + 9 * (mz >> 8);
+        const int s0 = nb[0], s1 = nb[1], s2 = nb[2];
+        const int line = ((mz & 255) * N + (my & 255)) * N;
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
-          int aa = 8 * h + q;
-          if (aa >= n1) break;
-          int ox, ix;
-          if ((v1 >> 2) == 0) { if (aa < m) { ox = -1; ix = N - m + aa; } else { aa -= m; ox = aa < N ? 0 : 1; ix = aa < N ? aa : aa - N; } }
-          else { ox = aa < N ? 0 : 1; ix = aa < N ? aa : aa - N; }
-          const int src = nb[ox + 1];
-          if (src >= 0) vals[q] = r[(size_t)src * N3 + line + ix];
+          const int mx = s.gmap[0][8 * h + q];
+          if (mx < 0) continue;
+          const int o = mx >> 8;
+          const int src = o == 0 ? s0 : (o == 1 ? s1 : s2);
+          if (src >= 0) vals[q] = r[(size_t)src * N3 + line + (mx & 255)];
         }
       }
       unsigned char* t = s.A[0][0] + (row >> 7) * (128 * 16 * 2);
@@ -367,7 +379,7 @@ __global__ void __launch_bounds__(128, 8) k_fd_tc(const LevelView<float> L, cons
       tc_read1(tmem, t, x);
       const float d0 = g0 + g1 * s.lam[0][rr >> 4] + g2 * s.lam[1][rr & 15];
 #pragma unroll
-      for (int q = 0; q < 16; ++q) x[q] = x[q] / (d0 + g3 * s.lam[2][q]);
+      for (int q = 0; q < 16; ++q) x[q] = __fdividef(x[q], d0 + g3 * s.lam[2][q]);
       st_k(s.A[1][0], rr, x);
     }
     // 4: S3 along c: rows (a', b') -> x c''; write rows (a', c''), K = b' (MN-major)

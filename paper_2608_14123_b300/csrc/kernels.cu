@@ -634,99 +634,118 @@ int launch_fd(Ctx& c, int l, int prec, const void* r) {
 }
 
 // ============================================================================ combine
-// One CTA per element (deterministic pull, no atomics): each own node sums the
-// weighted patch entries of every subdomain that covers it, i.e. its own
-// element's and those of the up to 26 neighbours whose overlap layers reach it
-// (at most 2 candidates per direction, 8 in all).  The neighbour ids and their
-// left-side flags are staged in shared memory once per element.  Frozen
-// elements are left untouched (ADD) or zeroed (!ADD).
-template <typename T, bool ADD, typename TO>
-__global__ void k_combine(const LevelView<T> L, const T* __restrict__ patch,
-                          TO* __restrict__ u) {
-  __shared__ int s_nb[27];
-  __shared__ unsigned char s_ml[27][3];
-  const int e = blockIdx.x;
-  const int N = L.N, N3 = N * N * N, m = L.m, nsm = L.nsm;
-  const size_t NS3 = (size_t)nsm * nsm * nsm;
-  const bool frozen = L.cls[e] == DGFAS_FROZEN;
-  if (threadIdx.x < 27) {
-    int src = L.nbr27[27 * e + threadIdx.x];
-    if (src >= 0 && L.cls[src] == DGFAS_FROZEN) src = -1;
-    s_nb[threadIdx.x] = src;
-    for (int d = 0; d < 3; ++d) {
-      const int v = src >= 0 ? L.var[3 * src + d] : 0;
-      // bit 0..1: left-layer count flag, bit 2: left side interior, bit 3: right side interior
-      s_ml[threadIdx.x][d] = (unsigned char)(((v >> 2) == 0 ? m : 0) | (((v >> 2) == 0) << 6) |
-                                             (((v & 3) == 0) << 7));
+// Deterministic pull (no atomics): each own node sums the weighted patch
+// entries of every subdomain that covers it, i.e. its own element's and those
+// of the up to 26 neighbours whose overlap layers reach it (at most 2
+// candidates per direction, 8 in all).  The patch position of own node
+// (i, j, k) inside neighbour slot (ox, oy, oz)'s patch is (i, j, k) plus a
+// per-slot shift, so each slot is reduced once per element to one offset
+// (src NS^3 + shift, or -1 when the slot contributes nothing: no neighbour, a
+// frozen one, or a boundary side that carries no layers) staged in shared
+// memory; per node only the candidate test and the load remain.  Elements of
+// small degree are packed several to a CTA.  Frozen elements are left
+// untouched (ADD) or zeroed (!ADD).
+template <int N, typename T, bool ADD, typename TO>
+__global__ void __launch_bounds__(256) k_combine(const LevelView<T> L, const T* __restrict__ patch,
+                                                  TO* __restrict__ u) {
+  constexpr int N3 = N * N * N;
+  constexpr int EPB = N3 >= 256 ? 1 : 256 / N3;
+  __shared__ long long s_off[EPB][27];
+  const int m = L.m, nsm = L.nsm;
+  const long long NS3 = (long long)nsm * nsm * nsm;
+  const int e0 = blockIdx.x * EPB;
+  for (int t = threadIdx.x; t < EPB * 27; t += blockDim.x) {
+    const int el = t / 27, slot = t % 27, e = e0 + el;
+    long long off = -1;
+    if (e < L.ne) {
+      const int src = L.nbr27[27 * e + slot];
+      if (src >= 0 && L.cls[src] != DGFAS_FROZEN) {
+        const int o[3] = {slot % 3 - 1, (slot / 3) % 3 - 1, slot / 9 - 1};
+        int shift[3];
+        bool reach = true;
+        for (int d = 0; d < 3; ++d) {
+          const int v = L.var[3 * src + d];
+          const bool left_i = (v >> 2) == 0, right_i = (v & 3) == 0;
+          const int ml = left_i ? m : 0;   // the neighbour's left layers
+          // the neighbour's patch reaches this element only through interior sides
+          if ((o[d] < 0 && !right_i) || (o[d] > 0 && !left_i)) reach = false;
+          shift[d] = o[d] == 0 ? ml : (o[d] < 0 ? ml + N : -(N - m));
+        }
+        if (reach) off = (long long)src * NS3 + ((long long)shift[2] * nsm + shift[1]) * nsm + shift[0];
+      }
     }
+    s_off[el][slot] = off;
   }
   __syncthreads();
-  const size_t eo = (size_t)e * N3;
-  for (int n = threadIdx.x; n < N3; n += blockDim.x) {
-    if (frozen) {
-      if (!ADD) u[eo + n] = TO(0);
+  for (int t = threadIdx.x; t < EPB * N3; t += blockDim.x) {
+    const int el = EPB == 1 ? 0 : t / N3, n = EPB == 1 ? t : t % N3;
+    const int e = e0 + el;
+    if (e >= L.ne) continue;
+    const size_t g = (size_t)e * N3 + n;
+    if (L.cls[e] == DGFAS_FROZEN) {
+      if (!ADD) u[g] = TO(0);
       continue;
     }
     const int i = n % N, j = (n / N) % N, k = n / (N * N);
-    const int lx = i < m ? -1 : 0, hx = i >= N - m ? 1 : 0;
-    const int ly = j < m ? -1 : 0, hy = j >= N - m ? 1 : 0;
-    const int lz = k < m ? -1 : 0, hz = k >= N - m ? 1 : 0;
+    const int lx = i < m ? 0 : 1, hx = i >= N - m ? 2 : 1;
+    const int ly = j < m ? 0 : 1, hy = j >= N - m ? 2 : 1;
+    const int lz = k < m ? 0 : 1, hz = k >= N - m ? 2 : 1;
+    const long long loc = ((long long)k * nsm + j) * nsm + i;
     T s = T(0);   // accumulated in the smoother precision
     for (int oz = lz; oz <= hz; ++oz)
       for (int oy = ly; oy <= hy; ++oy)
         for (int ox = lx; ox <= hx; ++ox) {
-          const int slot = (ox + 1) + 3 * (oy + 1) + 9 * (oz + 1);
-          const int src = s_nb[slot];
-          if (src < 0) continue;
-          const int fx = s_ml[slot][0], fy = s_ml[slot][1], fz = s_ml[slot][2];
-          // the neighbour's patch reaches this element only through interior sides
-          if ((ox < 0 && !(fx & 128)) || (ox > 0 && !(fx & 64)) || (oy < 0 && !(fy & 128)) ||
-              (oy > 0 && !(fy & 64)) || (oz < 0 && !(fz & 128)) || (oz > 0 && !(fz & 64)))
-            continue;
-          const int mx = fx & 63, my = fy & 63, mz = fz & 63;
-          const int px = ox == 0 ? i + mx : (ox < 0 ? mx + N + i : i - (N - m));
-          const int py = oy == 0 ? j + my : (oy < 0 ? my + N + j : j - (N - m));
-          const int pz = oz == 0 ? k + mz : (oz < 0 ? mz + N + k : k - (N - m));
-          s += patch[(size_t)src * NS3 + ((size_t)pz * nsm + py) * nsm + px];
+          const long long off = s_off[el][ox + 3 * oy + 9 * oz];
+          if (off >= 0) s += patch[off + loc];
         }
-    if (ADD) u[eo + n] += (TO)s;
-    else u[eo + n] = (TO)s;
+    if (ADD) u[g] += (TO)s;
+    else u[g] = (TO)s;
   }
 }
 
-static int combine_threads(int N) {
-  const int N3 = N * N * N;
-  return N3 >= 256 ? 256 : ((N3 + 31) / 32) * 32;
+template <typename T, bool ADD, typename TO>
+static int combine_launch(const LevelView<T>& L, int N, const T* patch, TO* u, cudaStream_t st) {
+  auto go = [&](auto kern, int n3) {
+    const int epb = n3 >= 256 ? 1 : 256 / n3;
+    const int bs = n3 >= 256 ? 256 : ((epb * n3 + 31) / 32) * 32;
+    kern<<<(unsigned)((L.ne + epb - 1) / epb), bs, 0, st>>>(L, patch, u);
+  };
+  switch (N) {
+    case 2: go(k_combine<2, T, ADD, TO>, 8); break;
+    case 3: go(k_combine<3, T, ADD, TO>, 27); break;
+    case 4: go(k_combine<4, T, ADD, TO>, 64); break;
+    case 5: go(k_combine<5, T, ADD, TO>, 125); break;
+    case 6: go(k_combine<6, T, ADD, TO>, 216); break;
+    case 7: go(k_combine<7, T, ADD, TO>, 343); break;
+    case 8: go(k_combine<8, T, ADD, TO>, 512); break;
+    case 9: go(k_combine<9, T, ADD, TO>, 729); break;
+    case 10: go(k_combine<10, T, ADD, TO>, 1000); break;
+    case 11: go(k_combine<11, T, ADD, TO>, 1331); break;
+    default:
+      set_error("combine: unsupported N");
+      return DGFAS_ERR_UNSUPPORTED;
+  }
+  ++g_kernels;
+  CK(cudaGetLastError());
+  return DGFAS_OK;
 }
 
 // delta += sum of the weighted patches (delta in the smoother precision)
 int launch_combine(Ctx& c, int l, int prec, void* delta) {
   LevelHost& H = c.lv[l];
-  const int bs = combine_threads(H.N);
-  const unsigned grd = (unsigned)H.ne;
   if (prec == DGFAS_FP64)
-    k_combine<double, true, double><<<grd, bs, 0, c.stream>>>(H.v64, (const double*)c.patch,
-                                                              (double*)delta);
-  else
-    k_combine<float, true, float><<<grd, bs, 0, c.stream>>>(H.v32, (const float*)c.patch,
-                                                            (float*)delta);
-  ++g_kernels;
-  CK(cudaGetLastError());
-  return DGFAS_OK;
+    return combine_launch<double, true, double>(H.v64, H.N, (const double*)c.patch,
+                                                (double*)delta, c.stream);
+  return combine_launch<float, true, float>(H.v32, H.N, (const float*)c.patch, (float*)delta,
+                                            c.stream);
 }
 
 // z = sum of the weighted patches (FP64 output, SCG preconditioner)
 int launch_combine_to(Ctx& c, int l, int prec, double* z) {
   LevelHost& H = c.lv[l];
-  const int bs = combine_threads(H.N);
-  const unsigned grd = (unsigned)H.ne;
   if (prec == DGFAS_FP64)
-    k_combine<double, false, double><<<grd, bs, 0, c.stream>>>(H.v64, (const double*)c.patch, z);
-  else
-    k_combine<float, false, double><<<grd, bs, 0, c.stream>>>(H.v32, (const float*)c.patch, z);
-  ++g_kernels;
-  CK(cudaGetLastError());
-  return DGFAS_OK;
+    return combine_launch<double, false, double>(H.v64, H.N, (const double*)c.patch, z, c.stream);
+  return combine_launch<float, false, double>(H.v32, H.N, (const float*)c.patch, z, c.stream);
 }
 
 // ============================================================================ transfers
@@ -1187,9 +1206,5 @@ int launch_fd_patch(Ctx& c, int l, const double* r, double* patch) {
 
 int launch_combine_patch(Ctx& c, int l, const double* patch, double* u) {
   LevelHost& H = c.lv[l];
-  k_combine<double, true, double><<<(unsigned)H.ne, combine_threads(H.N), 0, c.stream>>>(
-      H.v64, patch, u);
-  ++g_kernels;
-  CK(cudaGetLastError());
-  return DGFAS_OK;
+  return combine_launch<double, true, double>(H.v64, H.N, patch, u, c.stream);
 }
