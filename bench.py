@@ -63,12 +63,60 @@ def fd_flops_per_dof(N, m):
     return 12.0 * ns ** 4 / N ** 3
 
 
+class _CtypesNvml:
+    """The four NVML queries the clock sampler needs, through ctypes on the
+    driver's libnvidia-ml (read-only queries; nothing is set)."""
+
+    def __init__(self):
+        import ctypes
+        self.ct = ctypes
+        self.lib = ctypes.CDLL("libnvidia-ml.so.1")
+        rc = self.lib.nvmlInit_v2()
+        if rc != 0:
+            raise RuntimeError(f"nvmlInit_v2 returned {rc}")
+        self.reasons_fn = getattr(self.lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            self.lib.nvmlDeviceGetCurrentClocksThrottleReasons
+
+    def _handle(self, fn, arg):
+        h = self.ct.c_void_p()
+        rc = fn(arg, self.ct.byref(h))
+        if rc != 0:
+            raise RuntimeError(f"NVML handle lookup returned {rc}")
+        return h
+
+    def handle_by_uuid(self, uuid):
+        return self._handle(self.lib.nvmlDeviceGetHandleByUUID, uuid.encode())
+
+    def handle_by_index(self, i):
+        return self._handle(self.lib.nvmlDeviceGetHandleByIndex_v2, self.ct.c_uint(i))
+
+    def _clock(self, fn, h):
+        v = self.ct.c_uint()
+        rc = fn(h, self.ct.c_int(1), self.ct.byref(v))   # NVML_CLOCK_SM = 1
+        if rc != 0:
+            raise RuntimeError(f"NVML clock query returned {rc}")
+        return v.value
+
+    def sm_clock(self, h):
+        return self._clock(self.lib.nvmlDeviceGetClockInfo, h)
+
+    def max_sm_clock(self, h):
+        return self._clock(self.lib.nvmlDeviceGetMaxClockInfo, h)
+
+    def event_reasons(self, h):
+        v = self.ct.c_ulonglong()
+        rc = self.reasons_fn(h, self.ct.byref(v))
+        if rc != 0:
+            raise RuntimeError(f"NVML reasons query returned {rc}")
+        return v.value
+
+
 class ClockSampler:
     """SM clocks and clock-event reasons sampled DURING the timed region.
 
     NVML is polled from a background thread every 5 ms (the timed region of the
-    default run is well under a second, too short for nvidia-smi's 200 ms
-    loop); nvidia-smi is the fallback when NVML cannot be loaded."""
+    default run is well under a second, too short for nvidia-smi's loop);
+    nvidia-smi is the fallback when the NVML library cannot be loaded."""
     # clock-event reason bits (nvml.h): sw power cap, hw slowdown,
     # sw thermal slowdown, hw thermal slowdown
     BITS = {"sw_power_cap": 0x4, "hw_slowdown": 0x8, "sw_thermal_slowdown": 0x20,
@@ -80,17 +128,13 @@ class ClockSampler:
         self.thread = self.proc = self.fh = None
         self.err = None
         try:
-            import pynvml as nv
-            nv.nvmlInit()
-            self.nv = nv
+            self.nv = _CtypesNvml()
             import torch
-            h = None
             try:
                 uuid = str(torch.cuda.get_device_properties(device).uuid)
-                h = nv.nvmlDeviceGetHandleByUUID(uuid if uuid.startswith("GPU-") else "GPU-" + uuid)
-            except Exception:
-                h = nv.nvmlDeviceGetHandleByIndex(device)
-            self.h = h
+                self.h = self.nv.handle_by_uuid(uuid if uuid.startswith("GPU-") else "GPU-" + uuid)
+            except Exception:   # noqa: BLE001 - fall back to the ordinal
+                self.h = self.nv.handle_by_index(device)
             self.thread = threading.Thread(target=self._poll, daemon=True)
             self.thread.start()
         except Exception as ex:   # noqa: BLE001 - any NVML failure falls back to nvidia-smi
@@ -100,18 +144,16 @@ class ClockSampler:
 
     def _poll(self):
         nv = self.nv
-        get_r = getattr(nv, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
-            nv.nvmlDeviceGetCurrentClocksThrottleReasons
-        mx = nv.nvmlDeviceGetMaxClockInfo(self.h, nv.NVML_CLOCK_SM)
+        mx = nv.max_sm_clock(self.h)
         while not self.stop_ev.is_set():
             try:
-                self.sm.append(float(nv.nvmlDeviceGetClockInfo(self.h, nv.NVML_CLOCK_SM)))
+                self.sm.append(float(nv.sm_clock(self.h)))
                 self.mx.append(float(mx))
-                bits = get_r(self.h)
+                bits = nv.event_reasons(self.h)
                 for nm, b in self.BITS.items():
                     if bits & b:
                         self.reasons.add(nm)
-            except Exception:
+            except Exception:   # noqa: BLE001 - a failed sample is skipped
                 pass
             self.stop_ev.wait(0.005)
 
@@ -132,7 +174,7 @@ class ClockSampler:
         if self.thread is not None:
             self.stop_ev.set()
             self.thread.join(timeout=2)
-            src = "nvml, 5 ms"
+            src = "nvml (ctypes), 5 ms"
         elif self.proc is not None:
             self.proc.terminate()
             try:

@@ -43,6 +43,7 @@ struct LevelView {
 
 struct TransferView {
   int nef, nec, Nf, Nc, h;    // h: 1 for h-refinement (8 children)
+  int cs;                     // p-transfer whose matrices are centrosymmetric (even-odd kernels)
   const int* parent;          // [nef]
   const int* octant;          // [nef]
   const int* children;        // [nec][8] (-1 none); p-refinement: children[E][0] = E
@@ -120,6 +121,7 @@ int launch_fd_tc(Ctx& c, int l, const float* r);
 int launch_combine(Ctx& c, int l, int prec, void* delta);
 int launch_add_delta(Ctx& c, long long n, int prec, const void* d, double* u);
 int launch_combine_to(Ctx& c, int l, int prec, double* z);
+int prepare_transfer(const TransferView& T);          // set-up: kernel attributes
 int launch_project(Ctx& c, int l, const double* uf);   // lv[l-1].u = ubar = P uf
 int launch_restrict(Ctx& c, int l, const double* rf, double* rc);
 int launch_prolong(Ctx& c, int l, double* uf, int prec, void* delta);  // delta = I (u_c - ubar)

@@ -1,5 +1,6 @@
 // C ABI of the hot path: level setup, operator, smoother, FAS V-cycle (Alg. 2)
 // and solve with crossover smoothing; CUDA-graph replay of the cycle body.
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -349,6 +350,24 @@ static int build_transfer(LevelHost& C, LevelHost& F) {
   RET(upload(&F.d_parent, F.parent));
   RET(upload(&F.d_octant, F.octant));
   F.tr.nef = F.ne; F.tr.nec = C.ne; F.tr.Nf = Nf; F.tr.Nc = Nc; F.tr.h = h ? 1 : 0;
+  // a p-transfer between symmetric GLL node sets has centrosymmetric matrices
+  // (M[n-1-r][m-1-c] = M[r][c]); the even-odd transfer kernels rely on it
+  F.tr.cs = 0;
+  if (!h) {
+    double dev = 0.0, big = 0.0;
+    for (int r = 0; r < Nf; ++r)
+      for (int q = 0; q < Nc; ++q) {
+        dev = std::max(dev, std::fabs(I[r * Nc + q] - I[(Nf - 1 - r) * Nc + (Nc - 1 - q)]));
+        big = std::max(big, std::fabs(I[r * Nc + q]));
+      }
+    for (int r = 0; r < Nc; ++r)
+      for (int q = 0; q < Nf; ++q) {
+        dev = std::max(dev, std::fabs(P[r * Nf + q] - P[(Nc - 1 - r) * Nf + (Nf - 1 - q)]));
+        big = std::max(big, std::fabs(P[r * Nf + q]));
+      }
+    F.tr.cs = dev <= 1e-13 * big ? 1 : 0;
+  }
+  RET(prepare_transfer(F.tr));
   F.tr.parent = F.d_parent; F.tr.octant = F.d_octant; F.tr.children = F.d_children;
   F.tr.clsf = F.d_cls; F.tr.I = F.d_I; F.tr.P = F.d_P;
   return DGFAS_OK;

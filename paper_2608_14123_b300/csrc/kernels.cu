@@ -326,6 +326,180 @@ __global__ void k_apply_box(const LevelView<T> L, const T* __restrict__ bx,
   }
 }
 
+// Line form of the box operator with even-odd products.  Per direction d a
+// thread owns one node line (a, b) along d and does everything that direction
+// contributes to it:
+//   volume   g_d w_a w_b (Lhat x)_l,
+//   faces    at both ends of the line the flux mu W [[u]] - {{grad u . n}}
+//            (own derivative dm from the line, the neighbour's dp from its
+//            line in global memory) and the lifting -1/2 [[u]] c_n D[end][l]
+//            (or the Dirichlet forms 2 mu W u - q_m and -u c_n).
+// GLL symmetry makes Lhat centrosymmetric and D anti-centrosymmetric
+// (D[N-1-i][N-1-l] = -D[i][l]), so with e_r = x_r + x_{N-1-r},
+// o_r = x_r - x_{N-1-r} every product splits into an even and an odd half of
+// about N^2/4 multiply-adds each, and the two end derivatives and the two
+// liftings share one pass through the row D[0].  The three passes add into
+// one accumulator in shared memory; the z pass writes out = b + alpha R.
+template <int N, typename T>
+struct BoxEo {
+  static constexpr int H = N / 2, HC = (N + 1) / 2;
+  T le[HC][H > 0 ? H : 1];   // (Lhat[r][q] + Lhat[r][N-1-q]) / 2, r < HC
+  T lo[H > 0 ? H : 1][H > 0 ? H : 1];   // (Lhat[r][q] - Lhat[r][N-1-q]) / 2, r < H
+  T lm[HC];                  // Lhat[r][H] (odd N)
+  T de[HC], dO[H > 0 ? H : 1];   // (D0_r +- D0_{N-1-r}) / 2; de[H] = D0_H for odd N
+  T D0[N], DN[N];            // rows D[0] and D[N-1]
+  T w[N];
+};
+
+template <int N, typename T, typename TU, typename TB, typename TO>
+__global__ void k_apply_box_eo(const LevelView<T> L, const T* __restrict__ bx,
+                               const T* __restrict__ Lhat, const TU* __restrict__ u,
+                               const TB* __restrict__ b, TO* __restrict__ out, T alpha) {
+  constexpr int N2 = N * N, N3 = N * N * N, H = N / 2, HC = (N + 1) / 2;
+  __shared__ BoxEo<N, T> M;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int team = threadIdx.y, tid = threadIdx.y * blockDim.x + threadIdx.x;
+  const int nth = blockDim.x * blockDim.y;
+  T* us = reinterpret_cast<T*>(smem_raw) + (size_t)team * 2 * N3;
+  T* R = us + N3;
+  for (int t = tid; t < HC * N; t += nth) {
+    const int r = t / N, q = t % N;
+    if (q < H) {
+      M.le[r][q] = T(0.5) * (Lhat[r * N + q] + Lhat[r * N + N - 1 - q]);
+      if (r < H) M.lo[r][q] = T(0.5) * (Lhat[r * N + q] - Lhat[r * N + N - 1 - q]);
+    } else if ((N & 1) && q == H) {
+      M.lm[r] = Lhat[r * N + H];
+    }
+  }
+  for (int t = tid; t < N; t += nth) {
+    M.D0[t] = L.D[t];
+    M.DN[t] = L.D[(N - 1) * N + t];
+    M.w[t] = L.w[t];
+    if (t < H) {
+      M.de[t] = T(0.5) * (L.D[t] + L.D[N - 1 - t]);
+      M.dO[t] = T(0.5) * (L.D[t] - L.D[N - 1 - t]);
+    } else if ((N & 1) && t == H) {
+      M.de[t] = L.D[t];
+    }
+  }
+  const int e = blockIdx.x * blockDim.y + team;
+  const bool valid = e < L.ne && threadIdx.x < N2;
+  const size_t eo = (size_t)e * N3;
+  if (e < L.ne)
+    for (int t = threadIdx.x; t < N3; t += blockDim.x) us[t] = (T)u[eo + t];
+  __syncthreads();
+  const int a = threadIdx.x % N, bb = threadIdx.x / N;
+  T kap = 0;
+  if (valid) kap = L.kappa * T(0.125) * L.h[3 * e] * L.h[3 * e + 1] * L.h[3 * e + 2];
+  const T wab = M.w[a] * M.w[bb];
+#pragma unroll 1
+  for (int d = 0; d < 3; ++d) {
+    // node (line l) of this thread's line: x: (k,j,i) = (bb,a,l); y: (bb,l,a); z: (l,bb,a)
+    const int st = d == 0 ? 1 : (d == 1 ? N : N2);
+    const int base = d == 0 ? (bb * N + a) * N : (d == 1 ? bb * N2 + a : bb * N + a);
+    T y[N];
+    if (valid) {
+      const T gd = bx[6 * e + d], afd = bx[6 * e + 3 + d];
+      T x[N];
+#pragma unroll
+      for (int l = 0; l < N; ++l) x[l] = us[base + l * st];
+      T ev[H > 0 ? H : 1], od[H > 0 ? H : 1];
+#pragma unroll
+      for (int r = 0; r < H; ++r) {
+        ev[r] = x[r] + x[N - 1 - r];
+        od[r] = x[r] - x[N - 1 - r];
+      }
+      // end derivatives of the own line: dm0 = D[0] x, dm1 = D[N-1] x
+      T A = (N & 1) ? M.de[H] * x[H] : T(0), B = 0;
+#pragma unroll
+      for (int r = 0; r < H; ++r) {
+        A += M.de[r] * ev[r];
+        B += M.dO[r] * od[r];
+      }
+      const T dm[2] = {A + B, B - A};
+      // faces at both ends
+      T flux[2] = {0, 0}, lift[2] = {0, 0};
+#pragma unroll
+      for (int sd = 0; sd < 2; ++sd) {
+        const int f = 2 * d + sd;
+        const int nb = L.nbr[6 * e + f];
+        if (nb == -2) continue;   // Neumann: no face term
+        const T sgn = sd ? T(1) : T(-1);
+        const T cn = sgn * gd * wab;   // nu W n . grad xi_d
+        const T Wf = afd * wab;        // nu * surface weight
+        const T mu = L.mu[6 * e + f];
+        const T um = x[sd ? N - 1 : 0];
+        const T qm = cn * dm[sd];
+        if (nb >= 0) {
+          // the neighbour's line through the shared face node; its face end is the opposite one
+          const TU* z = u + (size_t)nb * N3 + base;
+          const T* Dp = sd ? M.D0 : M.DN;
+          T dp = 0, up = 0;
+#pragma unroll
+          for (int l = 0; l < N; ++l) {
+            const T zl = (T)z[l * st];
+            dp += Dp[l] * zl;
+            if (l == (sd ? 0 : N - 1)) up = zl;
+          }
+          const T qp = -sgn * bx[6 * nb + d] * wab * dp;
+          const T jump = um - up;
+          flux[sd] = mu * Wf * jump - T(0.5) * (qm - qp);
+          lift[sd] = T(-0.5) * jump * cn;
+        } else {
+          flux[sd] = T(2) * mu * Wf * um - qm;
+          lift[sd] = -um * cn;
+        }
+      }
+      // volume + lifting: y = g_d w_a w_b Lhat x + D[0]^T lift0 + D[N-1]^T lift1
+      const T cd = gd * wab;
+      const T Ls = lift[0] - lift[1], La = lift[0] + lift[1];
+#pragma unroll
+      for (int r = 0; r < HC; ++r) {
+        T E = (N & 1) ? M.lm[r] * x[H] : T(0);
+#pragma unroll
+        for (int q = 0; q < H; ++q) E += M.le[r][q] * ev[q];
+        E = cd * E + M.de[r] * Ls;
+        if (r < H) {
+          T O = 0;
+#pragma unroll
+          for (int q = 0; q < H; ++q) O += M.lo[r][q] * od[q];
+          O = cd * O + M.dO[r] * La;
+          y[r] = E + O;
+          y[N - 1 - r] = E - O;
+        } else {
+          y[r] = E;
+        }
+      }
+      y[0] += flux[0];
+      y[N - 1] += flux[1];
+      if (d == 0 && kap != T(0)) {
+        const T kl = kap * wab;
+#pragma unroll
+        for (int l = 0; l < N; ++l) y[l] += kl * M.w[l] * x[l];
+      }
+    }
+    if (d < 2) {
+      if (valid) {
+#pragma unroll
+        for (int l = 0; l < N; ++l) {
+          const int n = base + l * st;
+          R[n] = d == 0 ? y[l] : R[n] + y[l];
+        }
+      }
+      __syncthreads();
+    } else if (valid) {
+      const bool frozen = L.cls[e] == DGFAS_FROZEN;
+#pragma unroll
+      for (int l = 0; l < N; ++l) {
+        const int n = base + l * st;
+        T o = alpha * (R[n] + y[l]);
+        if (b) o += (T)b[eo + n];
+        out[eo + n] = frozen ? TO(0) : (TO)o;
+      }
+    }
+  }
+}
+
 template <int N, typename T, typename TU, typename TB, typename TO>
 static int apply_N(const LevelView<T>& L, const TU* u, const TB* b, TO* out, T alpha,
                    cudaStream_t st) {
@@ -340,16 +514,18 @@ static int apply_N(const LevelView<T>& L, const TU* u, const TB* b, TO* out, T a
   // the attribute is set once per instantiation (never inside a graph capture)
   if (L.box) {
     int epb2 = (128 + N2 - 1) / N2;
-    size_t smem2 = (2 * N2 + 16 + (size_t)3 * N3 * epb2) * sizeof(T);
-    while (epb2 > 1 && smem2 > 100 * 1024) {
+    size_t smem2 = (size_t)2 * N3 * epb2 * sizeof(T);
+    while (epb2 > 1 && smem2 > 96 * 1024) {
       --epb2;
-      smem2 = (2 * N2 + 16 + (size_t)3 * N3 * epb2) * sizeof(T);
+      smem2 = (size_t)2 * N3 * epb2 * sizeof(T);
     }
-    auto kf = k_apply_box<N, T, TU, TB, TO>;
-    static bool attr = false;
-    if (!attr) {
-      CK(cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024));
-      attr = true;
+    auto kf = k_apply_box_eo<N, T, TU, TB, TO>;
+    if (smem2 > 40 * 1024) {
+      static bool attr = false;
+      if (!attr) {
+        CK(cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024));
+        attr = true;
+      }
     }
     dim3 blk2(N2, epb2), grd2((L.ne + epb2 - 1) / epb2);
     kf<<<grd2, blk2, smem2, st>>>(L, L.bx, L.Lhat, u, b, out, alpha);
@@ -869,10 +1045,208 @@ static size_t transfer_smem(const TransferView& T) {
   return n * sizeof(double);
 }
 
+// ---------------------------------------------------------------- p-transfers
+// Between two GLL node sets of one element (p-coarsening) the matrices M
+// [NO][NI] of P, I^T and I are centrosymmetric (M[NO-1-r][NI-1-q] = M[r][q]),
+// so each 1D product y = M x splits into an even and an odd half:
+// e_q = x_q + x_{NI-1-q}, o_q = x_q - x_{NI-1-q} (q < NI/2), x_mid;
+// E_r = sum_q Me[r][q] e_q + Mm[r] x_mid, O_r = sum_q Mo[r][q] o_q with
+// Me = (M[r][q] + M[r][NI-1-q])/2, Mo = (M[r][q] - M[r][NI-1-q])/2, and
+// y_r = E_r + O_r, y_{NO-1-r} = E_r - O_r.  That takes about half the FP64
+// multiply-adds of the plain product, the bound of these kernels on a part
+// whose FP64 rate is 1/64 of its FP32 rate.  Each thread owns whole lines
+// (loaded once into registers); EPB elements share a CTA so that all three
+// passes keep the warps busy.
+template <int NI, int NO>
+struct EoMat {
+  static constexpr int HI = NI / 2, HO = NO / 2, HOC = (NO + 1) / 2;
+  double e[HOC][HI > 0 ? HI : 1], o[HO > 0 ? HO : 1][HI > 0 ? HI : 1], m[HOC];
+};
+
+template <int NI, int NO>
+__device__ __forceinline__ void eo_line(const EoMat<NI, NO>& M, const double (&x)[NI],
+                                        double (&y)[NO]) {
+  constexpr int HI = NI / 2, HO = NO / 2, HOC = (NO + 1) / 2;
+  double ev[HI > 0 ? HI : 1], od[HI > 0 ? HI : 1];
+#pragma unroll
+  for (int q = 0; q < HI; ++q) {
+    ev[q] = x[q] + x[NI - 1 - q];
+    od[q] = x[q] - x[NI - 1 - q];
+  }
+#pragma unroll
+  for (int r = 0; r < HOC; ++r) {
+    double E = (NI & 1) ? M.m[r] * x[HI] : 0.0;
+#pragma unroll
+    for (int q = 0; q < HI; ++q) E += M.e[r][q] * ev[q];
+    if (r < HO) {
+      double O = 0.0;
+#pragma unroll
+      for (int q = 0; q < HI; ++q) O += M.o[r][q] * od[q];
+      y[r] = E + O;
+      y[NO - 1 - r] = E - O;
+    } else {
+      y[r] = E;   // middle row of an odd NO (its odd part vanishes)
+    }
+  }
+}
+
+// MODE 0: projection P (fine -> coarse, writes xc and its copy ubar);
+// MODE 1: restriction I^T (fine -> coarse); MODE 2: correction prolongation
+// I (coarse -> fine) with the frozen update, as k_prolong.
+template <int NI, int NO, int MODE, typename TD>
+__global__ void __launch_bounds__(128) k_ptransfer(const TransferView T, const double* __restrict__ x0,
+                                                   const double* __restrict__ x1,
+                                                   double* __restrict__ y0, double* __restrict__ y1,
+                                                   TD* __restrict__ delta) {
+  constexpr int EPB = 4, NI3 = NI * NI * NI, NO3 = NO * NO * NO;
+  constexpr int HI = NI / 2, HO = NO / 2, HOC = (NO + 1) / 2;
+  extern __shared__ __align__(16) double tsm[];
+  __shared__ EoMat<NI, NO> M;
+  __shared__ int s_src[EPB], s_dst[EPB], s_frz[EPB];
+  double* X = tsm;                          // [EPB][NI^3]
+  double* T1 = X + EPB * NI3;               // [EPB][NI][NI][NO]
+  double* T2 = T1 + EPB * NI * NI * NO;     // [EPB][NI][NO][NO]
+  const int tid = threadIdx.x;
+  // matrix M [NO][NI]: P (side 0), I^T or I
+  for (int t = tid; t < HOC * NI; t += blockDim.x) {
+    const int r = t / NI, q = t % NI;
+    auto Mat = [&](int rr, int qq) {
+      return MODE == 0 ? T.P[rr * NI + qq] : (MODE == 1 ? T.I[qq * NO + rr] : T.I[rr * NI + qq]);
+    };
+    if (q < HI) {
+      M.e[r][q] = 0.5 * (Mat(r, q) + Mat(r, NI - 1 - q));
+      if (r < HO) M.o[r][q] = 0.5 * (Mat(r, q) - Mat(r, NI - 1 - q));
+    } else if ((NI & 1) && q == HI) {
+      M.m[r] = Mat(r, HI);
+    }
+  }
+  const int n_out = MODE == 2 ? T.nef : T.nec;
+  const int b0 = blockIdx.x * EPB;
+  if (tid < EPB) {
+    const int E = b0 + tid;
+    int src = -1, frz = 0;
+    if (E < n_out) {
+      if (MODE == 2) {
+        src = T.parent[E];
+        frz = T.clsf[E] == DGFAS_FROZEN;
+      } else {
+        const int ch = T.children[8 * E];
+        src = (ch < 0 || T.clsf[ch] == DGFAS_FROZEN) ? -1 : ch;
+      }
+    }
+    s_src[tid] = src;
+    s_dst[tid] = E < n_out ? E : -1;
+    s_frz[tid] = frz;
+  }
+  __syncthreads();
+  for (int t = tid; t < EPB * NI3; t += blockDim.x) {
+    const int el = t / NI3, n = t % NI3, src = s_src[el];
+    double v = 0.0;
+    if (src >= 0) {
+      v = x0[(size_t)src * NI3 + n];
+      if (MODE == 2 && !s_frz[el]) v -= x1[(size_t)src * NI3 + n];
+    }
+    X[t] = v;
+  }
+  __syncthreads();
+  // pass 1: contract i along lines (k, j)
+  for (int t = tid; t < EPB * NI * NI; t += blockDim.x) {
+    const int el = t / (NI * NI), line = t % (NI * NI);
+    double x[NI], y[NO];
+#pragma unroll
+    for (int q = 0; q < NI; ++q) x[q] = X[el * NI3 + line * NI + q];
+    eo_line<NI, NO>(M, x, y);
+#pragma unroll
+    for (int a = 0; a < NO; ++a) T1[(el * NI * NI + line) * NO + a] = y[a];
+  }
+  __syncthreads();
+  // pass 2: contract j along lines (k, a)
+  for (int t = tid; t < EPB * NI * NO; t += blockDim.x) {
+    const int el = t / (NI * NO), k = (t / NO) % NI, a = t % NO;
+    double x[NI], y[NO];
+#pragma unroll
+    for (int q = 0; q < NI; ++q) x[q] = T1[((el * NI + k) * NI + q) * NO + a];
+    eo_line<NI, NO>(M, x, y);
+#pragma unroll
+    for (int b = 0; b < NO; ++b) T2[((el * NI + k) * NO + b) * NO + a] = y[b];
+  }
+  __syncthreads();
+  // pass 3: contract k along lines (b, a), straight to global memory
+  for (int t = tid; t < EPB * NO * NO; t += blockDim.x) {
+    const int el = t / (NO * NO), ba = t % (NO * NO);
+    if (s_src[el] < 0) continue;   // no active child: coarse values stay as they are
+    double x[NI], y[NO];
+#pragma unroll
+    for (int q = 0; q < NI; ++q) x[q] = T2[(el * NI + q) * NO * NO + ba];
+    eo_line<NI, NO>(M, x, y);
+    const size_t o = (size_t)s_dst[el] * NO3 + ba;
+#pragma unroll
+    for (int c = 0; c < NO; ++c) {
+      const size_t g = o + (size_t)c * NO * NO;
+      if (MODE == 0) {
+        y0[g] = y[c];
+        y1[g] = y[c];
+      } else if (MODE == 1) {
+        y0[g] = y[c];
+      } else if (s_frz[el]) {
+        y0[g] = y[c];
+        delta[g] = TD(0);
+      } else {
+        delta[g] = (TD)y[c];
+      }
+    }
+  }
+}
+
+template <int NI, int NO>
+static size_t ptransfer_smem() {
+  return (size_t)4 * (NI * NI * NI + NI * NI * NO + NI * NO * NO) * sizeof(double);
+}
+
+// launches the even-odd kernel for the supported (fine, coarse) node counts
+// (p_c = p_f / 2); returns false when the pair has no instantiation
+// (prepare = true: only raise the kernel's shared-memory limit, done at set-up
+// so that no attribute call falls inside a graph capture)
+template <int MODE, typename TD>
+static bool ptransfer_launch(const TransferView& T, const double* x0, const double* x1, double* y0,
+                             double* y1, TD* delta, cudaStream_t st, bool prepare = false) {
+  if (T.h || !T.cs) return false;
+  const int n_out = MODE == 2 ? T.nef : T.nec;
+  const unsigned grid = (unsigned)((n_out + 3) / 4);
+  auto go = [&](auto kern, size_t smem) {
+    if (prepare) {
+      if (smem > 48 * 1024)
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      return;
+    }
+    kern<<<grid, 128, smem, st>>>(T, x0, x1, y0, y1, delta);
+  };
+#define DGFAS_PT(NF, NC)                                                                  \
+  if (T.Nf == NF && T.Nc == NC) {                                                         \
+    if (MODE == 2) go(k_ptransfer<NC, NF, MODE, TD>, ptransfer_smem<NC, NF>());          \
+    else go(k_ptransfer<NF, NC, MODE, TD>, ptransfer_smem<NF, NC>());                    \
+    return true;                                                                          \
+  }
+  DGFAS_PT(3, 2) DGFAS_PT(4, 2) DGFAS_PT(5, 3) DGFAS_PT(6, 3) DGFAS_PT(7, 4)
+  DGFAS_PT(8, 4) DGFAS_PT(9, 5) DGFAS_PT(10, 5) DGFAS_PT(11, 6)
+#undef DGFAS_PT
+  return false;
+}
+
+int prepare_transfer(const TransferView& T) {
+  ptransfer_launch<0, double>(T, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, true);
+  ptransfer_launch<1, double>(T, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, true);
+  ptransfer_launch<2, double>(T, nullptr, nullptr, nullptr, nullptr, (double*)nullptr, nullptr, true);
+  ptransfer_launch<2, float>(T, nullptr, nullptr, nullptr, nullptr, (float*)nullptr, nullptr, true);
+  CK(cudaGetLastError());
+  return DGFAS_OK;
+}
+
 int launch_project(Ctx& c, int l, const double* uf) {
   LevelHost& F = c.lv[l];
   LevelHost& C = c.lv[l - 1];
-  k_gather_children<false><<<C.ne, 256, transfer_smem(F.tr), c.stream>>>(F.tr, uf, C.u, C.ubar);
+  if (!ptransfer_launch<0, double>(F.tr, uf, nullptr, C.u, C.ubar, nullptr, c.stream))
+    k_gather_children<false><<<C.ne, 256, transfer_smem(F.tr), c.stream>>>(F.tr, uf, C.u, C.ubar);
   ++g_kernels;
   CK(cudaGetLastError());
   return DGFAS_OK;
@@ -881,7 +1255,8 @@ int launch_project(Ctx& c, int l, const double* uf) {
 int launch_restrict(Ctx& c, int l, const double* rf, double* rc) {
   LevelHost& F = c.lv[l];
   LevelHost& C = c.lv[l - 1];
-  k_gather_children<true><<<C.ne, 256, transfer_smem(F.tr), c.stream>>>(F.tr, rf, rc, nullptr);
+  if (!ptransfer_launch<1, double>(F.tr, rf, nullptr, rc, nullptr, nullptr, c.stream))
+    k_gather_children<true><<<C.ne, 256, transfer_smem(F.tr), c.stream>>>(F.tr, rf, rc, nullptr);
   ++g_kernels;
   CK(cudaGetLastError());
   return DGFAS_OK;
@@ -890,10 +1265,13 @@ int launch_restrict(Ctx& c, int l, const double* rf, double* rc) {
 int launch_prolong(Ctx& c, int l, double* uf, int prec, void* delta) {
   LevelHost& F = c.lv[l];
   LevelHost& C = c.lv[l - 1];
-  if (prec == DGFAS_FP64)
-    k_prolong<double><<<F.ne, 128, transfer_smem(F.tr), c.stream>>>(F.tr, C.u, C.ubar, uf, (double*)delta);
-  else
-    k_prolong<float><<<F.ne, 128, transfer_smem(F.tr), c.stream>>>(F.tr, C.u, C.ubar, uf, (float*)delta);
+  if (prec == DGFAS_FP64) {
+    if (!ptransfer_launch<2, double>(F.tr, C.u, C.ubar, uf, nullptr, (double*)delta, c.stream))
+      k_prolong<double><<<F.ne, 128, transfer_smem(F.tr), c.stream>>>(F.tr, C.u, C.ubar, uf, (double*)delta);
+  } else {
+    if (!ptransfer_launch<2, float>(F.tr, C.u, C.ubar, uf, nullptr, (float*)delta, c.stream))
+      k_prolong<float><<<F.ne, 128, transfer_smem(F.tr), c.stream>>>(F.tr, C.u, C.ubar, uf, (float*)delta);
+  }
   ++g_kernels;
   CK(cudaGetLastError());
   return DGFAS_OK;
