@@ -189,18 +189,24 @@ extern "C" int dgfas_tc_selftest(float* out_host, int* timeout_host) {
 }
 
 // ---------------------------------------------------------------- FD on tensor cores
+// operand tile geometry: K-major tiles (gather, D^-1 step) use LBO 128 / SBO 256
+// in the first 4096 B; MN-major tiles use a padded M stride
+#define TC_MN_SBO 144
+#define TC_MN_LBO (16 * TC_MN_SBO)
+#define TC_TILE (2 * TC_MN_LBO + 16)
 struct FdTcSmem {
-  unsigned char A[2][2][128 * 16 * 2];   // ping-pong A operand, two M = 128 tiles each
+  unsigned char A[2][2][TC_TILE];        // ping-pong A operand, two M = 128 tiles each
   unsigned char B[6][16 * 16 * 2];       // per direction: S^T (n = out, k = in) and S
   float lam[3][16], W[3][16];
   int gmap[3][16];                       // patch position -> (neighbour offset + 1) << 8 | node, or -1
+  int nb[27];                            // the element's 27-neighbourhood
   uint64_t mbar;
   uint32_t tslot;
 };
 
 __device__ __forceinline__ void put_bf16(unsigned char* tile2, int row, int k, float v) {
   // row in [0, 256): tile row / 128, K-major
-  *reinterpret_cast<__nv_bfloat16*>(tile2 + (row >> 7) * (128 * 16 * 2) + tile_off(row & 127, k)) =
+  *reinterpret_cast<__nv_bfloat16*>(tile2 + (row >> 7) * TC_TILE + tile_off(row & 127, k)) =
       __float2bfloat16(v);
 }
 
@@ -216,20 +222,22 @@ __device__ __forceinline__ uint4 pack8(const float* v) {
 }
 
 // 16 values of rows m0..m0+15 (m0 % 16 == 0) at column k of an MN-major tile
-// pair: (m, k) at byte (m/8)*128 + (k/8)*2048 + (k%8)*16 + (m%8)*2 of tile m/128
-// (descriptor: leading byte offset 2048 = next core matrix along K, stride
-// byte offset 128 = next core matrix along M)
+// pair: (m, k) at byte (m/8)*TC_MN_SBO + (k/8)*TC_MN_LBO + (k%8)*16 + (m%8)*2
+// of tile m/128 (descriptor: leading byte offset = next core matrix along K,
+// stride byte offset = next core matrix along M).  The core matrices along M
+// are 144 B apart instead of 128 so that lanes writing different M groups at
+// one k land in different banks.
 __device__ __forceinline__ void st_mn(unsigned char* tile2, int m0, int k, const float* v) {
-  unsigned char* t = tile2 + (m0 >> 7) * (128 * 16 * 2);
+  unsigned char* t = tile2 + (m0 >> 7) * TC_TILE;
   const int ml = m0 & 127;
-  const uint32_t off = (uint32_t)((ml >> 3) * 128 + (k >> 3) * 2048 + (k & 7) * 16);
+  const uint32_t off = (uint32_t)((ml >> 3) * TC_MN_SBO + (k >> 3) * TC_MN_LBO + (k & 7) * 16);
   *reinterpret_cast<uint4*>(t + off) = pack8(v);
-  *reinterpret_cast<uint4*>(t + off + 128) = pack8(v + 8);
+  *reinterpret_cast<uint4*>(t + off + TC_MN_SBO) = pack8(v + 8);
 }
 
 // 16 values k = 0..15 of row m of a K-major tile pair
 __device__ __forceinline__ void st_k(unsigned char* tile2, int m, const float* v) {
-  unsigned char* t = tile2 + (m >> 7) * (128 * 16 * 2);
+  unsigned char* t = tile2 + (m >> 7) * TC_TILE;
   const int ml = m & 127;
   const uint32_t off = (uint32_t)((ml >> 3) * 256 + (ml & 7) * 16);
   *reinterpret_cast<uint4*>(t + off) = pack8(v);
@@ -247,15 +255,18 @@ __device__ __forceinline__ bool tc_step(FdTcSmem& s, int ain, int bsel, bool mn,
   if (threadIdx.x == 0) {
     const uint32_t idesc = idesc_bf16(128, 16) | (mn ? (1u << 15) : 0u);
     const uint64_t bd = sdesc(smem_u32(s.B[bsel]), 128, 256);
-    const uint32_t lbo = mn ? 2048 : 128, sbo = mn ? 128 : 256;
+    const uint32_t lbo = mn ? TC_MN_LBO : 128, sbo = mn ? TC_MN_SBO : 256;
     mma_bf16(tmem, sdesc(smem_u32(s.A[ain][0]), lbo, sbo), bd, idesc, 0);
     mma_bf16(tmem + 16, sdesc(smem_u32(s.A[ain][1]), lbo, sbo), bd, idesc, 0);
     commit(smem_u32(&s.mbar));
   }
-  const bool ok = mbar_wait(smem_u32(&s.mbar), phase);
+  // only the issuing thread polls the barrier; the others wait at the CTA
+  // barrier (no issue slots spent spinning) and order their TMEM reads after it
+  const bool ok0 = threadIdx.x == 0 ? mbar_wait(smem_u32(&s.mbar), phase) : true;
   phase ^= 1u;
+  const bool ok = __syncthreads_and(ok0 ? 1 : 0) != 0;
   fence_after();
-  return __syncthreads_and(ok ? 1 : 0) != 0;
+  return ok;
 }
 
 // this thread's TMEM row of tile `t` (row 128 t + 32 w + lane), 16 FP32 values
@@ -291,6 +302,7 @@ __global__ void __launch_bounds__(128, 8) k_fd_tc(const LevelView<float> L, cons
     __syncthreads();   // the previous element's patch store has read s.W
     const int v1 = L.var[3 * e], v2 = L.var[3 * e + 1], v3 = L.var[3 * e + 2];
     const int key = v1 | (v2 << 4) | (v3 << 8);
+    if (tid < 27) s.nb[tid] = L.nbr27[27 * e + tid];
     if (key != prev) {
       // the per-variant tables (B operands S_d^T and S_d from the setup-time
       // BF16 tiles, eigenvalues, weights, gather map) change only with the
@@ -323,8 +335,8 @@ __global__ void __launch_bounds__(128, 8) k_fd_tc(const LevelView<float> L, cons
         s.gmap[d][q] = code;
       }
       prev = key;
-      __syncthreads();
     }
+    __syncthreads();
     const int n1 = N + m * (((v1 >> 2) == 0) + ((v1 & 3) == 0));
     const int n2 = N + m * (((v2 >> 2) == 0) + ((v2 & 3) == 0));
     const int n3 = N + m * (((v3 >> 2) == 0) + ((v3 & 3) == 0));
@@ -337,7 +349,7 @@ __global__ void __launch_bounds__(128, 8) k_fd_tc(const LevelView<float> L, cons
       for (int q = 0; q < 8; ++q) vals[q] = 0.0f;
       const int my = s.gmap[1][b], mz = s.gmap[2][c];
       if (my >= 0 && mz >= 0) {
-        const int* nb = L.nbr27 + 27 * e + 3 * (my >> 8) + 9 * (mz >> 8);
+        const int* nb = s.nb + 3 * (my >> 8) + 9 * (mz >> 8);
         const int s0 = nb[0], s1 = nb[1], s2 = nb[2];
         const int line = ((mz & 255) * N + (my & 255)) * N;
 #pragma unroll
@@ -349,7 +361,7 @@ __global__ void __launch_bounds__(128, 8) k_fd_tc(const LevelView<float> L, cons
           if (src >= 0) vals[q] = r[(size_t)src * N3 + line + (mx & 255)];
         }
       }
-      unsigned char* t = s.A[0][0] + (row >> 7) * (128 * 16 * 2);
+      unsigned char* t = s.A[0][0] + (row >> 7) * TC_TILE;
       const int ml = row & 127;
       *reinterpret_cast<uint4*>(t + (ml >> 3) * 256 + (ml & 7) * 16 + h * 128) = pack8(vals);
     }
