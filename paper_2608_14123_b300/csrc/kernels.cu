@@ -203,129 +203,10 @@ __global__ void k_apply(const LevelView<T> L, const TU* __restrict__ u,
   }
 }
 
-// Axis-aligned box elements: the volume term is the Kronecker form
-// sum_d g_d (W x W x Lhat_d) u with Lhat = D^T W D (exact for boxes), so each
-// node costs 3N FMA instead of the 6N of gradient plus transposed gradient.
-// Faces add the flux at the face node and the lifting -c [[u]]/2 (or -c u_D)
-// along the node's normal line through the Lhat-free derivative row D.
-// bx[e] = {g_1, g_2, g_3, nu*|face_1|/4-factor a_1, a_2, a_3} with
-// g_d = nu h_j h_k / (2 h_d) and a_d = nu h_j h_k / 4.
-template <int N, typename T, typename TU, typename TB, typename TO>
-__global__ void k_apply_box(const LevelView<T> L, const T* __restrict__ bx,
-                            const T* __restrict__ Lhat, const TU* __restrict__ u,
-                            const TB* __restrict__ b, TO* __restrict__ out, T alpha) {
-  constexpr int N2 = N * N, N3 = N * N * N;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* sD = reinterpret_cast<T*>(smem_raw);
-  T* sL = sD + N2;
-  T* sw = sL + N2;
-  T* base = sw + 16;
-  const int team = threadIdx.y;
-  T* us = base + team * 3 * N3;
-  T* nb = us + N3;
-  T* R = nb + N3;
-  const int tx = threadIdx.x % N, ty = threadIdx.x / N;
-  const int e = blockIdx.x * blockDim.y + team;
-  const bool valid = e < L.ne;
-  const int tid = threadIdx.y * blockDim.x + threadIdx.x, nth = blockDim.x * blockDim.y;
-  for (int t = tid; t < N2; t += nth) {
-    sD[t] = L.D[t];
-    sL[t] = Lhat[t];
-  }
-  for (int t = tid; t < N; t += nth) sw[t] = L.w[t];
-  const size_t eo = (size_t)e * N3;
-  if (valid)
-    for (int k = 0; k < N; ++k) us[(k * N + ty) * N + tx] = (T)u[eo + (k * N + ty) * N + tx];
-  __syncthreads();
-  T g[3] = {0, 0, 0}, af[3] = {0, 0, 0};
-  if (valid) {
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      g[d] = bx[6 * e + d];
-      af[d] = bx[6 * e + 3 + d];
-    }
-    const T kap = L.kappa * T(0.125) * L.h[3 * e] * L.h[3 * e + 1] * L.h[3 * e + 2];
-    // per-thread constants of the k loop (the FP64 pipe is the bound: keep the
-    // per-node work at 3N FMA plus five operations)
-    const T wi = sw[tx], wj = sw[ty];
-    const T c0 = g[0] * wj, c1 = g[1] * wi, c2 = g[2] * wi * wj, ck = kap * wi * wj;
-    T lx[N], ly[N];
-#pragma unroll
-    for (int l = 0; l < N; ++l) {
-      lx[l] = sL[tx * N + l];
-      ly[l] = sL[ty * N + l];
-    }
-    for (int k = 0; k < N; ++k) {
-      T s0 = 0, s1 = 0, s2 = 0;
-#pragma unroll
-      for (int l = 0; l < N; ++l) {
-        s0 += lx[l] * us[(k * N + ty) * N + l];
-        s1 += ly[l] * us[(k * N + l) * N + tx];
-        s2 += sL[k * N + l] * us[(l * N + ty) * N + tx];
-      }
-      const int n = (k * N + ty) * N + tx;
-      const T wk = sw[k];
-      T rv = (c0 * wk) * s0 + (c1 * wk) * s1 + c2 * s2;
-      if (kap != T(0)) rv += ck * wk * us[n];
-      R[n] = rv;
-    }
-  }
-  __syncthreads();
-  for (int f = 0; f < 6; ++f) {
-    const int d = f >> 1, side = f & 1;
-    const int nbid = valid ? L.nbr[6 * e + f] : -2;
-    if (nbid >= 0) {
-      const size_t no = (size_t)nbid * N3;
-      for (int k = 0; k < N; ++k) nb[(k * N + ty) * N + tx] = (T)u[no + (k * N + ty) * N + tx];
-    }
-    __syncthreads();
-    if (valid && nbid != -2) {
-      const int a = tx, bb = ty;
-      const int end = side ? N - 1 : 0, endp = N - 1 - end;
-      // strides of the normal line and the face node offset
-      const int st = d == 0 ? 1 : (d == 1 ? N : N2);
-      const int fo = d == 0 ? (bb * N + a) * N : (d == 1 ? bb * N2 + a : bb * N + a);
-      const T wab = sw[a] * sw[bb];
-      const T sgn = side ? T(1) : T(-1);
-      const T cn = sgn * g[d] * wab;            // W n . grad xi_d (times nu)
-      const T W = af[d] * wab;                  // nu * surface weight
-      const T mu = L.mu[6 * e + f];
-      T dm = 0, dp = 0;
-#pragma unroll
-      for (int l = 0; l < N; ++l) {
-        dm += sD[end * N + l] * us[fo + l * st];
-        dp += sD[endp * N + l] * nb[fo + l * st];
-      }
-      const T um = us[fo + end * st];
-      const T qm = cn * dm;
-      T flux, lift;
-      if (nbid >= 0) {
-        const T gp = bx[6 * nbid + d];
-        const T qp = -sgn * gp * wab * dp;
-        const T jump = um - nb[fo + endp * st];
-        flux = mu * W * jump - T(0.5) * (qm - qp);
-        lift = T(-0.5) * jump * cn;
-      } else {
-        flux = T(2) * mu * W * um - qm;
-        lift = -um * cn;
-      }
-      R[fo + end * st] += flux;
-      // lifting: sum over the normal line of D[end][l] * lift
-#pragma unroll
-      for (int l = 0; l < N; ++l) R[fo + l * st] += sD[end * N + l] * lift;
-    }
-    __syncthreads();
-  }
-  if (!valid) return;
-  const bool frozen = L.cls[e] == DGFAS_FROZEN;
-  for (int k = 0; k < N; ++k) {
-    const int n = (k * N + ty) * N + tx;
-    T o = alpha * R[n];
-    if (b) o += (T)b[eo + n];
-    out[eo + n] = frozen ? TO(0) : (TO)o;
-  }
-}
-
+// Axis-aligned box elements: the volume term is the exact Kronecker form
+// sum_d g_d (W x W x Lhat_d) u with Lhat = D^T W D; bx[e] = {g_1, g_2, g_3,
+// a_1, a_2, a_3} with g_d = nu h_j h_k / (2 h_d) and a_d = nu h_j h_k / 4 (the
+// surface weight factor of the faces normal to d).
 // Line form of the box operator with even-odd products.  Per direction d a
 // thread owns one node line (a, b) along d and does everything that direction
 // contributes to it:
