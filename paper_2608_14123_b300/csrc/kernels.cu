@@ -232,8 +232,9 @@ struct BoxEo {
   T w[N];
 };
 
+// (FP32 instantiations are latency bound: registers capped for 4 CTAs per SM)
 template <int N, typename T, typename TU, typename TB, typename TO>
-__global__ void k_apply_box_eo(const LevelView<T> L, const T* __restrict__ bx,
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 1) k_apply_box_eo(const LevelView<T> L, const T* __restrict__ bx,
                                const T* __restrict__ Lhat, const TU* __restrict__ u,
                                const TB* __restrict__ b, TO* __restrict__ out, T alpha) {
   constexpr int N2 = N * N, N3 = N * N * N, H = N / 2, HC = (N + 1) / 2;
@@ -938,17 +939,17 @@ static size_t transfer_smem(const TransferView& T) {
 // whose FP64 rate is 1/64 of its FP32 rate.  Each thread owns whole lines
 // (loaded once into registers); EPB elements share a CTA so that all three
 // passes keep the warps busy.
-template <int NI, int NO>
+template <int NI, int NO, typename TA>
 struct EoMat {
   static constexpr int HI = NI / 2, HO = NO / 2, HOC = (NO + 1) / 2;
-  double e[HOC][HI > 0 ? HI : 1], o[HO > 0 ? HO : 1][HI > 0 ? HI : 1], m[HOC];
+  TA e[HOC][HI > 0 ? HI : 1], o[HO > 0 ? HO : 1][HI > 0 ? HI : 1], m[HOC];
 };
 
-template <int NI, int NO>
-__device__ __forceinline__ void eo_line(const EoMat<NI, NO>& M, const double (&x)[NI],
-                                        double (&y)[NO]) {
+template <int NI, int NO, typename TA>
+__device__ __forceinline__ void eo_line(const EoMat<NI, NO, TA>& M, const TA (&x)[NI],
+                                        TA (&y)[NO]) {
   constexpr int HI = NI / 2, HO = NO / 2, HOC = (NO + 1) / 2;
-  double ev[HI > 0 ? HI : 1], od[HI > 0 ? HI : 1];
+  TA ev[HI > 0 ? HI : 1], od[HI > 0 ? HI : 1];
 #pragma unroll
   for (int q = 0; q < HI; ++q) {
     ev[q] = x[q] + x[NI - 1 - q];
@@ -956,11 +957,11 @@ __device__ __forceinline__ void eo_line(const EoMat<NI, NO>& M, const double (&x
   }
 #pragma unroll
   for (int r = 0; r < HOC; ++r) {
-    double E = (NI & 1) ? M.m[r] * x[HI] : 0.0;
+    TA E = (NI & 1) ? M.m[r] * x[HI] : TA(0);
 #pragma unroll
     for (int q = 0; q < HI; ++q) E += M.e[r][q] * ev[q];
     if (r < HO) {
-      double O = 0.0;
+      TA O = TA(0);
 #pragma unroll
       for (int q = 0; q < HI; ++q) O += M.o[r][q] * od[q];
       y[r] = E + O;
@@ -973,20 +974,24 @@ __device__ __forceinline__ void eo_line(const EoMat<NI, NO>& M, const double (&x
 
 // MODE 0: projection P (fine -> coarse, writes xc and its copy ubar);
 // MODE 1: restriction I^T (fine -> coarse); MODE 2: correction prolongation
-// I (coarse -> fine) with the frozen update, as k_prolong.
-template <int NI, int NO, int MODE, typename TD>
+// I (coarse -> fine) with the frozen update, as k_prolong.  TA is the
+// arithmetic type: FP64, except for the correction prolongation of a
+// mixed-precision smoother on a level without frozen elements, whose result
+// is the smoother's FP32 starting correction (u_c - ubar is still formed in
+// FP64).
+template <int NI, int NO, int MODE, typename TD, typename TA>
 __global__ void __launch_bounds__(128) k_ptransfer(const TransferView T, const double* __restrict__ x0,
                                                    const double* __restrict__ x1,
                                                    double* __restrict__ y0, double* __restrict__ y1,
                                                    TD* __restrict__ delta) {
   constexpr int EPB = 4, NI3 = NI * NI * NI, NO3 = NO * NO * NO;
   constexpr int HI = NI / 2, HO = NO / 2, HOC = (NO + 1) / 2;
-  extern __shared__ __align__(16) double tsm[];
-  __shared__ EoMat<NI, NO> M;
+  extern __shared__ __align__(16) unsigned char tsm_raw[];
+  __shared__ EoMat<NI, NO, TA> M;
   __shared__ int s_src[EPB], s_dst[EPB], s_frz[EPB];
-  double* X = tsm;                          // [EPB][NI^3]
-  double* T1 = X + EPB * NI3;               // [EPB][NI][NI][NO]
-  double* T2 = T1 + EPB * NI * NI * NO;     // [EPB][NI][NO][NO]
+  TA* X = reinterpret_cast<TA*>(tsm_raw);   // [EPB][NI^3]
+  TA* T1 = X + EPB * NI3;                   // [EPB][NI][NI][NO]
+  TA* T2 = T1 + EPB * NI * NI * NO;         // [EPB][NI][NO][NO]
   const int tid = threadIdx.x;
   // matrix M [NO][NI]: P (side 0), I^T or I
   for (int t = tid; t < HOC * NI; t += blockDim.x) {
@@ -995,10 +1000,10 @@ __global__ void __launch_bounds__(128) k_ptransfer(const TransferView T, const d
       return MODE == 0 ? T.P[rr * NI + qq] : (MODE == 1 ? T.I[qq * NO + rr] : T.I[rr * NI + qq]);
     };
     if (q < HI) {
-      M.e[r][q] = 0.5 * (Mat(r, q) + Mat(r, NI - 1 - q));
-      if (r < HO) M.o[r][q] = 0.5 * (Mat(r, q) - Mat(r, NI - 1 - q));
+      M.e[r][q] = (TA)(0.5 * (Mat(r, q) + Mat(r, NI - 1 - q)));
+      if (r < HO) M.o[r][q] = (TA)(0.5 * (Mat(r, q) - Mat(r, NI - 1 - q)));
     } else if ((NI & 1) && q == HI) {
-      M.m[r] = Mat(r, HI);
+      M.m[r] = (TA)Mat(r, HI);
     }
   }
   const int n_out = MODE == 2 ? T.nef : T.nec;
@@ -1027,16 +1032,16 @@ __global__ void __launch_bounds__(128) k_ptransfer(const TransferView T, const d
       v = x0[(size_t)src * NI3 + n];
       if (MODE == 2 && !s_frz[el]) v -= x1[(size_t)src * NI3 + n];
     }
-    X[t] = v;
+    X[t] = (TA)v;
   }
   __syncthreads();
   // pass 1: contract i along lines (k, j)
   for (int t = tid; t < EPB * NI * NI; t += blockDim.x) {
     const int el = t / (NI * NI), line = t % (NI * NI);
-    double x[NI], y[NO];
+    TA x[NI], y[NO];
 #pragma unroll
     for (int q = 0; q < NI; ++q) x[q] = X[el * NI3 + line * NI + q];
-    eo_line<NI, NO>(M, x, y);
+    eo_line<NI, NO, TA>(M, x, y);
 #pragma unroll
     for (int a = 0; a < NO; ++a) T1[(el * NI * NI + line) * NO + a] = y[a];
   }
@@ -1044,10 +1049,10 @@ __global__ void __launch_bounds__(128) k_ptransfer(const TransferView T, const d
   // pass 2: contract j along lines (k, a)
   for (int t = tid; t < EPB * NI * NO; t += blockDim.x) {
     const int el = t / (NI * NO), k = (t / NO) % NI, a = t % NO;
-    double x[NI], y[NO];
+    TA x[NI], y[NO];
 #pragma unroll
     for (int q = 0; q < NI; ++q) x[q] = T1[((el * NI + k) * NI + q) * NO + a];
-    eo_line<NI, NO>(M, x, y);
+    eo_line<NI, NO, TA>(M, x, y);
 #pragma unroll
     for (int b = 0; b < NO; ++b) T2[((el * NI + k) * NO + b) * NO + a] = y[b];
   }
@@ -1056,21 +1061,21 @@ __global__ void __launch_bounds__(128) k_ptransfer(const TransferView T, const d
   for (int t = tid; t < EPB * NO * NO; t += blockDim.x) {
     const int el = t / (NO * NO), ba = t % (NO * NO);
     if (s_src[el] < 0) continue;   // no active child: coarse values stay as they are
-    double x[NI], y[NO];
+    TA x[NI], y[NO];
 #pragma unroll
     for (int q = 0; q < NI; ++q) x[q] = T2[(el * NI + q) * NO * NO + ba];
-    eo_line<NI, NO>(M, x, y);
+    eo_line<NI, NO, TA>(M, x, y);
     const size_t o = (size_t)s_dst[el] * NO3 + ba;
 #pragma unroll
     for (int c = 0; c < NO; ++c) {
       const size_t g = o + (size_t)c * NO * NO;
       if (MODE == 0) {
-        y0[g] = y[c];
-        y1[g] = y[c];
+        y0[g] = (double)y[c];
+        y1[g] = (double)y[c];
       } else if (MODE == 1) {
-        y0[g] = y[c];
+        y0[g] = (double)y[c];
       } else if (s_frz[el]) {
-        y0[g] = y[c];
+        y0[g] = (double)y[c];
         delta[g] = TD(0);
       } else {
         delta[g] = (TD)y[c];
@@ -1079,16 +1084,16 @@ __global__ void __launch_bounds__(128) k_ptransfer(const TransferView T, const d
   }
 }
 
-template <int NI, int NO>
+template <int NI, int NO, typename TA>
 static size_t ptransfer_smem() {
-  return (size_t)4 * (NI * NI * NI + NI * NI * NO + NI * NO * NO) * sizeof(double);
+  return (size_t)4 * (NI * NI * NI + NI * NI * NO + NI * NO * NO) * sizeof(TA);
 }
 
 // launches the even-odd kernel for the supported (fine, coarse) node counts
 // (p_c = p_f / 2); returns false when the pair has no instantiation
 // (prepare = true: only raise the kernel's shared-memory limit, done at set-up
 // so that no attribute call falls inside a graph capture)
-template <int MODE, typename TD>
+template <int MODE, typename TD, typename TA = double>
 static bool ptransfer_launch(const TransferView& T, const double* x0, const double* x1, double* y0,
                              double* y1, TD* delta, cudaStream_t st, bool prepare = false) {
   if (T.h || !T.cs) return false;
@@ -1104,8 +1109,8 @@ static bool ptransfer_launch(const TransferView& T, const double* x0, const doub
   };
 #define DGFAS_PT(NF, NC)                                                                  \
   if (T.Nf == NF && T.Nc == NC) {                                                         \
-    if (MODE == 2) go(k_ptransfer<NC, NF, MODE, TD>, ptransfer_smem<NC, NF>());          \
-    else go(k_ptransfer<NF, NC, MODE, TD>, ptransfer_smem<NF, NC>());                    \
+    if (MODE == 2) go(k_ptransfer<NC, NF, MODE, TD, TA>, ptransfer_smem<NC, NF, TA>());  \
+    else go(k_ptransfer<NF, NC, MODE, TD, TA>, ptransfer_smem<NF, NC, TA>());            \
     return true;                                                                          \
   }
   DGFAS_PT(3, 2) DGFAS_PT(4, 2) DGFAS_PT(5, 3) DGFAS_PT(6, 3) DGFAS_PT(7, 4)
@@ -1119,6 +1124,8 @@ int prepare_transfer(const TransferView& T) {
   ptransfer_launch<1, double>(T, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, true);
   ptransfer_launch<2, double>(T, nullptr, nullptr, nullptr, nullptr, (double*)nullptr, nullptr, true);
   ptransfer_launch<2, float>(T, nullptr, nullptr, nullptr, nullptr, (float*)nullptr, nullptr, true);
+  ptransfer_launch<2, float, float>(T, nullptr, nullptr, nullptr, nullptr, (float*)nullptr, nullptr,
+                                    true);
   CK(cudaGetLastError());
   return DGFAS_OK;
 }
@@ -1150,7 +1157,12 @@ int launch_prolong(Ctx& c, int l, double* uf, int prec, void* delta) {
     if (!ptransfer_launch<2, double>(F.tr, C.u, C.ubar, uf, nullptr, (double*)delta, c.stream))
       k_prolong<double><<<F.ne, 128, transfer_smem(F.tr), c.stream>>>(F.tr, C.u, C.ubar, uf, (double*)delta);
   } else {
-    if (!ptransfer_launch<2, float>(F.tr, C.u, C.ubar, uf, nullptr, (float*)delta, c.stream))
+    // FP32 arithmetic for the smoother's starting correction unless frozen
+    // elements take their values from this prolongation
+    const bool done = F.has_frozen
+        ? ptransfer_launch<2, float, double>(F.tr, C.u, C.ubar, uf, nullptr, (float*)delta, c.stream)
+        : ptransfer_launch<2, float, float>(F.tr, C.u, C.ubar, uf, nullptr, (float*)delta, c.stream);
+    if (!done)
       k_prolong<float><<<F.ne, 128, transfer_smem(F.tr), c.stream>>>(F.tr, C.u, C.ubar, uf, (float*)delta);
   }
   ++g_kernels;
