@@ -203,6 +203,8 @@ struct FdTcSmem {
   uint64_t mbar;
   uint32_t tslot;
 };
+// the operand buffers double as the staging area of one FP32 patch (<= 16^3)
+static_assert(sizeof(((FdTcSmem*)nullptr)->A) >= 16 * 16 * 16 * sizeof(float), "patch staging");
 
 __device__ __forceinline__ void put_bf16(unsigned char* tile2, int row, int k, float v) {
   // row in [0, 256): tile row / 128, K-major
@@ -340,30 +342,35 @@ __global__ void __launch_bounds__(128, 8) k_fd_tc(const LevelView<float> L, cons
     const int n1 = N + m * (((v1 >> 2) == 0) + ((v1 & 3) == 0));
     const int n2 = N + m * (((v2 >> 2) == 0) + ((v2 & 3) == 0));
     const int n3 = N + m * (((v3 >> 2) == 0) + ((v3 & 3) == 0));
-    // gather R_s r into A[0] (K-major): rows (c, b) = 16 c + b, K = a; each task
-    // fills 8 consecutive a of one row with one 16-byte store
-    for (int task = tid; task < 512; task += 128) {
-      const int row = task >> 1, h = task & 1, c = row >> 4, b = row & 15;
-      float vals[8];
+    // gather R_s r into A[0] (K-major): rows (c, b) = 16 c + b, K = a; one
+    // thread per row, whose three possible sources (the x-neighbours left,
+    // own, right of the row's y/z neighbour) are resolved once; the row is
+    // written as two 16-byte stores
+    for (int row = tid; row < 256; row += 128) {
+      const int c = row >> 4, b = row & 15;
+      float vals[16];
 #pragma unroll
-      for (int q = 0; q < 8; ++q) vals[q] = 0.0f;
+      for (int q = 0; q < 16; ++q) vals[q] = 0.0f;
       const int my = s.gmap[1][b], mz = s.gmap[2][c];
       if (my >= 0 && mz >= 0) {
         const int* nb = s.nb + 3 * (my >> 8) + 9 * (mz >> 8);
-        const int s0 = nb[0], s1 = nb[1], s2 = nb[2];
-        const int line = ((mz & 255) * N + (my & 255)) * N;
+        const long long line = ((mz & 255) * N + (my & 255)) * N;
+        const long long b0 = nb[0] >= 0 ? (long long)nb[0] * N3 + line : -1;
+        const long long b1 = nb[1] >= 0 ? (long long)nb[1] * N3 + line : -1;
+        const long long b2 = nb[2] >= 0 ? (long long)nb[2] * N3 + line : -1;
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          const int mx = s.gmap[0][8 * h + q];
+        for (int q = 0; q < 16; ++q) {
+          const int mx = s.gmap[0][q];
           if (mx < 0) continue;
           const int o = mx >> 8;
-          const int src = o == 0 ? s0 : (o == 1 ? s1 : s2);
-          if (src >= 0) vals[q] = r[(size_t)src * N3 + line + (mx & 255)];
+          const long long bs = o == 0 ? b0 : (o == 1 ? b1 : b2);
+          if (bs >= 0) vals[q] = r[bs + (mx & 255)];
         }
       }
       unsigned char* t = s.A[0][0] + (row >> 7) * TC_TILE;
       const int ml = row & 127;
-      *reinterpret_cast<uint4*>(t + (ml >> 3) * 256 + (ml & 7) * 16 + h * 128) = pack8(vals);
+      *reinterpret_cast<uint4*>(t + (ml >> 3) * 256 + (ml & 7) * 16) = pack8(vals);
+      *reinterpret_cast<uint4*>(t + (ml >> 3) * 256 + (ml & 7) * 16 + 128) = pack8(vals + 8);
     }
     const float g0 = L.g[4 * e], g1 = L.g[4 * e + 1], g2 = L.g[4 * e + 2], g3 = L.g[4 * e + 3];
     float x[16];
@@ -410,10 +417,13 @@ __global__ void __launch_bounds__(128, 8) k_fd_tc(const LevelView<float> L, cons
       tc_read1(tmem, t, x);
       st_mn(s.A[1][0], 16 * (rr & 15), rr >> 4, x);
     }
-    // 6: S1 along a: rows (c'', b'') -> x a''; weight and store the patch (FP32)
+    // 6: S1 along a: rows (c'', b'') -> x a''; weight, stage the patch in the
+    // (now free) operand buffers in its global layout and copy it out with
+    // coalesced stores.  Staged positions outside the element's variant
+    // extents are not written; the combine step never reads them.
     if (!(alive = tc_step(s, 1, 1, true, tmem, phase))) break;
     {
-      float* P = patch + (size_t)e * NS3;
+      float* Pst = reinterpret_cast<float*>(&s.A[0][0][0]);
 #pragma unroll
       for (int t = 0; t < 2; ++t) {
         const int rr = 128 * t + 32 * warp + lane;
@@ -421,12 +431,15 @@ __global__ void __launch_bounds__(128, 8) k_fd_tc(const LevelView<float> L, cons
         const int cc = rr >> 4, bb = rr & 15;
         if (cc < n3 && bb < n2) {
           const float w = s.W[2][cc] * s.W[1][bb];
-          float* row = P + ((size_t)cc * nsm + bb) * nsm;
+          float* row = Pst + (cc * nsm + bb) * nsm;
 #pragma unroll
           for (int q = 0; q < 16; ++q)
             if (q < n1) row[q] = x[q] * w * s.W[0][q];
         }
       }
+      __syncthreads();
+      float* P = patch + (size_t)e * NS3;
+      for (int t = tid; t < (int)NS3; t += 128) P[t] = Pst[t];
     }
   }
   if (!alive && tid == 0) atomicExch(err, 1);

@@ -745,17 +745,24 @@ __global__ void __launch_bounds__(256) k_combine(const LevelView<T> L, const T* 
       continue;
     }
     const int i = n % N, j = (n / N) % N, k = n / (N * N);
-    const int lx = i < m ? 0 : 1, hx = i >= N - m ? 2 : 1;
-    const int ly = j < m ? 0 : 1, hy = j >= N - m ? 2 : 1;
-    const int lz = k < m ? 0 : 1, hz = k >= N - m ? 2 : 1;
+    // per direction the own slot (1) and at most one neighbour slot (0 or 2)
+    const int cx = i < m ? 0 : (i >= N - m ? 2 : -1);
+    const int cy = j < m ? 0 : (j >= N - m ? 2 : -1);
+    const int cz = k < m ? 0 : (k >= N - m ? 2 : -1);
     const long long loc = ((long long)k * nsm + j) * nsm + i;
+    // the (up to) 8 candidate loads are independent: unrolled so that they are
+    // all in flight together
+    T v[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int sx = (q & 1) ? cx : 1, sy = (q & 2) ? cy : 1, sz = (q & 4) ? cz : 1;
+      const long long off = (sx < 0 || sy < 0 || sz < 0) ? -1 : s_off[el][sx + 3 * sy + 9 * sz];
+      v[q] = off >= 0 ? patch[off + loc] : T(0);
+    }
+    // summed in the fixed order own, x, y, xy, z, ... (deterministic)
     T s = T(0);   // accumulated in the smoother precision
-    for (int oz = lz; oz <= hz; ++oz)
-      for (int oy = ly; oy <= hy; ++oy)
-        for (int ox = lx; ox <= hx; ++ox) {
-          const long long off = s_off[el][ox + 3 * oy + 9 * oz];
-          if (off >= 0) s += patch[off + loc];
-        }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) s += v[q];
     if (ADD) u[g] += (TO)s;
     else u[g] = (TO)s;
   }
@@ -1119,6 +1126,76 @@ static bool ptransfer_launch(const TransferView& T, const double* x0, const doub
   return false;
 }
 
+// ---------------------------------------------------------------- h-transfers at p = 1
+// Between a p = 1 element and its 8 children every coarse node sees 8 fine
+// nodes per child: one thread per output node sums the tensor-product terms
+// directly (the per-direction 2 x 2 matrices of the child's side are read
+// from the transfer tables), instead of a CTA per element.
+// MODE 0: P, MODE 1: I^T (one thread per coarse node, over the active
+// children); MODE 2: correction prolongation with the frozen update (one
+// thread per fine node).
+template <int MODE, typename TD>
+__global__ void k_htransfer2(const TransferView T, const double* __restrict__ x0,
+                             const double* __restrict__ x1, double* __restrict__ y0,
+                             double* __restrict__ y1, TD* __restrict__ delta) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int n_out = MODE == 2 ? T.nef : T.nec;
+  if (t >= 8LL * n_out) return;
+  const int E = (int)(t >> 3), node = (int)(t & 7);
+  const int a = node & 1, bq = (node >> 1) & 1, cq = node >> 2;
+  // entry (row r, col q) of direction matrix for side sd
+  auto M = [&](int sd, int r, int q) {
+    return MODE == 0 ? T.P[(sd * 2 + r) * 2 + q]
+                     : (MODE == 1 ? T.I[(sd * 2 + q) * 2 + r] : T.I[(sd * 2 + r) * 2 + q]);
+  };
+  if (MODE == 2) {
+    const int par = T.parent[E], oct = T.octant[E];
+    const bool frozen = T.clsf[E] == DGFAS_FROZEN;
+    const int s1 = oct & 1, s2 = (oct >> 1) & 1, s3 = (oct >> 2) & 1;
+    double y = 0.0;
+#pragma unroll
+    for (int f = 0; f < 8; ++f) {
+      const int i = f & 1, j = (f >> 1) & 1, k = f >> 2;
+      double xv = x0[8LL * par + f];
+      if (!frozen) xv -= x1[8LL * par + f];
+      y += M(s3, cq, k) * M(s2, bq, j) * M(s1, a, i) * xv;
+    }
+    if (frozen) {
+      y0[t] = y;
+      delta[t] = TD(0);
+    } else {
+      delta[t] = (TD)y;
+    }
+    return;
+  }
+  double acc = 0.0;
+  int any = 0;
+  for (int sl = 0; sl < 8; ++sl) {
+    const int ch = T.children[8 * E + sl];
+    if (ch < 0 || T.clsf[ch] == DGFAS_FROZEN) continue;
+    any = 1;
+    const int oct = T.octant[ch];
+    const int s1 = oct & 1, s2 = (oct >> 1) & 1, s3 = (oct >> 2) & 1;
+#pragma unroll
+    for (int f = 0; f < 8; ++f) {
+      const int i = f & 1, j = (f >> 1) & 1, k = f >> 2;
+      acc += M(s3, cq, k) * M(s2, bq, j) * M(s1, a, i) * x0[8LL * ch + f];
+    }
+  }
+  if (!any) return;
+  y0[t] = acc;
+  if (MODE == 0) y1[t] = acc;
+}
+
+template <int MODE, typename TD>
+static bool htransfer_launch(const TransferView& T, const double* x0, const double* x1, double* y0,
+                             double* y1, TD* delta, cudaStream_t st) {
+  if (!T.h || T.Nf != 2 || T.Nc != 2) return false;
+  const long long n = 8LL * (MODE == 2 ? T.nef : T.nec);
+  k_htransfer2<MODE, TD><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(T, x0, x1, y0, y1, delta);
+  return true;
+}
+
 int prepare_transfer(const TransferView& T) {
   ptransfer_launch<0, double>(T, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, true);
   ptransfer_launch<1, double>(T, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, true);
@@ -1133,7 +1210,8 @@ int prepare_transfer(const TransferView& T) {
 int launch_project(Ctx& c, int l, const double* uf) {
   LevelHost& F = c.lv[l];
   LevelHost& C = c.lv[l - 1];
-  if (!ptransfer_launch<0, double>(F.tr, uf, nullptr, C.u, C.ubar, nullptr, c.stream))
+  if (!ptransfer_launch<0, double>(F.tr, uf, nullptr, C.u, C.ubar, nullptr, c.stream) &&
+      !htransfer_launch<0, double>(F.tr, uf, nullptr, C.u, C.ubar, nullptr, c.stream))
     k_gather_children<false><<<C.ne, 256, transfer_smem(F.tr), c.stream>>>(F.tr, uf, C.u, C.ubar);
   ++g_kernels;
   CK(cudaGetLastError());
@@ -1143,7 +1221,8 @@ int launch_project(Ctx& c, int l, const double* uf) {
 int launch_restrict(Ctx& c, int l, const double* rf, double* rc) {
   LevelHost& F = c.lv[l];
   LevelHost& C = c.lv[l - 1];
-  if (!ptransfer_launch<1, double>(F.tr, rf, nullptr, rc, nullptr, nullptr, c.stream))
+  if (!ptransfer_launch<1, double>(F.tr, rf, nullptr, rc, nullptr, nullptr, c.stream) &&
+      !htransfer_launch<1, double>(F.tr, rf, nullptr, rc, nullptr, nullptr, c.stream))
     k_gather_children<true><<<C.ne, 256, transfer_smem(F.tr), c.stream>>>(F.tr, rf, rc, nullptr);
   ++g_kernels;
   CK(cudaGetLastError());
@@ -1154,7 +1233,8 @@ int launch_prolong(Ctx& c, int l, double* uf, int prec, void* delta) {
   LevelHost& F = c.lv[l];
   LevelHost& C = c.lv[l - 1];
   if (prec == DGFAS_FP64) {
-    if (!ptransfer_launch<2, double>(F.tr, C.u, C.ubar, uf, nullptr, (double*)delta, c.stream))
+    if (!ptransfer_launch<2, double>(F.tr, C.u, C.ubar, uf, nullptr, (double*)delta, c.stream) &&
+        !htransfer_launch<2, double>(F.tr, C.u, C.ubar, uf, nullptr, (double*)delta, c.stream))
       k_prolong<double><<<F.ne, 128, transfer_smem(F.tr), c.stream>>>(F.tr, C.u, C.ubar, uf, (double*)delta);
   } else {
     // FP32 arithmetic for the smoother's starting correction unless frozen
@@ -1162,7 +1242,7 @@ int launch_prolong(Ctx& c, int l, double* uf, int prec, void* delta) {
     const bool done = F.has_frozen
         ? ptransfer_launch<2, float, double>(F.tr, C.u, C.ubar, uf, nullptr, (float*)delta, c.stream)
         : ptransfer_launch<2, float, float>(F.tr, C.u, C.ubar, uf, nullptr, (float*)delta, c.stream);
-    if (!done)
+    if (!done && !htransfer_launch<2, float>(F.tr, C.u, C.ubar, uf, nullptr, (float*)delta, c.stream))
       k_prolong<float><<<F.ne, 128, transfer_smem(F.tr), c.stream>>>(F.tr, C.u, C.ubar, uf, (float*)delta);
   }
   ++g_kernels;
