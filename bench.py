@@ -357,6 +357,8 @@ def run_gpu(args):
     S = dgfas.Solver(levels, pr["mu_star"], pr["delta"], pr["s1"], pr["s2"], pr["sc"],
                      precision=prec)
     S.dgfas_use_graph(True)
+    # launch shapes from the library's autotuner (set-up, outside every timed region)
+    tuning = [] if args.no_autotune else S.dgfas_autotune(reps=5)
     ndof = S.ndof(-1)
     xyz = S.node_coords(-1)
     f_nod = torch.from_numpy(wl.eval_f(cfg["rhs"], xyz.cpu().numpy())).to(dev)
@@ -454,6 +456,8 @@ def run_gpu(args):
         S2 = S if pmode == prec else dgfas.Solver(levels, pr["mu_star"], pr["delta"], pr["s1"],
                                                    pr["s2"], pr["sc"], precision=pmode)
         S2.dgfas_use_graph(True)
+        if S2 is not S and not args.no_autotune:
+            S2.dgfas_autotune(reps=5)
         us = u0.clone()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -491,6 +495,9 @@ def run_gpu(args):
                        "parallelism": "replicas" if ws > 1 else "single",
                        "l2": "inputs larger than L2 (top vector 191 MB > 126 MB)"},
             "gpu_launches": gpu_launches,
+            "autotune": {"tuned": len(tuning),
+                         "changed": [{k: (round(v, 4) if isinstance(v, float) else v)
+                                      for k, v in t.items()} for t in tuning if t["value"] != 0]},
             "roofline": roofline,
             "kernel_ms": {k: v["ms"] for k, v in kernels.items()},
             "kernel_share_ms_per_cycle": shares,
@@ -518,6 +525,8 @@ def main():
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-others", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the built-in launch shapes instead of the autotuner's")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

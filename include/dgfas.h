@@ -188,6 +188,34 @@ int dgfas_use_graph(void* ctx, int enable);
 int dgfas_profile_sweep(void* ctx, int level, double* u, const double* g, int reps,
                         double* ms_out);
 
+/* Launch-shape autotuner (the batching / tile-tuning step of the hot path):
+   for every level it times, with CUDA events on the context's stream, the
+   candidate launch shapes of the tunable kernels and keeps the fastest:
+     kernel 0  FP64 operator (residual, tau):        elements per CTA
+     kernel 1  smoother-precision operator:          elements per CTA
+     kernel 2  FD for subdomains narrower than 9:    elements per CTA
+     kernel 3  tensor-core FD (BF16, width >= 12):   CTAs per SM
+   Every candidate computes bit-identical results (the shapes only change how
+   elements are mapped to CTAs).  reps launches are timed per candidate
+   (the built-in default, value 0, included).  report [max_entries][5] (host,
+   nullable when max_entries = 0) receives (level, kernel, chosen value,
+   best ms, default ms) per tuned pair; *n_entries their number.  Synchronous.
+   The level work vectors and the patch buffer are used as scratch, so call it
+   between solves, never while a stream capture is active; a captured V-cycle
+   graph is dropped and captured again on next use. */
+int dgfas_autotune(void* ctx, int reps, double* report, int max_entries, int* n_entries);
+
+/* Forces the launch shape of `kernel` (0..3, as above) on `level`: value 0
+   restores the default, any other value must be one of the candidates that
+   dgfas_get_tuning lists (else DGFAS_ERR_INVALID). */
+int dgfas_set_tuning(void* ctx, int level, int kernel, int value);
+
+/* Current launch shape (*value, 0 = default) of `kernel` on `level` and,
+   if n_candidates is not null, its candidate values (candidates
+   [max_candidates], host) and their number. */
+int dgfas_get_tuning(void* ctx, int level, int kernel, int* value, int* candidates,
+                     int max_candidates, int* n_candidates);
+
 /* Measured FMA throughput of the current device in TFLOP/s (FP64 and FP32):
    the denominators of the roofline of ALU-bound kernels. */
 int dgfas_fma_peak(double* tflops_fp64, double* tflops_fp32);

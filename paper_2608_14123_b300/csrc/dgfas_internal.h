@@ -52,6 +52,13 @@ struct TransferView {
   const double* P;            // [2][Nc][Nf]
 };
 
+// Launch shapes chosen by the autotuner (0 = the built-in default):
+// elements per CTA of the FP64 and smoother-precision box operators and of
+// the narrow-subdomain FD kernel, CTAs per SM of the tensor-core FD kernel.
+struct Tune {
+  int apply64 = 0, apply32 = 0, fd = 0, fdtc = 0;
+};
+
 struct LevelHost {
   int p, N, ne, m, nsm, box;
   long long ndof;
@@ -81,6 +88,7 @@ struct LevelHost {
   LevelView<double> v64;
   LevelView<float> v32;
   TransferView tr;
+  Tune tune;
 };
 
 struct Ctx {
@@ -118,6 +126,8 @@ int launch_apply_corr(Ctx& c, int l, int prec, const void* delta, const double* 
                       int out_fp64);
 int launch_fd(Ctx& c, int l, int prec, const void* r);
 int launch_fd_tc(Ctx& c, int l, const float* r);
+// candidate launch shapes of the tunable kernels of level l (autotuner)
+int tune_candidates(Ctx& c, int l, int kernel, int* out, int max_out);
 int launch_combine(Ctx& c, int l, int prec, void* delta);
 int launch_add_delta(Ctx& c, long long n, int prec, const void* d, double* u);
 int launch_combine_to(Ctx& c, int l, int prec, double* z);

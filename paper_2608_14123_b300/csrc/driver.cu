@@ -983,6 +983,118 @@ extern "C" int dgfas_use_graph(void* ctx, int enable) {
   return DGFAS_OK;
 }
 
+// ---------------------------------------------------------------- autotuner
+// field of Tune that `kernel` (0..3) selects
+static int* tune_field(LevelHost& H, int kernel) {
+  switch (kernel) {
+    case 0: return &H.tune.apply64;
+    case 1: return &H.tune.apply32;
+    case 2: return &H.tune.fd;
+    case 3: return &H.tune.fdtc;
+  }
+  return nullptr;
+}
+
+// one launch of the tunable `kernel` on level l on scratch data
+static int tune_run(Ctx& c, int l, int kernel) {
+  LevelHost& H = c.lv[l];
+  const int prec = c.prm.precision;
+  if (kernel == 0) return launch_apply(c, l, DGFAS_FP64, H.delta, nullptr, H.r, 1.0);
+  if (kernel == 1) return launch_apply_corr(c, l, prec, H.delta, H.r, c.rw, 0);
+  return launch_fd(c, l, prec, c.rw);
+}
+
+extern "C" int dgfas_autotune(void* ctx, int reps, double* report, int max_entries,
+                              int* n_entries) {
+  Ctx* c = (Ctx*)ctx;
+  if (!c || reps <= 0 || (max_entries > 0 && !report)) return DGFAS_ERR_INVALID;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  int n_rep = 0, rc = DGFAS_OK;
+  for (int l = 0; l < (int)c->lv.size() && rc == DGFAS_OK; ++l) {
+    LevelHost& H = c->lv[l];
+    // the scratch operands: level work vectors (their contents are rebuilt at
+    // the start of every smoothing block and cycle)
+    CK(cudaMemsetAsync(H.delta, 0, H.ndof * sizeof(double), c->stream));
+    CK(cudaMemsetAsync(H.r, 0, H.ndof * sizeof(double), c->stream));
+    CK(cudaMemsetAsync(c->rw, 0, H.ndof * sizeof(double), c->stream));
+    for (int k = 0; k < 4 && rc == DGFAS_OK; ++k) {
+      if (l == 0 && k > 0) continue;   // the root level is not smoothed
+      int cand[16];
+      const int nc = tune_candidates(*c, l, k, cand + 1, 15);
+      if (nc == 0) continue;
+      cand[0] = 0;   // the built-in default
+      int* field = tune_field(H, k);
+      double best = 1e300, t_def = 0.0;
+      int best_v = 0;
+      for (int i = 0; i <= nc && rc == DGFAS_OK; ++i) {
+        *field = cand[i];
+        rc = tune_run(*c, l, k);   // warm-up (and first-use attributes)
+        if (rc != DGFAS_OK) break;
+        if (cudaEventRecord(e0, c->stream) != cudaSuccess) { rc = DGFAS_ERR_CUDA; break; }
+        for (int q = 0; q < reps && rc == DGFAS_OK; ++q) rc = tune_run(*c, l, k);
+        if (rc != DGFAS_OK) break;
+        if (cudaEventRecord(e1, c->stream) != cudaSuccess ||
+            cudaEventSynchronize(e1) != cudaSuccess) { rc = DGFAS_ERR_CUDA; break; }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        const double t = ms / reps;
+        if (i == 0) t_def = t;
+        if (t < best) { best = t; best_v = cand[i]; }
+      }
+      *field = best_v;
+      if (rc == DGFAS_OK && n_rep < max_entries) {
+        double* r5 = report + 5 * n_rep;
+        r5[0] = l; r5[1] = k; r5[2] = best_v; r5[3] = best; r5[4] = t_def;
+      }
+      if (rc == DGFAS_OK) ++n_rep;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  // launch shapes are baked into a captured graph: capture again on next use
+  if (c->gexec) { cudaGraphExecDestroy(c->gexec); c->gexec = nullptr; }
+  if (n_entries) *n_entries = n_rep;
+  return rc;
+}
+
+extern "C" int dgfas_set_tuning(void* ctx, int level, int kernel, int value) {
+  Ctx* c = (Ctx*)ctx;
+  if (!c || level < 0 || level >= (int)c->lv.size() || kernel < 0 || kernel > 3) {
+    set_error("set_tuning: invalid argument");
+    return DGFAS_ERR_INVALID;
+  }
+  if (value != 0) {
+    int cand[16];
+    const int nc = tune_candidates(*c, level, kernel, cand, 16);
+    bool ok = false;
+    for (int i = 0; i < nc; ++i) ok |= cand[i] == value;
+    if (!ok) {
+      set_error("set_tuning: value is not a candidate launch shape of this kernel and level");
+      return DGFAS_ERR_INVALID;
+    }
+  }
+  *tune_field(c->lv[level], kernel) = value;
+  if (c->gexec) { cudaGraphExecDestroy(c->gexec); c->gexec = nullptr; }
+  return DGFAS_OK;
+}
+
+extern "C" int dgfas_get_tuning(void* ctx, int level, int kernel, int* value, int* candidates,
+                                int max_candidates, int* n_candidates) {
+  Ctx* c = (Ctx*)ctx;
+  if (!c || level < 0 || level >= (int)c->lv.size() || kernel < 0 || kernel > 3 || !value)
+    return DGFAS_ERR_INVALID;
+  *value = *tune_field(c->lv[level], kernel);
+  if (n_candidates) {
+    int cand[16];
+    const int nc = tune_candidates(*c, level, kernel, cand, 16);
+    for (int i = 0; i < nc && i < max_candidates && candidates; ++i) candidates[i] = cand[i];
+    *n_candidates = nc;
+  }
+  return DGFAS_OK;
+}
+
 extern "C" const char* dgfas_strerror(int code) {
   switch (code) {
     case DGFAS_OK: return "ok";

@@ -460,7 +460,9 @@ int launch_fd_tc(Ctx& c, int l, const float* r) {
   int dev = 0, nsm = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  const int grid = std::min(H.ne, nsm * 8);
+  // CTAs per SM: the autotuner's choice, else the 8 that registers allow
+  const int per_sm = H.tune.fdtc > 0 ? std::min(H.tune.fdtc, 8) : 8;
+  const int grid = std::min(H.ne, nsm * per_sm);
   k_fd_tc<<<grid, 128, smem, c.stream>>>(H.v32, r, (float*)c.patch, c.tc_err);
   ++g_kernels;
   CK(cudaGetLastError());

@@ -5,6 +5,7 @@
 //  k_project / k_restrict / k_prolong   FAS transfers (Sec. 3.2, Alg. 2)
 //  k_root     dense root solve (inverse times vector)
 //  reductions, axpy, coordinates, right-hand side
+#include <algorithm>
 #include <atomic>
 #include <cstdio>
 
@@ -382,11 +383,20 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 1) k_apply_box_eo(co
   }
 }
 
+// largest number of elements per CTA of the box operator for N and the
+// arithmetic size (256 threads, 96 KB of shared memory)
+static int apply_epb_max(int N, size_t tsz) {
+  int e = 256 / (N * N);
+  while (e > 1 && (size_t)2 * N * N * N * e * tsz > 96 * 1024) --e;
+  return e < 1 ? 1 : e;
+}
+
 template <int N, typename T, typename TU, typename TB, typename TO>
 static int apply_N(const LevelView<T>& L, const TU* u, const TB* b, TO* out, T alpha,
-                   cudaStream_t st) {
+                   cudaStream_t st, int epb_req) {
   constexpr int N2 = N * N, N3 = N * N * N;
   int epb = (128 + N2 - 1) / N2;
+  if (epb_req > 0) epb = std::max(1, std::min(epb_req, 256 / N2));
   size_t smem = (N2 + 16 + (size_t)6 * N3 * epb) * sizeof(T);
   while (epb > 1 && smem > 100 * 1024) {
     --epb;
@@ -396,11 +406,9 @@ static int apply_N(const LevelView<T>& L, const TU* u, const TB* b, TO* out, T a
   // the attribute is set once per instantiation (never inside a graph capture)
   if (L.box) {
     int epb2 = (128 + N2 - 1) / N2;
-    size_t smem2 = (size_t)2 * N3 * epb2 * sizeof(T);
-    while (epb2 > 1 && smem2 > 96 * 1024) {
-      --epb2;
-      smem2 = (size_t)2 * N3 * epb2 * sizeof(T);
-    }
+    if (epb_req > 0) epb2 = epb_req;
+    epb2 = std::min(epb2, apply_epb_max(N, sizeof(T)));
+    const size_t smem2 = (size_t)2 * N3 * epb2 * sizeof(T);
     auto kf = k_apply_box_eo<N, T, TU, TB, TO>;
     if (smem2 > 40 * 1024) {
       static bool attr = false;
@@ -427,18 +435,18 @@ static int apply_N(const LevelView<T>& L, const TU* u, const TB* b, TO* out, T a
 
 template <typename T, typename TU, typename TB, typename TO>
 static int apply_disp(const LevelView<T>& L, const TU* u, const TB* b, TO* out, T alpha,
-                      cudaStream_t st) {
+                      cudaStream_t st, int epb = 0) {
   switch (L.N) {
-    case 2: return apply_N<2, T, TU, TB, TO>(L, u, b, out, alpha, st);
-    case 3: return apply_N<3, T, TU, TB, TO>(L, u, b, out, alpha, st);
-    case 4: return apply_N<4, T, TU, TB, TO>(L, u, b, out, alpha, st);
-    case 5: return apply_N<5, T, TU, TB, TO>(L, u, b, out, alpha, st);
-    case 6: return apply_N<6, T, TU, TB, TO>(L, u, b, out, alpha, st);
-    case 7: return apply_N<7, T, TU, TB, TO>(L, u, b, out, alpha, st);
-    case 8: return apply_N<8, T, TU, TB, TO>(L, u, b, out, alpha, st);
-    case 9: return apply_N<9, T, TU, TB, TO>(L, u, b, out, alpha, st);
-    case 10: return apply_N<10, T, TU, TB, TO>(L, u, b, out, alpha, st);
-    case 11: return apply_N<11, T, TU, TB, TO>(L, u, b, out, alpha, st);
+    case 2: return apply_N<2, T, TU, TB, TO>(L, u, b, out, alpha, st, epb);
+    case 3: return apply_N<3, T, TU, TB, TO>(L, u, b, out, alpha, st, epb);
+    case 4: return apply_N<4, T, TU, TB, TO>(L, u, b, out, alpha, st, epb);
+    case 5: return apply_N<5, T, TU, TB, TO>(L, u, b, out, alpha, st, epb);
+    case 6: return apply_N<6, T, TU, TB, TO>(L, u, b, out, alpha, st, epb);
+    case 7: return apply_N<7, T, TU, TB, TO>(L, u, b, out, alpha, st, epb);
+    case 8: return apply_N<8, T, TU, TB, TO>(L, u, b, out, alpha, st, epb);
+    case 9: return apply_N<9, T, TU, TB, TO>(L, u, b, out, alpha, st, epb);
+    case 10: return apply_N<10, T, TU, TB, TO>(L, u, b, out, alpha, st, epb);
+    case 11: return apply_N<11, T, TU, TB, TO>(L, u, b, out, alpha, st, epb);
   }
   set_error("apply: unsupported N");
   return DGFAS_ERR_UNSUPPORTED;
@@ -449,7 +457,7 @@ int launch_apply(Ctx& c, int l, int prec, const double* u, const double* b, void
                  double alpha) {
   (void)prec;
   return apply_disp<double, double, double, double>(c.lv[l].v64, u, b, (double*)out, alpha,
-                                                    c.stream);
+                                                    c.stream, c.lv[l].tune.apply64);
 }
 
 // Smoother-precision operator on a correction: out = b - A delta with b FP64,
@@ -460,12 +468,12 @@ int launch_apply_corr(Ctx& c, int l, int prec, const void* delta, const double* 
   LevelHost& H = c.lv[l];
   if (prec == DGFAS_FP64)
     return apply_disp<double, double, double, double>(H.v64, (const double*)delta, b,
-                                                      (double*)out, -1.0, c.stream);
+                                                      (double*)out, -1.0, c.stream, H.tune.apply64);
   if (out_fp64)
     return apply_disp<float, float, double, double>(H.v32, (const float*)delta, b, (double*)out,
-                                                    -1.0f, c.stream);
+                                                    -1.0f, c.stream, H.tune.apply32);
   return apply_disp<float, float, double, float>(H.v32, (const float*)delta, b, (float*)out,
-                                                 -1.0f, c.stream);
+                                                 -1.0f, c.stream, H.tune.apply32);
 }
 
 // ============================================================================ FD
@@ -637,9 +645,196 @@ __global__ void k_fd(const LevelView<T> L, const TR* __restrict__ r, T* __restri
     }
   }
 }
+// dynamic shared memory of k_fd_small: patches, coefficients, neighbourhoods,
+// variants; kept under 40 KB so that with the static variant tables (< 8 KB)
+// the CTA stays within the 48 KB available without an opt-in attribute
+#define FD_SMALL_DYN_MAX (40 * 1024)
+static size_t fd_small_smem(int NS, int epb, size_t tsz) {
+  return (size_t)epb * (NS * NS * NS + 4) * tsz + (size_t)epb * 31 * sizeof(int);
+}
+
+// Narrow subdomains (NS <= 8): a team of NS threads per element, EPB = 128/NS
+// elements per CTA.  Each mode product is done line by line with the 1D
+// matrix held in registers, so one shared-memory load of the matrix serves NS
+// lines and each line is loaded once (NS multiply-adds per load instead of
+// one).  The tables of all 16 side variants are staged once per CTA.  The
+// scaling by D^-1 is fused into the third product and the weights into the
+// last; the weighted patches of the CTA's elements leave through one
+// coalesced copy.  Positions outside an element's variant come out as zeros.
 template <int NS, typename T, typename TR>
-static int fd_NS(const LevelView<T>& L, const TR* r, T* patch, cudaStream_t st) {
+__global__ void __launch_bounds__(256) k_fd_small(const LevelView<T> L, const TR* __restrict__ r,
+                                                  T* __restrict__ patch, int EPB) {
   constexpr int NS2 = NS * NS, NS3 = NS2 * NS;
+  __shared__ T tS[16][NS2];
+  __shared__ T tl[16][NS], tw[16][NS];
+  __shared__ int tg[16][NS];   // patch position -> (neighbour offset + 1) << 8 | node, or -1
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* X = reinterpret_cast<T*>(smem_raw);            // [EPB][NS^3]
+  T* sg = X + (size_t)EPB * NS3;                     // [EPB][4] surrogate coefficients
+  int* snb = reinterpret_cast<int*>(sg + 4 * EPB);   // [EPB][27]
+  int* sv = snb + 27 * EPB;                          // [EPB][4] variants, active flag
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const int N = L.N, m = L.m, N3 = N * N * N;
+  for (int t = tid; t < 16 * NS2; t += nth) tS[t / NS2][t % NS2] = L.S[t];
+  for (int t = tid; t < 16 * NS; t += nth) {
+    const int v = t / NS, q = t % NS;
+    tl[v][q] = L.lam[t];
+    tw[v][q] = L.W[t];
+    int code = -1;
+    if (q < var_size(v, N, m)) {
+      int o, ix;
+      side_map(v, q, N, m, o, ix);
+      code = ((o + 1) << 8) | ix;
+    }
+    tg[v][q] = code;
+  }
+  const int e0 = blockIdx.x * EPB;
+  for (int t = tid; t < EPB * 27; t += nth) {
+    const int el = t / 27, e = e0 + el;
+    snb[t] = e < L.ne ? L.nbr27[27 * e + t % 27] : -1;
+  }
+  if (tid < EPB) {
+    const int e = e0 + tid;
+    const bool ok = e < L.ne;
+    for (int d = 0; d < 3; ++d) sv[4 * tid + d] = ok ? L.var[3 * e + d] : 0;
+    sv[4 * tid + 3] = ok && L.cls[e] != DGFAS_FROZEN;
+    for (int d = 0; d < 4; ++d) sg[4 * tid + d] = ok ? L.g[4 * e + d] : T(1);
+  }
+  __syncthreads();
+  // gather R_s r (unrolled: the independent loads of several positions are
+  // in flight together)
+#pragma unroll 8
+  for (int t = tid; t < EPB * NS3; t += nth) {
+    const int el = t / NS3, n = t % NS3;
+    const int a = n % NS, b = (n / NS) % NS, c = n / NS2;
+    T val = T(0);
+    if (sv[4 * el + 3]) {
+      const int gx = tg[sv[4 * el]][a], gy = tg[sv[4 * el + 1]][b], gz = tg[sv[4 * el + 2]][c];
+      if (gx >= 0 && gy >= 0 && gz >= 0) {
+        const int src = snb[27 * el + (gx >> 8) + 3 * (gy >> 8) + 9 * (gz >> 8)];
+        if (src >= 0)
+          val = (T)r[(size_t)src * N3 + ((gz & 255) * N + (gy & 255)) * N + (gx & 255)];
+      }
+    }
+    X[t] = val;
+  }
+  __syncthreads();
+  const int el = tid / NS, t0 = tid % NS;
+  const bool on = el < EPB;
+  T* Xe = X + (on ? el : 0) * NS3;
+  const int elc = on ? el : 0;
+  const int v1 = sv[4 * elc], v2 = sv[4 * elc + 1], v3 = sv[4 * elc + 2];
+  T Sm[NS][NS], x[NS], y[NS];
+  auto loadS = [&](int v) {
+#pragma unroll
+    for (int q = 0; q < NS; ++q)
+#pragma unroll
+      for (int p = 0; p < NS; ++p) Sm[q][p] = tS[v][q * NS + p];
+  };
+  // 1: S1^T along a, lines (c = t0, b); 2: S2^T along b, lines (c = t0, a)
+  if (on) {
+    loadS(v1);
+    for (int b = 0; b < NS; ++b) {
+      T* ln = Xe + (t0 * NS + b) * NS;
+#pragma unroll
+      for (int q = 0; q < NS; ++q) x[q] = ln[q];
+#pragma unroll
+      for (int p = 0; p < NS; ++p) {
+        T acc = T(0);
+#pragma unroll
+        for (int q = 0; q < NS; ++q) acc += Sm[q][p] * x[q];
+        ln[p] = acc;
+      }
+    }
+    loadS(v2);
+    for (int a = 0; a < NS; ++a) {
+      T* ln = Xe + t0 * NS2 + a;
+#pragma unroll
+      for (int q = 0; q < NS; ++q) x[q] = ln[q * NS];
+#pragma unroll
+      for (int p = 0; p < NS; ++p) {
+        T acc = T(0);
+#pragma unroll
+        for (int q = 0; q < NS; ++q) acc += Sm[q][p] * x[q];
+        ln[p * NS] = acc;
+      }
+    }
+  }
+  __syncthreads();
+  // 3: S3^T along c and D^-1, then 4: S3 along c; lines (b = t0, a)
+  if (on) {
+    loadS(v3);
+    const T g0 = sg[4 * el], g1 = sg[4 * el + 1], g2 = sg[4 * el + 2], g3 = sg[4 * el + 3];
+    for (int a = 0; a < NS; ++a) {
+      T* ln = Xe + t0 * NS + a;
+#pragma unroll
+      for (int q = 0; q < NS; ++q) x[q] = ln[q * NS2];
+      const T d0 = g0 + g1 * tl[v1][a] + g2 * tl[v2][t0];
+#pragma unroll
+      for (int p = 0; p < NS; ++p) {
+        T acc = T(0);
+#pragma unroll
+        for (int q = 0; q < NS; ++q) acc += Sm[q][p] * x[q];
+        y[p] = acc / (d0 + g3 * tl[v3][p]);
+      }
+#pragma unroll
+      for (int p = 0; p < NS; ++p) {
+        T acc = T(0);
+#pragma unroll
+        for (int q = 0; q < NS; ++q) acc += Sm[p][q] * y[q];
+        ln[p * NS2] = acc;
+      }
+    }
+  }
+  __syncthreads();
+  // 5: S2 along b, lines (c = t0, a); 6: S1 along a with the weights, lines (c = t0, b)
+  if (on) {
+    loadS(v2);
+    for (int a = 0; a < NS; ++a) {
+      T* ln = Xe + t0 * NS2 + a;
+#pragma unroll
+      for (int q = 0; q < NS; ++q) x[q] = ln[q * NS];
+#pragma unroll
+      for (int p = 0; p < NS; ++p) {
+        T acc = T(0);
+#pragma unroll
+        for (int q = 0; q < NS; ++q) acc += Sm[p][q] * x[q];
+        ln[p * NS] = acc;
+      }
+    }
+    loadS(v1);
+    for (int b = 0; b < NS; ++b) {
+      T* ln = Xe + (t0 * NS + b) * NS;
+      const T wcb = tw[v3][t0] * tw[v2][b];
+#pragma unroll
+      for (int q = 0; q < NS; ++q) x[q] = ln[q];
+#pragma unroll
+      for (int p = 0; p < NS; ++p) {
+        T acc = T(0);
+#pragma unroll
+        for (int q = 0; q < NS; ++q) acc += Sm[p][q] * x[q];
+        ln[p] = acc * wcb * tw[v1][p];
+      }
+    }
+  }
+  __syncthreads();
+  const int ne_here = min(EPB, L.ne - e0);
+  T* P = patch + (size_t)e0 * NS3;
+  for (int t = tid; t < ne_here * NS3; t += nth) P[t] = X[t];
+}
+
+template <int NS, typename T, typename TR>
+static int fd_NS(const LevelView<T>& L, const TR* r, T* patch, cudaStream_t st, int epb_req) {
+  constexpr int NS2 = NS * NS, NS3 = NS2 * NS;
+  if constexpr (NS <= 8 && (sizeof(T) == 4 || NS <= 5)) {
+    int epb = epb_req > 0 ? std::min(epb_req, 256 / NS) : 128 / NS;
+    while (epb > 1 && fd_small_smem(NS, epb, sizeof(T)) > FD_SMALL_DYN_MAX) --epb;
+    k_fd_small<NS, T, TR><<<(L.ne + epb - 1) / epb, epb * NS, fd_small_smem(NS, epb, sizeof(T)), st>>>(
+        L, r, patch, epb);
+    ++g_kernels;
+    CK(cudaGetLastError());
+    return DGFAS_OK;
+  }
   int epb = (128 + NS2 - 1) / NS2;
   size_t per = (2 * NS3 + 3 * NS2 + 6 * NS) * sizeof(T);
   while (epb > 1 && per * epb > 96 * 1024) --epb;
@@ -658,24 +853,24 @@ static int fd_NS(const LevelView<T>& L, const TR* r, T* patch, cudaStream_t st) 
 }
 
 template <typename T, typename TR>
-static int fd_disp(const LevelView<T>& L, const TR* r, T* patch, cudaStream_t st) {
+static int fd_disp(const LevelView<T>& L, const TR* r, T* patch, cudaStream_t st, int epb = 0) {
   // the patch stride is the level's nsm; instantiate NS == nsm exactly
   switch (L.nsm) {
-    case 2: return fd_NS<2>(L, r, patch, st);
-    case 3: return fd_NS<3>(L, r, patch, st);
-    case 4: return fd_NS<4>(L, r, patch, st);
-    case 5: return fd_NS<5>(L, r, patch, st);
-    case 6: return fd_NS<6>(L, r, patch, st);
-    case 7: return fd_NS<7>(L, r, patch, st);
-    case 8: return fd_NS<8>(L, r, patch, st);
-    case 9: return fd_NS<9>(L, r, patch, st);
-    case 10: return fd_NS<10>(L, r, patch, st);
-    case 11: return fd_NS<11>(L, r, patch, st);
-    case 12: return fd_NS<12>(L, r, patch, st);
-    case 13: return fd_NS<13>(L, r, patch, st);
-    case 14: return fd_NS<14>(L, r, patch, st);
-    case 15: return fd_NS<15>(L, r, patch, st);
-    case 16: return fd_NS<16>(L, r, patch, st);
+    case 2: return fd_NS<2>(L, r, patch, st, epb);
+    case 3: return fd_NS<3>(L, r, patch, st, epb);
+    case 4: return fd_NS<4>(L, r, patch, st, epb);
+    case 5: return fd_NS<5>(L, r, patch, st, epb);
+    case 6: return fd_NS<6>(L, r, patch, st, epb);
+    case 7: return fd_NS<7>(L, r, patch, st, epb);
+    case 8: return fd_NS<8>(L, r, patch, st, epb);
+    case 9: return fd_NS<9>(L, r, patch, st, epb);
+    case 10: return fd_NS<10>(L, r, patch, st, epb);
+    case 11: return fd_NS<11>(L, r, patch, st, epb);
+    case 12: return fd_NS<12>(L, r, patch, st, epb);
+    case 13: return fd_NS<13>(L, r, patch, st, epb);
+    case 14: return fd_NS<14>(L, r, patch, st, epb);
+    case 15: return fd_NS<15>(L, r, patch, st, epb);
+    case 16: return fd_NS<16>(L, r, patch, st, epb);
   }
   set_error("fd: unsupported subdomain width");
   return DGFAS_ERR_UNSUPPORTED;
@@ -687,8 +882,57 @@ int launch_fd(Ctx& c, int l, int prec, const void* r) {
   // 16^3); narrower levels keep the FP32 kernel in the BF16 mode
   if (prec == DGFAS_BF16 && H.nsm >= 12) return launch_fd_tc(c, l, (const float*)r);
   if (prec == DGFAS_FP64)
-    return fd_disp<double, double>(H.v64, (const double*)r, (double*)c.patch, c.stream);
-  return fd_disp<float, float>(H.v32, (const float*)r, (float*)c.patch, c.stream);
+    return fd_disp<double, double>(H.v64, (const double*)r, (double*)c.patch, c.stream, H.tune.fd);
+  return fd_disp<float, float>(H.v32, (const float*)r, (float*)c.patch, c.stream, H.tune.fd);
+}
+
+// ---------------------------------------------------------------- tuning candidates
+// Launch shapes the autotuner may try for `kernel` on level l (0: FP64 box or
+// curvilinear operator, elements per CTA; 1: smoother-precision operator,
+// elements per CTA; 2: narrow-subdomain FD, elements per CTA; 3: tensor-core
+// FD, CTAs per SM).  Returns how many were written; 0 if the kernel does not
+// run on this level in the context's precision.
+int tune_candidates(Ctx& c, int l, int kernel, int* out, int max_out) {
+  LevelHost& H = c.lv[l];
+  const int prec = c.prm.precision, N = H.N, N2 = N * N;
+  int n = 0;
+  auto add = [&](int v) {
+    for (int i = 0; i < n; ++i)
+      if (out[i] == v) return;
+    if (n < max_out) out[n++] = v;
+  };
+  if (kernel == 0 || kernel == 1) {
+    if (kernel == 1 && prec == DGFAS_FP64) return 0;
+    const size_t tsz = kernel == 0 ? sizeof(double) : sizeof(float);
+    int emax;
+    if (H.box) {
+      emax = apply_epb_max(N, tsz);
+    } else {
+      emax = std::max(1, 256 / N2);
+      while (emax > 1 && (N2 + 16 + (size_t)6 * N * N2 * emax) * tsz > 100 * 1024) --emax;
+    }
+    for (int e = 1; e <= emax; e *= 2) add(e);
+    add(emax);
+    add((128 + N2 - 1) / N2 <= emax ? (128 + N2 - 1) / N2 : emax);
+    return n;
+  }
+  if (kernel == 2) {
+    const int NS = H.nsm;
+    const bool tc = prec == DGFAS_BF16 && NS >= 12;
+    const bool small = NS <= 8 && (prec != DGFAS_FP64 || NS <= 5);
+    if (tc || !small) return 0;
+    const size_t tsz = prec == DGFAS_FP64 ? sizeof(double) : sizeof(float);
+    for (int e = std::max(1, 32 / NS); e <= 256 / NS; e *= 2)
+      if (fd_small_smem(NS, e, tsz) <= FD_SMALL_DYN_MAX) add(e);
+    if (fd_small_smem(NS, 128 / NS, tsz) <= FD_SMALL_DYN_MAX) add(128 / NS);
+    return n;
+  }
+  if (kernel == 3) {
+    if (!(prec == DGFAS_BF16 && H.nsm >= 12)) return 0;
+    for (int k : {2, 4, 6, 8}) add(k);
+    return n;
+  }
+  return 0;
 }
 
 // ============================================================================ combine

@@ -57,7 +57,8 @@ SYMBOLS = ["dgfas_setup_levels", "dgfas_destroy", "dgfas_level_ndof", "dgfas_nod
            "dgfas_use_graph", "dgfas_profile_sweep", "dgfas_fma_peak", "dgfas_schwarz_correct_static", "dgfas_kernel_launches", "dgfas_mlp_param_count",
            "dgfas_mlp_forward", "dgfas_mlp_grad", "dgfas_mlp_train", "dgfas_learned_surrogate",
            "dgfas_assemble_rhs_level", "dgfas_set_level_rhs", "dgfas_composite_residual",
-           "dgfas_get_level_solution", "dgfas_tc_selftest", "dgfas_tc_selftest_mn", "dgfas_tc_error", "dgfas_host_fd_variant", "dgfas_strerror", "dgfas_last_error"]
+           "dgfas_get_level_solution", "dgfas_tc_selftest", "dgfas_tc_selftest_mn", "dgfas_tc_error", "dgfas_host_fd_variant", "dgfas_autotune", "dgfas_set_tuning",
+           "dgfas_get_tuning", "dgfas_strerror", "dgfas_last_error"]
 
 _lib = None
 
@@ -103,6 +104,9 @@ def load():
         "dgfas_tc_selftest": (I, [P, ctypes.POINTER(I)]),
         "dgfas_tc_error": (I, [P]),
         "dgfas_tc_selftest_mn": (I, [P, ctypes.POINTER(I)]),
+        "dgfas_autotune": (I, [P, I, P, I, ctypes.POINTER(I)]),
+        "dgfas_set_tuning": (I, [P, I, I, I]),
+        "dgfas_get_tuning": (I, [P, I, I, ctypes.POINTER(I), P, I, ctypes.POINTER(I)]),
         "dgfas_strerror": (ctypes.c_char_p, [I]),
         "dgfas_last_error": (ctypes.c_char_p, []),
     }
@@ -231,6 +235,32 @@ class Solver:
         _check(load().dgfas_profile_sweep(self.ctx, level % self.n_levels, _ptr(u), _ptr(g), reps,
                                           ms.ctypes.data_as(ctypes.c_void_p)), "profile_sweep")
         return dict(residual_smoother=ms[0], fd=ms[1], combine=ms[2], residual_fp64=ms[3])
+
+    TUNE_KERNELS = ("apply_fp64_elements_per_cta", "apply_smoother_elements_per_cta",
+                    "fd_elements_per_cta", "fd_tensorcore_ctas_per_sm")
+
+    def dgfas_autotune(self, reps=5):
+        """Times the candidate launch shapes of the tunable kernels on every
+        level and keeps the fastest; returns one dict per tuned (level, kernel)."""
+        cap = 4 * 4 * self.n_levels
+        rep = np.zeros((cap, 5))
+        n = ctypes.c_int(0)
+        _check(load().dgfas_autotune(self.ctx, reps, rep.ctypes.data_as(ctypes.c_void_p), cap,
+                                     ctypes.byref(n)), "autotune")
+        return [dict(level=int(r[0]), kernel=self.TUNE_KERNELS[int(r[1])], value=int(r[2]),
+                     ms=float(r[3]), default_ms=float(r[4])) for r in rep[:n.value]]
+
+    def dgfas_set_tuning(self, level, kernel, value):
+        _check(load().dgfas_set_tuning(self.ctx, level % self.n_levels, kernel, value), "set_tuning")
+
+    def dgfas_get_tuning(self, level, kernel):
+        """(current value, candidate values) of `kernel` (0..3) on `level`."""
+        v, n = ctypes.c_int(0), ctypes.c_int(0)
+        cand = np.zeros(16, dtype=np.int32)
+        _check(load().dgfas_get_tuning(self.ctx, level % self.n_levels, kernel, ctypes.byref(v),
+                                       cand.ctypes.data_as(ctypes.c_void_p), 16, ctypes.byref(n)),
+               "get_tuning")
+        return v.value, [int(x) for x in cand[:n.value]]
 
     def dgfas_schwarz_correct_static(self, level, r, u):
         """u += weighted Schwarz correction of r, using the library's static
