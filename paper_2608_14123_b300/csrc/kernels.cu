@@ -25,6 +25,11 @@ std::atomic<long long> g_kernels{0};   // kernels launched through the library
 
 template <typename T> __device__ __forceinline__ T ld(const T* p) { return __ldg(p); }
 
+// x / y of the FD scaling by D^-1: exact in FP64; in FP32 the fast division
+// (reciprocal and multiply, 2 ulp), far below the smoother's own error
+__device__ __forceinline__ double fd_div(double x, double y) { return x / y; }
+__device__ __forceinline__ float fd_div(float x, float y) { return __fdividef(x, y); }
+
 // ============================================================================ apply
 // Team of N*N threads (tx, ty) per element, looping over k; EPB teams per CTA.
 // Shared memory per team: u, neighbour buffer, F1, F2, F3, face-flux R (6 N^3).
@@ -233,9 +238,10 @@ struct BoxEo {
   T w[N];
 };
 
-// (FP32 instantiations are latency bound: registers capped for 4 CTAs per SM)
+// (registers capped for 4 CTAs per SM in FP32, which is latency bound, and 2 in
+// FP64, so that two CTAs of 243 threads keep the FP64 pipe fed)
 template <int N, typename T, typename TU, typename TB, typename TO>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 1) k_apply_box_eo(const LevelView<T> L, const T* __restrict__ bx,
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_apply_box_eo(const LevelView<T> L, const T* __restrict__ bx,
                                const T* __restrict__ Lhat, const TU* __restrict__ u,
                                const TB* __restrict__ b, TO* __restrict__ out, T alpha) {
   constexpr int N2 = N * N, N3 = N * N * N, H = N / 2, HC = (N + 1) / 2;
@@ -605,7 +611,8 @@ __global__ void k_fd(const LevelView<T> L, const TR* __restrict__ r, T* __restri
   const T g0 = L.g[4 * e], g1 = L.g[4 * e + 1], g2 = L.g[4 * e + 2], g3 = L.g[4 * e + 3];
   if (in_ab)
     for (int c = 0; c < n3; ++c)
-      Y[(c * NS + b) * NS + a] /= (g0 + g1 * l1[a] + g2 * l2[b] + g3 * l3[c]);
+      Y[(c * NS + b) * NS + a] =
+          fd_div(Y[(c * NS + b) * NS + a], g0 + g1 * l1[a] + g2 * l2[b] + g3 * l3[c]);
   __syncthreads();
   // S3 along c: X[c][b][a] = sum_c' S3[c][c'] Y[c'][b][a], thread (a, c)
   if (in_ac) {
@@ -775,7 +782,7 @@ __global__ void __launch_bounds__(256) k_fd_small(const LevelView<T> L, const TR
         T acc = T(0);
 #pragma unroll
         for (int q = 0; q < NS; ++q) acc += Sm[q][p] * x[q];
-        y[p] = acc / (d0 + g3 * tl[v3][p]);
+        y[p] = fd_div(acc, d0 + g3 * tl[v3][p]);
       }
 #pragma unroll
       for (int p = 0; p < NS; ++p) {
