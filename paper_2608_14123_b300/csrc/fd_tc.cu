@@ -277,12 +277,16 @@ __device__ __forceinline__ void tc_read1(uint32_t tmem, int t, float* v) {
   tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + 16 * t, v);
 }
 
+// TN, TM > 0: instantiation for N = TN nodes and TM overlap layers, whose
+// gather resolves the row's three source segments at compile time; TN = 0:
+// any N and m (per-position gather maps).
+template <int TN, int TM>
 __global__ void __launch_bounds__(128, 8) k_fd_tc(const LevelView<float> L, const float* __restrict__ r,
                                                   float* __restrict__ patch, int* __restrict__ err) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   FdTcSmem& s = *reinterpret_cast<FdTcSmem*>(smem_raw);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int N = L.N, m = L.m, nsm = L.nsm, N3 = N * N * N;
+  const int N = TN > 0 ? TN : L.N, m = TN > 0 ? TM : L.m, nsm = L.nsm, N3 = N * N * N;
   const size_t NS3 = (size_t)nsm * nsm * nsm;
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 32;" ::"r"(smem_u32(&s.tslot)));
@@ -355,16 +359,44 @@ __global__ void __launch_bounds__(128, 8) k_fd_tc(const LevelView<float> L, cons
       if (my >= 0 && mz >= 0) {
         const int* nb = s.nb + 3 * (my >> 8) + 9 * (mz >> 8);
         const long long line = ((mz & 255) * N + (my & 255)) * N;
-        const long long b0 = nb[0] >= 0 ? (long long)nb[0] * N3 + line : -1;
-        const long long b1 = nb[1] >= 0 ? (long long)nb[1] * N3 + line : -1;
-        const long long b2 = nb[2] >= 0 ? (long long)nb[2] * N3 + line : -1;
+        if constexpr (TN > 0) {
+          // segments of the row along a: left layers (x-neighbour -1), own
+          // nodes, right layers (x-neighbour +1)
+          const float* p0 = nb[0] >= 0 ? r + (long long)nb[0] * N3 + line : nullptr;
+          const float* p1 = nb[1] >= 0 ? r + (long long)nb[1] * N3 + line : nullptr;
+          const float* p2 = nb[2] >= 0 ? r + (long long)nb[2] * N3 + line : nullptr;
+          const bool li = (v1 >> 2) == 0, ri = (v1 & 3) == 0;
+          if (li) {
 #pragma unroll
-        for (int q = 0; q < 16; ++q) {
-          const int mx = s.gmap[0][q];
-          if (mx < 0) continue;
-          const int o = mx >> 8;
-          const long long bs = o == 0 ? b0 : (o == 1 ? b1 : b2);
-          if (bs >= 0) vals[q] = r[bs + (mx & 255)];
+            for (int a = 0; a < TM; ++a) vals[a] = p0 ? p0[TN - TM + a] : 0.0f;
+#pragma unroll
+            for (int a = 0; a < TN; ++a) vals[TM + a] = p1 ? p1[a] : 0.0f;
+            if (ri) {
+#pragma unroll
+              for (int a = 0; a < TM; ++a)
+                if (2 * TM + TN + a - TM < 16) vals[TM + TN + a] = p2 ? p2[a] : 0.0f;
+            }
+          } else {
+#pragma unroll
+            for (int a = 0; a < TN; ++a) vals[a] = p1 ? p1[a] : 0.0f;
+            if (ri) {
+#pragma unroll
+              for (int a = 0; a < TM; ++a)
+                if (TN + a < 16) vals[TN + a] = p2 ? p2[a] : 0.0f;
+            }
+          }
+        } else {
+          const long long b0 = nb[0] >= 0 ? (long long)nb[0] * N3 + line : -1;
+          const long long b1 = nb[1] >= 0 ? (long long)nb[1] * N3 + line : -1;
+          const long long b2 = nb[2] >= 0 ? (long long)nb[2] * N3 + line : -1;
+#pragma unroll
+          for (int q = 0; q < 16; ++q) {
+            const int mx = s.gmap[0][q];
+            if (mx < 0) continue;
+            const int o = mx >> 8;
+            const long long bs = o == 0 ? b0 : (o == 1 ? b1 : b2);
+            if (bs >= 0) vals[q] = r[bs + (mx & 255)];
+          }
         }
       }
       unsigned char* t = s.A[0][0] + (row >> 7) * TC_TILE;
@@ -451,19 +483,33 @@ __global__ void __launch_bounds__(128, 8) k_fd_tc(const LevelView<float> L, cons
 
 int launch_fd_tc(Ctx& c, int l, const float* r) {
   LevelHost& H = c.lv[l];
-  static bool attr = false;
   const int smem = (int)sizeof(FdTcSmem) + 1024;
-  if (!attr) {
-    CK(cudaFuncSetAttribute(k_fd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    attr = true;
-  }
   int dev = 0, nsm = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   // CTAs per SM: the autotuner's choice, else the 8 that registers allow
   const int per_sm = H.tune.fdtc > 0 ? std::min(H.tune.fdtc, 8) : 8;
   const int grid = std::min(H.ne, nsm * per_sm);
-  k_fd_tc<<<grid, 128, smem, c.stream>>>(H.v32, r, (float*)c.patch, c.tc_err);
+  auto go = [&](auto kern) -> int {
+    static bool attr = false;   // one per instantiation
+    if (!attr) {
+      CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+      attr = true;
+    }
+    kern<<<grid, 128, smem, c.stream>>>(H.v32, r, (float*)c.patch, c.tc_err);
+    return DGFAS_OK;
+  };
+  int rc;
+  const int key = 16 * H.N + H.m;
+  switch (key) {
+    case 16 * 8 + 2: rc = go(k_fd_tc<8, 2>); break;
+    case 16 * 9 + 2: rc = go(k_fd_tc<9, 2>); break;
+    case 16 * 10 + 2: rc = go(k_fd_tc<10, 2>); break;
+    case 16 * 11 + 2: rc = go(k_fd_tc<11, 2>); break;
+    case 16 * 9 + 3: rc = go(k_fd_tc<9, 3>); break;
+    default: rc = go(k_fd_tc<0, 0>); break;
+  }
+  if (rc != DGFAS_OK) return rc;
   ++g_kernels;
   CK(cudaGetLastError());
   return DGFAS_OK;
