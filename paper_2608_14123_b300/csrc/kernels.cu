@@ -306,19 +306,19 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_apply_box_eo(co
         B += M.dO[r] * od[r];
       }
       const T dm[2] = {A + B, B - A};
-      // faces at both ends
+      // faces at both ends (sign s = -1 at the left end, +1 at the right; with
+      // c_n = s g_d w_a w_b the flux mu W [[u]] - (q_m - q_p)/2 and the
+      // lifting -[[u]] c_n / 2 are regrouped so that the factors shared by
+      // both ends are formed once)
+      const T cd = gd * wab, hcd = T(0.5) * cd, Wf = afd * wab;
       T flux[2] = {0, 0}, lift[2] = {0, 0};
 #pragma unroll
       for (int sd = 0; sd < 2; ++sd) {
         const int f = 2 * d + sd;
         const int nb = L.nbr[6 * e + f];
         if (nb == -2) continue;   // Neumann: no face term
-        const T sgn = sd ? T(1) : T(-1);
-        const T cn = sgn * gd * wab;   // nu W n . grad xi_d
-        const T Wf = afd * wab;        // nu * surface weight
-        const T mu = L.mu[6 * e + f];
+        const T muW = L.mu[6 * e + f] * Wf;   // nu mu * surface weight
         const T um = x[sd ? N - 1 : 0];
-        const T qm = cn * dm[sd];
         if (nb >= 0) {
           // the neighbour's line through the shared face node; its face end is the opposite one
           const TU* z = u + (size_t)nb * N3 + base;
@@ -330,17 +330,18 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_apply_box_eo(co
             dp += Dp[l] * zl;
             if (l == (sd ? 0 : N - 1)) up = zl;
           }
-          const T qp = -sgn * bx[6 * nb + d] * wab * dp;
+          const T hp = T(0.5) * bx[6 * nb + d] * wab;
+          const T t = hcd * dm[sd] + hp * dp;   // s (q_m - q_p) / 2
           const T jump = um - up;
-          flux[sd] = mu * Wf * jump - T(0.5) * (qm - qp);
-          lift[sd] = T(-0.5) * jump * cn;
+          flux[sd] = sd ? muW * jump - t : muW * jump + t;
+          lift[sd] = sd ? -hcd * jump : hcd * jump;
         } else {
-          flux[sd] = T(2) * mu * Wf * um - qm;
-          lift[sd] = -um * cn;
+          const T qm = cd * dm[sd];   // s q_m
+          flux[sd] = sd ? T(2) * muW * um - qm : T(2) * muW * um + qm;
+          lift[sd] = sd ? -cd * um : cd * um;
         }
       }
       // volume + lifting: y = g_d w_a w_b Lhat x + D[0]^T lift0 + D[N-1]^T lift1
-      const T cd = gd * wab;
       const T Ls = lift[0] - lift[1], La = lift[0] + lift[1];
 #pragma unroll
       for (int r = 0; r < HC; ++r) {
@@ -954,18 +955,24 @@ int tune_candidates(Ctx& c, int l, int kernel, int* out, int max_out) {
 // memory; per node only the candidate test and the load remain.  Elements of
 // small degree are packed several to a CTA.  Frozen elements are left
 // untouched (ADD) or zeroed (!ADD).
-template <int N, typename T, bool ADD, typename TO>
+// IDX: offset type (32-bit when every patch index of the level fits)
+template <int N, typename T, bool ADD, typename TO, typename IDX>
 __global__ void __launch_bounds__(256) k_combine(const LevelView<T> L, const T* __restrict__ patch,
                                                   TO* __restrict__ u) {
   constexpr int N3 = N * N * N;
   constexpr int EPB = N3 >= 256 ? 1 : 256 / N3;
-  __shared__ long long s_off[EPB][27];
+  __shared__ IDX s_off[EPB][27];
+  __shared__ int s_frz[EPB];
   const int m = L.m, nsm = L.nsm;
-  const long long NS3 = (long long)nsm * nsm * nsm;
+  const IDX NS3 = (IDX)nsm * nsm * nsm;
   const int e0 = blockIdx.x * EPB;
+  if (threadIdx.x < EPB) {
+    const int e = e0 + threadIdx.x;
+    s_frz[threadIdx.x] = e < L.ne && L.cls[e] == DGFAS_FROZEN;
+  }
   for (int t = threadIdx.x; t < EPB * 27; t += blockDim.x) {
     const int el = t / 27, slot = t % 27, e = e0 + el;
-    long long off = -1;
+    IDX off = -1;
     if (e < L.ne) {
       const int src = L.nbr27[27 * e + slot];
       if (src >= 0 && L.cls[src] != DGFAS_FROZEN) {
@@ -980,7 +987,7 @@ __global__ void __launch_bounds__(256) k_combine(const LevelView<T> L, const T* 
           if ((o[d] < 0 && !right_i) || (o[d] > 0 && !left_i)) reach = false;
           shift[d] = o[d] == 0 ? ml : (o[d] < 0 ? ml + N : -(N - m));
         }
-        if (reach) off = (long long)src * NS3 + ((long long)shift[2] * nsm + shift[1]) * nsm + shift[0];
+        if (reach) off = (IDX)src * NS3 + ((IDX)shift[2] * nsm + shift[1]) * nsm + shift[0];
       }
     }
     s_off[el][slot] = off;
@@ -991,7 +998,7 @@ __global__ void __launch_bounds__(256) k_combine(const LevelView<T> L, const T* 
     const int e = e0 + el;
     if (e >= L.ne) continue;
     const size_t g = (size_t)e * N3 + n;
-    if (L.cls[e] == DGFAS_FROZEN) {
+    if (s_frz[el]) {
       if (!ADD) u[g] = TO(0);
       continue;
     }
@@ -1000,14 +1007,14 @@ __global__ void __launch_bounds__(256) k_combine(const LevelView<T> L, const T* 
     const int cx = i < m ? 0 : (i >= N - m ? 2 : -1);
     const int cy = j < m ? 0 : (j >= N - m ? 2 : -1);
     const int cz = k < m ? 0 : (k >= N - m ? 2 : -1);
-    const long long loc = ((long long)k * nsm + j) * nsm + i;
+    const IDX loc = ((IDX)k * nsm + j) * nsm + i;
     // the (up to) 8 candidate loads are independent: unrolled so that they are
     // all in flight together
     T v[8];
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
       const int sx = (q & 1) ? cx : 1, sy = (q & 2) ? cy : 1, sz = (q & 4) ? cz : 1;
-      const long long off = (sx < 0 || sy < 0 || sz < 0) ? -1 : s_off[el][sx + 3 * sy + 9 * sz];
+      const IDX off = (sx < 0 || sy < 0 || sz < 0) ? IDX(-1) : s_off[el][sx + 3 * sy + 9 * sz];
       v[q] = off >= 0 ? patch[off + loc] : T(0);
     }
     // summed in the fixed order own, x, y, xy, z, ... (deterministic)
@@ -1021,22 +1028,30 @@ __global__ void __launch_bounds__(256) k_combine(const LevelView<T> L, const T* 
 
 template <typename T, bool ADD, typename TO>
 static int combine_launch(const LevelView<T>& L, int N, const T* patch, TO* u, cudaStream_t st) {
-  auto go = [&](auto kern, int n3) {
+  auto go = [&](auto k32, auto k64, int n3) {
     const int epb = n3 >= 256 ? 1 : 256 / n3;
     const int bs = n3 >= 256 ? 256 : ((epb * n3 + 31) / 32) * 32;
-    kern<<<(unsigned)((L.ne + epb - 1) / epb), bs, 0, st>>>(L, patch, u);
+    const unsigned grid = (unsigned)((L.ne + epb - 1) / epb);
+    const long long nsm = L.nsm;
+    if ((long long)L.ne * nsm * nsm * nsm < (1LL << 31))
+      k32<<<grid, bs, 0, st>>>(L, patch, u);
+    else
+      k64<<<grid, bs, 0, st>>>(L, patch, u);
   };
+#define DGFAS_CB(NN) \
+  go(k_combine<NN, T, ADD, TO, int>, k_combine<NN, T, ADD, TO, long long>, NN * NN * NN)
   switch (N) {
-    case 2: go(k_combine<2, T, ADD, TO>, 8); break;
-    case 3: go(k_combine<3, T, ADD, TO>, 27); break;
-    case 4: go(k_combine<4, T, ADD, TO>, 64); break;
-    case 5: go(k_combine<5, T, ADD, TO>, 125); break;
-    case 6: go(k_combine<6, T, ADD, TO>, 216); break;
-    case 7: go(k_combine<7, T, ADD, TO>, 343); break;
-    case 8: go(k_combine<8, T, ADD, TO>, 512); break;
-    case 9: go(k_combine<9, T, ADD, TO>, 729); break;
-    case 10: go(k_combine<10, T, ADD, TO>, 1000); break;
-    case 11: go(k_combine<11, T, ADD, TO>, 1331); break;
+    case 2: DGFAS_CB(2); break;
+    case 3: DGFAS_CB(3); break;
+    case 4: DGFAS_CB(4); break;
+    case 5: DGFAS_CB(5); break;
+    case 6: DGFAS_CB(6); break;
+    case 7: DGFAS_CB(7); break;
+    case 8: DGFAS_CB(8); break;
+    case 9: DGFAS_CB(9); break;
+    case 10: DGFAS_CB(10); break;
+    case 11: DGFAS_CB(11); break;
+#undef DGFAS_CB
     default:
       set_error("combine: unsupported N");
       return DGFAS_ERR_UNSUPPORTED;
