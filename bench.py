@@ -394,24 +394,48 @@ def run_gpu(args):
         torch.distributed.barrier()
     value = ndof * ws / (ms * 1e-3)
 
-    # ---- end to end through the public API with host buffers
+    # ---- end to end through the public API with host buffers: every step
+    # copies its inputs (u, f) from pinned host memory and reads its result u
+    # back; two device buffer pairs and two copy streams let step k+1's
+    # upload and step k-1's download overlap step k's V-cycle (the library
+    # keeps one captured graph per buffer pair)
     u_host = torch.from_numpy(cfg["u0"]).pin_memory()
     b_host = b.cpu().pin_memory()
-    u_back = torch.empty_like(u_host).pin_memory()
-    ud = torch.empty_like(u0)
-    bd = torch.empty_like(b)
-    steps_e2e = max(2, min(args.steps, 5))
+    u_back = [torch.empty_like(u_host).pin_memory() for _ in range(2)]
+    ud = [torch.empty_like(u0) for _ in range(2)]
+    bd = [torch.empty_like(b) for _ in range(2)]
+    comp = torch.cuda.current_stream()
+    s_h2d, s_d2h = torch.cuda.Stream(), torch.cuda.Stream()
+    h2d_done = [torch.cuda.Event() for _ in range(2)]
+    comp_done = [torch.cuda.Event() for _ in range(2)]
+    d2h_done = [torch.cuda.Event() for _ in range(2)]
+
+    def e2e_steps(n):
+        for k in range(n):
+            i = k % 2
+            with torch.cuda.stream(s_h2d):
+                if k >= 2:
+                    s_h2d.wait_event(d2h_done[i])
+                ud[i].copy_(u_host, non_blocking=True)
+                bd[i].copy_(b_host, non_blocking=True)
+                h2d_done[i].record(s_h2d)
+            comp.wait_event(h2d_done[i])
+            S.dgfas_fas_vcycle(ud[i], bd[i], want_norm=False)
+            comp_done[i].record(comp)
+            with torch.cuda.stream(s_d2h):
+                s_d2h.wait_event(comp_done[i])
+                u_back[i].copy_(ud[i], non_blocking=True)
+                d2h_done[i].record(s_d2h)
+
+    e2e_steps(2)   # first use of each buffer pair captures its graph
     torch.cuda.synchronize()
+    steps_e2e = max(4, min(args.steps, 10))
     t0 = time.perf_counter()
-    for _ in range(steps_e2e):
-        ud.copy_(u_host, non_blocking=True)
-        bd.copy_(b_host, non_blocking=True)
-        S.dgfas_fas_vcycle(ud, bd, want_norm=False)
-        u_back.copy_(ud, non_blocking=True)
+    e2e_steps(steps_e2e)
     torch.cuda.synchronize()
     e2e_s = (time.perf_counter() - t0) / steps_e2e
     e2e = {"value": ndof / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 2 * ndof * 8,
-           "d2h_bytes_per_step": ndof * 8}
+           "d2h_bytes_per_step": ndof * 8, "overlap": "double-buffered, 2 copy streams"}
 
     # ---- per-kernel timing of the top-level smoother and the roofline
     L = S.n_levels - 1

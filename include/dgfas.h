@@ -177,7 +177,9 @@ int dgfas_set_surrogate(void* ctx, int level, const double* g);
 int dgfas_get_surrogate(void* ctx, int level, double* g);
 
 /* Enables (1) or disables (0) CUDA-graph replay of the V-cycle body in
-   dgfas_fas_vcycle / dgfas_solve (captured on first use per (u, f) pair). */
+   dgfas_fas_vcycle / dgfas_solve (captured on first use per (u, f) pair; the
+   graphs of the four most recently used pairs are kept, so a caller may
+   alternate buffers, e.g. to overlap its own copies with the solve). */
 int dgfas_use_graph(void* ctx, int enable);
 
 /* Per-kernel timing of `reps` smoother sweeps on `level` (level >= 1) with CUDA

@@ -91,6 +91,9 @@ struct LevelHost {
   Tune tune;
 };
 
+struct Ctx;
+void drop_graphs(Ctx& c);   // destroys every captured cycle body
+
 struct Ctx {
   cudaStream_t stream = nullptr;
   dgfas_params prm{};
@@ -111,11 +114,20 @@ struct Ctx {
   int n_root = 0;
   // graphs
   int use_graph = 0;
-  cudaGraphExec_t gexec = nullptr;
-  const double* g_u = nullptr;
-  const double* g_f = nullptr;
-  int g_kind = -1;
-  long long graph_kernels = 0;   // kernel nodes of the captured graph
+  // captured cycle bodies, one per (u, f, kind) in use (a caller that
+  // alternates buffers, e.g. to overlap its copies with the solve, replays
+  // each without capturing again); least recently used entry replaced
+  struct GraphEntry {
+    cudaGraphExec_t exec = nullptr;
+    const double* u = nullptr;
+    const double* f = nullptr;
+    int kind = -1;
+    long long kernels = 0;       // kernel nodes of the captured graph
+    unsigned long long used = 0;
+  };
+  static constexpr int kGraphs = 4;
+  GraphEntry graphs[kGraphs];
+  unsigned long long graph_clock = 0;
   int local = 0;                 // leaves below the top or frozen elements exist
 };
 

@@ -444,7 +444,7 @@ extern "C" void dgfas_destroy(void* vctx) {
   if (!vctx) return;
   Ctx* c = (Ctx*)vctx;
   if (c->stream) cudaStreamSynchronize(c->stream);
-  if (c->gexec) cudaGraphExecDestroy(c->gexec);
+  drop_graphs(*c);
   if (c->cap) cudaStreamDestroy(c->cap);
   if (c->ev_in) cudaEventDestroy(c->ev_in);
   if (c->ev_out) cudaEventDestroy(c->ev_out);
@@ -733,6 +733,13 @@ static bool graph_ok(Ctx& c) { return c.use_graph && c.prm.smoother == DGFAS_WAS
 // Runs one cycle body on the caller's stream, or replays it as a CUDA graph
 // captured on the context's internal stream (ordered after and before the
 // caller's stream by events).
+void drop_graphs(Ctx& c) {
+  for (auto& g : c.graphs) {
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    g = Ctx::GraphEntry{};
+  }
+}
+
 static int run_body(Ctx& c, int kind, double* u, const double* f) {
   if (!graph_ok(c)) return kind == 0 ? vcycle_body(c, u, f) : solve_cycle_body(c, u, f);
   cudaStream_t user = c.stream;
@@ -740,8 +747,18 @@ static int run_body(Ctx& c, int kind, double* u, const double* f) {
   CK(cudaStreamWaitEvent(c.cap, c.ev_in, 0));
   c.stream = c.cap;
   int rc = DGFAS_OK;
-  if (!(c.gexec && c.g_u == u && c.g_f == f && c.g_kind == kind)) {
-    if (c.gexec) { cudaGraphExecDestroy(c.gexec); c.gexec = nullptr; }
+  Ctx::GraphEntry* hit = nullptr;
+  for (auto& g : c.graphs)
+    if (g.exec && g.u == u && g.f == f && g.kind == kind) hit = &g;
+  if (!hit) {
+    // the slot to (re)fill: an empty one, else the least recently used
+    Ctx::GraphEntry* slot = &c.graphs[0];
+    for (auto& g : c.graphs) {
+      if (!g.exec) { slot = &g; break; }
+      if (g.used < slot->used) slot = &g;
+    }
+    if (slot->exec) cudaGraphExecDestroy(slot->exec);
+    *slot = Ctx::GraphEntry{};
     // this call's cycle runs uncaptured (it also sets the kernels' attributes) ...
     rc = kind == 0 ? vcycle_body(c, u, f) : solve_cycle_body(c, u, f);
     if (rc == DGFAS_OK && cudaStreamSynchronize(c.cap) != cudaSuccess) rc = DGFAS_ERR_CUDA;
@@ -754,23 +771,29 @@ static int run_body(Ctx& c, int kind, double* u, const double* f) {
         const long long k0 = g_kernels.load();
         int rc2 = kind == 0 ? vcycle_body(c, u, f) : solve_cycle_body(c, u, f);
         cudaError_t ce = cudaStreamEndCapture(c.cap, &g);
-        c.graph_kernels = g_kernels.load() - k0;   // captured, not executed
-        g_kernels -= c.graph_kernels;
+        slot->kernels = g_kernels.load() - k0;   // captured, not executed
+        g_kernels -= slot->kernels;
         if (rc2 != DGFAS_OK) rc = rc2;
-        else if (ce != cudaSuccess || cudaGraphInstantiate(&c.gexec, g, 0) != cudaSuccess) {
+        else if (ce != cudaSuccess || cudaGraphInstantiate(&slot->exec, g, 0) != cudaSuccess) {
           set_error("graph capture/instantiate failed");
           rc = DGFAS_ERR_CUDA;
-          c.gexec = nullptr;
+          slot->exec = nullptr;
         }
         if (g) cudaGraphDestroy(g);
-        if (rc == DGFAS_OK) { c.g_u = u; c.g_f = f; c.g_kind = kind; }
+        if (rc == DGFAS_OK) {
+          slot->u = u;
+          slot->f = f;
+          slot->kind = kind;
+          slot->used = ++c.graph_clock;
+        }
       }
     }
-  } else if (cudaGraphLaunch(c.gexec, c.cap) != cudaSuccess) {
+  } else if (cudaGraphLaunch(hit->exec, c.cap) != cudaSuccess) {
     set_error("graph launch failed");
     rc = DGFAS_ERR_CUDA;
   } else {
-    g_kernels += c.graph_kernels;
+    g_kernels += hit->kernels;
+    hit->used = ++c.graph_clock;
   }
   c.stream = user;
   CK(cudaEventRecord(c.ev_out, c.cap));
@@ -979,7 +1002,7 @@ extern "C" int dgfas_use_graph(void* ctx, int enable) {
   Ctx* c = (Ctx*)ctx;
   if (!c) return DGFAS_ERR_INVALID;
   c->use_graph = enable ? 1 : 0;
-  if (!enable && c->gexec) { cudaGraphExecDestroy(c->gexec); c->gexec = nullptr; }
+  if (!enable) drop_graphs(*c);
   return DGFAS_OK;
 }
 
@@ -1054,7 +1077,7 @@ extern "C" int dgfas_autotune(void* ctx, int reps, double* report, int max_entri
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   // launch shapes are baked into a captured graph: capture again on next use
-  if (c->gexec) { cudaGraphExecDestroy(c->gexec); c->gexec = nullptr; }
+  drop_graphs(*c);
   if (n_entries) *n_entries = n_rep;
   return rc;
 }
@@ -1076,7 +1099,7 @@ extern "C" int dgfas_set_tuning(void* ctx, int level, int kernel, int value) {
     }
   }
   *tune_field(c->lv[level], kernel) = value;
-  if (c->gexec) { cudaGraphExecDestroy(c->gexec); c->gexec = nullptr; }
+  drop_graphs(*c);
   return DGFAS_OK;
 }
 
