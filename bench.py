@@ -58,6 +58,12 @@ def apply_flops_per_dof(N, box=True):
     return vol + face
 
 
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
+# dominant kernel on this workload, from one ncu capture of the current kernel
+# (32^3 elements, p = 8, BF16 smoother run); to be retaken whenever the kernel changes
+NCU_TRAFFIC = {"residual_fp64": 386993664 + 168107520}
+
+
 def fd_flops_per_dof(N, m):
     ns = N + 2 * m
     return 12.0 * ns ** 4 / N ** 3
@@ -466,7 +472,8 @@ def run_gpu(args):
     else:
         achieved = kd["flops"] / (kd["ms"] * 1e-3) / 1e12
     roofline = {"bound": kd["bound"], "kernel": dom, "achieved": achieved, "peak": kd["peak"],
-                "unit": kd["unit"], "frac": achieved / kd["peak"], "traffic": None,
+                "unit": kd["unit"], "frac": achieved / kd["peak"],
+                "traffic": NCU_TRAFFIC.get(dom) if prec == dgfas.DGFAS_BF16 else None,
                 "peak_source": ("measured FMA microbenchmark (dgfas_fma_peak)" if kd["bound"] == "alu"
                                 else f"{pk['src']} HBM copy")}
     shares = {k: v["count"] * v["ms"] for k, v in kernels.items()}
