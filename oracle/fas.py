@@ -72,12 +72,13 @@ class Hierarchy:
     def root_solve(self, g):
         return sla.cho_solve(self.root_chol, g)
 
-    def _down_up(self, u, f, r_top):
+    def _down_up(self, u, f, r_top, top=None):
         """Alg. 2 below the top pre-smoothing: given the top residual r_top of
         u[L], project, form the parent right-hand sides, solve the root,
         prolongate the corrections and smooth on levels L-1..1 (top-level
-        smoothing is left to the caller)."""
-        L = self.L
+        smoothing is left to the caller).  `top` makes a lower level act as
+        the top (the sub-hierarchy cycles of the full multigrid startup)."""
+        L = self.L if top is None else top
         u = list(u)
         g = [None] * (L + 1)
         g[L] = f
@@ -107,6 +108,25 @@ class Hierarchy:
         u = self._down_up(u, f, r)
         u[L] = self.smooth(L, u[L], f, self.s2)
         return u, np.linalg.norm(r)
+
+    def fmg(self, f_levels, cycles=1):
+        """Alg. 4 (FAS-FMG startup).  f_levels: each level's own right-hand
+        side, root first.  Level 1 of the paper's loop is the root, whose
+        V-cycle is its exact solve; then for l = 1 .. L-1 (root = 0) the
+        solution is interpolated, u_l = I_l u_{l-1}, and improved by `cycles`
+        FAS V-cycles (Alg. 2) on levels 0..l with f_l on top; the returned
+        top start value is I_L u_{L-1}."""
+        L = self.L
+        u = [np.zeros(o.ndof) for o in self.ops]
+        u[0] = self.root_solve(f_levels[0])
+        for l in range(1, L):
+            u[l] = self.tr[l].interpolate(u[l - 1])
+            for _ in range(cycles):
+                u[l] = self.smooth(l, u[l], f_levels[l], self.s1)
+                r = self.residual(l, u[l], f_levels[l])
+                u[:l + 1] = self._down_up(u[:l + 1], f_levels[l], r, top=l)
+                u[l] = self.smooth(l, u[l], f_levels[l], self.s2)
+        return self.tr[L].interpolate(u[L - 1])
 
     def cs_vcycle(self, u_top, f_top):
         """Alg. 1."""
