@@ -190,6 +190,20 @@ int dgfas_use_graph(void* ctx, int enable);
 int dgfas_profile_sweep(void* ctx, int level, double* u, const double* g, int reps,
                         double* ms_out);
 
+/* Full multigrid startup (FAS-FMG, Alg. 4): the root is solved exactly for
+   its own right-hand side f_levels[0]; then for l = 1 .. L-1 the root's (or
+   previous level's) solution is interpolated to level l, u_l = I u_{l-1},
+   and cycles_per_level FAS V-cycles (Alg. 2) with level l as the top and its
+   own right-hand side f_levels[l] improve it; finally u_top = I u_{L-1}.
+   u_top (device, top-level layout) is the start value for dgfas_solve /
+   dgfas_fas_vcycle on the full hierarchy.  f_levels: host array of
+   n_levels device pointers, f_levels[l] the assembled right-hand side of
+   level l (dgfas_assemble_rhs_level), f_levels[n_levels-1] the top's (read
+   only for validation).  Paper: one V-cycle per level.  Globally refined
+   hierarchies only (DGFAS_ERR_UNSUPPORTED when a level below the top has
+   leaf elements or any level frozen ones).  Stream-ordered, not captured. */
+int dgfas_fmg(void* ctx, const double* const* f_levels, int cycles_per_level, double* u_top);
+
 /* Launch-shape autotuner (the batching / tile-tuning step of the hot path):
    for every level it times, with CUDA events on the context's stream, the
    candidate launch shapes of the tunable kernels and keeps the fastest:

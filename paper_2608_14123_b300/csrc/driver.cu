@@ -673,8 +673,10 @@ static int smooth(Ctx& c, int l, double* u, const double* g, int n, bool zero_st
 // Alg. 2 below the top level: lv[L].r holds the top residual of uL (after the
 // top pre-smoothing).  Ends with the top correction I (u_{L-1} - P u_L) in
 // lv[L].delta, not yet added to uL (the caller's top smoothing adds it).
-static int down_up(Ctx& c, double* uL, const double* fL) {
-  const int L = (int)c.lv.size() - 1;
+static int down_up(Ctx& c, double* uL, const double* fL, int top = -1) {
+  // top: the level that acts as the top (default: the finest); levels below
+  // it keep their state in lv[l].u / lv[l].gv
+  const int L = top < 0 ? (int)c.lv.size() - 1 : top;
   const int prec = c.prm.precision;
   for (int l = L; l >= 1; --l) {
     double* ul = l == L ? uL : c.lv[l].u;
@@ -726,6 +728,27 @@ static int solve_cycle_body(Ctx& c, double* u, const double* f) {
   RET(smooth(c, L, u, f, c.prm.sc, false, false));
   RET(launch_apply(c, L, DGFAS_FP64, u, f, c.lv[L].r, -1.0));
   return launch_sumsq(c, c.lv[L].r, c.lv[L].ndof, c.red);
+}
+
+// Alg. 2 with level T < L as the top (u_T = lv[T].u, RHS f_T): the V-cycle
+// of the full multigrid startup on the sub-hierarchy 0..T.
+static int vcycle_sub(Ctx& c, int T, const double* fT) {
+  double* uT = c.lv[T].u;
+  RET(launch_apply(c, T, DGFAS_FP64, uT, fT, c.lv[T].r, -1.0));
+  RET(smooth(c, T, uT, fT, c.prm.s1, true, true));
+  RET(down_up(c, uT, fT, T));
+  return smooth(c, T, uT, fT, c.prm.s2, false, false);
+}
+
+// u = I (u_c) on level l from lv[l-1].u: the solution interpolation of the
+// full multigrid startup (the correction prolongation with a zero projection)
+static int interpolate_solution(Ctx& c, int l, double* ul) {
+  LevelHost& C = c.lv[l - 1];
+  LevelHost& F = c.lv[l];
+  CK(cudaMemsetAsync(C.ubar, 0, C.ndof * sizeof(double), c.stream));
+  RET(launch_prolong(c, l, ul, DGFAS_FP64, F.delta));
+  CK(cudaMemcpyAsync(ul, F.delta, F.ndof * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
+  return DGFAS_OK;
 }
 
 static bool graph_ok(Ctx& c) { return c.use_graph && c.prm.smoother == DGFAS_WAS; }
@@ -856,6 +879,28 @@ extern "C" int dgfas_assemble_rhs_level(void* ctx, int level, const double* f, c
   Ctx* c = (Ctx*)ctx;
   if (!c || !f || !b || level < 0 || level >= (int)c->lv.size()) return DGFAS_ERR_INVALID;
   return launch_rhs(*c, level, f, uD, b);
+}
+
+extern "C" int dgfas_fmg(void* ctx, const double* const* f_levels, int cycles_per_level,
+                         double* u_top) {
+  Ctx* c = (Ctx*)ctx;
+  if (!c || !f_levels || !u_top || cycles_per_level < 1) return DGFAS_ERR_INVALID;
+  const int L = (int)c->lv.size() - 1;
+  for (int l = 0; l <= L; ++l)
+    if (!f_levels[l]) return DGFAS_ERR_INVALID;
+  if (L < 1 || c->local) {
+    set_error("fmg: needs a globally refined hierarchy of at least two levels");
+    return DGFAS_ERR_UNSUPPORTED;
+  }
+  // level 0: the V-cycle on the root alone is its exact solve
+  CK(cudaMemcpyAsync(c->lv[0].gv, f_levels[0], c->lv[0].ndof * sizeof(double),
+                     cudaMemcpyDeviceToDevice, c->stream));
+  RET(launch_root(*c));
+  for (int l = 1; l < L; ++l) {
+    RET(interpolate_solution(*c, l, c->lv[l].u));
+    for (int k = 0; k < cycles_per_level; ++k) RET(vcycle_sub(*c, l, f_levels[l]));
+  }
+  return interpolate_solution(*c, L, u_top);
 }
 
 extern "C" int dgfas_set_level_rhs(void* ctx, int level, const double* f) {

@@ -58,7 +58,7 @@ SYMBOLS = ["dgfas_setup_levels", "dgfas_destroy", "dgfas_level_ndof", "dgfas_nod
            "dgfas_mlp_forward", "dgfas_mlp_grad", "dgfas_mlp_train", "dgfas_learned_surrogate",
            "dgfas_assemble_rhs_level", "dgfas_set_level_rhs", "dgfas_composite_residual",
            "dgfas_get_level_solution", "dgfas_tc_selftest", "dgfas_tc_selftest_mn", "dgfas_tc_error", "dgfas_host_fd_variant", "dgfas_autotune", "dgfas_set_tuning",
-           "dgfas_get_tuning", "dgfas_strerror", "dgfas_last_error"]
+           "dgfas_get_tuning", "dgfas_fmg", "dgfas_strerror", "dgfas_last_error"]
 
 _lib = None
 
@@ -105,6 +105,7 @@ def load():
         "dgfas_tc_error": (I, [P]),
         "dgfas_tc_selftest_mn": (I, [P, ctypes.POINTER(I)]),
         "dgfas_autotune": (I, [P, I, P, I, ctypes.POINTER(I)]),
+        "dgfas_fmg": (I, [P, ctypes.POINTER(P), I, P]),
         "dgfas_set_tuning": (I, [P, I, I, I]),
         "dgfas_get_tuning": (I, [P, I, I, ctypes.POINTER(I), P, I, ctypes.POINTER(I)]),
         "dgfas_strerror": (ctypes.c_char_p, [I]),
@@ -235,6 +236,13 @@ class Solver:
         _check(load().dgfas_profile_sweep(self.ctx, level % self.n_levels, _ptr(u), _ptr(g), reps,
                                           ms.ctypes.data_as(ctypes.c_void_p)), "profile_sweep")
         return dict(residual_smoother=ms[0], fd=ms[1], combine=ms[2], residual_fp64=ms[3])
+
+    def dgfas_fmg(self, f_levels, u_top, cycles_per_level=1):
+        """Full multigrid startup (Alg. 4): u_top <- the FMG start value from the
+        per-level right-hand sides f_levels (root first, device FP64)."""
+        assert len(f_levels) == self.n_levels
+        arr = (ctypes.c_void_p * self.n_levels)(*[f.data_ptr() for f in f_levels])
+        _check(load().dgfas_fmg(self.ctx, arr, cycles_per_level, _ptr(u_top)), "fmg")
 
     TUNE_KERNELS = ("apply_fp64_elements_per_cta", "apply_smoother_elements_per_cta",
                     "fd_elements_per_cta", "fd_tensorcore_ctas_per_sm")
