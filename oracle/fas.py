@@ -43,6 +43,15 @@ class Hierarchy:
         self.local = any(np.any(c == 2) for c in self.cls) or any(
             np.any(c == 0) for c in self.cls[:-1])
         A0 = assemble(self.ops[0]).toarray()
+        # kappa = 0 without Dirichlet faces (periodic or pure Neumann): A is
+        # semidefinite with the constants as null space (remark on IPCG for
+        # semidefinite systems).  The root is solved in the complement: for a
+        # consistent g (1^T g = 0) the solution x of (A0 + c 1 1^T) x = g has
+        # 1^T x = 0 and A0 x = g.
+        self.nullspace = kappa == 0.0 and not np.any(np.asarray(levels[0]["nbr"]) == -1)
+        if self.nullspace:
+            n = A0.shape[0]
+            A0 = A0 + (np.trace(A0) / n / n) * np.ones((n, n))
         self.root_chol = sla.cho_factor(A0)
 
     @property

@@ -111,8 +111,9 @@ def grading_ratio(n, total_over_min):
     return 0.5 * (lo + hi)
 
 
-def level_from_vertices(V, p, boundary=-1):
-    """Conforming structured level from a vertex grid V [nx+1, ny+1, nz+1, 3]."""
+def level_from_vertices(V, p, boundary=-1, periodic=False):
+    """Conforming structured level from a vertex grid V [nx+1, ny+1, nz+1, 3];
+    `periodic`: the faces of the box are identified (neighbours wrap around)."""
     nx, ny, nz = V.shape[0] - 1, V.shape[1] - 1, V.shape[2] - 1
     ne = nx * ny * nz
     x, y, z = np.meshgrid(np.arange(nx), np.arange(ny), np.arange(nz), indexing="ij")
@@ -126,6 +127,8 @@ def level_from_vertices(V, p, boundary=-1):
         corners[:, c, :] = V[x + cx, y + cy, z + cz]
 
     def eid(ix, iy, iz):
+        if periodic:
+            ix, iy, iz = ix % nx, iy % ny, iz % nz
         ok = (ix >= 0) & (ix < nx) & (iy >= 0) & (iy < ny) & (iz >= 0) & (iz < nz)
         return np.where(ok, ix + nx * (iy + ny * iz), -1), ok
 
@@ -144,7 +147,7 @@ def level_from_vertices(V, p, boundary=-1):
                 cls=np.full(ne, LEAF, np.int8), ijk=np.stack([x, y, z], 1).astype(np.int32))
 
 
-def hierarchy(V_top, p_levels, h_root=None, boundary=-1):
+def hierarchy(V_top, p_levels, h_root=None, boundary=-1, periodic=False):
     """Multilevel mesh with global refinement (all non-top elements are twigs).
 
     p_levels: degrees of the p-levels on the top mesh, finest first, e.g. [8,4,2,1].
@@ -154,7 +157,7 @@ def hierarchy(V_top, p_levels, h_root=None, boundary=-1):
     """
     levels_fine_first = []
     for p in p_levels:
-        levels_fine_first.append(level_from_vertices(V_top, p, boundary))
+        levels_fine_first.append(level_from_vertices(V_top, p, boundary, periodic))
     V = V_top
     if h_root is not None:
         n = V.shape[0] - 1
@@ -162,7 +165,7 @@ def hierarchy(V_top, p_levels, h_root=None, boundary=-1):
             assert n % 2 == 0 and all(s - 1 == n for s in V.shape[:3])
             V = V[::2, ::2, ::2]
             n //= 2
-            levels_fine_first.append(level_from_vertices(V, p_levels[-1], boundary))
+            levels_fine_first.append(level_from_vertices(V, p_levels[-1], boundary, periodic))
     levels = levels_fine_first[::-1]
     for l in range(1, len(levels)):
         fine, coarse = levels[l], levels[l - 1]
@@ -201,6 +204,8 @@ def eval_f(spec, xyz):
     if spec["kind"] == "sine":
         kp = spec["k"] * np.pi
         return 3.0 * kp * kp * np.sin(kp * x) * np.sin(kp * y) * np.sin(kp * z)
+    if spec["kind"] == "psine":
+        return 3.0 * np.sin(x) * np.sin(y) * np.sin(z)
     out = np.zeros_like(x)
     for (kx, ky, kz), a in zip(spec["k"], spec["a"]):
         out += a * np.sin(kx * np.pi * x) * np.sin(ky * np.pi * y) * np.sin(kz * np.pi * z)
@@ -213,11 +218,42 @@ def eval_u(spec, xyz):
     if spec["kind"] == "sine":
         kp = spec["k"] * np.pi
         return np.sin(kp * x) * np.sin(kp * y) * np.sin(kp * z)
+    if spec["kind"] == "psine":
+        return np.sin(x) * np.sin(y) * np.sin(z)
     out = np.zeros_like(x)
     for (kx, ky, kz), a in zip(spec["k"], spec["a"]):
         out += (a / (np.pi ** 2 * (kx * kx + ky * ky + kz * kz))
                 * np.sin(kx * np.pi * x) * np.sin(ky * np.pi * y) * np.sin(kz * np.pi * z))
     return out
+
+
+def periodic_sine_spec():
+    """u = sin x sin y sin z on the periodic box [0, 2 pi)^3, -lap u = 3 u
+    (zero mean: the right-hand side is consistent with the constant null space)."""
+    return dict(kind="psine")
+
+
+def paper_cartesian_periodic(p, kind, n=None, seed=6):
+    """The uniform Cartesian study of the paper (Sec. 6.2, uniform Cartesian):
+    [0, 2 pi)^3 with periodic conditions, (128/p)^3 elements (or n^3), mu_star =
+    2, delta = 0.08.  kind 'h': h-multigrid at degree p down to a 2^3 root;
+    kind 'p': p-multigrid p, p/2, ..., 1, then h down to a 2^3 root."""
+    n = 128 // p if n is None else n
+    V = uniform_vertices(n, hi=(2 * np.pi,) * 3)
+    if kind == "h":
+        p_levels = [p]
+    else:
+        p_levels = []
+        q = p
+        while q >= 1:
+            p_levels.append(q)
+            q //= 2
+    levels = hierarchy(V, p_levels, h_root=2, periodic=True)
+    rng = np.random.default_rng(SEED_BASE + 100 + seed)
+    ndof = levels[-1]["corners"].shape[0] * (p + 1) ** 3
+    return dict(levels=levels, rhs=periodic_sine_spec(),
+                params=dict(mu_star=2.0, delta=0.08, s1=1, s2=1, sc=2),
+                u0=random_start(rng, ndof))
 
 
 def random_start(rng, n):
