@@ -399,6 +399,17 @@ static int build_root(Ctx& c) {
       double s = 0.5 * (A[(size_t)i * n + j] + A[(size_t)j * n + i]);
       A[(size_t)i * n + j] = A[(size_t)j * n + i] = s;
     }
+  // kappa = 0 without Dirichlet faces (periodic or pure Neumann): the constants
+  // span the null space; invert A + c 1 1^T, which for a consistent right-hand
+  // side (1^T g = 0) returns the solution with 1^T u = 0
+  bool dirichlet = false;
+  for (int v : R.nbr) dirichlet |= v == -1;
+  if (c.kappa == 0.0 && !dirichlet) {
+    double tr = 0.0;
+    for (int i = 0; i < n; ++i) tr += A[(size_t)i * n + i];
+    const double cst = tr / n / n;
+    for (size_t i = 0; i < A.size(); ++i) A[i] += cst;
+  }
   for (int j = 0; j < n; ++j) {
     double s = A[(size_t)j * n + j];
     for (int k = 0; k < j; ++k) s -= A[(size_t)j * n + k] * A[(size_t)j * n + k];

@@ -8,6 +8,7 @@
 #include <algorithm>
 #include <atomic>
 #include <cstdio>
+#include <limits>
 
 #include "dgfas_internal.h"
 
@@ -950,7 +951,7 @@ int tune_candidates(Ctx& c, int l, int kernel, int* out, int max_out) {
 // candidates per direction, 8 in all).  The patch position of own node
 // (i, j, k) inside neighbour slot (ox, oy, oz)'s patch is (i, j, k) plus a
 // per-slot shift, so each slot is reduced once per element to one offset
-// (src NS^3 + shift, or -1 when the slot contributes nothing: no neighbour, a
+// (src NS^3 + shift, or a sentinel when the slot contributes nothing: no neighbour, a
 // frozen one, or a boundary side that carries no layers) staged in shared
 // memory; per node only the candidate test and the load remain.  Elements of
 // small degree are packed several to a CTA.  Frozen elements are left
@@ -970,9 +971,13 @@ __global__ void __launch_bounds__(256) k_combine(const LevelView<T> L, const T* 
     const int e = e0 + threadIdx.x;
     s_frz[threadIdx.x] = e < L.ne && L.cls[e] == DGFAS_FROZEN;
   }
+  // "no contribution" is a sentinel below every real offset: a real offset can
+  // be negative (a neighbour of small index whose layers precede this element's
+  // nodes in its patch, e.g. across a periodic boundary)
+  constexpr IDX kNone = std::numeric_limits<IDX>::min();
   for (int t = threadIdx.x; t < EPB * 27; t += blockDim.x) {
     const int el = t / 27, slot = t % 27, e = e0 + el;
-    IDX off = -1;
+    IDX off = kNone;
     if (e < L.ne) {
       const int src = L.nbr27[27 * e + slot];
       if (src >= 0 && L.cls[src] != DGFAS_FROZEN) {
@@ -1014,8 +1019,8 @@ __global__ void __launch_bounds__(256) k_combine(const LevelView<T> L, const T* 
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
       const int sx = (q & 1) ? cx : 1, sy = (q & 2) ? cy : 1, sz = (q & 4) ? cz : 1;
-      const IDX off = (sx < 0 || sy < 0 || sz < 0) ? IDX(-1) : s_off[el][sx + 3 * sy + 9 * sz];
-      v[q] = off >= 0 ? patch[off + loc] : T(0);
+      const IDX off = (sx < 0 || sy < 0 || sz < 0) ? kNone : s_off[el][sx + 3 * sy + 9 * sz];
+      v[q] = off != kNone ? patch[off + loc] : T(0);
     }
     // summed in the fixed order own, x, y, xy, z, ... (deterministic)
     T s = T(0);   // accumulated in the smoother precision

@@ -1,0 +1,76 @@
+"""The paper's uniform Cartesian study on the GPU: periodic box, constant null
+space, parity of the V-cycle with the oracle on a small periodic hierarchy,
+and the cycle counts n10 printed by the paper for h-multigrid at p = 4
+(tests/golden/paper_uniform_cartesian_n10.txt), which pin the smoother, the
+weights reading and the FAS cycle as a whole."""
+import os
+
+import numpy as np
+import pytest
+
+from paper_2608_14123_b300 import dgfas
+from paper_2608_14123_b300 import workloads as wl
+from tests.gpu_helpers import rel, torch_cuda
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_uniform_cartesian_n10.txt")
+
+
+def _paper_n10():
+    out = {}
+    for line in open(GOLDEN):
+        if line.startswith("#") or not line.strip():
+            continue
+        kind, p, s1, s2, sc, n10 = line.split()
+        out[(kind, int(p), int(s1), int(s2), int(sc))] = int(n10)
+    return out
+
+
+def _solver(cfg, s1, s2, sc, prec):
+    return dgfas.Solver(cfg["levels"], cfg["params"]["mu_star"], cfg["params"]["delta"], s1, s2, sc,
+                        precision=prec)
+
+
+def _rhs(cfg, S):
+    torch = torch_cuda()
+    xyz = S.node_coords(-1)
+    fn = torch.from_numpy(wl.eval_f(cfg["rhs"], xyz.cpu().numpy())).cuda()
+    b = torch.empty_like(fn)
+    S.dgfas_assemble_rhs(fn, None, b)
+    return b - b.mean()   # consistent with the constant null space
+
+
+def test_periodic_vcycle_matches_oracle():
+    torch = torch_cuda()
+    from oracle import fas, sip
+    cfg = wl.paper_cartesian_periodic(2, "h", n=4)
+    pr = cfg["params"]
+    S = _solver(cfg, pr["s1"], pr["s2"], pr["sc"], dgfas.DGFAS_FP64)
+    H = fas.Hierarchy(cfg["levels"], pr["mu_star"], pr["delta"], pr["s1"], pr["s2"], pr["sc"])
+    top = H.ops[-1]
+    X = top.geo["x"]
+    f_or = sip.rhs(top, wl.eval_f(cfg["rhs"], X), np.zeros(X.shape[:-1])).reshape(-1)
+    f_or -= f_or.mean()
+    b = _rhs(cfg, S)
+    assert rel(b.cpu().numpy(), f_or) < 1e-12
+    u = torch.from_numpy(cfg["u0"].copy()).cuda()
+    S.dgfas_fas_vcycle(u, b)
+    u_or, _ = H.fas_vcycle(H.zero_levels(cfg["u0"].copy()), f_or)
+    assert rel(u.cpu().numpy(), u_or[-1]) < 1e-11
+    one = torch.ones_like(u)
+    Au = torch.empty_like(u)
+    S.dgfas_apply_op(-1, one, None, Au)
+    assert float(Au.abs().max()) < 1e-10
+
+
+@pytest.mark.parametrize("s", [(1, 1, 2), (2, 2, 4)])
+@pytest.mark.parametrize("prec", [dgfas.DGFAS_FP64, dgfas.DGFAS_BF16])
+def test_h_multigrid_p4_cycle_counts_match_the_paper(s, prec):
+    torch = torch_cuda()
+    cfg = wl.paper_cartesian_periodic(4, "h")
+    S = _solver(cfg, *s, prec)
+    b = _rhs(cfg, S)
+    u = torch.from_numpy(cfg["u0"]).cuda()
+    info = S.dgfas_solve(u, b, 1e-10, 60)
+    assert info["cycles"] == _paper_n10()[("h", 4) + s]
