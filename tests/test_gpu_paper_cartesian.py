@@ -74,3 +74,18 @@ def test_h_multigrid_p4_cycle_counts_match_the_paper(s, prec):
     u = torch.from_numpy(cfg["u0"]).cuda()
     info = S.dgfas_solve(u, b, 1e-10, 60)
     assert info["cycles"] == _paper_n10()[("h", 4) + s]
+
+
+@pytest.mark.parametrize("p,s", [(4, (1, 1, 2)), (4, (2, 2, 4)), (8, (1, 1, 2)), (8, (2, 2, 4))])
+def test_p_multigrid_cycle_counts_near_the_paper(p, s):
+    """p-multigrid p, p/2, ..., 1: the paper solves the p = 1 level with SCG to
+    a tolerance, this hierarchy continues with h-levels down to a 2^3 root (one
+    V-cycle there instead of a converged solve), which moves n10 by at most
+    two cycles."""
+    torch = torch_cuda()
+    cfg = wl.paper_cartesian_periodic(p, "p")
+    S = _solver(cfg, *s, dgfas.DGFAS_FP64)
+    b = _rhs(cfg, S)
+    u = torch.from_numpy(cfg["u0"]).cuda()
+    info = S.dgfas_solve(u, b, 1e-10, 60)
+    assert abs(info["cycles"] - _paper_n10()[("p", p) + s]) <= 2
