@@ -693,7 +693,14 @@ static int down_up(Ctx& c, double* uL, const double* fL, int top = -1) {
     double* ul = l == L ? uL : c.lv[l].u;
     const double* gl = l == L ? fL : c.lv[l].gv;
     if (l < L) {
-      RET(launch_apply(c, l, DGFAS_FP64, ul, gl, c.lv[l].r, -1.0));
+      // u_l is the projection ubar_l and g_l = A_l ubar_l + R r_{l+1}, so the
+      // residual g_l - A_l u_l is R r_{l+1} (in lv[l].t) up to rounding; only
+      // leaf rows (g = f) and frozen rows need the operator
+      if (!c.lv[l].has_leaf && !c.lv[l].has_frozen)
+        CK(cudaMemcpyAsync(c.lv[l].r, c.lv[l].t, c.lv[l].ndof * sizeof(double),
+                           cudaMemcpyDeviceToDevice, c.stream));
+      else
+        RET(launch_apply(c, l, DGFAS_FP64, ul, gl, c.lv[l].r, -1.0));
       RET(smooth(c, l, ul, gl, c.prm.s1, true, true));
     }
     RET(launch_project(c, l, ul));                                   // u_{l-1} = P u_l
