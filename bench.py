@@ -61,7 +61,7 @@ def apply_flops_per_dof(N, box=True):
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
 # dominant kernel on this workload, from one ncu capture of the current kernel
 # (32^3 elements, p = 8, BF16 smoother run); to be retaken whenever the kernel changes
-NCU_TRAFFIC = {"residual_fp64": 386993664 + 168107520}
+NCU_TRAFFIC = {"residual_fp64": 387000320 + 168229632}
 
 
 def fd_flops_per_dof(N, m):
