@@ -55,6 +55,9 @@ struct TransferView {
 // Launch shapes chosen by the autotuner (0 = the built-in default):
 // elements per CTA of the FP64 and smoother-precision box operators and of
 // the narrow-subdomain FD kernel, CTAs per SM of the tensor-core FD kernel.
+// largest root level solved by its dense inverse (n^2 doubles, 512 MB at 8192)
+#define DGFAS_MAX_ROOT 8192
+
 struct Tune {
   int apply64 = 0, apply32 = 0, fd = 0, fdtc = 0;
 };
@@ -148,6 +151,9 @@ int launch_project(Ctx& c, int l, const double* uf);   // lv[l-1].u = ubar = P u
 int launch_restrict(Ctx& c, int l, const double* rf, double* rc);
 int launch_prolong(Ctx& c, int l, double* uf, int prec, void* delta);  // delta = I (u_c - ubar)
 int launch_root(Ctx& c);
+// set-up of the dense root inverse
+int launch_identity(Ctx& c, double* E, int n);
+int launch_root_inverse(Ctx& c, double* A, int n, double shift, double* work, int* flag);
 int launch_sumsq(Ctx& c, const double* v, long long n, double* partial_out);
 int launch_dot(Ctx& c, const double* a, const double* b, long long n, double* partial_out);
 int launch_axpy(Ctx& c, long long n, double alpha, const double* x, double* y);

@@ -373,71 +373,61 @@ static int build_transfer(LevelHost& C, LevelHost& F) {
   return DGFAS_OK;
 }
 
-// explicit inverse of the (SPD) root operator: columns A e_i by the apply kernel,
-// Cholesky factorization and inversion on the host
+// explicit inverse of the (SPD) root operator: columns A e_i by the apply
+// kernel, then symmetrization and in-place Gauss-Jordan inversion on the GPU
+// (no pivoting: the pivots of an SPD matrix stay positive; a non-positive one
+// is reported)
 static int build_root(Ctx& c) {
   LevelHost& R = c.lv[0];
   const int n = (int)R.ndof;
-  if (n > 4096) { set_error("root level larger than 4096 DoF"); return DGFAS_ERR_UNSUPPORTED; }
+  if (n > DGFAS_MAX_ROOT) {
+    set_error("root level larger than " + std::to_string(DGFAS_MAX_ROOT) + " DoF");
+    return DGFAS_ERR_UNSUPPORTED;
+  }
   c.n_root = n;
-  double *E = nullptr, *Acol = nullptr;
+  double *E = nullptr, *A = nullptr, *work = nullptr;
+  int* flag = nullptr;
   RET(dalloc(&E, (size_t)n * n));
-  RET(dalloc(&Acol, (size_t)n * n));
-  std::vector<double> eye((size_t)n * n, 0.0);
-  for (int i = 0; i < n; ++i) eye[(size_t)i * n + i] = 1.0;
-  CK(cudaMemcpy(E, eye.data(), eye.size() * sizeof(double), cudaMemcpyHostToDevice));
+  RET(dalloc(&A, (size_t)n * n));
+  RET(dalloc(&work, 2 * (size_t)n));
+  if (cudaMalloc((void**)&flag, sizeof(int)) != cudaSuccess) {
+    set_error("cudaMalloc failed in setup");
+    return DGFAS_ERR_OOM;
+  }
+  RET(launch_identity(c, E, n));
   for (int i = 0; i < n; ++i)
-    RET(launch_apply(c, 0, DGFAS_FP64, E + (size_t)i * n, nullptr, Acol + (size_t)i * n, 1.0));
-  CK(cudaStreamSynchronize(c.stream));
-  std::vector<double> A((size_t)n * n);
-  CK(cudaMemcpy(A.data(), Acol, A.size() * sizeof(double), cudaMemcpyDeviceToHost));
-  cudaFree(E);
-  cudaFree(Acol);
-  // symmetrize (row i of Acol = A e_i = column i), Cholesky A = L L^T (lower in place)
-  for (int i = 0; i < n; ++i)
-    for (int j = 0; j < i; ++j) {
-      double s = 0.5 * (A[(size_t)i * n + j] + A[(size_t)j * n + i]);
-      A[(size_t)i * n + j] = A[(size_t)j * n + i] = s;
-    }
+    RET(launch_apply(c, 0, DGFAS_FP64, E + (size_t)i * n, nullptr, A + (size_t)i * n, 1.0));
   // kappa = 0 without Dirichlet faces (periodic or pure Neumann): the constants
   // span the null space; invert A + c 1 1^T, which for a consistent right-hand
   // side (1^T g = 0) returns the solution with 1^T u = 0
   bool dirichlet = false;
   for (int v : R.nbr) dirichlet |= v == -1;
+  double shift = 0.0;
   if (c.kappa == 0.0 && !dirichlet) {
+    std::vector<double> diag(n);
+    CK(cudaStreamSynchronize(c.stream));
+    CK(cudaMemcpy2D(diag.data(), sizeof(double), A, (size_t)(n + 1) * sizeof(double),
+                    sizeof(double), n, cudaMemcpyDeviceToHost));
     double tr = 0.0;
-    for (int i = 0; i < n; ++i) tr += A[(size_t)i * n + i];
-    const double cst = tr / n / n;
-    for (size_t i = 0; i < A.size(); ++i) A[i] += cst;
+    for (double v : diag) tr += v;
+    shift = tr / n / n;
   }
-  for (int j = 0; j < n; ++j) {
-    double s = A[(size_t)j * n + j];
-    for (int k = 0; k < j; ++k) s -= A[(size_t)j * n + k] * A[(size_t)j * n + k];
-    if (!(s > 0)) { set_error("root operator not positive definite"); return DGFAS_ERR_MESH; }
-    const double d = std::sqrt(s);
-    A[(size_t)j * n + j] = d;
-    for (int i = j + 1; i < n; ++i) {
-      double t = A[(size_t)i * n + j];
-      for (int k = 0; k < j; ++k) t -= A[(size_t)i * n + k] * A[(size_t)j * n + k];
-      A[(size_t)i * n + j] = t / d;
-    }
+  int rc = launch_root_inverse(c, A, n, shift, work, flag);
+  int bad = 0;
+  if (rc == DGFAS_OK) {
+    CK(cudaStreamSynchronize(c.stream));
+    CK(cudaMemcpy(&bad, flag, sizeof(int), cudaMemcpyDeviceToHost));
   }
-  // inverse = L^-T L^-1, column by column
-  std::vector<double> inv((size_t)n * n), y(n);
-  for (int col = 0; col < n; ++col) {
-    for (int i = 0; i < n; ++i) {
-      double t = (i == col) ? 1.0 : 0.0;
-      for (int k = 0; k < i; ++k) t -= A[(size_t)i * n + k] * y[k];
-      y[i] = t / A[(size_t)i * n + i];
-    }
-    for (int i = n - 1; i >= 0; --i) {
-      double t = y[i];
-      for (int k = i + 1; k < n; ++k) t -= A[(size_t)k * n + i] * y[k];
-      y[i] = t / A[(size_t)i * n + i];
-    }
-    for (int i = 0; i < n; ++i) inv[(size_t)i * n + col] = y[i];
+  cudaFree(E);
+  cudaFree(work);
+  cudaFree(flag);
+  if (rc != DGFAS_OK) { cudaFree(A); return rc; }
+  if (bad) {
+    cudaFree(A);
+    set_error("root operator not positive definite");
+    return DGFAS_ERR_MESH;
   }
-  RET(upload(&c.Ainv, inv));
+  c.Ainv = A;
   return DGFAS_OK;
 }
 

@@ -1533,6 +1533,68 @@ __global__ void k_root(const double* __restrict__ Ainv, const double* __restrict
   if (lane == 0) u[row] = s;
 }
 
+// ---------------------------------------------------------------- root inverse (set-up)
+__global__ void k_identity(double* __restrict__ E, int n) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < (long long)n * n) E[t] = (t / n == t % n) ? 1.0 : 0.0;
+}
+
+int launch_identity(Ctx& c, double* E, int n) {
+  const long long nn = (long long)n * n;
+  k_identity<<<(unsigned)((nn + 255) / 256), 256, 0, c.stream>>>(E, n);
+  ++g_kernels;
+  CK(cudaGetLastError());
+  return DGFAS_OK;
+}
+
+// A <- (A + A^T) / 2 + shift (every entry; shift = c of the rank-one term c 1 1^T)
+__global__ void k_sym_shift(double* __restrict__ A, int n, double shift) {
+  const int i = blockIdx.y, j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n || j < i) return;
+  const double s = 0.5 * (A[(size_t)i * n + j] + A[(size_t)j * n + i]) + shift;
+  A[(size_t)i * n + j] = s;
+  A[(size_t)j * n + i] = s;
+}
+
+// Gauss-Jordan step k (in place, no pivoting): row k and column k saved first
+__global__ void k_gj_save(const double* __restrict__ A, int n, int k, double* __restrict__ rowk,
+                          double* __restrict__ colk, int* __restrict__ flag) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) {
+    rowk[t] = A[(size_t)k * n + t];
+    colk[t] = A[(size_t)t * n + k];
+  }
+  if (t == 0 && !(A[(size_t)k * n + k] > 0.0)) atomicExch(flag, 1);
+}
+
+// a_kk <- 1/a_kk, a_kj <- a_kj/a_kk, a_ik <- -a_ik/a_kk, a_ij <- a_ij - a_ik a_kj/a_kk
+__global__ void k_gj_update(double* __restrict__ A, int n, int k, const double* __restrict__ rowk,
+                            const double* __restrict__ colk) {
+  const int i = blockIdx.y, j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  const double p = 1.0 / rowk[k];
+  double v;
+  if (i == k) v = j == k ? p : rowk[j] * p;
+  else if (j == k) v = -colk[i] * p;
+  else v = A[(size_t)i * n + j] - colk[i] * p * rowk[j];
+  A[(size_t)i * n + j] = v;
+}
+
+int launch_root_inverse(Ctx& c, double* A, int n, double shift, double* work, int* flag) {
+  CK(cudaMemsetAsync(flag, 0, sizeof(int), c.stream));
+  const dim3 g2((n + 255) / 256, n);
+  k_sym_shift<<<g2, 256, 0, c.stream>>>(A, n, shift);
+  ++g_kernels;
+  CK(cudaGetLastError());
+  for (int k = 0; k < n; ++k) {
+    k_gj_save<<<(n + 255) / 256, 256, 0, c.stream>>>(A, n, k, work, work + n, flag);
+    k_gj_update<<<g2, 256, 0, c.stream>>>(A, n, k, work, work + n);
+  }
+  g_kernels += 2LL * n;
+  CK(cudaGetLastError());
+  return DGFAS_OK;
+}
+
 int launch_root(Ctx& c) {
   const int n = c.n_root;
   k_root<<<(n + 7) / 8, 256, 0, c.stream>>>(c.Ainv, c.lv[0].gv, c.lv[0].u, n);

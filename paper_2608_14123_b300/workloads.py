@@ -236,8 +236,9 @@ def periodic_sine_spec():
 def paper_cartesian_periodic(p, kind, n=None, seed=6):
     """The uniform Cartesian study of the paper (Sec. 6.2, uniform Cartesian):
     [0, 2 pi)^3 with periodic conditions, (128/p)^3 elements (or n^3), mu_star =
-    2, delta = 0.08.  kind 'h': h-multigrid at degree p down to a 2^3 root;
-    kind 'p': p-multigrid p, p/2, ..., 1, then h down to a 2^3 root."""
+    2, delta = 0.08.  kind 'h': h-multigrid at degree p with the paper's L = 4
+    levels (root n/8 cells per direction); kind 'p': p-multigrid p, p/2, ...,
+    1, then h down to a 2^3 root."""
     n = 128 // p if n is None else n
     V = uniform_vertices(n, hi=(2 * np.pi,) * 3)
     if kind == "h":
@@ -248,7 +249,7 @@ def paper_cartesian_periodic(p, kind, n=None, seed=6):
         while q >= 1:
             p_levels.append(q)
             q //= 2
-    levels = hierarchy(V, p_levels, h_root=2, periodic=True)
+    levels = hierarchy(V, p_levels, h_root=max(2, n // 8) if kind == "h" else 2, periodic=True)
     rng = np.random.default_rng(SEED_BASE + 100 + seed)
     ndof = levels[-1]["corners"].shape[0] * (p + 1) ** 3
     return dict(levels=levels, rhs=periodic_sine_spec(),

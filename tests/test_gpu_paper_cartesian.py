@@ -1,8 +1,8 @@
 """The paper's uniform Cartesian study on the GPU: periodic box, constant null
 space, parity of the V-cycle with the oracle on a small periodic hierarchy,
-and the cycle counts n10 printed by the paper for h-multigrid at p = 4
-(tests/golden/paper_uniform_cartesian_n10.txt), which pin the smoother, the
-weights reading and the FAS cycle as a whole."""
+and the cycle counts n10 printed by the paper for h-multigrid (its L = 4
+levels, p = 4 and 8; tests/golden/paper_uniform_cartesian_n10.txt), which pin
+the smoother, the weights reading and the FAS cycle as a whole."""
 import os
 
 import numpy as np
@@ -65,15 +65,20 @@ def test_periodic_vcycle_matches_oracle():
 
 
 @pytest.mark.parametrize("s", [(1, 1, 2), (2, 2, 4)])
-@pytest.mark.parametrize("prec", [dgfas.DGFAS_FP64, dgfas.DGFAS_BF16])
-def test_h_multigrid_p4_cycle_counts_match_the_paper(s, prec):
+@pytest.mark.parametrize("p,prec", [(4, dgfas.DGFAS_FP64), (4, dgfas.DGFAS_BF16),
+                                    (8, dgfas.DGFAS_FP64)])
+def test_h_multigrid_cycle_counts_match_the_paper(p, prec, s):
     torch = torch_cuda()
-    cfg = wl.paper_cartesian_periodic(4, "h")
+    cfg = wl.paper_cartesian_periodic(p, "h")
     S = _solver(cfg, *s, prec)
     b = _rhs(cfg, S)
     u = torch.from_numpy(cfg["u0"]).cuda()
     info = S.dgfas_solve(u, b, 1e-10, 60)
-    assert info["cycles"] == _paper_n10()[("h", 4) + s]
+    # p = 4 (overlap of one node layer) reproduces the paper's counts exactly;
+    # at p = 8 two layers carry the weights' transition, whose function the
+    # paper does not print (reading), and the counts agree within one cycle
+    tol = 0 if p == 4 else 1
+    assert abs(info["cycles"] - _paper_n10()[("h", p) + s]) <= tol
 
 
 @pytest.mark.parametrize("p,s", [(4, (1, 1, 2)), (4, (2, 2, 4)), (8, (1, 1, 2)), (8, (2, 2, 4))])
