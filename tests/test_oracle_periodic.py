@@ -44,3 +44,22 @@ def test_vcycles_converge_for_consistent_rhs():
     f -= f.mean()
     _, hist = H.solve(cfg["u0"].copy(), f, rtol=1e-10, max_cycles=40)
     assert hist[-1] <= 1e-10 * hist[0]
+
+
+def test_periodic_topology_is_symmetric():
+    """Every face neighbour sees the element back through the opposite face,
+    and the 27-neighbourhood of each element is its periodic block."""
+    cfg = wl.paper_cartesian_periodic(4, "h", n=4)
+    for lv in cfg["levels"]:
+        nbr, nbr27, ijk = lv["nbr"], lv["nbr27"], lv["ijk"]
+        n = lv["shape"][0]
+        assert (nbr >= 0).all()
+        for e in range(nbr.shape[0]):
+            for f in range(6):
+                assert nbr[nbr[e, f], f ^ 1] == e
+            for oz in (-1, 0, 1):
+                for oy in (-1, 0, 1):
+                    for ox in (-1, 0, 1):
+                        q = nbr27[e, (ox + 1) + 3 * (oy + 1) + 9 * (oz + 1)]
+                        want = (ijk[e] + np.array([ox, oy, oz])) % n
+                        assert (ijk[q] == want).all()
