@@ -5,8 +5,9 @@ This package is a plain, slow, obviously correct restatement of the method of
 full approximation scheme" (Stiller): the SIP discretization (Sec. 2.2,
 Eq. (2)), the multilevel FAS formulation and transfer operators (Sec. 3.2-3.3,
 Eq. (4)), the weighted additive Schwarz smoother with fast diagonalization
-(Sec. 4.3.1, Eqs. (9)-(11), Alg. 5), the SCG method (Alg. 6) and the FAS and CS
-V-cycles (Algs. 1-2).  Everything is float64 numpy.
+(Sec. 4.3.1, Eqs. (9)-(11), Alg. 5), the SCG method (Alg. 6), the FAS and CS
+V-cycles (Algs. 1-2) and the full multigrid startup (Alg. 4), on Dirichlet,
+Neumann or periodic meshes.  Everything is float64 numpy.
 
 It is test infrastructure only: the tests, the smoke check and the CPU
 baseline leg of the benchmark use it; the product path never imports it and
