@@ -56,7 +56,6 @@ static int dalloc(double** p, size_t n) {
   return DGFAS_OK;
 }
 
-static char side_char(int nb) { return nb >= 0 ? 'i' : (nb == -1 ? 'd' : 'n'); }
 // side type of a face: 0 interior, 1 Dirichlet, 2 Neumann, 3 interior face
 // whose neighbour is frozen (the subdomain takes no layers from it)
 static int side_idx(int nb, const std::vector<signed char>& cls) {
@@ -215,7 +214,6 @@ static int build_level(Ctx& c, const dgfas_level& in, const dgfas_params& prm, L
     g[4 * e] = c.kappa * dx[0] * dx[1] * dx[2] / 8.0;
     for (int i = 0; i < 3; ++i) g[4 * e + 1 + i] = nu * dx[(i + 1) % 3] * dx[(i + 2) % 3] / (2.0 * dx[i]);
   }
-  (void)side_char;
   // ---- uploads
   RET(upload(&H.d_nbr, H.nbr));
   RET(upload(&H.d_nbr27, H.nbr27));

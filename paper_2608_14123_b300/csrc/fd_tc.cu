@@ -206,12 +206,6 @@ struct FdTcSmem {
 // the operand buffers double as the staging area of one FP32 patch (<= 16^3)
 static_assert(sizeof(((FdTcSmem*)nullptr)->A) >= 16 * 16 * 16 * sizeof(float), "patch staging");
 
-__device__ __forceinline__ void put_bf16(unsigned char* tile2, int row, int k, float v) {
-  // row in [0, 256): tile row / 128, K-major
-  *reinterpret_cast<__nv_bfloat16*>(tile2 + (row >> 7) * TC_TILE + tile_off(row & 127, k)) =
-      __float2bfloat16(v);
-}
-
 __device__ __forceinline__ uint4 pack8(const float* v) {
   uint4 o;
   __nv_bfloat162 p0 = __floats2bfloat162_rn(v[0], v[1]), p1 = __floats2bfloat162_rn(v[2], v[3]),
