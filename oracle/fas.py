@@ -207,6 +207,31 @@ class LocalHierarchy(Hierarchy):
         N3 = self.ops[l].N ** 3
         return np.repeat(self.cls[l] == 0, N3)
 
+    def element_energy(self, l, eps):
+        """Element error indicators of the adaptive loop (Sec. 6.4): the
+        operator applied to the complete error vector eps of level l (active
+        and frozen columns), restricted to element e and weighted with the
+        element's error coefficients, eps_e . (A_l eps)_e, for every element."""
+        N3 = self.ops[l].N ** 3
+        Ae = apply(self.ops[l], eps).reshape(-1, N3)
+        return np.einsum("en,en->e", np.asarray(eps).reshape(-1, N3), Ae)
+
+    def energy_error(self, eps_levels):
+        """Energy norm of the error on the composite mesh (Sec. 6.1):
+        (sum_l sum over the leaf elements of level l of eps_e . (A_l eps)_e)^(1/2)."""
+        tot = 0.0
+        for l, eps in enumerate(eps_levels):
+            ind = self.element_energy(l, eps)
+            tot += ind[self.cls[l] == 0].sum()
+        return np.sqrt(tot)
+
+    @staticmethod
+    def mark_for_refinement(indicators, leaf, frac=0.7):
+        """Leaf elements whose indicator exceeds frac times the largest one over
+        all levels (Sec. 6.4); indicators and leaf are per-level arrays."""
+        top = max(float(np.max(np.where(lf, ind, -np.inf))) for ind, lf in zip(indicators, leaf))
+        return [lf & (ind > frac * top) for ind, lf in zip(indicators, leaf)]
+
     def composite_residual(self, u, f):
         """r_2 of Sec. 6.1: Euclidean norm of the leaf residuals of all levels,
         evaluated on the composite solution: the twigs of each level first take
