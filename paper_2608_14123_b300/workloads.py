@@ -438,6 +438,124 @@ def refined_hierarchy(spec, n_base=8, p=3, n_ref=3, n_root=4, buffer=2.0):
     return levels
 
 
+def geometric_marks(spec, n_base=8, n_ref=3, buffer=2.0):
+    """The refined cell sets of `refined_hierarchy`, level by level from the
+    base (grid n_base 2^k at refinement level k): cells within buffer * h of
+    the front among the active cells of the level."""
+    marks = []
+    n = n_base
+    cells = [(x, y, z) for z in range(n) for y in range(n) for x in range(n)]
+    for k in range(n_ref):
+        arr = np.array(cells, dtype=np.int64)
+        h = 1.0 / n
+        m = _cell_front_distance(spec, arr * h, h) <= buffer * h
+        mk = {c for c, f in zip(cells, m) if f}
+        marks.append(mk)
+        cells = sorted({(2 * c[0] + (o & 1), 2 * c[1] + ((o >> 1) & 1), 2 * c[2] + (o >> 2))
+                        for c in mk for o in range(8)})
+        n *= 2
+    return marks
+
+
+def close_marks(marks, n_base):
+    """Admissible refinement: adds to `marks` (refined cell sets per level,
+    base first, each a set of integer cells of grid n_base 2^k) what is needed
+    so that every face / edge / vertex neighbour of a refined cell inside the
+    domain is an element of its level (then the neighbours' children can be
+    frozen with a leaf parent).  A missing neighbour position is covered by a
+    leaf of a coarser level, which gets refined, down the levels until
+    nothing changes.  Returns the closed sets (new objects)."""
+    marks = [set(m) for m in marks]
+    changed = True
+    while changed:
+        changed = False
+        for k in range(len(marks)):
+            n = n_base << k
+            active = None if k == 0 else {
+                (2 * c[0] + (o & 1), 2 * c[1] + ((o >> 1) & 1), 2 * c[2] + (o >> 2))
+                for c in marks[k - 1] for o in range(8)}
+            for c in list(marks[k]):
+                for oz in (-1, 0, 1):
+                    for oy in (-1, 0, 1):
+                        for ox in (-1, 0, 1):
+                            q = (c[0] + ox, c[1] + oy, c[2] + oz)
+                            if min(q) < 0 or max(q) >= n or active is None or q in active:
+                                continue
+                            # q is covered by a coarser leaf: refine its parent at k-1
+                            par = (q[0] // 2, q[1] // 2, q[2] // 2)
+                            if par not in marks[k - 1]:
+                                marks[k - 1].add(par)
+                                changed = True
+    return marks
+
+
+def hierarchy_from_marks(marks, n_base=8, p=3, n_root=4):
+    """Multilevel mesh with local refinement from refined cell sets (as
+    `refined_hierarchy`, whose geometric marking `geometric_marks` returns):
+    the global part up to the base n_base^3 at degree p, then one level per
+    set, holding the children of the refined cells of the level below
+    (active) and of their unmarked neighbours (frozen).  The sets must be
+    admissible (`close_marks`)."""
+    V = uniform_vertices(n_base)
+    levels = hierarchy(V, [p, 1], h_root=n_root)
+    base_cells = levels[-1]["ijk"].astype(np.int64)
+    prev_index = {tuple(int(v) for v in c): i for i, c in enumerate(base_cells)}
+    m0 = marks[0] if marks else set()
+    levels[-1]["cls"] = np.array([TWIG if tuple(int(v) for v in c) in m0 else LEAF
+                                  for c in base_cells], np.int8)
+    n = n_base
+    active = set(prev_index)   # the active (non-frozen) elements of the level
+    for k, mset in enumerate(marks):
+        n2 = 2 * n
+        assert all(c in active for c in mset), "refined cell is not an active element of its level"
+        nbrs = set()
+        for c in mset:
+            for oz in (-1, 0, 1):
+                for oy in (-1, 0, 1):
+                    for ox in (-1, 0, 1):
+                        q = (c[0] + ox, c[1] + oy, c[2] + oz)
+                        if q in mset or min(q) < 0 or max(q) >= n:
+                            continue
+                        nbrs.add(q)
+        assert all(q in active for q in nbrs), "marks not admissible (close_marks)"
+        nxt = marks[k + 1] if k + 1 < len(marks) else set()
+        children, cls_list, parent, octant = [], [], [], []
+        for group, frozen in ((sorted(mset), False), (sorted(nbrs), True)):
+            for c in group:
+                for o in range(8):
+                    ch = (2 * c[0] + (o & 1), 2 * c[1] + ((o >> 1) & 1), 2 * c[2] + (o >> 2))
+                    children.append(ch)
+                    cls_list.append(FROZEN if frozen else (TWIG if ch in nxt else LEAF))
+                    parent.append(prev_index[c])
+                    octant.append(o)
+        cells = np.array(children, dtype=np.int64)
+        ne = len(cells)
+        index = {c: i for i, c in enumerate(children)}
+        h2 = 1.0 / n2
+        corners = np.zeros((ne, 8, 3))
+        for cc in range(8):
+            off = np.array([cc & 1, (cc >> 1) & 1, (cc >> 2) & 1])
+            corners[:, cc, :] = (cells + off) * h2
+        nbr = np.zeros((ne, 6), np.int32)
+        for f, (ox, oy, oz) in enumerate(_FACE_OFF):
+            for i, c in enumerate(children):
+                q = (c[0] + ox, c[1] + oy, c[2] + oz)
+                nbr[i, f] = -1 if (min(q) < 0 or max(q) >= n2) else index.get(q, -2)
+        nbr27 = np.full((ne, 27), -1, np.int32)
+        for oz in (-1, 0, 1):
+            for oy in (-1, 0, 1):
+                for ox in (-1, 0, 1):
+                    sl = (ox + 1) + 3 * (oy + 1) + 9 * (oz + 1)
+                    for i, c in enumerate(children):
+                        nbr27[i, sl] = index.get((c[0] + ox, c[1] + oy, c[2] + oz), -1)
+        levels.append(dict(p=int(p), shape=(n2, n2, n2), corners=corners, nbr=nbr, nbr27=nbr27,
+                           parent=np.array(parent, np.int32), octant=np.array(octant, np.int32),
+                           cls=np.array(cls_list, np.int8), ijk=cells.astype(np.int32)))
+        n, prev_index = n2, index
+        active = {c for c, cl in zip(children, cls_list) if cl != FROZEN}
+    return levels
+
+
 def config4(small=False):
     """Config 4: steep front (alpha = 50) on [0,1]^3, base 8^3 at p = 3 with up
     to 3 levels of local refinement towards the front (p = 3 on every level)."""
