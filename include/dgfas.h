@@ -204,6 +204,16 @@ int dgfas_profile_sweep(void* ctx, int level, double* u, const double* g, int re
    leaf elements or any level frozen ones).  Stream-ordered, not captured. */
 int dgfas_fmg(void* ctx, const double* const* f_levels, int cycles_per_level, double* u_top);
 
+/* Element error indicators of the adaptive loop (Sec. 6.4): the level-l
+   operator applied to the complete error vector eps [ndof(level)] (device),
+   restricted to each element and weighted with that element's error
+   coefficients: out[e] = eps_e . (A_l eps)_e, out [n_elem] (device).  Rows of
+   frozen elements are 0 (the operator's frozen rows).  Summed over the leaf
+   elements of every level it gives the square of the composite energy norm
+   of the error (Sec. 6.1).  Stream-ordered; uses the context's smoother
+   scratch, so not concurrently with a solve. */
+int dgfas_element_energy(void* ctx, int level, const double* eps, double* out);
+
 /* Launch-shape autotuner (the batching / tile-tuning step of the hot path):
    for every level it times, with CUDA events on the context's stream, the
    candidate launch shapes of the tunable kernels and keeps the fastest:

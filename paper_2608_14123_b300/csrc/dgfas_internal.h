@@ -153,6 +153,7 @@ int launch_prolong(Ctx& c, int l, double* uf, int prec, void* delta);  // delta 
 int launch_root(Ctx& c);
 // set-up of the dense root inverse
 int launch_identity(Ctx& c, double* E, int n);
+int launch_element_dot(Ctx& c, int l, const double* a, const double* b, double* out);
 int launch_root_inverse(Ctx& c, double* A, int n, double shift, double* work, int* flag);
 int launch_sumsq(Ctx& c, const double* v, long long n, double* partial_out);
 int launch_dot(Ctx& c, const double* a, const double* b, long long n, double* partial_out);

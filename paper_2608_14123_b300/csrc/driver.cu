@@ -909,6 +909,14 @@ extern "C" int dgfas_fmg(void* ctx, const double* const* f_levels, int cycles_pe
   return interpolate_solution(*c, L, u_top);
 }
 
+extern "C" int dgfas_element_energy(void* ctx, int level, const double* eps, double* out) {
+  Ctx* c = (Ctx*)ctx;
+  if (!c || !eps || !out || level < 0 || level >= (int)c->lv.size()) return DGFAS_ERR_INVALID;
+  double* Ae = (double*)c->rw;   // scratch of at least the level's ndof doubles
+  RET(launch_apply(*c, level, DGFAS_FP64, eps, nullptr, Ae, 1.0));
+  return launch_element_dot(*c, level, eps, Ae, out);
+}
+
 extern "C" int dgfas_set_level_rhs(void* ctx, int level, const double* f) {
   Ctx* c = (Ctx*)ctx;
   if (!c || !f || level < 0 || level >= (int)c->lv.size() - 1) return DGFAS_ERR_INVALID;

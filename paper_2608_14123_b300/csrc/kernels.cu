@@ -1533,6 +1533,31 @@ __global__ void k_root(const double* __restrict__ Ainv, const double* __restrict
   if (lane == 0) u[row] = s;
 }
 
+// ---------------------------------------------------------------- element error indicators
+// out[e] = eps_e . (A eps)_e: one warp per element, lanes over its nodes,
+// fixed-order tree sum (deterministic)
+__global__ void k_element_dot(const double* __restrict__ a, const double* __restrict__ b, int ne,
+                              int N3, double* __restrict__ out) {
+  const int w = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+  if (w >= ne) return;
+  const size_t o = (size_t)w * N3;
+  double s = 0.0;
+  for (int n = lane; n < N3; n += 32) s += a[o + n] * b[o + n];
+#pragma unroll
+  for (int k = 16; k > 0; k >>= 1) s += __shfl_down_sync(0xffffffffu, s, k);
+  if (lane == 0) out[w] = s;
+}
+
+int launch_element_dot(Ctx& c, int l, const double* a, const double* b, double* out) {
+  LevelHost& H = c.lv[l];
+  const int n3 = H.N * H.N * H.N;
+  const long long threads = 32LL * H.ne;
+  k_element_dot<<<(unsigned)((threads + 255) / 256), 256, 0, c.stream>>>(a, b, H.ne, n3, out);
+  ++g_kernels;
+  CK(cudaGetLastError());
+  return DGFAS_OK;
+}
+
 // ---------------------------------------------------------------- root inverse (set-up)
 __global__ void k_identity(double* __restrict__ E, int n) {
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;

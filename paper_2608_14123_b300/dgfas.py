@@ -58,7 +58,8 @@ SYMBOLS = ["dgfas_setup_levels", "dgfas_destroy", "dgfas_level_ndof", "dgfas_nod
            "dgfas_mlp_forward", "dgfas_mlp_grad", "dgfas_mlp_train", "dgfas_learned_surrogate",
            "dgfas_assemble_rhs_level", "dgfas_set_level_rhs", "dgfas_composite_residual",
            "dgfas_get_level_solution", "dgfas_tc_selftest", "dgfas_tc_selftest_mn", "dgfas_tc_error", "dgfas_host_fd_variant", "dgfas_autotune", "dgfas_set_tuning",
-           "dgfas_get_tuning", "dgfas_fmg", "dgfas_strerror", "dgfas_last_error"]
+           "dgfas_get_tuning", "dgfas_fmg", "dgfas_element_energy", "dgfas_strerror",
+           "dgfas_last_error"]
 
 _lib = None
 
@@ -106,6 +107,7 @@ def load():
         "dgfas_tc_selftest_mn": (I, [P, ctypes.POINTER(I)]),
         "dgfas_autotune": (I, [P, I, P, I, ctypes.POINTER(I)]),
         "dgfas_fmg": (I, [P, ctypes.POINTER(P), I, P]),
+        "dgfas_element_energy": (I, [P, I, P, P]),
         "dgfas_set_tuning": (I, [P, I, I, I]),
         "dgfas_get_tuning": (I, [P, I, I, ctypes.POINTER(I), P, I, ctypes.POINTER(I)]),
         "dgfas_strerror": (ctypes.c_char_p, [I]),
@@ -243,6 +245,11 @@ class Solver:
         assert len(f_levels) == self.n_levels
         arr = (ctypes.c_void_p * self.n_levels)(*[f.data_ptr() for f in f_levels])
         _check(load().dgfas_fmg(self.ctx, arr, cycles_per_level, _ptr(u_top)), "fmg")
+
+    def dgfas_element_energy(self, level, eps, out):
+        """out[e] = eps_e . (A eps)_e on `level` (element error indicators)."""
+        _check(load().dgfas_element_energy(self.ctx, level % self.n_levels, _ptr(eps), _ptr(out)),
+               "element_energy")
 
     TUNE_KERNELS = ("apply_fp64_elements_per_cta", "apply_smoother_elements_per_cta",
                     "fd_elements_per_cta", "fd_tensorcore_ctas_per_sm")
