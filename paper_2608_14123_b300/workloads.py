@@ -264,7 +264,7 @@ def random_start(rng, n):
 
 # ---------------------------------------------------------------- the configurations
 def config(cid, small=False):
-    """Workload `cid` in 1..5 (config 4 is built by adaptive.py).
+    """Workload `cid` in 1, 2, 3, 5 (config 4: `config4`).
 
     Returns dict(levels, rhs, u0, params) with params the solver parameters
     (mu_star, delta, s1, s2, sc).  `small` shrinks configs 2/3/5 to a mesh the
