@@ -248,8 +248,8 @@ class LocalHierarchy(Hierarchy):
                 s += np.sum(r[m] ** 2)
         return np.sqrt(s)
 
-    def _down_up_local(self, u, f, r_top):
-        L = self.L
+    def _down_up_local(self, u, f, r_top, top=None):
+        L = self.L if top is None else top
         u = list(u)
         g = [None] * (L + 1)
         g[L] = f[L]
@@ -271,6 +271,26 @@ class LocalHierarchy(Hierarchy):
             u[l] = self.tr[l].prolong_fas(u[l], u[l - 1], ubar[l - 1], self.cls[l])
             if l < L:
                 u[l] = self.smooth(l, u[l], g[l], self.s2)
+        return u
+
+    def fmg_local(self, f, cycles=1):
+        """Alg. 4 on a locally refined hierarchy: the root solved for its own
+        right-hand side, then for l = 1 .. L-1 the interpolation of the whole
+        level u_l = I_l u_{l-1} (frozen elements included) and `cycles` FAS
+        V-cycles with level l as the top (all its active rows use f_l; below
+        it the leaves keep their own f).  Returns the list of level vectors
+        with the top's I_L u_{L-1}: the start of the composite solve."""
+        L = self.L
+        u = [np.zeros(o.ndof) for o in self.ops]
+        u[0] = self.root_solve(f[0])
+        for l in range(1, L):
+            u[l] = self.tr[l].interpolate(u[l - 1])
+            for _ in range(cycles):
+                u[l] = self.smooth(l, u[l], f[l], self.s1)
+                r = self.residual(l, u[l], f[l])
+                u[:l + 1] = self._down_up_local(u[:l + 1], f[:l + 1], r, top=l)
+                u[l] = self.smooth(l, u[l], f[l], self.s2)
+        u[L] = self.tr[L].interpolate(u[L - 1])
         return u
 
     def fas_vcycle_local(self, u, f):

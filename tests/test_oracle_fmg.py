@@ -48,3 +48,32 @@ def test_fmg_start_saves_cycles():
     _, h_zero = H.solve(np.zeros_like(u_fmg), fl[L], rtol=1e-10)
     assert h_fmg[-1] <= 1e-10 * r_zero and h_zero[-1] <= 1e-10 * r_zero
     assert len(h_fmg) < len(h_zero)
+
+
+def test_local_fmg_equals_global_fmg_without_local_refinement():
+    """On a globally refined hierarchy the local variant reproduces Alg. 4."""
+    H, fl = _setup(1, False)
+    cfg = wl.config(1)
+    pr = cfg["params"]
+    HL = fas.LocalHierarchy(cfg["levels"], pr["mu_star"], pr["delta"], pr["s1"], pr["s2"], pr["sc"])
+    u_loc = HL.fmg_local(fl, cycles=1)
+    u_glob = H.fmg(fl, cycles=1)
+    assert np.abs(u_loc[-1] - u_glob).max() <= 1e-12 * np.abs(u_glob).max()
+
+
+def test_local_fmg_start_saves_cycles():
+    cfg = wl.config4(small=True)
+    pr = cfg["params"]
+    H = fas.LocalHierarchy(cfg["levels"], pr["mu_star"], pr["delta"], pr["s1"], pr["s2"], pr["sc"])
+    f = []
+    for op in H.ops:
+        X = op.geo["x"]
+        f.append(sip.rhs(op, wl.eval_front_f(cfg["rhs"], X), wl.eval_front_u(cfg["rhs"], X)).reshape(-1))
+    zero = [np.zeros(op.ndof) for op in H.ops]
+    r_zero = H.composite_residual(zero, f)
+    u_f = H.fmg_local(f, cycles=1)
+    r_f = H.composite_residual(u_f, f)
+    assert r_f < r_zero
+    _, h_f = H.solve_local(u_f, f, rtol=1e-10 * r_zero / r_f)
+    _, h_z = H.solve_local(zero, f, rtol=1e-10)
+    assert h_f[-1] <= 1e-10 * r_zero * (1 + 1e-9) and len(h_f) < len(h_z)
