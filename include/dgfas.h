@@ -199,9 +199,12 @@ int dgfas_profile_sweep(void* ctx, int level, double* u, const double* g, int re
    dgfas_fas_vcycle on the full hierarchy.  f_levels: host array of
    n_levels device pointers, f_levels[l] the assembled right-hand side of
    level l (dgfas_assemble_rhs_level), f_levels[n_levels-1] the top's (read
-   only for validation).  Paper: one V-cycle per level.  Globally refined
-   hierarchies only (DGFAS_ERR_UNSUPPORTED when a level below the top has
-   leaf elements or any level frozen ones).  Stream-ordered, not captured. */
+   only for validation).  Paper: one V-cycle per level.  On a locally refined
+   hierarchy level l's active rows all use f_levels[l] while it is the top,
+   the leaves below it the right-hand sides set by dgfas_set_level_rhs, and
+   the level solutions it leaves below the top (lv u) are the start of the
+   following composite solve.  DGFAS_ERR_UNSUPPORTED for a single level.
+   Stream-ordered, not captured. */
 int dgfas_fmg(void* ctx, const double* const* f_levels, int cycles_per_level, double* u_top);
 
 /* Element error indicators of the adaptive loop (Sec. 6.4): the level-l

@@ -751,10 +751,12 @@ static int vcycle_sub(Ctx& c, int T, const double* fT) {
 static int interpolate_solution(Ctx& c, int l, double* ul) {
   LevelHost& C = c.lv[l - 1];
   LevelHost& F = c.lv[l];
+  // with ubar = 0 the prolongation writes I u_c into delta on active elements
+  // and into u on frozen ones (delta = 0 there): u = 0, then u += delta
   CK(cudaMemsetAsync(C.ubar, 0, C.ndof * sizeof(double), c.stream));
+  CK(cudaMemsetAsync(ul, 0, F.ndof * sizeof(double), c.stream));
   RET(launch_prolong(c, l, ul, DGFAS_FP64, F.delta));
-  CK(cudaMemcpyAsync(ul, F.delta, F.ndof * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
-  return DGFAS_OK;
+  return launch_add_delta(c, F.ndof, DGFAS_FP64, F.delta, ul);
 }
 
 static bool graph_ok(Ctx& c) { return c.use_graph && c.prm.smoother == DGFAS_WAS; }
@@ -894,8 +896,8 @@ extern "C" int dgfas_fmg(void* ctx, const double* const* f_levels, int cycles_pe
   const int L = (int)c->lv.size() - 1;
   for (int l = 0; l <= L; ++l)
     if (!f_levels[l]) return DGFAS_ERR_INVALID;
-  if (L < 1 || c->local) {
-    set_error("fmg: needs a globally refined hierarchy of at least two levels");
+  if (L < 1) {
+    set_error("fmg: needs at least two levels");
     return DGFAS_ERR_UNSUPPORTED;
   }
   // level 0: the V-cycle on the root alone is its exact solve

@@ -60,13 +60,46 @@ def test_fmg_then_mixed_solve_reaches_1e10():
     assert info["r_final"] <= 1e-10 * r_zero * (1 + 1e-9)
 
 
-def test_fmg_rejects_local_refinement():
+def test_fmg_on_local_refinement_matches_oracle():
+    """Config 4 (small): the FP64 FMG start on every level (the top's and the
+    level solutions left for the composite solve) against the oracle, then
+    the mixed-precision solve from it reaches 1e-10 of the zero start's
+    composite residual."""
     torch = torch_cuda()
+    from oracle import fas, sip
     cfg = wl.config4(small=True)
     pr = cfg["params"]
-    S = dgfas.Solver(cfg["levels"], pr["mu_star"], pr["delta"], pr["s1"], pr["s2"], pr["sc"])
-    fs = [torch.zeros(S.ndof(l), dtype=torch.float64, device="cuda") for l in range(S.n_levels)]
-    u = torch.zeros(S.ndof(-1), dtype=torch.float64, device="cuda")
-    with pytest.raises(dgfas.DgfasError) as e:
-        S.dgfas_fmg(fs, u)
-    assert e.value.code == -7   # DGFAS_ERR_UNSUPPORTED
+    H = fas.LocalHierarchy(cfg["levels"], pr["mu_star"], pr["delta"], pr["s1"], pr["s2"], pr["sc"])
+    f_or = []
+    for op in H.ops:
+        X = op.geo["x"]
+        f_or.append(sip.rhs(op, wl.eval_front_f(cfg["rhs"], X),
+                            wl.eval_front_u(cfg["rhs"], X)).reshape(-1))
+    u_or = H.fmg_local(f_or, cycles=1)
+    for prec in (dgfas.DGFAS_FP64, dgfas.DGFAS_FP32):
+        S = dgfas.Solver(cfg["levels"], pr["mu_star"], pr["delta"], pr["s1"], pr["s2"], pr["sc"],
+                         precision=prec)
+        L = S.n_levels - 1
+        f_gpu = []
+        for l in range(S.n_levels):
+            xyz = S.node_coords(l).cpu().numpy()
+            fn = torch.from_numpy(wl.eval_front_f(cfg["rhs"], xyz)).cuda()
+            un = torch.from_numpy(wl.eval_front_u(cfg["rhs"], xyz)).cuda()
+            b = torch.empty_like(fn)
+            S.dgfas_assemble_rhs_level(l, fn, un, b)
+            if l < L:
+                S.dgfas_set_level_rhs(l, b)
+            f_gpu.append(b)
+        u = torch.zeros_like(f_gpu[-1])
+        S.dgfas_fmg(f_gpu, u)
+        if prec == dgfas.DGFAS_FP64:
+            assert rel(u.cpu().numpy(), u_or[L]) < 1e-11
+            for l in range(L):
+                ul = torch.empty(S.ndof(l), dtype=torch.float64, device="cuda")
+                S.dgfas_get_level_solution(l, ul)
+                assert rel(ul.cpu().numpy(), u_or[l]) < 1e-11, l
+        else:
+            r_zero = H.composite_residual([np.zeros(op.ndof) for op in H.ops], f_or)
+            r_f = S.dgfas_composite_residual(u, f_gpu[-1])
+            info = S.dgfas_solve(u, f_gpu[-1], 1e-10 * r_zero / r_f, 40)
+            assert info["r_final"] <= 1e-10 * r_zero * (1 + 1e-9)
