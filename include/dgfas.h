@@ -52,9 +52,19 @@ extern "C" {
                           scaling by the inverse eigenvalue sums) */
 
 /* smoother (Sec. 4.3): weighted additive Schwarz (Alg. 5) or Schwarz-
-   preconditioned inexact CG (Alg. 6) */
+   preconditioned inexact CG (Alg. 6).  SCG takes the preconditioned residual
+   as its first search direction (p = z), as in the inexact PCG of Golub and
+   Ye that Sec. 4.3.2 adopts; all its scalar products stay on the device, so an
+   SCG smoother issues no host synchronization. */
 #define DGFAS_WAS 0
 #define DGFAS_SCG 1
+
+/* root (coarsest-level) solver (Sec. 4.3.2: SCG also serves as the solver of
+   the coarse problem): the exact dense inverse (root <= 8192 DoF), or FP64 SCG
+   from the projected solution, root_steps steps or until
+   |r| <= root_rtol |r_start| */
+#define DGFAS_COARSE_DENSE 0
+#define DGFAS_COARSE_SCG 1
 
 /* One level of the multilevel mesh (Sec. 3.1): a conforming hexahedral mesh
    with one polynomial degree.  All arrays are host arrays of n_elem rows. */
@@ -89,6 +99,11 @@ typedef struct {
   int precision;             /* DGFAS_FP64, DGFAS_FP32 or DGFAS_BF16 smoother */
   int smoother;              /* DGFAS_WAS or DGFAS_SCG */
   int max_cycles;            /* default cap for dgfas_solve when <= 0 is passed */
+  int coarse;                /* DGFAS_COARSE_DENSE or DGFAS_COARSE_SCG */
+  double root_rtol;          /* SCG root: relative exit tolerance (<= 0: 1e-3) */
+  int root_steps;            /* SCG root: step cap per visit (<= 0: 64); the
+                                steps past the exit test leave u unchanged, so
+                                a visit is a fixed launch sequence (graphs) */
 } dgfas_params;
 
 typedef struct {
@@ -318,15 +333,18 @@ long long dgfas_kernel_launches(void);
    for callers that cannot allocate device memory when they smooth, e.g. code
    running inside its own stream capture or under an allocator that owns all
    device memory).  Adds to u [ndof] the FP64 weighted Schwarz correction
-   sum_e R_s^T W^e (A~_s^e)^-1 R_s r of the residual r [ndof] on `level` (>= 1),
-   i.e. the update of one sweep of Alg. 5 given its residual.  Both are device
-   pointers; u is updated in place, r is read only.
+   u += sum_e R_s^T W^e (A~_s^e)^-1 R_s r of the residual r [ndof] on `level`
+   (>= 1): the subdomain patches of r, the fast-diagonalization solves with the
+   level's surrogate, the overlap weights, and the sum back into u.  Both are
+   device pointers; u is updated in place, r is read only.
    Scratch: a fixed 16 MiB device array inside the library (2^21 FP64 patch
    entries) replaces the context's patch buffer; levels needing more, i.e.
    n_elem (p+1+2m)^3 > 2^21, are rejected with DGFAS_ERR_UNSUPPORTED.  The call
    makes no device allocation of any kind.  Its first call on a device looks up
    the array's device address (cudaGetSymbolAddress), so make that first call
-   before any stream capture.  All calls share the one array: calls whose work
+   before any stream capture.  The address is kept for the life of the process:
+   do not reset the device (cudaDeviceReset) between calls.  Devices numbered
+   64 or higher are refused (DGFAS_ERR_UNSUPPORTED).  All calls share the one array: calls whose work
    overlaps on the GPU (different streams, or several contexts) race on it. */
 int dgfas_schwarz_correct_static(void* ctx, int level, const double* r, double* u);
 

@@ -16,7 +16,7 @@ element of a non-top level is a twig and the top level holds the leaves.
   the first down-leg step of each cycle is the stopping test
   r_2 <= rtol * r_2^0 (Euclidean norm over the leaf DoF, Sec. 6.1).
 * The root problem is solved exactly (dense Cholesky of the assembled root
-  matrix).
+  matrix), or by SCG from the projected solution (coarse = "scg").
 * `scg` is Alg. 6.
 """
 import numpy as np
@@ -29,19 +29,28 @@ from .transfer import Transfer
 
 class Hierarchy:
     def __init__(self, levels, mu_star, delta, s1=2, s2=2, sc=4, nu=1.0, kappa=0.0,
-                 gcoefs=None, smoother="was"):
+                 gcoefs=None, smoother="was", scg_first="z", coarse="dense", root_rtol=1e-3,
+                 root_steps=64):
         self.levels = levels
         self.smoother = smoother
+        self.scg_first = scg_first
+        self.coarse = coarse
+        self.root_rtol, self.root_steps = root_rtol, root_steps
         self.s1, self.s2, self.sc = s1, s2, sc
         self.ops = [LevelOps(lv, mu_star, nu, kappa) for lv in levels]
-        self.sw = [None] + [Schwarz(lv, delta, mu_star, nu, kappa,
-                                    None if gcoefs is None else gcoefs[l])
-                            for l, lv in enumerate(levels) if l > 0]
+        self.sw = [Schwarz(lv, delta, mu_star, nu, kappa,
+                           None if gcoefs is None else gcoefs[l])
+                   if (l > 0 or coarse == "scg") else None
+                   for l, lv in enumerate(levels)]
         self.tr = [None] + [Transfer(levels[l - 1], levels[l]) for l in range(1, len(levels))]
         self.cls = [np.asarray(lv["cls"]) for lv in levels]
         self.active = [c != 2 for c in self.cls]
         self.local = any(np.any(c == 2) for c in self.cls) or any(
             np.any(c == 0) for c in self.cls[:-1])
+        if coarse == "scg":
+            self.nullspace = False
+            self.root_chol = None
+            return
         A0 = assemble(self.ops[0]).toarray()
         # kappa = 0 without Dirichlet faces (periodic or pure Neumann): A is
         # semidefinite with the constants as null space (remark on IPCG for
@@ -78,8 +87,16 @@ class Hierarchy:
             u = u + self.sw[l].correction(r)
         return u
 
-    def root_solve(self, g):
-        return sla.cho_solve(self.root_chol, g)
+    def root_solve(self, g, u0=None):
+        """The root problem A_0 u = g: exactly (dense Cholesky), or with
+        coarse = "scg" by Alg. 6 as the coarse solver (Sec. 4.3.2): from u0
+        (the projected solution in a V-cycle; zero if None) at most
+        root_steps steps, leaving as soon as |r| <= root_rtol |r_start|."""
+        if self.coarse != "scg":
+            return sla.cho_solve(self.root_chol, g)
+        u = np.zeros(self.ops[0].ndof) if u0 is None else u0
+        r_max = self.root_rtol * np.linalg.norm(g - self.A(0, u))
+        return self.scg(0, u, g, self.root_steps, r_max)
 
     def _down_up(self, u, f, r_top, top=None):
         """Alg. 2 below the top pre-smoothing: given the top residual r_top of
@@ -100,7 +117,7 @@ class Hierarchy:
             u[l - 1] = self.tr[l].project(u[l])
             ubar[l - 1] = u[l - 1].copy()
             g[l - 1] = self.A(l - 1, u[l - 1]) + self.tr[l].restrict(r)
-        u[0] = self.root_solve(g[0])
+        u[0] = self.root_solve(g[0], u[0])
         for l in range(1, L + 1):
             u[l] = u[l] + self.tr[l].interpolate(u[l - 1] - ubar[l - 1])
             if l < L:
@@ -176,17 +193,30 @@ class Hierarchy:
             u[L] = self.smooth(L, u[L], f, self.sc)
         return u[L], hist
 
-    def scg(self, l, u, f, n, r_max):
-        """Alg. 6 (inexact PCG with one Schwarz sweep as preconditioner)."""
+    def scg(self, l, u, f, n, r_max, precond=None, first=None):
+        """Alg. 6: inexact preconditioned CG with one Schwarz sweep z = M r as
+        the preconditioner, n steps or until |r| <= r_max.
+
+        The first search direction is a reading (`first`, default the
+        hierarchy's `scg_first`): "z" takes p = z in the first step, as in the
+        inexact PCG the algorithm adopts (Golub and Ye), so that the step
+        length gamma / p.q = z.r / z.A z is the exact line minimum along p;
+        "r" takes the algorithm's printed initialization p = r unchanged in
+        step 1.  `precond` replaces the Schwarz sweep (pins: identity ->
+        textbook CG, exact inverse -> one step)."""
+        first = self.scg_first if first is None else first
+        M = self.sw[l].correction if precond is None else precond
         r = f - self.A(l, u)
         p = r.copy()
         r0 = None
         gamma = None
         for i in range(1, n + 1):
-            z = self.sw[l].correction(r)
+            z = M(r)
             if i > 1:
                 beta = z @ (r - r0) / gamma
                 p = beta * p + z
+            elif first == "z":
+                p = z.copy()
             q = self.A(l, p)
             gamma = z @ r
             alpha = gamma / (p @ q)
@@ -266,7 +296,7 @@ class LocalHierarchy(Hierarchy):
             leaf = self.leaf_mask(l - 1)
             gl[leaf] = f[l - 1][leaf]
             g[l - 1] = gl
-        u[0] = self.root_solve(g[0])
+        u[0] = self.root_solve(g[0], u[0])
         for l in range(1, L + 1):
             u[l] = self.tr[l].prolong_fas(u[l], u[l - 1], ubar[l - 1], self.cls[l])
             if l < L:

@@ -94,14 +94,16 @@ def run(spec, n_base=4, p=3, n_root=2, max_ref=2, rounds=3, cycles=3, mu_star=5.
         levels = wl.hierarchy_from_marks(marks, n_base=n_base, p=p, n_root=n_root)
         base = len(levels) - 1 - len(marks)
         S = dgfas.Solver(levels, mu_star, delta, *s, precision=precision)
-        b = level_rhs(S, spec)
-        u = torch.zeros_like(b)
-        S.dgfas_solve(u, b, 1e-300, cycles, raise_on_fail=False)   # exactly `cycles` cycles
-        ind = indicators(S, spec, u)
+        try:
+            b = level_rhs(S, spec)
+            u = torch.zeros_like(b)
+            S.dgfas_solve(u, b, 1e-300, cycles, raise_on_fail=False)   # exactly `cycles` cycles
+            ind = indicators(S, spec, u)
+        finally:
+            S.close()
         leaf = [np.asarray(lv["cls"]) == wl.LEAF for lv in levels]
         err = float(np.sqrt(sum(x[lf].sum() for x, lf in zip(ind, leaf))))
         hist.append(dict(marks=[sorted(m) for m in marks], leaves=[int(lf.sum()) for lf in leaf],
                          energy_error=err))
         marks = new_marks(levels, marks, ind, base, max_ref, spec, n_base)
-        S.close()
     return hist, marks

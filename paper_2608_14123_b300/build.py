@@ -1,14 +1,20 @@
-"""Builds the sm_103a shared library libdgfas.so in-tree with nvcc."""
+"""Builds the sm_103a shared library libdgfas.so in-tree with nvcc.
+
+Each .cu file is compiled to an object in parallel (no device symbol crosses a
+file, so whole-program device compilation per file is enough), then the
+objects are linked into the shared library."""
 import os
 import subprocess
 import sys
+from concurrent.futures import ThreadPoolExecutor
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 SRC = os.path.join(HERE, "csrc")
+OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libdgfas.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-shared", "-Xcompiler", "-fPIC,-O3",
+FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O3",
          "--expt-relaxed-constexpr", "-I", os.path.join(ROOT, "include")]
 
 
@@ -16,22 +22,46 @@ def sources():
     return sorted(os.path.join(SRC, f) for f in os.listdir(SRC) if f.endswith(".cu"))
 
 
-def stale():
-    if not os.path.exists(LIB):
+def headers():
+    hs = [os.path.join(SRC, f) for f in os.listdir(SRC) if f.endswith(".h")]
+    return hs + [os.path.join(ROOT, "include", "dgfas.h"), os.path.abspath(__file__)]
+
+
+def _obj(src):
+    return os.path.join(OBJ, os.path.basename(src)[:-3] + ".o")
+
+
+def _stale(target, deps):
+    if not os.path.exists(target):
         return True
-    t = os.path.getmtime(LIB)
-    deps = sources() + [os.path.join(SRC, f) for f in os.listdir(SRC) if f.endswith(".h")]
-    deps.append(os.path.join(ROOT, "include", "dgfas.h"))
+    t = os.path.getmtime(target)
     return any(os.path.getmtime(d) > t for d in deps)
+
+
+def stale():
+    return _stale(LIB, sources() + headers())
 
 
 def build(force=False, verbose=False):
     if not force and not stale():
         return LIB
     nvcc = os.environ.get("NVCC", "nvcc")
-    cmd = [nvcc] + ARCH + FLAGS + sources() + ["-o", LIB + ".tmp"]
+    os.makedirs(OBJ, exist_ok=True)
+    todo = [s for s in sources() if force or _stale(_obj(s), [s] + headers())]
+
+    def compile_one(src):
+        cmd = [nvcc] + ARCH + FLAGS + ["-c", src, "-o", _obj(src) + ".tmp"]
+        if verbose:
+            print(" ".join(cmd), flush=True)
+        subprocess.run(cmd, check=True)
+        os.replace(_obj(src) + ".tmp", _obj(src))
+
+    with ThreadPoolExecutor(max_workers=max(1, min(len(todo), os.cpu_count() or 1))) as ex:
+        for f in [ex.submit(compile_one, s) for s in todo]:
+            f.result()
+    cmd = [nvcc] + ARCH + ["-shared", "-o", LIB + ".tmp"] + [_obj(s) for s in sources()]
     if verbose:
-        print(" ".join(cmd))
+        print(" ".join(cmd), flush=True)
     subprocess.run(cmd, check=True)
     os.replace(LIB + ".tmp", LIB)
     return LIB

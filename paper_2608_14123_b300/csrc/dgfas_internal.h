@@ -108,10 +108,12 @@ struct Ctx {
   void* rw = nullptr;           // smoother working residual (smoother precision)
   cudaStream_t cap = nullptr;   // internal stream for graph capture / replay
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
-  double* red = nullptr;        // reduction partials
+  int red_blocks = 0;           // CTAs of the reductions: 4 per SM of the device
+  double* red = nullptr;        // reduction partials [2 * red_blocks + 64]
   double* red_host = nullptr;   // pinned
   double* scg_buf = nullptr;    // SCG vectors (p, q, z, r0) for the largest level
   double* dscal = nullptr;      // device scalars of the SCG recurrences
+  int* dcnt = nullptr;          // ticket counters of the single-pass reductions
   int* tc_err = nullptr;        // set by the tensor-core FD kernel when a wait ran out
   double* Ainv = nullptr;       // root inverse
   int n_root = 0;
@@ -146,6 +148,8 @@ int tune_candidates(Ctx& c, int l, int kernel, int* out, int max_out);
 int launch_combine(Ctx& c, int l, int prec, void* delta);
 int launch_add_delta(Ctx& c, long long n, int prec, const void* d, double* u);
 int launch_combine_to(Ctx& c, int l, int prec, double* z);
+int launch_combine_to32(Ctx& c, int l, float* z);
+int launch_apply32(Ctx& c, int l, const float* u, float* out);
 int prepare_transfer(const TransferView& T);          // set-up: kernel attributes
 int launch_project(Ctx& c, int l, const double* uf);   // lv[l-1].u = ubar = P uf
 int launch_restrict(Ctx& c, int l, const double* rf, double* rc);
@@ -163,7 +167,8 @@ int launch_rhs(Ctx& c, int l, const double* f, const double* uD, double* b);
 int launch_sumsq_leaf(Ctx& c, int l, const double* v, double* part);
 int launch_leaf_rhs(Ctx& c, int l, const double* f, double* g);
 int launch_to_float(Ctx& c, const double* x, float* y, long long n);
-extern int g_red_blocks;
+// scg.cu: Alg. 6 with device-resident scalars (no host synchronization)
+int scg_run(Ctx& c, int l, double* u, int n, double rtol, int prec);
 extern std::atomic<long long> g_kernels;   // kernels launched (graph replays included)
 
 void set_error(const std::string& s);

@@ -448,7 +448,7 @@ extern "C" void dgfas_destroy(void* vctx) {
   if (c->ev_in) cudaEventDestroy(c->ev_in);
   if (c->ev_out) cudaEventDestroy(c->ev_out);
   for (auto& H : c->lv) free_level(H);
-  void* ptrs[] = {c->patch, c->rw, c->red, c->scg_buf, c->dscal, c->Ainv, c->tc_err};
+  void* ptrs[] = {c->patch, c->rw, c->red, c->scg_buf, c->dscal, c->dcnt, c->Ainv, c->tc_err};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->red_host) cudaFreeHost(c->red_host);
@@ -471,9 +471,26 @@ extern "C" int dgfas_setup_levels(const dgfas_mesh* mesh, const dgfas_params* pr
     set_error("setup: unknown precision");
     return DGFAS_ERR_INVALID;
   }
+  if (prm->coarse != DGFAS_COARSE_DENSE && prm->coarse != DGFAS_COARSE_SCG) {
+    set_error("setup: unknown root solver");
+    return DGFAS_ERR_INVALID;
+  }
   Ctx* c = new Ctx();
   c->stream = (cudaStream_t)stream;
+  {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        sms <= 0) {
+      set_error("setup: no CUDA device");
+      delete c;
+      return DGFAS_ERR_CUDA;
+    }
+    c->red_blocks = 4 * sms;
+  }
   c->prm = *prm;
+  if (!(c->prm.root_rtol > 0)) c->prm.root_rtol = 1e-3;
+  if (c->prm.root_steps <= 0) c->prm.root_steps = 64;
   c->nu = mesh->nu;
   c->kappa = mesh->kappa;
   c->lv.resize(mesh->n_levels);
@@ -523,13 +540,21 @@ extern "C" int dgfas_setup_levels(const dgfas_mesh* mesh, const dgfas_params* pr
     set_error("stream/event creation");
     rc = DGFAS_ERR_CUDA;
   }
-  if (rc == DGFAS_OK) rc = dalloc(&c->red, g_red_blocks + 64);
-  if (rc == DGFAS_OK && cudaMallocHost((void**)&c->red_host, (g_red_blocks + 64) * sizeof(double)) != cudaSuccess) {
+  if (rc == DGFAS_OK) rc = dalloc(&c->red, 2 * c->red_blocks + 64);
+  if (rc == DGFAS_OK && cudaMallocHost((void**)&c->red_host, (2 * c->red_blocks + 64) * sizeof(double)) != cudaSuccess) {
     set_error("pinned host buffer");
     rc = DGFAS_ERR_OOM;
   }
-  if (rc == DGFAS_OK && prm->smoother == DGFAS_SCG) rc = dalloc(&c->scg_buf, 5 * maxdof);
+  if (rc == DGFAS_OK && (prm->smoother == DGFAS_SCG || prm->coarse == DGFAS_COARSE_SCG))
+    rc = dalloc(&c->scg_buf, 4 * maxdof);
   if (rc == DGFAS_OK) rc = dalloc(&c->dscal, 64);
+  if (rc == DGFAS_OK) {
+    if (cudaMalloc((void**)&c->dcnt, 8 * sizeof(int)) != cudaSuccess ||
+        cudaMemset(c->dcnt, 0, 8 * sizeof(int)) != cudaSuccess) {
+      set_error("reduction counters");
+      rc = DGFAS_ERR_OOM;
+    }
+  }
   if (rc == DGFAS_OK) {
     if (cudaMalloc((void**)&c->tc_err, sizeof(int)) != cudaSuccess ||
         cudaMemset(c->tc_err, 0, sizeof(int)) != cudaSuccess) {
@@ -537,7 +562,7 @@ extern "C" int dgfas_setup_levels(const dgfas_mesh* mesh, const dgfas_params* pr
       rc = DGFAS_ERR_OOM;
     }
   }
-  if (rc == DGFAS_OK) rc = build_root(*c);
+  if (rc == DGFAS_OK && prm->coarse != DGFAS_COARSE_SCG) rc = build_root(*c);
   if (rc != DGFAS_OK) {
     dgfas_destroy(c);
     return rc;
@@ -549,23 +574,12 @@ extern "C" int dgfas_setup_levels(const dgfas_mesh* mesh, const dgfas_params* pr
 // ---------------------------------------------------------------- reductions
 static int norm_dev(Ctx& c, const double* v, long long n, double* out) {
   RET(launch_sumsq(c, v, n, c.red));
-  CK(cudaMemcpyAsync(c.red_host, c.red, g_red_blocks * sizeof(double), cudaMemcpyDeviceToHost,
+  CK(cudaMemcpyAsync(c.red_host, c.red, c.red_blocks * sizeof(double), cudaMemcpyDeviceToHost,
                      c.stream));
   CK(cudaStreamSynchronize(c.stream));
   double s = 0.0;
-  for (int i = 0; i < g_red_blocks; ++i) s += c.red_host[i];
+  for (int i = 0; i < c.red_blocks; ++i) s += c.red_host[i];
   *out = std::sqrt(s);
-  return DGFAS_OK;
-}
-
-static int dot_dev(Ctx& c, const double* a, const double* b, long long n, double* out) {
-  RET(launch_dot(c, a, b, n, c.red));
-  CK(cudaMemcpyAsync(c.red_host, c.red, g_red_blocks * sizeof(double), cudaMemcpyDeviceToHost,
-                     c.stream));
-  CK(cudaStreamSynchronize(c.stream));
-  double s = 0.0;
-  for (int i = 0; i < g_red_blocks; ++i) s += c.red_host[i];
-  *out = s;
   return DGFAS_OK;
 }
 
@@ -607,45 +621,6 @@ static int was_block(Ctx& c, int l, double* u, int n, bool zero_start, bool want
   return launch_add_delta(c, H.ndof, prec, H.delta, u);
 }
 
-// Alg. 6 with n iterations: FP64 recurrences and operator, the Schwarz sweep
-// in the smoother precision.  Starts from the FP64 residual in lv[l].r; u
-// updated in place; lv[l].r ends as the CG residual.  Synchronizes for the
-// scalar products.
-static int scg_block(Ctx& c, int l, double* u, const double* g, int n) {
-  LevelHost& H = c.lv[l];
-  const long long nd = H.ndof;
-  const int prec = c.prm.precision;
-  double *r = H.r, *p = c.scg_buf, *q = p + nd, *z = q + nd, *r0 = z + nd;
-  (void)g;
-  double gamma = 0.0;
-  for (int i = 1; i <= n; ++i) {
-    if (prec == DGFAS_FP32) RET(launch_to_float(c, r, (float*)c.rw, nd));
-    else CK(cudaMemcpyAsync(c.rw, r, nd * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
-    RET(launch_fd(c, l, prec, c.rw));
-    RET(launch_combine_to(c, l, prec, z));
-    if (i > 1) {
-      CK(cudaMemcpyAsync(q, r, nd * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
-      RET(launch_axpy(c, nd, -1.0, r0, q));   // q = r - r0
-      double num;
-      RET(dot_dev(c, z, q, nd, &num));
-      const double beta = num / gamma;
-      RET(launch_axpy(c, nd, beta - 1.0, p, p));   // p = beta p
-      RET(launch_axpy(c, nd, 1.0, z, p));          // p += z
-    } else {
-      CK(cudaMemcpyAsync(p, z, nd * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
-    }
-    RET(launch_apply(c, l, DGFAS_FP64, p, nullptr, q, 1.0));
-    RET(dot_dev(c, z, r, nd, &gamma));
-    double pq;
-    RET(dot_dev(c, p, q, nd, &pq));
-    const double alpha = gamma / pq;
-    CK(cudaMemcpyAsync(r0, r, nd * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
-    RET(launch_axpy(c, nd, -alpha, q, r));
-    RET(launch_axpy(c, nd, alpha, p, u));
-  }
-  return DGFAS_OK;
-}
-
 // Smoothing of A u = g on level l with lv[l].r = g - A u on entry.  With
 // want_res, lv[l].r = g - A u of the smoothed u on exit.  zero_start = false
 // means lv[l].delta holds a prolongated correction not yet added to u.
@@ -656,7 +631,7 @@ static int smooth(Ctx& c, int l, double* u, const double* g, int n, bool zero_st
       RET(launch_add_delta(c, c.lv[l].ndof, c.prm.precision, c.lv[l].delta, u));
       RET(launch_apply(c, l, DGFAS_FP64, u, g, c.lv[l].r, -1.0));
     }
-    RET(scg_block(c, l, u, g, n));
+    RET(scg_run(c, l, u, n, 0.0, c.prm.precision));
     if (want_res) RET(launch_apply(c, l, DGFAS_FP64, u, g, c.lv[l].r, -1.0));
     return DGFAS_OK;
   }
@@ -666,6 +641,17 @@ static int smooth(Ctx& c, int l, double* u, const double* g, int n, bool zero_st
     return DGFAS_OK;
   }
   return was_block(c, l, u, n, zero_start, want_res);
+}
+
+// Root solve of lv[0] (A u_0 = g_0, g_0 in lv[0].gv): the dense inverse, or
+// FP64 SCG (Alg. 6 as the coarse solver) from the current lv[0].u (the
+// projection ubar_0 in a V-cycle) or from zero (zero_start).
+static int root_solve(Ctx& c, bool zero_start) {
+  if (c.prm.coarse != DGFAS_COARSE_SCG) return launch_root(c);
+  LevelHost& R = c.lv[0];
+  if (zero_start) CK(cudaMemsetAsync(R.u, 0, R.ndof * sizeof(double), c.stream));
+  RET(launch_apply(c, 0, DGFAS_FP64, R.u, R.gv, R.r, -1.0));
+  return scg_run(c, 0, R.u, c.prm.root_steps, c.prm.root_rtol, DGFAS_FP64);
 }
 
 // ---------------------------------------------------------------- FAS V-cycle
@@ -696,7 +682,7 @@ static int down_up(Ctx& c, double* uL, const double* fL, int top = -1) {
     RET(launch_apply(c, l - 1, DGFAS_FP64, c.lv[l - 1].u, c.lv[l - 1].t, c.lv[l - 1].gv, 1.0));
     if (c.lv[l - 1].has_leaf) RET(launch_leaf_rhs(c, l - 1, c.lv[l - 1].fl, c.lv[l - 1].gv));
   }
-  RET(launch_root(c));
+  RET(root_solve(c, false));
   for (int l = 1; l <= L; ++l) {
     double* ul = l == L ? uL : c.lv[l].u;
     const double* gl = l == L ? fL : c.lv[l].gv;
@@ -759,7 +745,7 @@ static int interpolate_solution(Ctx& c, int l, double* ul) {
   return launch_add_delta(c, F.ndof, DGFAS_FP64, F.delta, ul);
 }
 
-static bool graph_ok(Ctx& c) { return c.use_graph && c.prm.smoother == DGFAS_WAS; }
+static bool graph_ok(Ctx& c) { return c.use_graph != 0; }
 
 // Runs one cycle body on the caller's stream, or replays it as a CUDA graph
 // captured on the context's internal stream (ordered after and before the
@@ -848,10 +834,10 @@ static int composite_norm(Ctx& c, double* u, const double* f, double* out) {
     double* r = l == L ? H.r : H.t;
     RET(launch_apply(c, l, DGFAS_FP64, ul, gl, r, -1.0));
     RET(launch_sumsq_leaf(c, l, r, c.red));
-    CK(cudaMemcpyAsync(c.red_host, c.red, g_red_blocks * sizeof(double), cudaMemcpyDeviceToHost,
+    CK(cudaMemcpyAsync(c.red_host, c.red, c.red_blocks * sizeof(double), cudaMemcpyDeviceToHost,
                        c.stream));
     CK(cudaStreamSynchronize(c.stream));
-    for (int i = 0; i < g_red_blocks; ++i) s += c.red_host[i];
+    for (int i = 0; i < c.red_blocks; ++i) s += c.red_host[i];
   }
   *out = std::sqrt(s);
   return DGFAS_OK;
@@ -859,7 +845,7 @@ static int composite_norm(Ctx& c, double* u, const double* f, double* out) {
 
 static double host_norm(Ctx& c) {
   double s = 0.0;
-  for (int i = 0; i < g_red_blocks; ++i) s += c.red_host[i];
+  for (int i = 0; i < c.red_blocks; ++i) s += c.red_host[i];
   return std::sqrt(s);
 }
 
@@ -903,7 +889,7 @@ extern "C" int dgfas_fmg(void* ctx, const double* const* f_levels, int cycles_pe
   // level 0: the V-cycle on the root alone is its exact solve
   CK(cudaMemcpyAsync(c->lv[0].gv, f_levels[0], c->lv[0].ndof * sizeof(double),
                      cudaMemcpyDeviceToDevice, c->stream));
-  RET(launch_root(*c));
+  RET(root_solve(*c, true));
   for (int l = 1; l < L; ++l) {
     RET(interpolate_solution(*c, l, c->lv[l].u));
     for (int k = 0; k < cycles_per_level; ++k) RET(vcycle_sub(*c, l, f_levels[l]));
@@ -974,7 +960,7 @@ extern "C" int dgfas_fas_vcycle(void* ctx, double* u, const double* f, double* r
   if (!c || !u || !f) return DGFAS_ERR_INVALID;
   RET(run_body(*c, 0, u, f));
   if (rnorm) {
-    CK(cudaMemcpyAsync(c->red_host, c->red, g_red_blocks * sizeof(double), cudaMemcpyDeviceToHost,
+    CK(cudaMemcpyAsync(c->red_host, c->red, c->red_blocks * sizeof(double), cudaMemcpyDeviceToHost,
                        c->stream));
     CK(cudaStreamSynchronize(c->stream));
     *rnorm = host_norm(*c);
@@ -1008,7 +994,7 @@ extern "C" int dgfas_solve(void* ctx, double* u, const double* f, double rtol, i
       RET(composite_norm(*c, u, f, &r));
       // the next cycle starts from the top residual (composite_norm left it in lv[L].r)
     } else {
-      CK(cudaMemcpyAsync(c->red_host, c->red, g_red_blocks * sizeof(double),
+      CK(cudaMemcpyAsync(c->red_host, c->red, c->red_blocks * sizeof(double),
                          cudaMemcpyDeviceToHost, c->stream));
       CK(cudaStreamSynchronize(c->stream));
       r = host_norm(*c);

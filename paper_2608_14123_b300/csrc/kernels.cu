@@ -12,7 +12,6 @@
 
 #include "dgfas_internal.h"
 
-int g_red_blocks = 592;   // 4 x 148 SMs
 std::atomic<long long> g_kernels{0};   // kernels launched through the library
 
 #define CK(x)                                                                 \
@@ -1084,6 +1083,19 @@ int launch_combine_to(Ctx& c, int l, int prec, double* z) {
   return combine_launch<float, false, double>(H.v32, H.N, (const float*)c.patch, z, c.stream);
 }
 
+// z = sum of the weighted patches in FP32 (FP32 SCG preconditioner)
+int launch_combine_to32(Ctx& c, int l, float* z) {
+  LevelHost& H = c.lv[l];
+  return combine_launch<float, false, float>(H.v32, H.N, (const float*)c.patch, z, c.stream);
+}
+
+// out = A u in FP32 (FP32 SCG in correction form)
+int launch_apply32(Ctx& c, int l, const float* u, float* out) {
+  LevelHost& H = c.lv[l];
+  return apply_disp<float, float, double, float>(H.v32, u, nullptr, out, 1.0f, c.stream,
+                                                 H.tune.apply32);
+}
+
 // ============================================================================ transfers
 // Tensor-product application Y = (A3 x A2 x A1) X on one element, A_d [no][ni]
 // row-major, by three passes through shared memory.  Team-wide (all threads of
@@ -1630,7 +1642,7 @@ int launch_root(Ctx& c) {
 
 // ============================================================================ reductions
 // Deterministic: fixed grid, per-block tree sums in a fixed order; the host (or a
-// final kernel) adds the g_red_blocks partials in index order.
+// final kernel) adds the c.red_blocks partials in index order.
 template <bool DOT>
 __global__ void k_partial(const double* __restrict__ a, const double* __restrict__ b,
                           long long n, double* __restrict__ part) {
@@ -1667,7 +1679,7 @@ __global__ void k_partial_leaf(const double* __restrict__ v, const signed char* 
 
 int launch_sumsq_leaf(Ctx& c, int l, const double* v, double* part) {
   LevelHost& H = c.lv[l];
-  k_partial_leaf<<<g_red_blocks, 256, 0, c.stream>>>(v, H.d_cls, H.N * H.N * H.N, H.ndof, part);
+  k_partial_leaf<<<c.red_blocks, 256, 0, c.stream>>>(v, H.d_cls, H.N * H.N * H.N, H.ndof, part);
   ++g_kernels;
   CK(cudaGetLastError());
   return DGFAS_OK;
@@ -1690,14 +1702,14 @@ int launch_leaf_rhs(Ctx& c, int l, const double* f, double* g) {
 }
 
 int launch_sumsq(Ctx& c, const double* v, long long n, double* part) {
-  k_partial<false><<<g_red_blocks, 256, 0, c.stream>>>(v, nullptr, n, part);
+  k_partial<false><<<c.red_blocks, 256, 0, c.stream>>>(v, nullptr, n, part);
   ++g_kernels;
   CK(cudaGetLastError());
   return DGFAS_OK;
 }
 
 int launch_dot(Ctx& c, const double* a, const double* b, long long n, double* part) {
-  k_partial<true><<<g_red_blocks, 256, 0, c.stream>>>(a, b, n, part);
+  k_partial<true><<<c.red_blocks, 256, 0, c.stream>>>(a, b, n, part);
   ++g_kernels;
   CK(cudaGetLastError());
   return DGFAS_OK;

@@ -30,9 +30,13 @@ static double* g_addr[64] = {nullptr};
 
 static int static_patch_address(double** out) {
   int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) {
     set_error("no current CUDA device");
     return DGFAS_ERR_CUDA;
+  }
+  if (dev >= 64) {
+    set_error("schwarz_correct_static: device ordinals of 64 and above are not supported");
+    return DGFAS_ERR_UNSUPPORTED;
   }
   std::lock_guard<std::mutex> lock(g_mu);
   if (!g_addr[dev]) {

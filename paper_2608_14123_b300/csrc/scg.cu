@@ -1,0 +1,267 @@
+// Schwarz-preconditioned inexact conjugate gradients (Alg. 6) with every
+// scalar of the recurrence kept on the device.
+//
+// Each scalar product is one kernel: the CTAs write per-CTA partial sums, and
+// the last CTA to finish (ticket counter) adds the partials in index order and
+// evaluates the recurrence coefficient it feeds (beta, gamma, alpha, |r|^2).
+// The kernels that follow read the coefficients from device memory, so an SCG
+// block issues no host synchronization and can be captured in a CUDA graph.
+// The sums are deterministic: fixed grid, fixed per-thread ranges, fixed tree
+// and fixed order of the partials.
+//
+// Reading of the first search direction: p = z (the preconditioned residual)
+// in the first step, as in the inexact PCG of Golub and Ye that the method
+// adopts; the step length gamma / p.q = z.r / z.A z is then the exact line
+// minimum along p.  (The printed initialization p = r, left unchanged in step
+// 1, makes the SCG-smoothed V-cycle diverge on the Cartesian and perturbed
+// workloads.)
+//
+// Exit test |r| <= r_max: once it holds, a device flag sets alpha = 0 in every
+// remaining step, so u and r stay as they were when the test first held (the
+// same result as leaving the loop); the step count of a block is fixed, which
+// is what graph capture needs.
+#include "dgfas_internal.h"
+
+namespace {
+
+enum { S_GAMMA = 0, S_BETA = 1, S_ALPHA = 2, S_PQ = 3, S_RR = 4, S_DONE = 5, S_RMAX2 = 6,
+       S_STEPS = 7 };
+
+constexpr int kThreads = 256;
+
+// Block-wide sums of K values per thread (fixed tree); thread 0 gets the result.
+template <int K>
+__device__ void block_sum(double (&v)[K], double (*sh)[kThreads]) {
+  for (int k = 0; k < K; ++k) sh[k][threadIdx.x] = v[k];
+  __syncthreads();
+  for (int o = kThreads / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o)
+      for (int k = 0; k < K; ++k) sh[k][threadIdx.x] += sh[k][threadIdx.x + o];
+    __syncthreads();
+  }
+  for (int k = 0; k < K; ++k) v[k] = sh[k][0];
+}
+
+// Writes this CTA's K partial sums to part[k * G + cta] and takes a ticket;
+// returns true in the last CTA, which then holds the totals (partials added in
+// CTA order by a fixed tree) in tot[] on every thread.
+template <int K>
+__device__ bool partials_and_ticket(double (&v)[K], double* part, int* counter,
+                                    double (&tot)[K]) {
+  __shared__ double sh[K][kThreads];
+  __shared__ int last;
+  block_sum<K>(v, sh);
+  const int G = gridDim.x;
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < K; ++k) part[k * G + blockIdx.x] = v[k];
+    __threadfence();
+    last = atomicAdd(counter, 1) == G - 1;
+  }
+  __syncthreads();
+  if (!last) return false;
+  __threadfence();
+  double s[K];
+  for (int k = 0; k < K; ++k) s[k] = 0.0;
+  for (int i = threadIdx.x; i < G; i += kThreads)
+    for (int k = 0; k < K; ++k) s[k] += __ldcg(part + k * G + i);
+  block_sum<K>(s, sh);
+  for (int k = 0; k < K; ++k) tot[k] = s[k];
+  if (threadIdx.x == 0) *counter = 0;   // ready for the next reduction
+  return true;
+}
+
+// |r|^2 of the start residual: r_max^2 = rtol^2 |r|^2, done = (r == 0), steps = 0
+template <typename T>
+__global__ void k_scg_init(const T* __restrict__ r, long long n, double rtol2, double* part,
+                           int* counter, double* scal) {
+  double v[1] = {0.0};
+  for (long long i = (long long)blockIdx.x * kThreads + threadIdx.x; i < n;
+       i += (long long)gridDim.x * kThreads) {
+    const double ri = r[i];
+    v[0] += ri * ri;
+  }
+  double t[1];
+  if (partials_and_ticket<1>(v, part, counter, t) && threadIdx.x == 0) {
+    scal[S_RR] = t[0];
+    scal[S_RMAX2] = rtol2 * t[0];
+    scal[S_DONE] = t[0] > 0.0 ? 0.0 : 1.0;
+    scal[S_STEPS] = 0.0;
+  }
+}
+
+// gamma_new = z.r; for step > 1 also z.r0 and beta = (z.r - z.r0) / gamma_old
+// (products and sums in FP64)
+template <typename T, bool FIRST>
+__global__ void k_scg_zr(const T* __restrict__ z, const T* __restrict__ r,
+                         const T* __restrict__ r0, long long n, double* part, int* counter,
+                         double* scal) {
+  double v[2] = {0.0, 0.0};
+  for (long long i = (long long)blockIdx.x * kThreads + threadIdx.x; i < n;
+       i += (long long)gridDim.x * kThreads) {
+    const double zi = z[i];
+    v[0] += zi * (double)r[i];
+    if (!FIRST) v[1] += zi * (double)r0[i];
+  }
+  double t[2];
+  if (partials_and_ticket<2>(v, part, counter, t) && threadIdx.x == 0) {
+    const bool done = scal[S_DONE] != 0.0;
+    if (!FIRST) scal[S_BETA] = done ? 0.0 : (t[0] - t[1]) / scal[S_GAMMA];
+    scal[S_GAMMA] = t[0];
+  }
+}
+
+// p = z (first step) or p = beta p + z
+template <typename T, bool FIRST>
+__global__ void k_scg_dir(T* __restrict__ p, const T* __restrict__ z, long long n,
+                          const double* __restrict__ scal) {
+  const T beta = FIRST ? T(0) : (T)scal[S_BETA];
+  for (long long i = (long long)blockIdx.x * kThreads + threadIdx.x; i < n;
+       i += (long long)gridDim.x * kThreads)
+    p[i] = FIRST ? z[i] : beta * p[i] + z[i];
+}
+
+// pq = p.q, alpha = gamma / pq (0 once the exit test held, or for pq = 0)
+template <typename T>
+__global__ void k_scg_pq(const T* __restrict__ p, const T* __restrict__ q, long long n,
+                         double* part, int* counter, double* scal) {
+  double v[1] = {0.0};
+  for (long long i = (long long)blockIdx.x * kThreads + threadIdx.x; i < n;
+       i += (long long)gridDim.x * kThreads)
+    v[0] += (double)p[i] * (double)q[i];
+  double t[1];
+  if (partials_and_ticket<1>(v, part, counter, t) && threadIdx.x == 0) {
+    scal[S_PQ] = t[0];
+    const bool done = scal[S_DONE] != 0.0;
+    scal[S_ALPHA] = (done || t[0] == 0.0) ? 0.0 : scal[S_GAMMA] / t[0];
+  }
+}
+
+// r0 = r; r -= alpha q; x += alpha p; |r|^2 and the exit test |r| <= r_max
+template <typename T>
+__global__ void k_scg_update(T* __restrict__ r, T* __restrict__ r0, T* __restrict__ x,
+                             const T* __restrict__ p, const T* __restrict__ q, long long n,
+                             double* part, int* counter, double* scal) {
+  const T alpha = (T)scal[S_ALPHA];
+  double v[1] = {0.0};
+  for (long long i = (long long)blockIdx.x * kThreads + threadIdx.x; i < n;
+       i += (long long)gridDim.x * kThreads) {
+    const T ri = r[i];
+    const T rn = ri - alpha * q[i];
+    r0[i] = ri;
+    r[i] = rn;
+    x[i] += alpha * p[i];
+    v[0] += (double)rn * (double)rn;
+  }
+  double t[1];
+  if (partials_and_ticket<1>(v, part, counter, t) && threadIdx.x == 0) {
+    if (scal[S_DONE] == 0.0) {
+      scal[S_RR] = t[0];
+      scal[S_STEPS] += 1.0;
+      if (t[0] <= scal[S_RMAX2]) scal[S_DONE] = 1.0;
+    }
+  }
+}
+
+}  // namespace
+
+#define LAUNCH_CHECK()                                      \
+  do {                                                      \
+    ++g_kernels;                                            \
+    if (cudaGetLastError() != cudaSuccess) {                \
+      set_error("scg kernel launch");                       \
+      return DGFAS_ERR_CUDA;                                \
+    }                                                       \
+  } while (0)
+
+// The Schwarz sweep z = sum_e R^T W A~^-1 R r of SCG in precision prec, and the
+// operator q = A p in the vectors' precision T.
+static int scg_sweep(Ctx& c, int l, int prec, const double* r, double* z) {
+  const long long nd = c.lv[l].ndof;
+  if (prec == DGFAS_FP64) {
+    if (cudaMemcpyAsync(c.rw, r, nd * sizeof(double), cudaMemcpyDeviceToDevice, c.stream) !=
+        cudaSuccess) {
+      set_error("scg: copy");
+      return DGFAS_ERR_CUDA;
+    }
+  } else {
+    int rc = launch_to_float(c, r, (float*)c.rw, nd);
+    if (rc != DGFAS_OK) return rc;
+  }
+  int rc = launch_fd(c, l, prec, c.rw);
+  return rc == DGFAS_OK ? launch_combine_to(c, l, prec, z) : rc;
+}
+static int scg_sweep(Ctx& c, int l, int prec, const float* r, float* z) {
+  int rc = launch_fd(c, l, prec, r);
+  return rc == DGFAS_OK ? launch_combine_to32(c, l, z) : rc;
+}
+static int scg_apply(Ctx& c, int l, const double* p, double* q) {
+  return launch_apply(c, l, DGFAS_FP64, p, nullptr, q, 1.0);
+}
+static int scg_apply(Ctx& c, int l, const float* p, float* q) { return launch_apply32(c, l, p, q); }
+
+// n steps of Alg. 6 on A x = b given the start residual r = b - A x; x and r
+// updated in place; p, q, z, r0 work vectors of the level's size.
+template <typename T>
+static int scg_steps(Ctx& c, int l, int prec, T* x, T* r, T* p, T* q, T* z, T* r0, int n,
+                     double rtol) {
+  const long long nd = c.lv[l].ndof;
+  double* scal = c.dscal;
+  int* cnt = c.dcnt;
+  const int G = c.red_blocks;
+  k_scg_init<T><<<G, kThreads, 0, c.stream>>>(r, nd, rtol * rtol, c.red, cnt, scal);
+  LAUNCH_CHECK();
+  for (int i = 1; i <= n; ++i) {
+    int rc = scg_sweep(c, l, prec, r, z);
+    if (rc != DGFAS_OK) return rc;
+    if (i == 1) {
+      k_scg_zr<T, true><<<G, kThreads, 0, c.stream>>>(z, r, nullptr, nd, c.red, cnt, scal);
+      LAUNCH_CHECK();
+      k_scg_dir<T, true><<<G, kThreads, 0, c.stream>>>(p, z, nd, scal);
+      LAUNCH_CHECK();
+    } else {
+      k_scg_zr<T, false><<<G, kThreads, 0, c.stream>>>(z, r, r0, nd, c.red, cnt, scal);
+      LAUNCH_CHECK();
+      k_scg_dir<T, false><<<G, kThreads, 0, c.stream>>>(p, z, nd, scal);
+      LAUNCH_CHECK();
+    }
+    rc = scg_apply(c, l, p, q);
+    if (rc != DGFAS_OK) return rc;
+    k_scg_pq<T><<<G, kThreads, 0, c.stream>>>(p, q, nd, c.red, cnt, scal);
+    LAUNCH_CHECK();
+    k_scg_update<T><<<G, kThreads, 0, c.stream>>>(r, r0, x, p, q, nd, c.red, cnt, scal);
+    LAUNCH_CHECK();
+  }
+  return DGFAS_OK;
+}
+
+// Alg. 6 on level l with n steps from the FP64 residual in lv[l].r (= g - A u),
+// u updated in place; rtol > 0 adds the exit test |r| <= rtol |r_start|.  No
+// host synchronization.
+// prec = FP64: the iteration itself, in FP64; lv[l].r ends as the CG residual.
+// prec = FP32 / BF16: correction form, as the WAS smoother: SCG on A d = r
+// from d = 0 in FP32 vectors (FP32 operator, Schwarz sweep in prec, FP64
+// scalar products), then u += d.  In exact arithmetic the iterates are the
+// same; the FP64 residual of the outer cycle drives the iterative refinement.
+// lv[l].r is then stale (the caller recomputes it when it needs it).
+int scg_run(Ctx& c, int l, double* u, int n, double rtol, int prec) {
+  LevelHost& H = c.lv[l];
+  const long long nd = H.ndof;
+  if (!c.scg_buf) {
+    set_error("scg: no SCG work vectors (context not set up for SCG)");
+    return DGFAS_ERR_INVALID;
+  }
+  if (prec == DGFAS_FP64) {
+    double *p = c.scg_buf, *q = p + nd, *z = q + nd, *r0 = z + nd;
+    return scg_steps<double>(c, l, prec, u, H.r, p, q, z, r0, n, rtol);
+  }
+  float* d = (float*)H.delta;
+  float *r = (float*)c.scg_buf, *p = r + nd, *q = p + nd, *z = q + nd, *r0 = z + nd;
+  if (cudaMemsetAsync(d, 0, nd * sizeof(float), c.stream) != cudaSuccess) {
+    set_error("scg: memset");
+    return DGFAS_ERR_CUDA;
+  }
+  int rc = launch_to_float(c, H.r, r, nd);
+  if (rc == DGFAS_OK) rc = scg_steps<float>(c, l, prec, d, r, p, q, z, r0, n, rtol);
+  if (rc == DGFAS_OK) rc = launch_add_delta(c, nd, prec, d, u);
+  return rc;
+}

@@ -16,6 +16,7 @@ LIB_PATH = os.path.join(HERE, "libdgfas.so")
 
 DGFAS_FP64, DGFAS_FP32, DGFAS_BF16 = 0, 1, 2
 DGFAS_WAS, DGFAS_SCG = 0, 1
+DGFAS_COARSE_DENSE, DGFAS_COARSE_SCG = 0, 1
 ERRORS = {0: "ok", -1: "INVALID", -2: "OOM", -3: "CUDA", -4: "MESH", -5: "NOT_CONVERGED",
           -6: "DIVERGED", -7: "UNSUPPORTED"}
 
@@ -43,7 +44,8 @@ class dgfas_params(ctypes.Structure):
     _fields_ = [("mu_star", ctypes.c_double), ("delta", ctypes.c_double),
                 ("s1", ctypes.c_int), ("s2", ctypes.c_int), ("sc", ctypes.c_int),
                 ("precision", ctypes.c_int), ("smoother", ctypes.c_int),
-                ("max_cycles", ctypes.c_int)]
+                ("max_cycles", ctypes.c_int), ("coarse", ctypes.c_int),
+                ("root_rtol", ctypes.c_double), ("root_steps", ctypes.c_int)]
 
 
 class dgfas_info(ctypes.Structure):
@@ -127,10 +129,19 @@ def _check(code, where):
     return code
 
 
-def _ptr(t):
+def _ptr(t, numel=None, dtype="float64"):
+    """Device pointer of tensor t after checking what the kernels will assume:
+    element type `dtype` (a torch dtype name), at least `numel` elements, a
+    contiguous CUDA tensor.  A mismatch raises here, before any launch: a
+    short or mistyped vector would otherwise be read or written out of bounds."""
     if t is None:
         return None
-    assert t.is_cuda and t.is_contiguous(), "device tensors must be contiguous CUDA tensors"
+    if str(t.dtype) != "torch." + dtype:
+        raise TypeError(f"expected a {dtype} tensor, got {t.dtype}")
+    if numel is not None and t.numel() < numel:
+        raise ValueError(f"tensor has {t.numel()} elements, the call needs {numel}")
+    if not (t.is_cuda and t.is_contiguous()):
+        raise ValueError("device tensors must be contiguous CUDA tensors")
     return ctypes.c_void_p(t.data_ptr())
 
 
@@ -144,7 +155,8 @@ class Solver:
     paper_2608_14123_b300.workloads) and the solver parameters."""
 
     def __init__(self, levels, mu_star, delta, s1=2, s2=2, sc=4, precision=DGFAS_FP64,
-                 smoother=DGFAS_WAS, nu=1.0, kappa=0.0, max_cycles=50):
+                 smoother=DGFAS_WAS, nu=1.0, kappa=0.0, max_cycles=50,
+                 coarse=DGFAS_COARSE_DENSE, root_rtol=1e-3, root_steps=64):
         lib = load()
         self._keep = []
         arr = (dgfas_level * len(levels))()
@@ -165,7 +177,8 @@ class Solver:
                                  octant.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
                                  cls.ctypes.data_as(ctypes.POINTER(ctypes.c_byte)))
         mesh = dgfas_mesh(len(levels), arr, nu, kappa)
-        prm = dgfas_params(mu_star, delta, s1, s2, sc, precision, smoother, max_cycles)
+        prm = dgfas_params(mu_star, delta, s1, s2, sc, precision, smoother, max_cycles, coarse,
+                           root_rtol, root_steps)
         ctx = ctypes.c_void_p()
         _check(lib.dgfas_setup_levels(ctypes.byref(mesh), ctypes.byref(prm), _stream(),
                                       ctypes.byref(ctx)), "dgfas_setup_levels")
@@ -190,29 +203,38 @@ class Solver:
         level = level % self.n_levels
         return int(load().dgfas_level_ndof(self.ctx, level))
 
+    def n_elem(self, level=-1):
+        return int(self.levels[level % self.n_levels]["nbr"].shape[0])
+
     def dgfas_node_coords(self, level, xyz):
-        _check(load().dgfas_node_coords(self.ctx, level % self.n_levels, _ptr(xyz)), "node_coords")
+        _check(load().dgfas_node_coords(self.ctx, level % self.n_levels,
+                                            _ptr(xyz, 3 * self.ndof(level))), "node_coords")
 
     def dgfas_assemble_rhs(self, f, uD, b):
-        _check(load().dgfas_assemble_rhs(self.ctx, _ptr(f), _ptr(uD), _ptr(b)), "assemble_rhs")
+        n = self.ndof()
+        _check(load().dgfas_assemble_rhs(self.ctx, _ptr(f, n), _ptr(uD, n), _ptr(b, n)), "assemble_rhs")
 
     def dgfas_apply_op(self, level, u, g, out):
-        _check(load().dgfas_apply_op(self.ctx, level % self.n_levels, _ptr(u), _ptr(g), _ptr(out)),
+        n = self.ndof(level)
+        _check(load().dgfas_apply_op(self.ctx, level % self.n_levels, _ptr(u, n), _ptr(g, n),
+                                     _ptr(out, n)),
                "apply_op")
 
     def dgfas_schwarz_smooth(self, level, u, g, n):
-        _check(load().dgfas_schwarz_smooth(self.ctx, level % self.n_levels, _ptr(u), _ptr(g), n),
+        nd = self.ndof(level)
+        _check(load().dgfas_schwarz_smooth(self.ctx, level % self.n_levels, _ptr(u, nd), _ptr(g, nd),
+                                           n),
                "schwarz_smooth")
 
     def dgfas_fas_vcycle(self, u, f, want_norm=True):
         r = ctypes.c_double(0.0)
-        _check(load().dgfas_fas_vcycle(self.ctx, _ptr(u), _ptr(f),
+        _check(load().dgfas_fas_vcycle(self.ctx, _ptr(u, self.ndof()), _ptr(f, self.ndof()),
                                        ctypes.byref(r) if want_norm else None), "fas_vcycle")
         return r.value
 
     def dgfas_solve(self, u, f, rtol=1e-10, max_cycles=50, raise_on_fail=True):
         info = dgfas_info()
-        code = load().dgfas_solve(self.ctx, _ptr(u), _ptr(f), rtol, max_cycles, ctypes.byref(info))
+        code = load().dgfas_solve(self.ctx, _ptr(u, self.ndof()), _ptr(f, self.ndof()), rtol, max_cycles, ctypes.byref(info))
         if raise_on_fail:
             _check(code, "solve")
         hist = [info.r0] + list(info.history[:min(info.cycles, 128)])
@@ -221,21 +243,25 @@ class Solver:
 
     def dgfas_norm(self, level, v):
         r = ctypes.c_double(0.0)
-        _check(load().dgfas_norm(self.ctx, level % self.n_levels, _ptr(v), ctypes.byref(r)), "norm")
+        _check(load().dgfas_norm(self.ctx, level % self.n_levels, _ptr(v, self.ndof(level)),
+                                  ctypes.byref(r)), "norm")
         return r.value
 
     def dgfas_set_surrogate(self, level, g):
-        _check(load().dgfas_set_surrogate(self.ctx, level % self.n_levels, _ptr(g)), "set_surrogate")
+        _check(load().dgfas_set_surrogate(self.ctx, level % self.n_levels,
+                                          _ptr(g, 4 * self.n_elem(level))), "set_surrogate")
 
     def dgfas_get_surrogate(self, level, g):
-        _check(load().dgfas_get_surrogate(self.ctx, level % self.n_levels, _ptr(g)), "get_surrogate")
+        _check(load().dgfas_get_surrogate(self.ctx, level % self.n_levels,
+                                          _ptr(g, 4 * self.n_elem(level))), "get_surrogate")
 
     def dgfas_use_graph(self, enable):
         _check(load().dgfas_use_graph(self.ctx, 1 if enable else 0), "use_graph")
 
     def dgfas_profile_sweep(self, level, u, g, reps):
         ms = np.zeros(4)
-        _check(load().dgfas_profile_sweep(self.ctx, level % self.n_levels, _ptr(u), _ptr(g), reps,
+        _check(load().dgfas_profile_sweep(self.ctx, level % self.n_levels, _ptr(u, self.ndof(level)),
+                                          _ptr(g, self.ndof(level)), reps,
                                           ms.ctypes.data_as(ctypes.c_void_p)), "profile_sweep")
         return dict(residual_smoother=ms[0], fd=ms[1], combine=ms[2], residual_fp64=ms[3])
 
@@ -243,12 +269,15 @@ class Solver:
         """Full multigrid startup (Alg. 4): u_top <- the FMG start value from the
         per-level right-hand sides f_levels (root first, device FP64)."""
         assert len(f_levels) == self.n_levels
-        arr = (ctypes.c_void_p * self.n_levels)(*[f.data_ptr() for f in f_levels])
-        _check(load().dgfas_fmg(self.ctx, arr, cycles_per_level, _ptr(u_top)), "fmg")
+        arr = (ctypes.c_void_p * self.n_levels)(*[_ptr(f, self.ndof(l)).value
+                                                  for l, f in enumerate(f_levels)])
+        _check(load().dgfas_fmg(self.ctx, arr, cycles_per_level, _ptr(u_top, self.ndof())), "fmg")
 
     def dgfas_element_energy(self, level, eps, out):
         """out[e] = eps_e . (A eps)_e on `level` (element error indicators)."""
-        _check(load().dgfas_element_energy(self.ctx, level % self.n_levels, _ptr(eps), _ptr(out)),
+        _check(load().dgfas_element_energy(self.ctx, level % self.n_levels,
+                                            _ptr(eps, self.ndof(level)),
+                                            _ptr(out, self.n_elem(level))),
                "element_energy")
 
     TUNE_KERNELS = ("apply_fp64_elements_per_cta", "apply_smoother_elements_per_cta",
@@ -280,32 +309,37 @@ class Solver:
     def dgfas_schwarz_correct_static(self, level, r, u):
         """u += weighted Schwarz correction of r, using the library's static
         scratch array (no device allocation in the call)."""
-        _check(load().dgfas_schwarz_correct_static(self.ctx, level % self.n_levels, _ptr(r), _ptr(u)),
+        _check(load().dgfas_schwarz_correct_static(self.ctx, level % self.n_levels,
+                                                    _ptr(r, self.ndof(level)),
+                                                    _ptr(u, self.ndof(level))),
                "schwarz_correct_static")
 
     def dgfas_learned_surrogate(self, level, params, max_log_scaling=2.5):
         """Surrogate coefficients of `level` from the MLP; returns the number of
         elements that kept their geometric coefficients."""
         nf = ctypes.c_int(0)
-        _check(load().dgfas_learned_surrogate(self.ctx, level % self.n_levels, _ptr(params),
+        _check(load().dgfas_learned_surrogate(self.ctx, level % self.n_levels,
+                                              _ptr(params, load().dgfas_mlp_param_count(), "float32"),
                                               max_log_scaling, ctypes.byref(nf)), "learned_surrogate")
         return nf.value
 
     def dgfas_assemble_rhs_level(self, level, f, uD, b):
-        _check(load().dgfas_assemble_rhs_level(self.ctx, level % self.n_levels, _ptr(f), _ptr(uD),
-                                               _ptr(b)), "assemble_rhs_level")
+        n = self.ndof(level)
+        _check(load().dgfas_assemble_rhs_level(self.ctx, level % self.n_levels, _ptr(f, n),
+                                               _ptr(uD, n), _ptr(b, n)), "assemble_rhs_level")
 
     def dgfas_set_level_rhs(self, level, f):
-        _check(load().dgfas_set_level_rhs(self.ctx, level, _ptr(f)), "set_level_rhs")
+        _check(load().dgfas_set_level_rhs(self.ctx, level, _ptr(f, self.ndof(level))), "set_level_rhs")
 
     def dgfas_composite_residual(self, u, f):
         r = ctypes.c_double(0.0)
-        _check(load().dgfas_composite_residual(self.ctx, _ptr(u), _ptr(f), ctypes.byref(r)),
+        _check(load().dgfas_composite_residual(self.ctx, _ptr(u, self.ndof()), _ptr(f, self.ndof()),
+                                               ctypes.byref(r)),
                "composite_residual")
         return r.value
 
     def dgfas_get_level_solution(self, level, u):
-        _check(load().dgfas_get_level_solution(self.ctx, level, _ptr(u)), "get_level_solution")
+        _check(load().dgfas_get_level_solution(self.ctx, level, _ptr(u, self.ndof(level))), "get_level_solution")
 
     def dgfas_tc_error(self):
         return int(load().dgfas_tc_error(self.ctx))

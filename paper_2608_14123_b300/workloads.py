@@ -263,13 +263,17 @@ def random_start(rng, n):
 
 
 # ---------------------------------------------------------------- the configurations
-def config(cid, small=False):
+def config(cid, small=False, root=None):
     """Workload `cid` in 1, 2, 3, 5 (config 4: `config4`).
 
     Returns dict(levels, rhs, u0, params) with params the solver parameters
-    (mu_star, delta, s1, s2, sc).  `small` shrinks configs 2/3/5 to a mesh the
-    oracle handles in seconds while keeping the structure (degree, hierarchy
-    shape, perturbation, grading).
+    (mu_star, delta, s1, s2, sc, and for an SCG root coarse / root_rtol /
+    root_steps).  `small` shrinks configs 2/3/5 to a mesh the oracle handles
+    in seconds while keeping the structure (degree, hierarchy shape,
+    perturbation, grading).  `root` chooses the bottom of the curvilinear
+    hierarchies (configs 3, 5): "p1" ends at the p = 1 level of the fine mesh,
+    solved by SCG (p-multigrid 7 -> 3 -> 1); "h" continues with h-coarsening
+    at p = 1 down to a 4^3 root solved exactly.
     """
     rng = np.random.default_rng(SEED_BASE + cid)
     if cid == 1:
@@ -288,7 +292,7 @@ def config(cid, small=False):
         n = 4 if small else 16
         r = grading_ratio(n, (4.0 if small else 16.0) * n)
         V = perturbed_vertices(n, 0.25, rng, graded_ratio_z=r)
-        levels = hierarchy(V, [7, 3, 1], h_root=min(4, n))
+        levels = hierarchy(V, [7, 3, 1], h_root=None if root == "p1" else min(4, n))
         rhs = modes_rhs_spec(rng)
         # mu_star = 5 leaves this SIP operator indefinite on perturbed cells;
         # 10 (upper end of the paper's tested range) keeps it SPD
@@ -296,11 +300,13 @@ def config(cid, small=False):
     elif cid == 5:
         n = 8 if small else 64
         V = perturbed_vertices(n, 0.15, rng)
-        levels = hierarchy(V, [7, 3, 1], h_root=4)
+        levels = hierarchy(V, [7, 3, 1], h_root=None if root == "p1" else 4)
         rhs = modes_rhs_spec(rng)
         prm = dict(mu_star=5.0, delta=0.08, s1=2, s2=2, sc=4)
     else:
         raise ValueError(f"unknown config {cid}")
+    if root == "p1":
+        prm.update(coarse="scg", root_rtol=1e-3, root_steps=64)
     top = levels[-1]
     N = top["p"] + 1
     ndof = top["corners"].shape[0] * N ** 3

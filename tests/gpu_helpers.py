@@ -11,19 +11,31 @@ def torch_cuda():
     return torch
 
 
+SOLVER_KW = ("coarse", "root_rtol", "root_steps")
+
+
 def make_solver(cfg, precision=0, smoother=0, **over):
+    """CUDA-path solver of workload cfg; `over` replaces solver parameters
+    (mu_star, delta, s1, s2, sc, coarse, root_rtol, root_steps; coarse as the
+    oracle's name "dense" / "scg")."""
     from paper_2608_14123_b300 import dgfas
     pr = dict(cfg["params"])
     pr.update(over)
+    kw = {k: pr[k] for k in SOLVER_KW if k in pr}
+    if "coarse" in kw:
+        kw["coarse"] = {"dense": dgfas.DGFAS_COARSE_DENSE, "scg": dgfas.DGFAS_COARSE_SCG}[kw["coarse"]]
     return dgfas.Solver(cfg["levels"], pr["mu_star"], pr["delta"], pr["s1"], pr["s2"], pr["sc"],
-                        precision=precision, smoother=smoother)
+                        precision=precision, smoother=smoother, **kw)
 
 
-def make_oracle(cfg, **over):
+def make_oracle(cfg, smoother="was", **over):
+    """Oracle hierarchy of the same workload and parameters."""
     from oracle import fas
     pr = dict(cfg["params"])
     pr.update(over)
-    return fas.Hierarchy(cfg["levels"], pr["mu_star"], pr["delta"], pr["s1"], pr["s2"], pr["sc"])
+    kw = {k: pr[k] for k in SOLVER_KW if k in pr}
+    return fas.Hierarchy(cfg["levels"], pr["mu_star"], pr["delta"], pr["s1"], pr["s2"], pr["sc"],
+                         smoother=smoother, **kw)
 
 
 def rhs_both(cfg, S, H):

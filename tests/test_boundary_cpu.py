@@ -63,3 +63,19 @@ def test_host_fd_rejects_bad_arguments():
         dgfas.dgfas_host_fd_variant(4, 0.08, 5.0, 16)
     with pytest.raises(dgfas.DgfasError):
         dgfas.dgfas_host_fd_variant(4, 0.6, 5.0, 0)
+
+
+def test_binding_rejects_wrong_dtype_and_short_vectors_before_any_launch():
+    """The binding checks element type and length of every vector argument on
+    the host: a float32 or short tensor where the kernels expect FP64 of the
+    level's size raises before the library is called."""
+    import torch
+    with pytest.raises(TypeError):
+        dgfas._ptr(torch.zeros(16, dtype=torch.float32), 16)
+    with pytest.raises(ValueError):
+        dgfas._ptr(torch.zeros(8, dtype=torch.float64), 16)
+    with pytest.raises(TypeError):
+        dgfas._ptr(torch.zeros(16, dtype=torch.float64), 16, "float32")
+    with pytest.raises(ValueError):   # right type and size, but host memory
+        dgfas._ptr(torch.zeros(16, dtype=torch.float64), 16)
+    assert dgfas._ptr(None, 16) is None
