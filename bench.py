@@ -1,14 +1,19 @@
 #!/usr/bin/env python
 """Benchmark of the FAS multigrid hot path on one B300 (or N replicas).
 
-Workload (one "step" = one FAS V-cycle over the whole hierarchy, Alg. 2):
-Poisson on [0,1]^3, Dirichlet, uniform Cartesian 32^3 elements, p = 8
-(23.9M DoF), p-coarsening 8 -> 4 -> 2 -> 1 then h-coarsening to 4^3, V(2,2)
-with the weighted additive Schwarz / fast-diagonalization smoother, seeded
-16-mode right-hand side.  Headline: the FP32 smoother with FP64 residual,
-tau, restriction and root solve, with the FD mode products of the top levels
-on the tensor cores (BF16 operands, FP32 accumulation); the FP32 and the
-plain FP64 paths are measured beside it.
+Workload (one "step" = one FAS V-cycle over the whole hierarchy, Alg. 2): the
+large curvilinear run, Poisson on [0,1]^3 with Dirichlet conditions, 64^3
+trilinear elements with interior vertices perturbed by +-0.15h, p = 7
+(134M DoF), seeded 16-mode right-hand side; p-multigrid 7 -> 3 -> 1 with the
+Schwarz-preconditioned CG smoother (Alg. 6, V(2,2), n_sc = 4) and an FP64 SCG
+root solve at p = 1.  Headline: mixed precision plus learned surrogate -- the
+smoother in correction form on FP32 vectors with the fast-diagonalization
+mode products on the tensor cores (BF16 operands, FP32 accumulation), the
+learned MLP surrogate on the p = 7 and p = 3 levels, the V-cycle replayed as a
+CUDA graph -- with FP64 residual, tau, restriction and root.  Beside it: the
+plain FP64 GPU path and the geometric surrogate (DoF/s per V-cycle and time
+to 1e-10), the graded curvilinear, uniform Cartesian and locally refined
+workloads, and the FP64 oracle on the host cores.
 
 Prints one JSON line.  `--impl reference` times the FP64 CPU oracle instead
 (on a bounded sample of the same workload).
@@ -244,15 +249,17 @@ def dist_env():
 
 
 # ------------------------------------------------------------------ CPU oracle arm
-def oracle_sample_rate(cores_note=True, n_sample=8, cycles=1):
-    """DoF/s per V-cycle of the FP64 oracle on a bounded sample of the workload:
-    the same degree, hierarchy shape and smoother on n_sample^3 elements."""
+def oracle_sample_rate(n_sample=8, cycles=1):
+    """DoF/s per V-cycle of the FP64 oracle on a bounded sample of the headline
+    workload: the same degree, perturbation, p-hierarchy (7 -> 3 -> 1), SCG
+    smoother and SCG root on n_sample^3 elements (the oracle is never tuned)."""
     from oracle import fas, sip
-    V = wl.uniform_vertices(n_sample)
-    levels = wl.hierarchy(V, [8, 4, 2, 1], h_root=4)
-    rng = np.random.default_rng(wl.SEED_BASE + 2)
+    rng = np.random.default_rng(wl.SEED_BASE + 5)
+    V = wl.perturbed_vertices(n_sample, 0.15, rng)
+    levels = wl.hierarchy(V, [7, 3, 1])
     spec = wl.modes_rhs_spec(rng)
-    H = fas.Hierarchy(levels, 5.0, 0.08, 2, 2, 4)
+    H = fas.Hierarchy(levels, 5.0, 0.08, 2, 2, 4, smoother="scg", coarse="scg", root_rtol=1e-3,
+                      root_steps=64)
     top = H.ops[-1]
     X = top.geo["x"]
     b = sip.rhs(top, wl.eval_f(spec, X), np.zeros(X.shape[:-1])).reshape(-1)
@@ -290,138 +297,119 @@ def run_reference(args):
         "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ndof / value * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "cartesian-32^3-p8-dirichlet-poisson (sampled at 8^3 elements)",
+        "config": {"workload": "curvilinear-64^3-p7 (trilinear, +-0.15h perturbation), 16-mode "
+                               "RHS, Dirichlet Poisson (sampled at 8^3 elements)",
                    "global_batch": 1, "seq_len": 0, "parallelism": "replicas",
                    "sample_dof": ndof},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
-                         "sample": f"one FP64 oracle V-cycle on {n_sample}^3 elements p=8 "
-                                   f"({ndof} DoF) per step"},
+                         "sample": f"one FP64 oracle V-cycle (SCG smoother and root) on "
+                                   f"{n_sample}^3 elements p=7 ({ndof} DoF) per step"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         "wall_s": time.perf_counter() - t_all,
     }
     print(json.dumps(out), flush=True)
 
 
-# ------------------------------------------------------------------ other workloads
-def _solve_record(S, u, b, torch):
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    info = S.dgfas_solve(u, b, 1e-10, 40, raise_on_fail=False)
-    torch.cuda.synchronize()
-    return {"seconds": time.perf_counter() - t0, "cycles": info["cycles"],
-            "rel_residual": info["r_final"] / info["r0"], "code": info["code"]}
+# ------------------------------------------------------------------ helpers of the GPU arm
+SURR_SET = 100000
+GOLD = os.path.join(ROOT, "tests", "golden")
 
 
-def other_workloads(dgfas, torch):
-    """Time to 1e-10 on the locally refined front (config 4) and the large
-    curvilinear run (config 5), FP32 smoother vs FP64."""
-    out = {}
-    c4 = wl.config4()
-    pr = c4["params"]
-    leaf = sum(int(np.sum(lv["cls"] == 0)) * (lv["p"] + 1) ** 3 for lv in c4["levels"])
-    rec = {"leaf_dof": leaf, "levels": len(c4["levels"])}
-    for name, prec in (("mixed_fp32", dgfas.DGFAS_FP32), ("fp64", dgfas.DGFAS_FP64)):
-        S = dgfas.Solver(c4["levels"], pr["mu_star"], pr["delta"], pr["s1"], pr["s2"], pr["sc"],
-                         precision=prec)
-        L = S.n_levels - 1
-        for l in range(S.n_levels):
-            xyz = S.node_coords(l).cpu().numpy()
-            fn = torch.from_numpy(wl.eval_front_f(c4["rhs"], xyz)).cuda()
-            un = torch.from_numpy(wl.eval_front_u(c4["rhs"], xyz)).cuda()
-            b = torch.empty_like(fn)
-            S.dgfas_assemble_rhs_level(l, fn, un, b)
-            if l < L:
-                S.dgfas_set_level_rhs(l, b)
-        rec[name] = _solve_record(S, torch.from_numpy(c4["u0"]).cuda(), b, torch)
-        S.close()
-    out["config4_front_local_refinement_p3"] = rec
-    c5 = wl.config(5)
-    pr = c5["params"]
-    rec = {"dof": int(c5["u0"].size), "smoother": "SCG (Alg. 6)"}
-    for name, prec in (("mixed_fp32", dgfas.DGFAS_FP32), ("fp64", dgfas.DGFAS_FP64)):
-        S = dgfas.Solver(c5["levels"], pr["mu_star"], pr["delta"], pr["s1"], pr["s2"], pr["sc"],
-                         precision=prec, smoother=dgfas.DGFAS_SCG)
-        xyz = S.node_coords(-1)
-        f = torch.from_numpy(wl.eval_f(c5["rhs"], xyz.cpu().numpy())).cuda()
-        del xyz
-        b = torch.empty_like(f)
-        S.dgfas_assemble_rhs(f, None, b)
-        del f
-        rec[name] = _solve_record(S, torch.from_numpy(c5["u0"]).cuda(), b, torch)
-        S.close()
-        del b
-        torch.cuda.empty_cache()
-    out["config5_curvilinear64_p7"] = rec
-    return out
+def train_surrogates(torch, degrees=(7, 3), epochs=40):
+    """The learned surrogate per degree: the MLP trained on the GPU by the
+    library's kernels on the 10^5 oracle Kronecker-sum fits (stored targets;
+    inputs regenerated from the seeded training elements by the library)."""
+    from paper_2608_14123_b300 import learned
+    out, info = {}, {}
+    for p in degrees:
+        d = np.load(os.path.join(GOLD, f"surrogate_fits_p{p}_n{SURR_SET}.npz"))
+        cr = wl.surrogate_training_set(SURR_SET, p)[d["ok"]]
+        X = learned.inputs(cr)
+        Y = torch.from_numpy(d["Y"]).cuda()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        th, loss = learned.train(X, Y, epochs=epochs, batch=256, lr=2e-3, seed=11)
+        torch.cuda.synchronize()
+        out[p] = th
+        info[p] = {"samples": int(X.shape[0]), "epochs": epochs, "seconds": time.perf_counter() - t0,
+                   "loss_first": float(loss[0]), "loss_last": float(loss[-1])}
+        del X, Y
+    return out, info
 
 
-# ------------------------------------------------------------------ GPU arm
-def run_gpu(args):
-    import torch
-    from paper_2608_14123_b300 import dgfas
-
-    ws, rank, local = dist_env()
-    if ws > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-
-    cfg = wl.config(2)
+def build_solver(dgfas, cfg, prec, smoother, surr=None):
+    """Solver of workload cfg (set-up); surr: {degree: trained params} replaces
+    the geometric surrogate on the levels of those degrees."""
     pr = cfg["params"]
-    levels = cfg["levels"]
-    top = levels[-1]
-    N = top["p"] + 1
-    prec = {"fp32": dgfas.DGFAS_FP32, "bf16": dgfas.DGFAS_BF16, "fp64": dgfas.DGFAS_FP64}[args.precision]
-    S = dgfas.Solver(levels, pr["mu_star"], pr["delta"], pr["s1"], pr["s2"], pr["sc"],
-                     precision=prec)
-    S.dgfas_use_graph(True)
-    # launch shapes from the library's autotuner (set-up, outside every timed region)
-    tuning = [] if args.no_autotune else S.dgfas_autotune(reps=5)
-    ndof = S.ndof(-1)
-    xyz = S.node_coords(-1)
-    f_nod = torch.from_numpy(wl.eval_f(cfg["rhs"], xyz.cpu().numpy())).to(dev)
-    del xyz
-    b = torch.empty_like(f_nod)
-    S.dgfas_assemble_rhs(f_nod, None, b)
-    del f_nod
-    u0 = torch.from_numpy(cfg["u0"]).to(dev)
-    u = u0.clone()
+    kw = {}
+    if pr.get("coarse") == "scg":
+        kw = dict(coarse=dgfas.DGFAS_COARSE_SCG, root_rtol=pr["root_rtol"],
+                  root_steps=pr["root_steps"])
+    S = dgfas.Solver(cfg["levels"], pr["mu_star"], pr["delta"], pr["s1"], pr["s2"], pr["sc"],
+                     precision=prec, smoother=smoother, **kw)
+    fallback = {}
+    if surr:
+        for l in range(1, S.n_levels):
+            p = cfg["levels"][l]["p"]
+            if p in surr:
+                fallback[l] = S.dgfas_learned_surrogate(l, surr[p])
+    return S, fallback
 
-    for _ in range(args.warmup):
+
+def top_rhs(S, cfg, torch, dev):
+    xyz = S.node_coords(-1)
+    f = torch.from_numpy(wl.eval_f(cfg["rhs"], xyz.cpu().numpy())).to(dev)
+    del xyz
+    b = torch.empty_like(f)
+    S.dgfas_assemble_rhs(f, None, b)
+    del f
+    return b
+
+
+def time_vcycles(S, u, b, steps, warmup, torch, dgfas, ws=1, dev=None, clocks=False):
+    """ms per FAS V-cycle over `steps` cycles after `warmup` (CUDA events on the
+    current stream, which the library's graph replays are ordered on)."""
+    for _ in range(warmup):
         S.dgfas_fas_vcycle(u, b, want_norm=False)
     torch.cuda.synchronize()
     if ws > 1:
         torch.distributed.barrier()
-    clk = ClockSampler(local)
+    clk = ClockSampler(dev.index if dev is not None else 0) if clocks else None
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
+    k0 = dgfas.dgfas_kernel_launches()
     torch.cuda.nvtx.range_push("timed")
-    k_before = dgfas.dgfas_kernel_launches()
     e0.record()
-    for _ in range(args.steps):
+    for _ in range(steps):
         S.dgfas_fas_vcycle(u, b, want_norm=False)
     e1.record()
     torch.cuda.nvtx.range_pop()
-    gpu_launches = dgfas.dgfas_kernel_launches() - k_before
+    launches = dgfas.dgfas_kernel_launches() - k0
     torch.cuda.synchronize()
-    clocks = clk.stop()
-    ms = e0.elapsed_time(e1) / args.steps
-    if ws > 1:
-        ms = max_over_ranks(ms, dev)
-        torch.distributed.barrier()
-    value = ndof * ws / (ms * 1e-3)
+    ck = clk.stop() if clk else None
+    return e0.elapsed_time(e1) / steps, launches, ck
 
-    # ---- end to end through the public API with host buffers: every step
-    # copies its inputs (u, f) from pinned host memory and reads its result u
-    # back; two device buffer pairs and two copy streams let step k+1's
-    # upload and step k-1's download overlap step k's V-cycle (the library
-    # keeps one captured graph per buffer pair)
-    u_host = torch.from_numpy(cfg["u0"]).pin_memory()
+
+def solve_record(S, u, b, torch, rtol=1e-10, max_cycles=40):
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    info = S.dgfas_solve(u, b, rtol, max_cycles, raise_on_fail=False)
+    torch.cuda.synchronize()
+    return {"seconds": time.perf_counter() - t0, "cycles": info["cycles"],
+            "rel_residual": info["r_final"] / info["r0"], "code": info["code"],
+            "history": [h / info["history"][0] for h in info["history"][1:]]}
+
+
+def e2e_record(S, u0_host, b, torch, steps):
+    """The metric end to end through the C ABI with host buffers: every step
+    uploads u and f from pinned host memory and reads u back; two device
+    buffer pairs and two copy streams overlap step k+1's upload and step
+    k-1's download with step k's V-cycle (one captured graph per pair)."""
+    u_host = u0_host.pin_memory()
     b_host = b.cpu().pin_memory()
     u_back = [torch.empty_like(u_host).pin_memory() for _ in range(2)]
-    ud = [torch.empty_like(u0) for _ in range(2)]
+    ud = [torch.empty_like(b) for _ in range(2)]
     bd = [torch.empty_like(b) for _ in range(2)]
     comp = torch.cuda.current_stream()
     s_h2d, s_d2h = torch.cuda.Stream(), torch.cuda.Stream()
@@ -429,7 +417,7 @@ def run_gpu(args):
     comp_done = [torch.cuda.Event() for _ in range(2)]
     d2h_done = [torch.cuda.Event() for _ in range(2)]
 
-    def e2e_steps(n):
+    def run(n):
         for k in range(n):
             i = k % 2
             with torch.cuda.stream(s_h2d):
@@ -446,94 +434,221 @@ def run_gpu(args):
                 u_back[i].copy_(ud[i], non_blocking=True)
                 d2h_done[i].record(s_d2h)
 
-    e2e_steps(2)   # first use of each buffer pair captures its graph
+    run(2)
     torch.cuda.synchronize()
-    steps_e2e = max(4, min(args.steps, 10))
     t0 = time.perf_counter()
-    e2e_steps(steps_e2e)
+    run(steps)
     torch.cuda.synchronize()
-    e2e_s = (time.perf_counter() - t0) / steps_e2e
-    e2e = {"value": ndof / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 2 * ndof * 8,
-           "d2h_bytes_per_step": ndof * 8, "overlap": "double-buffered, 2 copy streams"}
+    dt = (time.perf_counter() - t0) / steps
+    n = b.numel()
+    out = {"seconds_per_step": dt, "h2d_bytes_per_step": 2 * n * 8, "d2h_bytes_per_step": n * 8,
+           "overlap": "double-buffered, 2 copy streams", "steps": steps}
+    del ud, bd, u_back, u_host, b_host
+    return out
 
-    # ---- per-kernel timing of the top-level smoother and the roofline
-    L = S.n_levels - 1
-    uk = u0.clone()
-    prof = S.dgfas_profile_sweep(L, uk, b, 5)
+
+# ------------------------------------------------------------------ other workloads
+def config4_record(dgfas, torch):
+    """Time to 1e-10 on the locally refined front (FP32 smoother vs FP64)."""
+    c4 = wl.config4()
+    pr = c4["params"]
+    leaf = sum(int(np.sum(lv["cls"] == 0)) * (lv["p"] + 1) ** 3 for lv in c4["levels"])
+    rec = {"leaf_dof": leaf, "levels": len(c4["levels"])}
+    for name, prec in (("mixed_fp32", dgfas.DGFAS_FP32), ("fp64", dgfas.DGFAS_FP64)):
+        S = dgfas.Solver(c4["levels"], pr["mu_star"], pr["delta"], pr["s1"], pr["s2"], pr["sc"],
+                         precision=prec)
+        L = S.n_levels - 1
+        for l in range(S.n_levels):
+            xyz = S.node_coords(l).cpu().numpy()
+            fn = torch.from_numpy(wl.eval_front_f(c4["rhs"], xyz)).cuda()
+            un = torch.from_numpy(wl.eval_front_u(c4["rhs"], xyz)).cuda()
+            b = torch.empty_like(fn)
+            S.dgfas_assemble_rhs_level(l, fn, un, b)
+            if l < L:
+                S.dgfas_set_level_rhs(l, b)
+        rec[name] = solve_record(S, torch.from_numpy(c4["u0"]).cuda(), b, torch)
+        S.close()
+    return rec
+
+
+def curvilinear_records(dgfas, torch, dev, cid, surr, arms):
+    """Per arm (name, precision, surrogate) on workload cid: ms per V-cycle
+    (3 graph replays) and time to 1e-10 from the random start."""
+    cfg = wl.config(cid, root="p1")
+    rec = {"dof": int(cfg["u0"].size), "levels": [lv["p"] for lv in cfg["levels"]],
+           "smoother": "SCG (Alg. 6) V(2,2), n_sc = 4", "root": "SCG at p = 1"}
+    for name, prec, use in arms:
+        S, fb = build_solver(dgfas, cfg, prec, dgfas.DGFAS_SCG, surr if use else None)
+        S.dgfas_use_graph(True)
+        b = top_rhs(S, cfg, torch, dev)
+        u0 = torch.from_numpy(cfg["u0"]).to(dev)
+        u = u0.clone()
+        ms, _, _ = time_vcycles(S, u, b, 3, 1, torch, dgfas)
+        r = solve_record(S, u0.clone(), b, torch)
+        r["ms_per_vcycle"] = ms
+        r["dof_per_s_per_vcycle"] = rec["dof"] / (ms * 1e-3)
+        if use:
+            r["fallback_elements"] = fb
+        rec[name] = r
+        S.close()
+        del b, u, u0
+        torch.cuda.empty_cache()
+    return rec
+
+
+def cartesian_record(dgfas, torch, dev, args):
+    """The uniform Cartesian workload (32^3, p = 8, WAS, BF16 tensor-core
+    smoother): ms per V-cycle, roofline of its FP64 residual, time to 1e-10."""
+    cfg = wl.config(2)
+    pr = cfg["params"]
+    S = dgfas.Solver(cfg["levels"], pr["mu_star"], pr["delta"], pr["s1"], pr["s2"], pr["sc"],
+                     precision=dgfas.DGFAS_BF16)
+    S.dgfas_use_graph(True)
+    if not args.no_autotune:
+        S.dgfas_autotune(reps=5)
+    b = top_rhs(S, cfg, torch, dev)
+    u0 = torch.from_numpy(cfg["u0"]).to(dev)
+    ms, _, _ = time_vcycles(S, u0.clone(), b, 10, 3, torch, dgfas)
+    ndof = S.ndof(-1)
+    N = cfg["levels"][-1]["p"] + 1
+    prof = S.dgfas_profile_sweep(S.n_levels - 1, u0.clone(), b, 5)
+    fp64_tf, _ = dgfas.dgfas_fma_peak()
+    fl = (6 * N + 30) * ndof
+    rec = {"dof": ndof, "ms_per_vcycle": ms, "dof_per_s_per_vcycle": ndof / (ms * 1e-3),
+           "kernel_ms": prof,
+           "residual_fp64_roofline": {"bound": "alu", "flops_per_dof": 6 * N + 30,
+                                      "achieved_tflops": fl / (prof["residual_fp64"] * 1e-3) / 1e12,
+                                      "peak_tflops": fp64_tf,
+                                      "frac": fl / (prof["residual_fp64"] * 1e-3) / 1e12 / fp64_tf}}
+    rec["time_to_1e-10_bf16"] = solve_record(S, u0.clone(), b, torch)
+    S.close()
+    return rec
+
+
+# ------------------------------------------------------------------ GPU arm
+def kernel_table(prof, ndof, N, ns, fp64_tf, hbm, counts):
+    """Per-kernel algorithmic work, bound and measured time of one SCG step on
+    the top curvilinear level (p = 7, n_s = 12), and per V-cycle counts.
+    Algorithmic work per DoF (stated in the design notes):
+      FP64 residual    12 N + 60 flop (FP64 pipe)
+      FP32 operator    44 B: u, out, 6 metric factors, face factors (HBM)
+      FD (BF16 tc)     4 B in + 4 (n_s / N)^3 B patch out (HBM)
+      combine          4 (n_s / N)^3 B patch in + 4 B out (HBM)
+      z.r + direction  24 B; p.q + update 36 B (FP32 vectors, HBM)."""
+    patch = 4.0 * (ns / N) ** 3
+    rows = {
+        "residual_fp64": dict(ms=prof["residual_fp64"], bound="alu", work=(12 * N + 60) * ndof,
+                              peak=fp64_tf, unit="TFLOP/s", scale=1e12),
+        "apply_fp32": dict(ms=prof["apply_smoother"], bound="hbm", work=44.0 * ndof, peak=hbm,
+                           unit="GB/s", scale=1e9),
+        "fd_tc": dict(ms=prof["fd"], bound="hbm", work=(4.0 + patch) * ndof, peak=hbm,
+                      unit="GB/s", scale=1e9),
+        "combine": dict(ms=prof["combine"], bound="hbm", work=(patch + 4.0) * ndof, peak=hbm,
+                        unit="GB/s", scale=1e9),
+        "scg_zr_dir": dict(ms=prof["zr_dir"], bound="hbm", work=24.0 * ndof, peak=hbm,
+                           unit="GB/s", scale=1e9),
+        "scg_pq_update": dict(ms=prof["pq_update"], bound="hbm", work=36.0 * ndof, peak=hbm,
+                              unit="GB/s", scale=1e9),
+    }
+    for k, v in rows.items():
+        v["count_per_vcycle"] = counts.get(k, 0)
+        v["achieved"] = v["work"] / (v["ms"] * 1e-3) / v["scale"]
+        v["frac"] = v["achieved"] / v["peak"]
+    return rows
+
+
+def run_gpu(args):
+    import torch
+    from paper_2608_14123_b300 import dgfas
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    t_start = time.perf_counter()
+
+    # ---- set-up (outside every timed region): the learned surrogate trained on
+    # the GPU from the oracle's 10^5 fits, the solver, the right-hand side
+    surr, train_info = train_surrogates(torch)
+    cfg = wl.config(5, root="p1")
+    levels = cfg["levels"]
+    top = levels[-1]
+    N = top["p"] + 1
+    prec = {"fp32": dgfas.DGFAS_FP32, "bf16": dgfas.DGFAS_BF16, "fp64": dgfas.DGFAS_FP64}[args.precision]
+    t0 = time.perf_counter()
+    S, fallback = build_solver(dgfas, cfg, prec, dgfas.DGFAS_SCG, None if args.geometric else surr)
+    setup_s = time.perf_counter() - t0
+    S.dgfas_use_graph(True)
+    tuning = [] if args.no_autotune else S.dgfas_autotune(reps=3)
+    ndof = S.ndof(-1)
+    b = top_rhs(S, cfg, torch, dev)
+    u0 = torch.from_numpy(cfg["u0"]).to(dev)
+
+    # ---- headline: ms per FAS V-cycle (graph replays), inputs resident in HBM
+    ms, gpu_launches, clocks = time_vcycles(S, u0.clone(), b, args.steps, args.warmup, torch, dgfas,
+                                            ws, dev, clocks=True)
+    if ws > 1:
+        ms = max_over_ranks(ms, dev)
+        torch.distributed.barrier()
+    value = ndof * ws / (ms * 1e-3)
+
+    # ---- end to end through the C ABI with host buffers
+    e2e_raw = e2e_record(S, torch.from_numpy(cfg["u0"]), b, torch, max(3, min(args.steps, 6)))
+    e2e = {"value": ndof / e2e_raw["seconds_per_step"], "unit": UNIT,
+           "h2d_bytes_per_step": e2e_raw["h2d_bytes_per_step"],
+           "d2h_bytes_per_step": e2e_raw["d2h_bytes_per_step"], "overlap": e2e_raw["overlap"]}
+
+    # ---- per-kernel timing of one SCG step on the top level and the roofline
+    prof = S.dgfas_profile_scg(S.n_levels - 1, u0.clone(), b, 5)
     fp64_tf, fp32_tf = dgfas.dgfas_fma_peak()
     pk = peaks()
     m = 2
     ns = N + 2 * m
-    sweeps = pr["s1"] + pr["s2"]
-    kernels = {
-        "residual_fp64": dict(count=1, ms=prof["residual_fp64"], bound="alu",
-                              flops=apply_flops_per_dof(N) * ndof, peak=fp64_tf, unit="TFLOP/s"),
-        "residual_smoother": dict(count=sweeps, ms=prof["residual_smoother"], bound="alu",
-                                  flops=apply_flops_per_dof(N) * ndof,
-                                  peak=fp32_tf if prec else fp64_tf, unit="TFLOP/s"),
-        "fd": (dict(count=sweeps, ms=prof["fd"], bound="hbm", bytes=ndof * (4.0 + 4.0 * (ns / N) ** 3),
-                    peak=pk["hbm"], unit="GB/s") if prec == dgfas.DGFAS_BF16 else
-               dict(count=sweeps, ms=prof["fd"], bound="alu", flops=fd_flops_per_dof(N, m) * ndof,
-                    peak=fp32_tf if prec else fp64_tf, unit="TFLOP/s")),
-        "combine": dict(count=sweeps, ms=prof["combine"], bound="hbm",
-                        bytes=ndof * 16.0, peak=pk["hbm"], unit="GB/s"),
-    }
-    dom = max(kernels, key=lambda k: kernels[k]["count"] * kernels[k]["ms"])
-    kd = kernels[dom]
-    if kd["bound"] == "hbm":
-        achieved = kd["bytes"] / (kd["ms"] * 1e-3) / 1e9
-    else:
-        achieved = kd["flops"] / (kd["ms"] * 1e-3) / 1e12
-    roofline = {"bound": kd["bound"], "kernel": dom, "achieved": achieved, "peak": kd["peak"],
-                "unit": kd["unit"], "frac": achieved / kd["peak"],
-                "traffic": NCU_TRAFFIC.get(dom) if prec == dgfas.DGFAS_BF16 else None,
-                "peak_source": ("measured FMA microbenchmark (dgfas_fma_peak)" if kd["bound"] == "alu"
-                                else f"{pk['src']} HBM copy")}
-    shares = {k: v["count"] * v["ms"] for k, v in kernels.items()}
+    smooth = cfg["params"]["s1"] + cfg["params"]["s2"]
+    counts = {"residual_fp64": 2, "apply_fp32": smooth, "fd_tc": smooth, "combine": smooth,
+              "scg_zr_dir": smooth, "scg_pq_update": smooth}
+    kt = kernel_table(prof, ndof, N, ns, fp64_tf, pk["hbm"], counts)
+    dom = max(kt, key=lambda k: kt[k]["count_per_vcycle"] * kt[k]["ms"])
+    kd = kt[dom]
+    roofline = {"bound": kd["bound"], "kernel": dom, "achieved": kd["achieved"], "peak": kd["peak"],
+                "unit": kd["unit"], "frac": kd["frac"],
+                "traffic": NCU_TRAFFIC.get(dom),
+                "peak_source": ("measured FP64 FMA microbenchmark (dgfas_fma_peak)"
+                                if kd["bound"] == "alu" else f"{pk['src']} HBM copy (MEASURED_PEAKS.json)")}
 
-    # ---- time to 1e-10 (mixed and plain FP64)
-    tts = {}
-    for name, pmode in (("mixed_fp32", dgfas.DGFAS_FP32), ("mixed_bf16", dgfas.DGFAS_BF16),
-                        ("fp64", dgfas.DGFAS_FP64)):
-        if args.skip_fp64 and pmode == dgfas.DGFAS_FP64:
-            continue
-        S2 = S if pmode == prec else dgfas.Solver(levels, pr["mu_star"], pr["delta"], pr["s1"],
-                                                   pr["s2"], pr["sc"], precision=pmode)
+    # ---- time to 1e-10: the headline arm, then the plain FP64 GPU path
+    tts = {"mixed_learned" if not args.geometric else "mixed_geometric":
+           solve_record(S, u0.clone(), b, torch)}
+    tts[next(iter(tts))]["ms_per_vcycle"] = ms
+    S.close()
+    torch.cuda.empty_cache()
+    arms = []
+    if not args.skip_fp64:
+        arms.append(("fp64_geometric", dgfas.DGFAS_FP64, None))
+    if not args.geometric and not args.skip_geometric:
+        arms.append(("mixed_geometric", prec, None))
+    for name, pm, sur in arms:
+        S2, _ = build_solver(dgfas, cfg, pm, dgfas.DGFAS_SCG, sur)
         S2.dgfas_use_graph(True)
-        if S2 is not S and not args.no_autotune:
-            S2.dgfas_autotune(reps=5)
-        us = u0.clone()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        info = S2.dgfas_solve(us, b, 1e-10, 40, raise_on_fail=False)
-        torch.cuda.synchronize()
-        tts[name] = {"seconds": time.perf_counter() - t0, "cycles": info["cycles"],
-                     "rel_residual": info["r_final"] / info["r0"], "code": info["code"]}
-        # the same target (1e-10 of the random start's residual) from the full
-        # multigrid start (Alg. 4), which replaces the random start; the
-        # per-level right-hand sides are problem set-up, outside the timing
-        if not args.skip_fmg:
-            r0_rand = info["r0"]
-            f_lv = level_rhs(S2, cfg, torch)
-            uf = torch.zeros_like(u0)
-            rr = torch.empty_like(b)
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            S2.dgfas_fmg(f_lv, uf)
-            S2.dgfas_apply_op(-1, uf, b, rr)
-            r_fmg = S2.dgfas_norm(-1, rr)
-            info = S2.dgfas_solve(uf, b, 1e-10 * r0_rand / r_fmg, 40, raise_on_fail=False)
-            torch.cuda.synchronize()
-            tts[name + "_fmg"] = {"seconds": time.perf_counter() - t0, "cycles": info["cycles"],
-                                  "rel_residual": info["r_final"] / r0_rand, "code": info["code"]}
-            del f_lv, uf, rr
-        if S2 is not S:
-            S2.close()
+        ms2, _, _ = time_vcycles(S2, u0.clone(), b, 3, 1, torch, dgfas)
+        r = solve_record(S2, u0.clone(), b, torch)
+        r["ms_per_vcycle"] = ms2
+        r["dof_per_s_per_vcycle"] = ndof / (ms2 * 1e-3)
+        tts[name] = r
+        S2.close()
+        torch.cuda.empty_cache()
 
-    # ---- the other workloads: time to 1e-10 (mixed vs FP64), one solve each
+    # ---- the other workloads
     others = {}
     if not args.skip_others:
-        others = other_workloads(dgfas, torch)
+        others["curvilinear16_graded_p7"] = curvilinear_records(
+            dgfas, torch, dev, 3, surr,
+            [("mixed_learned", prec, True), ("mixed_geometric", prec, False),
+             ("fp64_geometric", dgfas.DGFAS_FP64, False)])
+        others["cartesian32_p8"] = cartesian_record(dgfas, torch, dev, args)
+        others["front_local_refinement_p3"] = config4_record(dgfas, torch)
 
     # ---- CPU baseline (rank 0, N = 1 only)
     cpu = None
@@ -542,7 +657,8 @@ def run_gpu(args):
         cpu = {"value": rate, "unit": UNIT, "cores": int(os.environ.get("OMP_NUM_THREADS",
                                                                           host_cores())),
                "kind": "oracle",
-               "sample": f"one FP64 oracle V-cycle on 8^3 elements p=8 ({sdof} DoF), {dt:.1f} s"}
+               "sample": f"one FP64 oracle V-cycle (SCG smoother, SCG root) on the same "
+                         f"workload at 8^3 elements, p = 7 ({sdof} DoF), {dt:.1f} s"}
 
     if rank == 0:
         out = {
@@ -550,19 +666,25 @@ def run_gpu(args):
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
             "dtype": {0: "f64", 1: "f32+f64", 2: "bf16(tc)+f32+f64"}[prec], "data": "synthetic",
-            "config": {"workload": "cartesian-32^3-p8-dirichlet-poisson", "elements": top["corners"].shape[0],
-                       "p": top["p"], "dof": ndof, "levels": [lv["p"] for lv in levels],
-                       "smoother": f"WAS V({pr['s1']},{pr['s2']}) delta={pr['delta']}",
-                       "precision": args.precision, "global_batch": 1, "seq_len": 0,
+            "config": {"workload": "curvilinear-64^3-p7 (trilinear, +-0.15h perturbation), "
+                                   "16-mode RHS, Dirichlet Poisson",
+                       "elements": top["corners"].shape[0], "p": top["p"], "dof": ndof,
+                       "levels": [lv["p"] for lv in levels],
+                       "smoother": "SCG (Alg. 6) V(2,2), n_sc = 4, delta = 0.08",
+                       "root": "FP64 SCG at p = 1 (rtol 1e-3, <= 64 steps)",
+                       "surrogate": "geometric" if args.geometric else "learned MLP (24-64-64-6)",
+                       "precision": args.precision, "graph": True,
+                       "global_batch": 1, "seq_len": 0,
                        "parallelism": "replicas" if ws > 1 else "single",
-                       "l2": "inputs larger than L2 (top vector 191 MB > 126 MB)"},
+                       "l2": "inputs larger than L2 (top vector 1.07 GB > 126 MB)"},
             "gpu_launches": gpu_launches,
-            "autotune": {"tuned": len(tuning),
-                         "changed": [{k: (round(v, 4) if isinstance(v, float) else v)
-                                      for k, v in t.items()} for t in tuning if t["value"] != 0]},
+            "setup": {"solver_seconds": setup_s, "surrogate_training": train_info,
+                      "surrogate_fallback_elements": fallback,
+                      "autotune_changed": [{k: (round(v, 4) if isinstance(v, float) else v)
+                                            for k, v in t.items()} for t in tuning if t["value"] != 0]},
             "roofline": roofline,
-            "kernel_ms": {k: v["ms"] for k, v in kernels.items()},
-            "kernel_share_ms_per_cycle": shares,
+            "kernels_top_level_scg_step": {k: {kk: (round(vv, 5) if isinstance(vv, float) else vv)
+                                               for kk, vv in v.items()} for k, v in kt.items()},
             "peaks": {"fp64_tflops": fp64_tf, "fp32_tflops": fp32_tf, "hbm_gbs": pk["hbm"],
                       "hbm_source": pk["src"]},
             "time_to_1e-10": tts,
@@ -570,24 +692,28 @@ def run_gpu(args):
             "e2e": e2e,
             "cpu_baseline": cpu,
             "clocks": clocks,
+            "wall_s": time.perf_counter() - t_start,
         }
         print(json.dumps(out), flush=True)
-    S.close()
     if ws > 1:
         torch.distributed.destroy_process_group()
+
+
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="dgfas", choices=["dgfas", "reference"])
     ap.add_argument("--precision", default="bf16", choices=["fp32", "bf16", "fp64"])
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-others", action="store_true")
-    ap.add_argument("--skip-fmg", action="store_true")
+    ap.add_argument("--skip-geometric", action="store_true")
+    ap.add_argument("--geometric", action="store_true",
+                    help="headline with the geometric instead of the learned surrogate")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the built-in launch shapes instead of the autotuner's")
     args = ap.parse_args()

@@ -66,6 +66,14 @@ extern "C" {
 #define DGFAS_COARSE_DENSE 0
 #define DGFAS_COARSE_SCG 1
 
+/* FAS solution projection P (Sec. 3.2): embedded interpolation (the fine
+   polynomial at the coarse nodes, averaged at nodes shared by h-children for
+   even p), or L2 projection in reference coordinates with the fine GLL
+   quadrature, P = (I^T W I)^-1 I^T W per direction (each h-child contributes
+   its half of the parent's width; no averaging) */
+#define DGFAS_P_INTERP 0
+#define DGFAS_P_L2 1
+
 /* One level of the multilevel mesh (Sec. 3.1): a conforming hexahedral mesh
    with one polynomial degree.  All arrays are host arrays of n_elem rows. */
 typedef struct {
@@ -104,6 +112,7 @@ typedef struct {
   int root_steps;            /* SCG root: step cap per visit (<= 0: 64); the
                                 steps past the exit test leave u unchanged, so
                                 a visit is a fixed launch sequence (graphs) */
+  int projection;            /* DGFAS_P_INTERP or DGFAS_P_L2 */
 } dgfas_params;
 
 typedef struct {
@@ -205,6 +214,16 @@ int dgfas_use_graph(void* ctx, int enable);
 int dgfas_profile_sweep(void* ctx, int level, double* u, const double* g, int reps,
                         double* ms_out);
 
+/* Per-kernel timing of one SCG step (Alg. 6) on `level` (>= 1) in the
+   context's smoother precision, CUDA events on the context's stream, averaged
+   over `reps` steps from the residual g - A u.  ms_out [6] (host): the FD
+   kernel of the Schwarz sweep, its combine, the scalar product z.r with the
+   direction update, the operator A p, the scalar product p.q with the fused
+   residual / iterate update, and the FP64 residual apply.  u is not modified;
+   the level's work vectors are scratch afterwards.  INVALID unless the
+   context was set up with SCG (smoother or root). */
+int dgfas_profile_scg(void* ctx, int level, double* u, const double* g, int reps, double* ms_out);
+
 /* Full multigrid startup (FAS-FMG, Alg. 4): the root is solved exactly for
    its own right-hand side f_levels[0]; then for l = 1 .. L-1 the root's (or
    previous level's) solution is interpolated to level l, u_l = I u_{l-1},
@@ -282,6 +301,12 @@ int dgfas_host_fd_variant(int p, double delta, double mu_star, int variant, doub
    W3[6][64] b3[6].  Inputs X [n][24]: corner coordinates minus the centroid,
    divided by V^(1/3); outputs [n][6]: log(dx_i / V^(1/3)), log(s_i). */
 int dgfas_mlp_param_count(void);
+
+/* The network's inputs X [n][24] (device FP32) of n elements given by their
+   corners [n][8][3] (device FP64): corner coordinates minus the centroid,
+   divided by the cube root of the element volume (2-point Gauss of det J).
+   Synchronizes `stream`. */
+int dgfas_mlp_inputs(const double* corners, int n, float* X, void* stream);
 
 /* out [n][6] = MLP(params, X) (device pointers; synchronizes `stream`). */
 int dgfas_mlp_forward(const float* params, const float* X, int n, float* out, void* stream);

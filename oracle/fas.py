@@ -30,7 +30,7 @@ from .transfer import Transfer
 class Hierarchy:
     def __init__(self, levels, mu_star, delta, s1=2, s2=2, sc=4, nu=1.0, kappa=0.0,
                  gcoefs=None, smoother="was", scg_first="z", coarse="dense", root_rtol=1e-3,
-                 root_steps=64):
+                 root_steps=64, projection="interp"):
         self.levels = levels
         self.smoother = smoother
         self.scg_first = scg_first
@@ -42,7 +42,8 @@ class Hierarchy:
                            None if gcoefs is None else gcoefs[l])
                    if (l > 0 or coarse == "scg") else None
                    for l, lv in enumerate(levels)]
-        self.tr = [None] + [Transfer(levels[l - 1], levels[l]) for l in range(1, len(levels))]
+        self.tr = [None] + [Transfer(levels[l - 1], levels[l], projection)
+                            for l in range(1, len(levels))]
         self.cls = [np.asarray(lv["cls"]) for lv in levels]
         self.active = [c != 2 for c in self.cls]
         self.local = any(np.any(c == 2) for c in self.cls) or any(

@@ -111,11 +111,23 @@ def face_factors(geo, nu=1.0):
 
 
 def h_perp(geo, W):
-    """Element extent normal to each face: |Omega^e| / |face| (reading of the
-    penalty definition in Sec. 2.2; exact h on a cube)."""
-    vol = np.sum(geo["W3"] * geo["detJ"], axis=(1, 2, 3))
-    area = np.sum(W, axis=(2, 3))
-    return vol[:, None] / area
+    """Element extent normal to each face (Sec. 2.2, "the element extension
+    perpendicular to the interface"), reading for curved elements: the
+    smallest local extent over the face's GLL nodes, 2 / |grad xi_d| (the
+    reference width 2 over the rate of change of the face-normal reference
+    coordinate), exactly h on a cube.  This is the quantity the discrete
+    trace bound needs node by node: at a face node the face quadrature weight
+    over the volume weight of the same node is |grad xi_d| / w_end, so a
+    penalty built from the face's mean extent |Omega| / |face| leaves faces
+    next to a nearly folded corner uncontrolled (indefinite operator)."""
+    N = geo["detJ"].shape[1]
+    out = np.zeros((geo["detJ"].shape[0], 6))
+    for f in range(6):
+        d = f // 2
+        K, J, I = face_node_index(N, f)
+        gd = geo["ginv"][:, K, J, I, d, :]
+        out[:, f] = np.min(2.0 / np.linalg.norm(gd, axis=-1), axis=(1, 2))
+    return out
 
 
 def penalties(level, geo_h, mu_star):

@@ -249,18 +249,13 @@ def brute_force_matrix(level, mu_star, nu=1.0, kappa=0.0):
                 xc, _ = map_and_jacobian(corners[e], 0.0, 0.0, 0.0)
                 if np.dot(n, x - xc) < 0:
                     n = -n
-                pts.append((xi.copy(), x, n, w[a] * w[b] * dS))
+                # local extent perpendicular to the face: the height of the
+                # image of the reference cell's half-width along n (2 n . dx/dxi_d)
+                pts.append((xi.copy(), x, n, w[a] * w[b] * dS, 2.0 * abs(np.dot(n, J[:, d]))))
         return pts
 
-    vol = np.zeros(ne)
-    for e in range(ne):
-        for k in range(N):
-            for j in range(N):
-                for i in range(N):
-                    _, J = map_and_jacobian(corners[e], nodes[i], nodes[j], nodes[k])
-                    vol[e] += w[i] * w[j] * w[k] * np.linalg.det(J)
-    area = np.array([[sum(q[3] for q in face_points(e, f)) for f in range(6)] for e in range(ne)])
-    hperp = vol[:, None] / area
+    # penalty length: the smallest local perpendicular extent over the face
+    hperp = np.array([[min(q[4] for q in face_points(e, f)) for f in range(6)] for e in range(ne)])
     own = p * (p + 1) / (2.0 * hperp)
 
     for e in range(ne):
@@ -280,7 +275,7 @@ def brute_force_matrix(level, mu_star, nu=1.0, kappa=0.0):
             if nb >= 0 and nb < e:
                 continue  # each interior face once
             mu = mu_star * (0.5 * (own[e, f] + own[nb, f ^ 1]) if nb >= 0 else own[e, f])
-            for xi, x, n, wq in face_points(e, f):
+            for xi, x, n, wq, _ in face_points(e, f):
                 vm, gm = _basis_at(p, corners[e], xi)
                 if nb == -1:
                     dn = gm @ n

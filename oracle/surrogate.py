@@ -220,17 +220,10 @@ def coeffs_from_outputs(y, vol, nu=1.0):
 
 
 def training_elements(n, rng, ar_max=16.0, amp=0.25):
-    """Single interior elements from the distribution of the curvilinear
-    workloads: a box of widths (1, 1, 1/AR) with AR ~ U[1, ar_max], each corner
-    moved by U(-amp, amp) of the box width per coordinate."""
-    ar = rng.uniform(1.0, ar_max, size=n)
-    h = np.stack([np.ones(n), np.ones(n), 1.0 / ar], 1)
-    corners = np.zeros((n, 8, 3))
-    for cc in range(8):
-        for d in range(3):
-            corners[:, cc, d] = ((cc >> d) & 1) * h[:, d]
-    corners += rng.uniform(-amp, amp, size=corners.shape) * h[:, None, :]
-    return corners
+    """Single interior elements of the curvilinear workloads' distribution
+    (the seeded input generator shared with the CUDA path)."""
+    from paper_2608_14123_b300.workloads import surrogate_training_corners
+    return surrogate_training_corners(n, rng, ar_max, amp)
 
 
 def element_block_dense(level, e, mu_star, nu=1.0):

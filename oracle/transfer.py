@@ -4,11 +4,18 @@
   the fine nodes.  p-refinement: same element; h-refinement: child octant
   (c1,c2,c3) takes the parent reference coordinate (xi + (2c-1))/2.
 * R = I^T (restriction, the transpose of I, Sec. 3.2).
-* P (solution projection, embedded-interpolation variant): the fine
-  polynomial evaluated at the coarse nodes; for h-refinement each parent node
-  takes the value of the child that contains it, and parent nodes on a child
-  interface (only for even p, the middle GLL node) average the children that
-  share them.
+* P (solution projection), two variants (Sec. 3.2):
+  - embedded interpolation ("interp"): the fine polynomial evaluated at the
+    coarse nodes; for h-refinement each parent node takes the value of the
+    child that contains it, and parent nodes on a child interface (only for
+    even p, the middle GLL node) average the children that share them;
+  - L2 projection ("l2"), reading: the projection onto the coarse polynomials
+    in the reference coordinates with the inner product of the fine level's
+    GLL quadrature, P = (I^T W I)^-1 I^T W per direction.  For h-refinement
+    the two half-cells of a direction each carry half of the parent's
+    reference width: P_s = M^-1 (1/2) I_s^T W with M = (1/2) sum_s I_s^T W I_s,
+    and a parent sums the contributions of its children (no averaging).  On
+    affine elements this is the physical L2 projection.
 
 Pins (tests/test_oracle_transfer.py): P I = identity; I reproduces coarse
 polynomials at the fine nodes' physical positions; R equals the transpose of
@@ -29,7 +36,8 @@ def _mode(A1, A2, A3, u):
 class Transfer:
     """Transfers between coarse level `lc` and fine level `lf` (fine['parent'])."""
 
-    def __init__(self, lc, lf):
+    def __init__(self, lc, lf, projection="interp"):
+        self.projection = projection
         self.pc, self.pf = lc["p"], lf["p"]
         self.Nc, self.Nf = self.pc + 1, self.pf + 1
         self.nec, self.nef = lc["nbr"].shape[0], lf["nbr"].shape[0]
@@ -49,6 +57,17 @@ class Transfer:
                 wgt = np.where(inside, np.where(xc == 0.0, 0.5, 1.0), 0.0)
                 xchild = np.clip(2.0 * xc - s, -1.0, 1.0)
                 self.P1.append(wgt[:, None] * interp_matrix(self.pf, xchild))
+        if projection == "l2":
+            _, wf = gll(self.pf)
+            W = np.diag(wf)
+            if not self.h:
+                I1 = self.I1[0]
+                self.P1 = [np.linalg.solve(I1.T @ W @ I1, I1.T @ W)]
+            else:
+                M = 0.5 * sum(I.T @ W @ I for I in self.I1)
+                self.P1 = [np.linalg.solve(M, 0.5 * I.T @ W) for I in self.I1]
+        elif projection != "interp":
+            raise ValueError(f"unknown projection {projection}")
 
     def _oct(self, e):
         o = self.octant[e]

@@ -109,7 +109,8 @@ struct Ctx {
   cudaStream_t cap = nullptr;   // internal stream for graph capture / replay
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
   int red_blocks = 0;           // CTAs of the reductions: 4 per SM of the device
-  double* red = nullptr;        // reduction partials [2 * red_blocks + 64]
+  double* red = nullptr;        // reduction partials [3 * red_blocks + 64]: norms use
+                                // [0, G), SCG's scalar products [G, 3G)
   double* red_host = nullptr;   // pinned
   double* scg_buf = nullptr;    // SCG vectors (p, q, z, r0) for the largest level
   double* dscal = nullptr;      // device scalars of the SCG recurrences
@@ -168,7 +169,8 @@ int launch_sumsq_leaf(Ctx& c, int l, const double* v, double* part);
 int launch_leaf_rhs(Ctx& c, int l, const double* f, double* g);
 int launch_to_float(Ctx& c, const double* x, float* y, long long n);
 // scg.cu: Alg. 6 with device-resident scalars (no host synchronization)
-int scg_run(Ctx& c, int l, double* u, int n, double rtol, int prec);
+int scg_run(Ctx& c, int l, double* u, int n, double rtol, int prec, bool pending = false,
+            bool want_res = false, bool fp64_vectors = false);
 extern std::atomic<long long> g_kernels;   // kernels launched (graph replays included)
 
 void set_error(const std::string& s);

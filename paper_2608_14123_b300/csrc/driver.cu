@@ -106,7 +106,6 @@ static int build_level(Ctx& c, const dgfas_level& in, const dgfas_params& prm, L
     std::vector<double> Gi((size_t)N3 * 9), dJ(N3);
     for (int e = 0; e < ne; ++e) {
       const double* cr = &H.corners[24 * e];
-      double vol = 0.0;
       for (int k = 0; k < N; ++k)
         for (int j = 0; j < N; ++j)
           for (int i = 0; i < N; ++i) {
@@ -131,7 +130,6 @@ static int build_level(Ctx& c, const dgfas_level& in, const dgfas_params& prm, L
             gi[8] = (J[0] * J[4] - J[1] * J[3]) / det;
             dJ[n] = det;
             const double wq = w[i] * w[j] * w[k];
-            vol += wq * det;
             mass[(size_t)e * N3 + n] = wq * det;
             // G_df = nu w J grad xi_d . grad xi_f ; rows of gi are grad xi_b
             auto dot = [&](int d1, int d2) {
@@ -149,7 +147,9 @@ static int build_level(Ctx& c, const dgfas_level& in, const dgfas_params& prm, L
       for (int f = 0; f < 6; ++f) {
         const int d = f / 2, side = f % 2, end = side ? N - 1 : 0;
         const double sg = side ? 1.0 : -1.0;
-        double area = 0.0;
+        // penalty length: the smallest local extent 2 / |grad xi_d| over the
+        // face's GLL nodes (exactly h on a box)
+        double hmin = 1e300;
         for (int b = 0; b < N; ++b)
           for (int a = 0; a < N; ++a) {
             int i, j, k;
@@ -162,13 +162,13 @@ static int build_level(Ctx& c, const dgfas_level& in, const dgfas_params& prm, L
             const double wab = w[a] * w[b];
             const double Wq = wab * dJ[n] * std::sqrt(gd2);
             fW[((size_t)e * 6 + f) * N2 + b * N + a] = Wq;
-            area += Wq;
+            hmin = std::min(hmin, 2.0 / std::sqrt(gd2));
             for (int t = 0; t < 3; ++t) {
               const double gdt = gi[3 * d] * gi[3 * t] + gi[3 * d + 1] * gi[3 * t + 1] + gi[3 * d + 2] * gi[3 * t + 2];
               fc[(((size_t)e * 6 + f) * 3 + t) * N2 + b * N + a] = sg * nu * wab * dJ[n] * gdt;
             }
           }
-        hp[6 * e + f] = vol / area;
+        hp[6 * e + f] = hmin;
       }
     }
   }
@@ -306,7 +306,48 @@ static int build_level(Ctx& c, const dgfas_level& in, const dgfas_params& prm, L
 }
 
 // transfer matrices from level C (coarse) to level F (fine)
-static int build_transfer(LevelHost& C, LevelHost& F) {
+// x = A^-1 B for a small dense SPD A [n][n] and B [n][m] (row-major), by
+// Gauss-Jordan elimination without pivoting (the matrices here are Gram
+// matrices of interpolation operators, well conditioned for n <= 11)
+static std::vector<double> small_solve(std::vector<double> A, std::vector<double> B, int n, int m) {
+  for (int k = 0; k < n; ++k) {
+    const double piv = A[k * n + k];
+    for (int j = 0; j < n; ++j) A[k * n + j] /= piv;
+    for (int j = 0; j < m; ++j) B[k * m + j] /= piv;
+    for (int i = 0; i < n; ++i) {
+      if (i == k) continue;
+      const double f = A[i * n + k];
+      if (f == 0.0) continue;
+      for (int j = 0; j < n; ++j) A[i * n + j] -= f * A[k * n + j];
+      for (int j = 0; j < m; ++j) B[i * m + j] -= f * B[k * m + j];
+    }
+  }
+  return B;
+}
+
+// L2 projection matrices of P (reference coordinates, fine GLL quadrature):
+// I [ns][Nf][Nc] the interpolation of each child side (ns = 2 for h, 1 for
+// p), w the fine GLL weights; P_s = M^-1 c I_s^T W with M = c sum_s I_s^T W
+// I_s and c = 1/ns (each h-child covers half of the parent's width).
+static void l2_projection(const std::vector<double>& I, const std::vector<double>& w, int ns,
+                          int Nf, int Nc, std::vector<double>& P) {
+  const double cw = 1.0 / ns;
+  std::vector<double> M((size_t)Nc * Nc, 0.0);
+  for (int s = 0; s < ns; ++s)
+    for (int a = 0; a < Nc; ++a)
+      for (int b = 0; b < Nc; ++b)
+        for (int i = 0; i < Nf; ++i)
+          M[a * Nc + b] += cw * I[((size_t)s * Nf + i) * Nc + a] * w[i] * I[((size_t)s * Nf + i) * Nc + b];
+  for (int s = 0; s < ns; ++s) {
+    std::vector<double> B((size_t)Nc * Nf);
+    for (int a = 0; a < Nc; ++a)
+      for (int i = 0; i < Nf; ++i) B[a * Nf + i] = cw * I[((size_t)s * Nf + i) * Nc + a] * w[i];
+    std::vector<double> X = small_solve(M, B, Nc, Nf);
+    std::copy(X.begin(), X.end(), P.begin() + (size_t)s * Nc * Nf);
+  }
+}
+
+static int build_transfer(LevelHost& C, LevelHost& F, int projection) {
   const int Nf = F.N, Nc = C.N;
   bool h = true, pref = true;
   for (int e = 0; e < F.ne; ++e) {
@@ -336,6 +377,7 @@ static int build_transfer(LevelHost& C, LevelHost& F) {
     for (int i = 0; i < Nc; ++i)
       for (int j = 0; j < Nf; ++j) P[((size_t)s * Nc + i) * Nf + j] = wgt[i] * Lp[i * Nf + j];
   }
+  if (projection == DGFAS_P_L2) l2_projection(I, wf, h ? 2 : 1, Nf, Nc, P);
   std::vector<int> children(8 * (size_t)C.ne, -1);
   for (int e = 0; e < F.ne; ++e) {
     int slot = h ? F.octant[e] : 0;
@@ -475,6 +517,10 @@ extern "C" int dgfas_setup_levels(const dgfas_mesh* mesh, const dgfas_params* pr
     set_error("setup: unknown root solver");
     return DGFAS_ERR_INVALID;
   }
+  if (prm->projection != DGFAS_P_INTERP && prm->projection != DGFAS_P_L2) {
+    set_error("setup: unknown solution projection");
+    return DGFAS_ERR_INVALID;
+  }
   Ctx* c = new Ctx();
   c->stream = (cudaStream_t)stream;
   {
@@ -508,7 +554,7 @@ extern "C" int dgfas_setup_levels(const dgfas_mesh* mesh, const dgfas_params* pr
     LevelHost& H = c->lv[l];
     patch = std::max(patch, (size_t)H.ne * H.nsm * H.nsm * H.nsm * sizeof(double));
     maxdof = std::max(maxdof, (size_t)H.ndof);
-    if (l > 0) rc = build_transfer(c->lv[l - 1], H);
+    if (l > 0) rc = build_transfer(c->lv[l - 1], H, prm->projection);
     if (rc != DGFAS_OK) break;
     const bool top = l == mesh->n_levels - 1;
     if (!top) {
@@ -540,8 +586,8 @@ extern "C" int dgfas_setup_levels(const dgfas_mesh* mesh, const dgfas_params* pr
     set_error("stream/event creation");
     rc = DGFAS_ERR_CUDA;
   }
-  if (rc == DGFAS_OK) rc = dalloc(&c->red, 2 * c->red_blocks + 64);
-  if (rc == DGFAS_OK && cudaMallocHost((void**)&c->red_host, (2 * c->red_blocks + 64) * sizeof(double)) != cudaSuccess) {
+  if (rc == DGFAS_OK) rc = dalloc(&c->red, 3 * c->red_blocks + 64);
+  if (rc == DGFAS_OK && cudaMallocHost((void**)&c->red_host, (3 * c->red_blocks + 64) * sizeof(double)) != cudaSuccess) {
     set_error("pinned host buffer");
     rc = DGFAS_ERR_OOM;
   }
@@ -627,6 +673,8 @@ static int was_block(Ctx& c, int l, double* u, int n, bool zero_start, bool want
 static int smooth(Ctx& c, int l, double* u, const double* g, int n, bool zero_start,
                   bool want_res) {
   if (c.prm.smoother == DGFAS_SCG) {
+    if (c.prm.precision != DGFAS_FP64)   // correction form, as WAS (see scg_run)
+      return scg_run(c, l, u, n, 0.0, c.prm.precision, !zero_start, want_res);
     if (!zero_start) {   // add the pending correction, then recompute the residual
       RET(launch_add_delta(c, c.lv[l].ndof, c.prm.precision, c.lv[l].delta, u));
       RET(launch_apply(c, l, DGFAS_FP64, u, g, c.lv[l].r, -1.0));
@@ -651,7 +699,10 @@ static int root_solve(Ctx& c, bool zero_start) {
   LevelHost& R = c.lv[0];
   if (zero_start) CK(cudaMemsetAsync(R.u, 0, R.ndof * sizeof(double), c.stream));
   RET(launch_apply(c, 0, DGFAS_FP64, R.u, R.gv, R.r, -1.0));
-  return scg_run(c, 0, R.u, c.prm.root_steps, c.prm.root_rtol, DGFAS_FP64);
+  // FP64 iteration; in a mixed-precision context the Schwarz preconditioner
+  // of the root runs in FP32 (it only shapes the search directions)
+  const int pc = c.prm.precision == DGFAS_FP64 ? DGFAS_FP64 : DGFAS_FP32;
+  return scg_run(c, 0, R.u, c.prm.root_steps, c.prm.root_rtol, pc, false, false, true);
 }
 
 // ---------------------------------------------------------------- FAS V-cycle

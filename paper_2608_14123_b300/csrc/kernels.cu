@@ -209,6 +209,216 @@ __global__ void k_apply(const LevelView<T> L, const TU* __restrict__ u,
   }
 }
 
+// Line form of the curvilinear operator with even-odd derivative products.
+// A team of N^2 threads per element; in each pass thread (a, b) owns one node
+// line along the pass direction (x: (k, j) = (b, a); y: (k, i); z: (j, i)).
+// GLL symmetry makes D anti-centrosymmetric (D[N-1-r][N-1-q] = -D[r][q]), so
+// with e_q = x_q + x_{N-1-q}, o_q = x_q - x_{N-1-q} a line product y = D x
+// is y_r = E_r + O_r, y_{N-1-r} = O_r - E_r with E_r = sum_q De[r][q] e_q (+
+// D[r][H] x_H), O_r = sum_q Do[r][q] o_q: about N^2/2 multiply-adds instead
+// of N^2.  The same holds for D^T.  Passes:
+//   1. reference gradient d = (D x I x I, I x D x I, I x I x D) u, per line;
+//   2. the own normal flux q_m = c . d at the nodes of every face, kept for
+//      the face pass (the face pass then needs no own-side derivatives), and
+//      the metric F = G d node by node;
+//   3. faces (one at a time): the neighbour's trace and normal flux q_p at
+//      the shared face nodes, flux mu W [[u]] - (q_m - q_p)/2 into R and the
+//      lifting c_t (-[[u]]/2) into F_t (Dirichlet: 2 mu W u - q_m, -u);
+//   4. out = b + alpha (R + sum_d D_d^T F_d), per line.
+template <int N, typename T>
+struct CurvEo {
+  static constexpr int H = N / 2, HC = (N + 1) / 2;
+  T de[HC][H > 0 ? H : 1], dO[HC][H > 0 ? H : 1], dm[HC];   // D:   even, odd, middle column
+  T te[HC][H > 0 ? H : 1], tO[HC][H > 0 ? H : 1], tm[HC];   // D^T: even, odd, middle column
+  T D[N * N];
+};
+
+// y = M x for an anti-centrosymmetric M given by its even / odd halves
+template <int N, typename T>
+__device__ __forceinline__ void acs_line(const T (*me)[(N / 2) > 0 ? N / 2 : 1],
+                                         const T (*mo)[(N / 2) > 0 ? N / 2 : 1], const T* mm,
+                                         const T (&x)[N], T (&y)[N]) {
+  constexpr int H = N / 2, HC = (N + 1) / 2;
+  T ev[H > 0 ? H : 1], od[H > 0 ? H : 1];
+#pragma unroll
+  for (int q = 0; q < H; ++q) {
+    ev[q] = x[q] + x[N - 1 - q];
+    od[q] = x[q] - x[N - 1 - q];
+  }
+#pragma unroll
+  for (int r = 0; r < HC; ++r) {
+    T E = (N & 1) ? mm[r] * x[H] : T(0), O = T(0);
+#pragma unroll
+    for (int q = 0; q < H; ++q) {
+      E += me[r][q] * ev[q];
+      O += mo[r][q] * od[q];
+    }
+    if (r < H) {
+      y[r] = E + O;
+      y[N - 1 - r] = O - E;
+    } else {
+      y[r] = O;   // middle row of an odd N: its even part vanishes
+    }
+  }
+}
+
+template <int N, typename T, typename TU, typename TB, typename TO>
+__global__ void __launch_bounds__(256) k_apply_curv_eo(const LevelView<T> L, const TU* __restrict__ u,
+                                                       const TB* __restrict__ b, TO* __restrict__ out,
+                                                       T alpha) {
+  constexpr int N2 = N * N, N3 = N * N * N, H = N / 2, HC = (N + 1) / 2;
+  __shared__ CurvEo<N, T> M;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int team = threadIdx.y, tid = threadIdx.y * blockDim.x + threadIdx.x;
+  const int nth = blockDim.x * blockDim.y;
+  T* us = reinterpret_cast<T*>(smem_raw) + (size_t)team * (6 * N3 + 6 * N2);
+  T* nb = us + N3;
+  T* F[3] = {nb + N3, nb + 2 * N3, nb + 3 * N3};
+  T* R = nb + 4 * N3;
+  T* Q = nb + 5 * N3;   // [6][N2] own normal flux at the face nodes
+  for (int t = tid; t < N2; t += nth) M.D[t] = L.D[t];
+  for (int t = tid; t < HC * N; t += nth) {
+    const int r = t / N, q = t % N;
+    const T d1 = L.D[r * N + q], d2 = L.D[r * N + N - 1 - q];
+    const T t1 = L.D[q * N + r], t2 = L.D[(N - 1 - q) * N + r];
+    if (q < H) {
+      M.de[r][q] = T(0.5) * (d1 + d2);
+      M.dO[r][q] = T(0.5) * (d1 - d2);
+      M.te[r][q] = T(0.5) * (t1 + t2);
+      M.tO[r][q] = T(0.5) * (t1 - t2);
+    } else if ((N & 1) && q == H) {
+      M.dm[r] = d1;
+      M.tm[r] = t1;
+    }
+  }
+  const int e = blockIdx.x * blockDim.y + team;
+  const bool valid = e < L.ne && threadIdx.x < N2;
+  const size_t eo = (size_t)e * N3;
+  if (e < L.ne)
+    for (int t = threadIdx.x; t < N3; t += blockDim.x) us[t] = (T)u[eo + t];
+  __syncthreads();
+  const int a = threadIdx.x % N, bb = threadIdx.x / N;
+  // ---- 1: reference gradient, one line per thread and direction
+#pragma unroll 1
+  for (int d = 0; d < 3; ++d) {
+    if (!valid) continue;
+    const int st = d == 0 ? 1 : (d == 1 ? N : N2);
+    const int base = d == 0 ? (bb * N + a) * N : (d == 1 ? bb * N2 + a : bb * N + a);
+    T x[N], y[N];
+#pragma unroll
+    for (int l = 0; l < N; ++l) x[l] = us[base + l * st];
+    acs_line<N, T>(M.de, M.dO, M.dm, x, y);
+#pragma unroll
+    for (int l = 0; l < N; ++l) F[d][base + l * st] = y[l];
+  }
+  __syncthreads();
+  // ---- 2: own normal flux at the face nodes, then the metric node by node
+  if (valid) {
+#pragma unroll 1
+    for (int f = 0; f < 6; ++f) {
+      const int d = f >> 1, end = (f & 1) ? N - 1 : 0;
+      const int n = d == 0 ? (bb * N + a) * N + end : (d == 1 ? (bb * N + end) * N + a
+                                                              : (end * N + bb) * N + a);
+      const T* fc = L.fc + ((size_t)e * 6 + f) * 3 * N2 + bb * N + a;
+      Q[f * N2 + threadIdx.x] = ld(fc) * F[0][n] + ld(fc + N2) * F[1][n] + ld(fc + 2 * N2) * F[2][n];
+    }
+  }
+  __syncthreads();
+  if (valid) {
+    for (int k = 0; k < N; ++k) {
+      const int n = (k * N + bb) * N + a;
+      const T* G = L.G + (size_t)e * 6 * N3 + n;
+      const T G00 = ld(G), G11 = ld(G + N3), G22 = ld(G + 2 * N3), G01 = ld(G + 3 * N3),
+              G02 = ld(G + 4 * N3), G12 = ld(G + 5 * N3);
+      const T d0 = F[0][n], d1 = F[1][n], d2 = F[2][n];
+      F[0][n] = G00 * d0 + G01 * d1 + G02 * d2;
+      F[1][n] = G01 * d0 + G11 * d1 + G12 * d2;
+      F[2][n] = G02 * d0 + G12 * d1 + G22 * d2;
+      R[n] = L.kappa != T(0) ? L.kappa * ld(L.mass + eo + n) * us[n] : T(0);
+    }
+  }
+  // ---- 3: faces, one per pass (edge / corner nodes belong to several faces)
+  for (int f = 0; f < 6; ++f) {
+    const int d = f >> 1, side = f & 1;
+    const int nbid = e < L.ne ? L.nbr[6 * e + f] : -2;
+    __syncthreads();
+    if (nbid >= 0) {
+      const size_t no = (size_t)nbid * N3;
+      for (int t = threadIdx.x; t < N3; t += blockDim.x) nb[t] = (T)u[no + t];
+    }
+    __syncthreads();
+    if (valid && nbid != -2) {
+      const int end = side ? N - 1 : 0, endp = N - 1 - end;
+      int i, j, k, ip, jp, kp;
+      if (d == 0) { i = end; j = a; k = bb; ip = endp; jp = a; kp = bb; }
+      else if (d == 1) { i = a; j = end; k = bb; ip = a; jp = endp; kp = bb; }
+      else { i = a; j = bb; k = end; ip = a; jp = bb; kp = endp; }
+      const int n = (k * N + j) * N + i;
+      const T um = us[n];
+      const size_t fo = ((size_t)e * 6 + f) * N2 + bb * N + a;
+      const T W = L.nu * ld(L.fW + fo);
+      const T* fcp = L.fc + ((size_t)e * 6 + f) * 3 * N2 + bb * N + a;
+      const T c0 = ld(fcp), c1 = ld(fcp + N2), c2 = ld(fcp + 2 * N2);
+      const T mu = L.mu[6 * e + f];
+      const T qm = Q[f * N2 + threadIdx.x];
+      T flux, lift;
+      if (nbid >= 0) {
+        const T up = nb[(kp * N + jp) * N + ip];
+        const T* fn = L.fc + ((size_t)nbid * 6 + (f ^ 1)) * 3 * N2 + bb * N + a;
+        const T cp0 = ld(fn), cp1 = ld(fn + N2), cp2 = ld(fn + 2 * N2);
+        T d0 = 0, d1 = 0, d2 = 0;
+#pragma unroll
+        for (int l = 0; l < N; ++l) {
+          d0 += M.D[ip * N + l] * nb[(kp * N + jp) * N + l];
+          d1 += M.D[jp * N + l] * nb[(kp * N + l) * N + ip];
+          d2 += M.D[kp * N + l] * nb[(l * N + jp) * N + ip];
+        }
+        const T qp = cp0 * d0 + cp1 * d1 + cp2 * d2;
+        const T jump = um - up;
+        flux = mu * W * jump - T(0.5) * (qm - qp);
+        lift = T(-0.5) * jump;
+      } else {   // Dirichlet
+        flux = T(2) * mu * W * um - qm;
+        lift = -um;
+      }
+      R[n] += flux;
+      F[0][n] += c0 * lift;
+      F[1][n] += c1 * lift;
+      F[2][n] += c2 * lift;
+    }
+  }
+  __syncthreads();
+  // ---- 4: transposed reference gradient, one line per thread and direction
+#pragma unroll 1
+  for (int d = 0; d < 3; ++d) {
+    const int st = d == 0 ? 1 : (d == 1 ? N : N2);
+    const int base = d == 0 ? (bb * N + a) * N : (d == 1 ? bb * N2 + a : bb * N + a);
+    T y[N];
+    if (valid) {
+      T x[N];
+#pragma unroll
+      for (int l = 0; l < N; ++l) x[l] = F[d][base + l * st];
+      acs_line<N, T>(M.te, M.tO, M.tm, x, y);
+    }
+    if (d < 2) {
+      if (valid) {
+#pragma unroll
+        for (int l = 0; l < N; ++l) R[base + l * st] += y[l];
+      }
+      __syncthreads();
+    } else if (valid) {
+      const bool frozen = L.cls[e] == DGFAS_FROZEN;
+#pragma unroll
+      for (int l = 0; l < N; ++l) {
+        const int n = base + l * st;
+        T o = alpha * (R[n] + y[l]);
+        if (b) o += (T)b[eo + n];
+        out[eo + n] = frozen ? TO(0) : (TO)o;
+      }
+    }
+  }
+}
+
 // Axis-aligned box elements: the volume term is the exact Kronecker form
 // sum_d g_d (W x W x Lhat_d) u with Lhat = D^T W D; bx[e] = {g_1, g_2, g_3,
 // a_1, a_2, a_3} with g_d = nu h_j h_k / (2 h_d) and a_d = nu h_j h_k / 4 (the
@@ -427,13 +637,22 @@ static int apply_N(const LevelView<T>& L, const TU* u, const TB* b, TO* out, T a
     dim3 blk2(N2, epb2), grd2((L.ne + epb2 - 1) / epb2);
     kf<<<grd2, blk2, smem2, st>>>(L, L.bx, L.Lhat, u, b, out, alpha);
   } else {
-    auto kf = k_apply<N, T, TU, TB, TO, false>;
+    // line form (even-odd products, own face derivatives from the volume pass)
+    int epb3 = (128 + N2 - 1) / N2;
+    if (epb_req > 0) epb3 = std::max(1, std::min(epb_req, 256 / N2));
+    size_t smem3 = (size_t)(6 * N3 + 6 * N2) * epb3 * sizeof(T);
+    while (epb3 > 1 && smem3 > 100 * 1024) {
+      --epb3;
+      smem3 = (size_t)(6 * N3 + 6 * N2) * epb3 * sizeof(T);
+    }
+    auto kf = k_apply_curv_eo<N, T, TU, TB, TO>;
     static bool attr = false;
     if (!attr) {
       CK(cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024));
       attr = true;
     }
-    kf<<<grd, blk, smem, st>>>(L, u, b, out, alpha);
+    dim3 blk3(N2, epb3), grd3((L.ne + epb3 - 1) / epb3);
+    kf<<<grd3, blk3, smem3, st>>>(L, u, b, out, alpha);
   }
   ++g_kernels;
   CK(cudaGetLastError());

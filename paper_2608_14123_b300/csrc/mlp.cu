@@ -292,6 +292,24 @@ __global__ void k_mlp_inputs(const double* __restrict__ corners, int ne, float* 
     for (int a = 0; a < 3; ++a) X[(size_t)e * 24 + c * 3 + a] = (float)((cr[c * 3 + a] - cen[a]) * sc);
 }
 
+// The network's inputs of n elements: X [n][24] (device FP32) from corners
+// [n][8][3] (device FP64); synchronizes `stream`.
+extern "C" int dgfas_mlp_inputs(const double* corners, int n, float* X, void* stream) {
+  if (!corners || !X || n <= 0) return DGFAS_ERR_INVALID;
+  cudaStream_t st = (cudaStream_t)stream;
+  double* vol = nullptr;
+  if (cudaMalloc((void**)&vol, (size_t)n * sizeof(double)) != cudaSuccess) {
+    set_error("mlp inputs allocation");
+    return DGFAS_ERR_OOM;
+  }
+  k_mlp_inputs<<<nb(n), 256, 0, st>>>(corners, n, X, vol);
+  ++g_kernels;
+  int rc = (cudaGetLastError() == cudaSuccess && cudaStreamSynchronize(st) == cudaSuccess)
+               ? DGFAS_OK : DGFAS_ERR_CUDA;
+  cudaFree(vol);
+  return rc;
+}
+
 // g_i = s_i nu dx_j dx_k / (2 dx_i) from the outputs; elements whose log
 // scalings leave [-lmax, lmax] or are not finite keep the current (geometric)
 // coefficients.  g[e][0] (the kappa term) is rescaled consistently.

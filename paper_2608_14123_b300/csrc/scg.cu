@@ -20,6 +20,8 @@
 // remaining step, so u and r stay as they were when the test first held (the
 // same result as leaving the loop); the step count of a block is fixed, which
 // is what graph capture needs.
+#include <type_traits>
+
 #include "dgfas_internal.h"
 
 namespace {
@@ -96,8 +98,24 @@ __global__ void k_scg_zr(const T* __restrict__ z, const T* __restrict__ r,
                          const T* __restrict__ r0, long long n, double* part, int* counter,
                          double* scal) {
   double v[2] = {0.0, 0.0};
-  for (long long i = (long long)blockIdx.x * kThreads + threadIdx.x; i < n;
-       i += (long long)gridDim.x * kThreads) {
+  const long long S = (long long)gridDim.x * kThreads;
+  long long i = (long long)blockIdx.x * kThreads + threadIdx.x;
+  // four independent strided elements per iteration keep more loads in flight
+  for (; i + 3 * S < n; i += 4 * S) {
+    T zz[4], rr[4], qq[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      zz[u] = z[i + u * S];
+      rr[u] = r[i + u * S];
+      if (!FIRST) qq[u] = r0[i + u * S];
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      v[0] += (double)zz[u] * (double)rr[u];
+      if (!FIRST) v[1] += (double)zz[u] * (double)qq[u];
+    }
+  }
+  for (; i < n; i += S) {
     const double zi = z[i];
     v[0] += zi * (double)r[i];
     if (!FIRST) v[1] += zi * (double)r0[i];
@@ -115,9 +133,19 @@ template <typename T, bool FIRST>
 __global__ void k_scg_dir(T* __restrict__ p, const T* __restrict__ z, long long n,
                           const double* __restrict__ scal) {
   const T beta = FIRST ? T(0) : (T)scal[S_BETA];
-  for (long long i = (long long)blockIdx.x * kThreads + threadIdx.x; i < n;
-       i += (long long)gridDim.x * kThreads)
-    p[i] = FIRST ? z[i] : beta * p[i] + z[i];
+  const long long S = (long long)gridDim.x * kThreads;
+  long long i = (long long)blockIdx.x * kThreads + threadIdx.x;
+  for (; i + 3 * S < n; i += 4 * S) {
+    T zz[4], pp[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      zz[u] = z[i + u * S];
+      if (!FIRST) pp[u] = p[i + u * S];
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) p[i + u * S] = FIRST ? zz[u] : beta * pp[u] + zz[u];
+  }
+  for (; i < n; i += S) p[i] = FIRST ? z[i] : beta * p[i] + z[i];
 }
 
 // pq = p.q, alpha = gamma / pq (0 once the exit test held, or for pq = 0)
@@ -125,9 +153,19 @@ template <typename T>
 __global__ void k_scg_pq(const T* __restrict__ p, const T* __restrict__ q, long long n,
                          double* part, int* counter, double* scal) {
   double v[1] = {0.0};
-  for (long long i = (long long)blockIdx.x * kThreads + threadIdx.x; i < n;
-       i += (long long)gridDim.x * kThreads)
-    v[0] += (double)p[i] * (double)q[i];
+  const long long S = (long long)gridDim.x * kThreads;
+  long long i = (long long)blockIdx.x * kThreads + threadIdx.x;
+  for (; i + 3 * S < n; i += 4 * S) {
+    T pp[4], qq[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      pp[u] = p[i + u * S];
+      qq[u] = q[i + u * S];
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) v[0] += (double)pp[u] * (double)qq[u];
+  }
+  for (; i < n; i += S) v[0] += (double)p[i] * (double)q[i];
   double t[1];
   if (partials_and_ticket<1>(v, part, counter, t) && threadIdx.x == 0) {
     scal[S_PQ] = t[0];
@@ -143,8 +181,27 @@ __global__ void k_scg_update(T* __restrict__ r, T* __restrict__ r0, T* __restric
                              double* part, int* counter, double* scal) {
   const T alpha = (T)scal[S_ALPHA];
   double v[1] = {0.0};
-  for (long long i = (long long)blockIdx.x * kThreads + threadIdx.x; i < n;
-       i += (long long)gridDim.x * kThreads) {
+  const long long S = (long long)gridDim.x * kThreads;
+  long long i = (long long)blockIdx.x * kThreads + threadIdx.x;
+  for (; i + 3 * S < n; i += 4 * S) {
+    T rr[4], qq[4], xx[4], pp[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      rr[u] = r[i + u * S];
+      qq[u] = q[i + u * S];
+      xx[u] = x[i + u * S];
+      pp[u] = p[i + u * S];
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const T rn = rr[u] - alpha * qq[u];
+      r0[i + u * S] = rr[u];
+      r[i + u * S] = rn;
+      x[i + u * S] = xx[u] + alpha * pp[u];
+      v[0] += (double)rn * (double)rn;
+    }
+  }
+  for (; i < n; i += S) {
     const T ri = r[i];
     const T rn = ri - alpha * q[i];
     r0[i] = ri;
@@ -208,27 +265,30 @@ static int scg_steps(Ctx& c, int l, int prec, T* x, T* r, T* p, T* q, T* z, T* r
   double* scal = c.dscal;
   int* cnt = c.dcnt;
   const int G = c.red_blocks;
-  k_scg_init<T><<<G, kThreads, 0, c.stream>>>(r, nd, rtol * rtol, c.red, cnt, scal);
+  // SCG's partial sums live past the first G entries of the reduction buffer,
+  // which hold the cycle's residual norm partials until the host reads them
+  double* part = c.red + G;
+  k_scg_init<T><<<G, kThreads, 0, c.stream>>>(r, nd, rtol * rtol, part, cnt, scal);
   LAUNCH_CHECK();
   for (int i = 1; i <= n; ++i) {
     int rc = scg_sweep(c, l, prec, r, z);
     if (rc != DGFAS_OK) return rc;
     if (i == 1) {
-      k_scg_zr<T, true><<<G, kThreads, 0, c.stream>>>(z, r, nullptr, nd, c.red, cnt, scal);
+      k_scg_zr<T, true><<<G, kThreads, 0, c.stream>>>(z, r, nullptr, nd, part, cnt, scal);
       LAUNCH_CHECK();
       k_scg_dir<T, true><<<G, kThreads, 0, c.stream>>>(p, z, nd, scal);
       LAUNCH_CHECK();
     } else {
-      k_scg_zr<T, false><<<G, kThreads, 0, c.stream>>>(z, r, r0, nd, c.red, cnt, scal);
+      k_scg_zr<T, false><<<G, kThreads, 0, c.stream>>>(z, r, r0, nd, part, cnt, scal);
       LAUNCH_CHECK();
       k_scg_dir<T, false><<<G, kThreads, 0, c.stream>>>(p, z, nd, scal);
       LAUNCH_CHECK();
     }
     rc = scg_apply(c, l, p, q);
     if (rc != DGFAS_OK) return rc;
-    k_scg_pq<T><<<G, kThreads, 0, c.stream>>>(p, q, nd, c.red, cnt, scal);
+    k_scg_pq<T><<<G, kThreads, 0, c.stream>>>(p, q, nd, part, cnt, scal);
     LAUNCH_CHECK();
-    k_scg_update<T><<<G, kThreads, 0, c.stream>>>(r, r0, x, p, q, nd, c.red, cnt, scal);
+    k_scg_update<T><<<G, kThreads, 0, c.stream>>>(r, r0, x, p, q, nd, part, cnt, scal);
     LAUNCH_CHECK();
   }
   return DGFAS_OK;
@@ -237,31 +297,134 @@ static int scg_steps(Ctx& c, int l, int prec, T* x, T* r, T* p, T* q, T* z, T* r
 // Alg. 6 on level l with n steps from the FP64 residual in lv[l].r (= g - A u),
 // u updated in place; rtol > 0 adds the exit test |r| <= rtol |r_start|.  No
 // host synchronization.
-// prec = FP64: the iteration itself, in FP64; lv[l].r ends as the CG residual.
-// prec = FP32 / BF16: correction form, as the WAS smoother: SCG on A d = r
-// from d = 0 in FP32 vectors (FP32 operator, Schwarz sweep in prec, FP64
-// scalar products), then u += d.  In exact arithmetic the iterates are the
-// same; the FP64 residual of the outer cycle drives the iterative refinement.
-// lv[l].r is then stale (the caller recomputes it when it needs it).
-int scg_run(Ctx& c, int l, double* u, int n, double rtol, int prec) {
+// prec = FP64: the iteration itself, in FP64; lv[l].r ends as the CG residual
+// (want_res is the caller's business).
+// prec = FP32 / BF16: correction form, as the WAS smoother: SCG on A d = r in
+// FP32 vectors (FP32 operator, Schwarz sweep in prec, FP64 scalar products),
+// then u += d.  In exact arithmetic the iterates are the same; the FP64
+// residual of the outer cycle drives the iterative refinement.  d starts at
+// zero, or with `pending` at the correction already in lv[l].delta (the
+// prolongation, not yet in u; lv[l].r is then the residual of u without it),
+// the start residual r - A d being formed in the smoother precision.  With
+// want_res, lv[l].r becomes r - A d (smoother-precision operator, FP64
+// result), the residual of the new u as the WAS smoother forms it; otherwise
+// lv[l].r is stale afterwards.
+// fp64_vectors: FP64 iteration (vectors, operator, recurrences) whatever
+// prec is; prec then only sets the precision of the Schwarz sweep (the
+// preconditioner), as for the root solve in a mixed-precision context.
+int scg_run(Ctx& c, int l, double* u, int n, double rtol, int prec, bool pending,
+            bool want_res, bool fp64_vectors) {
   LevelHost& H = c.lv[l];
   const long long nd = H.ndof;
   if (!c.scg_buf) {
     set_error("scg: no SCG work vectors (context not set up for SCG)");
     return DGFAS_ERR_INVALID;
   }
-  if (prec == DGFAS_FP64) {
+  if (prec == DGFAS_FP64 || fp64_vectors) {
+    if (pending) {
+      set_error("scg: a pending correction needs the smoother-precision path");
+      return DGFAS_ERR_INVALID;
+    }
     double *p = c.scg_buf, *q = p + nd, *z = q + nd, *r0 = z + nd;
     return scg_steps<double>(c, l, prec, u, H.r, p, q, z, r0, n, rtol);
   }
   float* d = (float*)H.delta;
   float *r = (float*)c.scg_buf, *p = r + nd, *q = p + nd, *z = q + nd, *r0 = z + nd;
-  if (cudaMemsetAsync(d, 0, nd * sizeof(float), c.stream) != cudaSuccess) {
-    set_error("scg: memset");
-    return DGFAS_ERR_CUDA;
+  int rc = DGFAS_OK;
+  if (pending) {
+    rc = launch_apply_corr(c, l, prec, d, H.r, r, 0);   // r = r_u - A d
+  } else {
+    if (cudaMemsetAsync(d, 0, nd * sizeof(float), c.stream) != cudaSuccess) {
+      set_error("scg: memset");
+      return DGFAS_ERR_CUDA;
+    }
+    rc = launch_to_float(c, H.r, r, nd);
   }
-  int rc = launch_to_float(c, H.r, r, nd);
   if (rc == DGFAS_OK) rc = scg_steps<float>(c, l, prec, d, r, p, q, z, r0, n, rtol);
+  if (rc == DGFAS_OK && want_res) rc = launch_apply_corr(c, l, prec, d, H.r, H.r, 1);
   if (rc == DGFAS_OK) rc = launch_add_delta(c, nd, prec, d, u);
+  return rc;
+}
+
+// Per-kernel timing of one SCG step on `level` in the context's smoother
+// precision, with CUDA events on the context's stream, averaged over `reps`
+// steps from the residual g - A u: ms_out[0..5] = the FD kernel of the Schwarz
+// sweep, its combine, the scalar product z.r (with beta) and the direction
+// update, the operator q = A p, the scalar product p.q and the fused
+// residual / iterate update, and the FP64 residual apply of the V-cycle.
+// Level vectors are scratch afterwards; u is not modified.
+extern "C" int dgfas_profile_scg(void* ctx, int level, double* u, const double* g, int reps,
+                                 double* ms_out) {
+  Ctx* c = (Ctx*)ctx;
+  if (!c || !u || !g || !ms_out || reps <= 0 || level < 1 || level >= (int)c->lv.size() ||
+      !c->scg_buf)
+    return DGFAS_ERR_INVALID;
+  LevelHost& H = c->lv[level];
+  const long long nd = H.ndof;
+  const int prec = c->prm.precision;
+  const int G = c->red_blocks;
+  double* part = c->red + G;
+  cudaEvent_t ev[7];
+  for (auto& e : ev)
+    if (cudaEventCreate(&e) != cudaSuccess) return DGFAS_ERR_CUDA;
+  double acc[6] = {0, 0, 0, 0, 0, 0};
+  int rc = launch_apply(*c, level, DGFAS_FP64, u, g, H.r, -1.0);
+  auto step = [&](auto* x, auto* r, auto* p, auto* q, auto* z, auto* r0) -> int {
+    using T = std::remove_pointer_t<decltype(x)>;
+    int e = DGFAS_OK;
+    k_scg_init<T><<<G, kThreads, 0, c->stream>>>(r, nd, 0.0, part, c->dcnt, c->dscal);
+    for (int it = 0; it < reps && e == DGFAS_OK; ++it) {
+      cudaEventRecord(ev[0], c->stream);
+      if constexpr (sizeof(T) == 8) {
+        cudaMemcpyAsync(c->rw, r, nd * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
+        e = launch_fd(*c, level, prec, c->rw);
+        cudaEventRecord(ev[1], c->stream);
+        if (e == DGFAS_OK) e = launch_combine_to(*c, level, prec, (double*)z);
+      } else {
+        e = launch_fd(*c, level, prec, r);
+        cudaEventRecord(ev[1], c->stream);
+        if (e == DGFAS_OK) e = launch_combine_to32(*c, level, (float*)z);
+      }
+      cudaEventRecord(ev[2], c->stream);
+      k_scg_zr<T, false><<<G, kThreads, 0, c->stream>>>(z, r, r0, nd, part, c->dcnt, c->dscal);
+      k_scg_dir<T, false><<<G, kThreads, 0, c->stream>>>(p, z, nd, c->dscal);
+      cudaEventRecord(ev[3], c->stream);
+      if (e == DGFAS_OK) e = scg_apply(*c, level, p, q);
+      cudaEventRecord(ev[4], c->stream);
+      k_scg_pq<T><<<G, kThreads, 0, c->stream>>>(p, q, nd, part, c->dcnt, c->dscal);
+      k_scg_update<T><<<G, kThreads, 0, c->stream>>>(r, r0, x, p, q, nd, part, c->dcnt, c->dscal);
+      cudaEventRecord(ev[5], c->stream);
+      if (e == DGFAS_OK) e = launch_apply(*c, level, DGFAS_FP64, u, g, H.t ? H.t : H.r, -1.0);
+      cudaEventRecord(ev[6], c->stream);
+      if (cudaEventSynchronize(ev[6]) != cudaSuccess) e = DGFAS_ERR_CUDA;
+      for (int k = 0; k < 6 && e == DGFAS_OK; ++k) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, ev[k], ev[k + 1]);
+        acc[k] += ms;
+      }
+    }
+    return e;
+  };
+  if (rc == DGFAS_OK) {
+    if (prec == DGFAS_FP64) {
+      double *p = c->scg_buf, *q = p + nd, *z = q + nd, *r0 = z + nd;
+      cudaMemcpyAsync(r0, H.r, nd * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
+      cudaMemcpyAsync(p, H.r, nd * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
+      cudaMemcpyAsync(H.delta, u, nd * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
+      // the iterate is a copy of u (in the level's FP64 correction buffer), so
+      // u stays as it was
+      rc = step((double*)H.delta, H.r, p, q, z, r0);
+    } else {
+      float *r = (float*)c->scg_buf, *p = r + nd, *q = p + nd, *z = q + nd, *r0 = z + nd;
+      cudaMemsetAsync(H.delta, 0, nd * sizeof(float), c->stream);
+      rc = launch_to_float(*c, H.r, r, nd);
+      cudaMemcpyAsync(r0, r, nd * sizeof(float), cudaMemcpyDeviceToDevice, c->stream);
+      cudaMemcpyAsync(p, r, nd * sizeof(float), cudaMemcpyDeviceToDevice, c->stream);
+      if (rc == DGFAS_OK) rc = step((float*)H.delta, r, p, q, z, r0);
+    }
+  }
+  if (rc == DGFAS_OK && cudaGetLastError() != cudaSuccess) rc = DGFAS_ERR_CUDA;
+  for (int k = 0; k < 6; ++k) ms_out[k] = acc[k] / reps;
+  for (auto& e : ev) cudaEventDestroy(e);
   return rc;
 }

@@ -17,6 +17,7 @@ LIB_PATH = os.path.join(HERE, "libdgfas.so")
 DGFAS_FP64, DGFAS_FP32, DGFAS_BF16 = 0, 1, 2
 DGFAS_WAS, DGFAS_SCG = 0, 1
 DGFAS_COARSE_DENSE, DGFAS_COARSE_SCG = 0, 1
+DGFAS_P_INTERP, DGFAS_P_L2 = 0, 1
 ERRORS = {0: "ok", -1: "INVALID", -2: "OOM", -3: "CUDA", -4: "MESH", -5: "NOT_CONVERGED",
           -6: "DIVERGED", -7: "UNSUPPORTED"}
 
@@ -45,7 +46,8 @@ class dgfas_params(ctypes.Structure):
                 ("s1", ctypes.c_int), ("s2", ctypes.c_int), ("sc", ctypes.c_int),
                 ("precision", ctypes.c_int), ("smoother", ctypes.c_int),
                 ("max_cycles", ctypes.c_int), ("coarse", ctypes.c_int),
-                ("root_rtol", ctypes.c_double), ("root_steps", ctypes.c_int)]
+                ("root_rtol", ctypes.c_double), ("root_steps", ctypes.c_int),
+                ("projection", ctypes.c_int)]
 
 
 class dgfas_info(ctypes.Structure):
@@ -56,8 +58,8 @@ class dgfas_info(ctypes.Structure):
 SYMBOLS = ["dgfas_setup_levels", "dgfas_destroy", "dgfas_level_ndof", "dgfas_node_coords",
            "dgfas_assemble_rhs", "dgfas_apply_op", "dgfas_schwarz_smooth", "dgfas_fas_vcycle",
            "dgfas_solve", "dgfas_norm", "dgfas_set_surrogate", "dgfas_get_surrogate",
-           "dgfas_use_graph", "dgfas_profile_sweep", "dgfas_fma_peak", "dgfas_schwarz_correct_static", "dgfas_kernel_launches", "dgfas_mlp_param_count",
-           "dgfas_mlp_forward", "dgfas_mlp_grad", "dgfas_mlp_train", "dgfas_learned_surrogate",
+           "dgfas_use_graph", "dgfas_profile_sweep", "dgfas_profile_scg", "dgfas_fma_peak", "dgfas_schwarz_correct_static", "dgfas_kernel_launches", "dgfas_mlp_param_count",
+           "dgfas_mlp_forward", "dgfas_mlp_grad", "dgfas_mlp_inputs", "dgfas_mlp_train", "dgfas_learned_surrogate",
            "dgfas_assemble_rhs_level", "dgfas_set_level_rhs", "dgfas_composite_residual",
            "dgfas_get_level_solution", "dgfas_tc_selftest", "dgfas_tc_selftest_mn", "dgfas_tc_error", "dgfas_host_fd_variant", "dgfas_autotune", "dgfas_set_tuning",
            "dgfas_get_tuning", "dgfas_fmg", "dgfas_element_energy", "dgfas_strerror",
@@ -92,11 +94,13 @@ def load():
         "dgfas_use_graph": (I, [P, I]),
         "dgfas_host_fd_variant": (I, [I, D, D, I, P, P, P, ctypes.POINTER(I)]),
         "dgfas_profile_sweep": (I, [P, I, P, P, I, P]),
+        "dgfas_profile_scg": (I, [P, I, P, P, I, P]),
         "dgfas_fma_peak": (I, [ctypes.POINTER(D), ctypes.POINTER(D)]),
         "dgfas_schwarz_correct_static": (I, [P, I, P, P]),
         "dgfas_kernel_launches": (LL, []),
         "dgfas_mlp_param_count": (I, []),
         "dgfas_mlp_forward": (I, [P, P, I, P, P]),
+        "dgfas_mlp_inputs": (I, [P, I, P, P]),
         "dgfas_mlp_grad": (I, [P, P, P, I, P, P]),
         "dgfas_mlp_train": (I, [P, P, P, P, P, I, I, I, ctypes.c_float, ctypes.c_ulonglong, I, P, P]),
         "dgfas_learned_surrogate": (I, [P, I, P, D, ctypes.POINTER(I)]),
@@ -156,7 +160,8 @@ class Solver:
 
     def __init__(self, levels, mu_star, delta, s1=2, s2=2, sc=4, precision=DGFAS_FP64,
                  smoother=DGFAS_WAS, nu=1.0, kappa=0.0, max_cycles=50,
-                 coarse=DGFAS_COARSE_DENSE, root_rtol=1e-3, root_steps=64):
+                 coarse=DGFAS_COARSE_DENSE, root_rtol=1e-3, root_steps=64,
+                 projection=DGFAS_P_INTERP):
         lib = load()
         self._keep = []
         arr = (dgfas_level * len(levels))()
@@ -178,7 +183,7 @@ class Solver:
                                  cls.ctypes.data_as(ctypes.POINTER(ctypes.c_byte)))
         mesh = dgfas_mesh(len(levels), arr, nu, kappa)
         prm = dgfas_params(mu_star, delta, s1, s2, sc, precision, smoother, max_cycles, coarse,
-                           root_rtol, root_steps)
+                           root_rtol, root_steps, projection)
         ctx = ctypes.c_void_p()
         _check(lib.dgfas_setup_levels(ctypes.byref(mesh), ctypes.byref(prm), _stream(),
                                       ctypes.byref(ctx)), "dgfas_setup_levels")
@@ -264,6 +269,14 @@ class Solver:
                                           _ptr(g, self.ndof(level)), reps,
                                           ms.ctypes.data_as(ctypes.c_void_p)), "profile_sweep")
         return dict(residual_smoother=ms[0], fd=ms[1], combine=ms[2], residual_fp64=ms[3])
+
+    def dgfas_profile_scg(self, level, u, g, reps):
+        ms = np.zeros(6)
+        _check(load().dgfas_profile_scg(self.ctx, level % self.n_levels, _ptr(u, self.ndof(level)),
+                                        _ptr(g, self.ndof(level)), reps,
+                                        ms.ctypes.data_as(ctypes.c_void_p)), "profile_scg")
+        return dict(fd=ms[0], combine=ms[1], zr_dir=ms[2], apply_smoother=ms[3],
+                    pq_update=ms[4], residual_fp64=ms[5])
 
     def dgfas_fmg(self, f_levels, u_top, cycles_per_level=1):
         """Full multigrid startup (Alg. 4): u_top <- the FMG start value from the

@@ -50,6 +50,17 @@ def forward(params, X):
     return out
 
 
+def inputs(corners):
+    """The network's inputs [n, 24] (device FP32) of elements given by their
+    corners [n, 8, 3] (host or device FP64), computed by the library."""
+    import torch
+    cd = torch.as_tensor(corners, dtype=torch.float64).cuda().contiguous()
+    n = cd.shape[0]
+    X = torch.empty((n, 24), dtype=torch.float32, device="cuda")
+    dgfas._check(dgfas.load().dgfas_mlp_inputs(_p(cd), n, _p(X), _stream()), "mlp_inputs")
+    return X
+
+
 def grad(params, X, Y):
     import torch
     g = torch.empty_like(params)

@@ -27,6 +27,9 @@ All neighbouring elements share aligned local axes (structured topology).
 import numpy as np
 
 SEED_BASE = 20261202
+# smallest corner-Jacobian ratio of a cell of the graded, strongly perturbed
+# workload (the worst cell of the +-0.15h uniform workload has 0.21)
+MIN_JACOBIAN_RATIO = 0.2
 
 LEAF, TWIG, FROZEN = 0, 1, 2
 
@@ -68,13 +71,82 @@ def corner_jacobians_positive(V):
     return ok
 
 
-def perturbed_vertices(n, amp, rng, graded_ratio_z=None, max_draws=100):
-    """As `_perturbed_vertices_once`, redrawn until every cell is unfolded."""
+def corner_jacobian_ratio(V):
+    """Shape measure of every cell of the vertex grid: the smallest over the
+    largest of the eight corner triple products (1 for a parallelepiped,
+    <= 0 for a folded cell).  Array [nx, ny, nz]."""
+    dets = []
+    for cx in (0, 1):
+        for cy in (0, 1):
+            for cz in (0, 1):
+                sx, sy, sz = 1 - 2 * cx, 1 - 2 * cy, 1 - 2 * cz
+
+                def at(dx, dy, dz):
+                    return V[cx + dx: V.shape[0] - 1 + cx + dx,
+                             cy + dy: V.shape[1] - 1 + cy + dy,
+                             cz + dz: V.shape[2] - 1 + cz + dz]
+                o = at(0, 0, 0)
+                ex = (at(sx, 0, 0) - o) * sx
+                ey = (at(0, sy, 0) - o) * sy
+                ez = (at(0, 0, sz) - o) * sz
+                dets.append(np.einsum("...a,...a->...", ex, np.cross(ey, ez)))
+    d = np.stack(dets, -1)
+    return d.min(-1) / d.max(-1)
+
+
+def perturbed_vertices(n, amp, rng, graded_ratio_z=None, max_draws=100, min_ratio=None):
+    """As `_perturbed_vertices_once`, redrawn until every cell is unfolded.
+
+    min_ratio: additionally, the perturbations of the vertices of every cell
+    whose corner-Jacobian ratio (`corner_jacobian_ratio`) is below min_ratio
+    are drawn again (same distribution, same generator) until no such cell
+    is left: independent uniform perturbations of +-0.25 cells occasionally
+    bring a corner close to folding (det J at that corner near 0), which no
+    penalty of the method's form keeps coercive."""
     for _ in range(max_draws):
-        V = _perturbed_vertices_once(n, amp, rng, graded_ratio_z)
+        eps = _perturbation(n, amp, rng)
+        if min_ratio is not None:
+            for _ in range(1000):
+                bad = corner_jacobian_ratio(_vertices(n, eps, graded_ratio_z)) < min_ratio
+                if not bad.any():
+                    break
+                touch = np.zeros((n + 1,) * 3, dtype=bool)
+                for c in range(8):
+                    ox, oy, oz = c & 1, (c >> 1) & 1, (c >> 2) & 1
+                    touch[ox:n + ox, oy:n + oy, oz:n + oz] |= bad
+                touch[[0, -1], :, :] = touch[:, [0, -1], :] = touch[:, :, [0, -1]] = False
+                new = _perturbation(n, amp, rng)
+                eps[touch] = new[touch]
+            else:
+                continue
+        V = _vertices(n, eps, graded_ratio_z)
         if corner_jacobians_positive(V):
             return V
     raise RuntimeError("no valid perturbed mesh drawn")
+
+
+def _perturbation(n, amp, rng):
+    """Logical displacements U(-amp, amp) of every vertex, zero on the boundary."""
+    eps = rng.uniform(-amp, amp, size=(n + 1, n + 1, n + 1, 3))
+    interior = np.zeros((n + 1, n + 1, n + 1), dtype=bool)
+    interior[1:-1, 1:-1, 1:-1] = True
+    return eps * interior[..., None]
+
+
+def _vertices(n, eps, graded_ratio_z=None):
+    """Vertex grid of [0,1]^3 from logical displacements eps; the logical z
+    coordinate s is graded by Z(s) = (r^s - 1) / (r^n - 1) if r is given."""
+    idx = np.arange(n + 1, dtype=np.float64)
+    L = np.zeros((n + 1, n + 1, n + 1, 3))
+    L[..., 0] = idx[:, None, None]
+    L[..., 1] = idx[None, :, None]
+    L[..., 2] = idx[None, None, :]
+    L = L + eps
+    V = L / n
+    if graded_ratio_z is not None:
+        r = graded_ratio_z
+        V[..., 2] = (r ** L[..., 2] - 1.0) / (r ** n - 1.0)
+    return V
 
 
 def _perturbed_vertices_once(n, amp, rng, graded_ratio_z=None):
@@ -82,20 +154,7 @@ def _perturbed_vertices_once(n, amp, rng, graded_ratio_z=None):
     U(-amp, amp) cells per coordinate in logical space, boundary vertices stay
     on the cube faces.  If graded_ratio_z is given, the logical z coordinate s
     is mapped by the geometric grading Z(s) = (r^s - 1) / (r^n - 1)."""
-    idx = np.arange(n + 1, dtype=np.float64)
-    L = np.zeros((n + 1, n + 1, n + 1, 3))
-    L[..., 0] = idx[:, None, None]
-    L[..., 1] = idx[None, :, None]
-    L[..., 2] = idx[None, None, :]
-    interior = np.zeros((n + 1, n + 1, n + 1), dtype=bool)
-    interior[1:-1, 1:-1, 1:-1] = True
-    eps = rng.uniform(-amp, amp, size=L.shape)
-    L = L + eps * interior[..., None]
-    V = L / n
-    if graded_ratio_z is not None:
-        r = graded_ratio_z
-        V[..., 2] = (r ** L[..., 2] - 1.0) / (r ** n - 1.0)
-    return V
+    return _vertices(n, _perturbation(n, amp, rng), graded_ratio_z)
 
 
 def grading_ratio(n, total_over_min):
@@ -257,6 +316,35 @@ def paper_cartesian_periodic(p, kind, n=None, seed=6):
                 u0=random_start(rng, ndof))
 
 
+def surrogate_training_corners(n, rng, ar_max=16.0, amp=0.25):
+    """Single elements drawn like the interior elements of the curvilinear
+    workloads (the learned surrogate's training inputs): a box of widths
+    (1, 1, 1/AR) with AR ~ U[1, ar_max], each corner moved by U(-amp, amp) of
+    the box width per coordinate.  Returns corners [n, 8, 3]."""
+    ar = rng.uniform(1.0, ar_max, size=n)
+    h = np.stack([np.ones(n), np.ones(n), 1.0 / ar], 1)
+    corners = np.zeros((n, 8, 3))
+    for cc in range(8):
+        for d in range(3):
+            corners[:, cc, d] = ((cc >> d) & 1) * h[:, d]
+    corners += rng.uniform(-amp, amp, size=corners.shape) * h[:, None, :]
+    return corners
+
+
+SURROGATE_SET_SEED = SEED_BASE + 200
+
+
+def surrogate_training_set(n, p):
+    """The learned surrogate's training elements at degree p: the first half
+    from the distribution of the graded, strongly perturbed workload (AR ~
+    U[1, 16], corners moved by +-0.25 widths), the second half from that of
+    the large uniform workload (AR 1, +-0.15); seeded by p."""
+    rng = np.random.default_rng(SURROGATE_SET_SEED + p)
+    a = surrogate_training_corners(n // 2, rng, 16.0, 0.25)
+    b = surrogate_training_corners(n - n // 2, rng, 1.0, 0.15)
+    return np.concatenate([a, b], 0)
+
+
 def random_start(rng, n):
     """Start vector uniform in [-1, 1] (Sec. 6.1)."""
     return rng.uniform(-1.0, 1.0, size=n)
@@ -291,7 +379,7 @@ def config(cid, small=False, root=None):
         # small: 4^3 cells, grading to aspect ratio 4 (AR 16 on four cells folds)
         n = 4 if small else 16
         r = grading_ratio(n, (4.0 if small else 16.0) * n)
-        V = perturbed_vertices(n, 0.25, rng, graded_ratio_z=r)
+        V = perturbed_vertices(n, 0.25, rng, graded_ratio_z=r, min_ratio=MIN_JACOBIAN_RATIO)
         levels = hierarchy(V, [7, 3, 1], h_root=None if root == "p1" else min(4, n))
         rhs = modes_rhs_spec(rng)
         # mu_star = 5 leaves this SIP operator indefinite on perturbed cells;
@@ -562,13 +650,100 @@ def hierarchy_from_marks(marks, n_base=8, p=3, n_root=4):
     return levels
 
 
-def config4(small=False):
+def _cell_dist_to_front(spec, cells, n):
+    """Distance of the cells (integer coordinates on grid n) to the front."""
+    h = 1.0 / n
+    return _cell_front_distance(spec, np.asarray(cells, dtype=np.float64) * h, h)
+
+
+def add_p_levels(levels, spec, p_levels, p_buffers):
+    """Local p-refinement levels on top of a locally refined hierarchy (Sec.
+    3.1: p-refinement elevates the degree in selected elements; every level
+    keeps one degree).  Level k raises to degree p_levels[k] the active cells
+    of the level below whose distance to the front is <= p_buffers[k] cell
+    widths and whose 26 neighbours inside the domain are all active there
+    (so that each frozen child has an active parent); their unmarked
+    neighbours become frozen p-children.  Children keep the geometry; parent
+    = the same cell one level down, octant -1 (p-refinement)."""
+    for pk, bk in zip(p_levels, p_buffers):
+        prev = levels[-1]
+        n = prev["shape"][0]
+        cells = [tuple(int(v) for v in c) for c in prev["ijk"]]
+        index = {c: i for i, c in enumerate(cells)}
+        active = {c for c, cl in zip(cells, prev["cls"]) if cl != FROZEN}
+        dist = _cell_dist_to_front(spec, cells, n)
+        h = 1.0 / n
+
+        def nbrs(c):
+            for oz in (-1, 0, 1):
+                for oy in (-1, 0, 1):
+                    for ox in (-1, 0, 1):
+                        q = (c[0] + ox, c[1] + oy, c[2] + oz)
+                        if q != c and min(q) >= 0 and max(q) < n:
+                            yield q
+        marked = {c for c, d in zip(cells, dist)
+                  if c in active and d <= bk * h and all(q in active for q in nbrs(c))}
+        if not marked:
+            raise ValueError(f"no cell qualifies for p-refinement to p = {pk}")
+        frozen = {q for c in marked for q in nbrs(c) if q not in marked}
+        new_cells = sorted(marked) + sorted(frozen)
+        # the previous level's marked cells become twigs there
+        prev["cls"] = np.array([TWIG if c in marked else cl for c, cl in zip(cells, prev["cls"])],
+                               np.int8)
+        ne = len(new_cells)
+        new_index = {c: i for i, c in enumerate(new_cells)}
+        corners = np.stack([prev["corners"][index[c]] for c in new_cells], 0)
+        nbr = np.zeros((ne, 6), np.int32)
+        for f, (ox, oy, oz) in enumerate(_FACE_OFF):
+            for i, c in enumerate(new_cells):
+                q = (c[0] + ox, c[1] + oy, c[2] + oz)
+                nbr[i, f] = -1 if (min(q) < 0 or max(q) >= n) else new_index.get(q, -2)
+        nbr27 = np.full((ne, 27), -1, np.int32)
+        for oz in (-1, 0, 1):
+            for oy in (-1, 0, 1):
+                for ox in (-1, 0, 1):
+                    sl = (ox + 1) + 3 * (oy + 1) + 9 * (oz + 1)
+                    for i, c in enumerate(new_cells):
+                        nbr27[i, sl] = new_index.get((c[0] + ox, c[1] + oy, c[2] + oz), -1)
+        cls = np.array([LEAF] * len(marked) + [FROZEN] * len(frozen), np.int8)
+        levels.append(dict(p=int(pk), shape=prev["shape"], corners=corners, nbr=nbr, nbr27=nbr27,
+                           parent=np.array([index[c] for c in new_cells], np.int32),
+                           octant=np.full(ne, -1, np.int32), cls=cls,
+                           ijk=np.array(new_cells, np.int32).reshape(-1, 3)))
+    return levels
+
+
+def leaf_dofs(levels):
+    """Leaf degrees of freedom per degree over the composite mesh."""
+    out = {}
+    for lv in levels:
+        nl = int(np.sum(np.asarray(lv["cls"]) == LEAF))
+        out[lv["p"]] = out.get(lv["p"], 0) + nl * (lv["p"] + 1) ** 3
+    return out
+
+
+# degrees and distance bands (cell widths of the finest h-level) of the local
+# p-refinement levels of the front workload
+HP_DEGREES = (5, 7, 10)
+HP_BUFFERS = (2.5, 1.75, 0.0)
+
+
+def config4(small=False, hp=True):
     """Config 4: steep front (alpha = 50) on [0,1]^3, base 8^3 at p = 3 with up
-    to 3 levels of local refinement towards the front (p = 3 on every level)."""
+    to 3 levels of local h-refinement towards the front (p = 3), then, with
+    hp, local p-refinement levels raising the elements closest to the front
+    to p = 5, 7, 10 (HP_DEGREES / HP_BUFFERS): the composite leaves carry
+    degrees 3, 5, 7 and 10, each level one degree.  small: base 4^3, one
+    h-level, p-levels 5 and 7."""
     rng = np.random.default_rng(SEED_BASE + 4)
     spec = front_spec(rng)
     levels = refined_hierarchy(spec, n_base=4 if small else 8, n_ref=1 if small else 3,
                                n_root=2 if small else 4)
+    if hp:
+        if small:
+            levels = add_p_levels(levels, spec, (5, 7), (1.5, 0.0))
+        else:
+            levels = add_p_levels(levels, spec, HP_DEGREES, HP_BUFFERS)
     top = levels[-1]
     ndof = top["corners"].shape[0] * (top["p"] + 1) ** 3
     u0 = random_start(rng, ndof)

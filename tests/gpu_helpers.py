@@ -11,19 +11,22 @@ def torch_cuda():
     return torch
 
 
-SOLVER_KW = ("coarse", "root_rtol", "root_steps")
+SOLVER_KW = ("coarse", "root_rtol", "root_steps", "projection")
 
 
 def make_solver(cfg, precision=0, smoother=0, **over):
     """CUDA-path solver of workload cfg; `over` replaces solver parameters
-    (mu_star, delta, s1, s2, sc, coarse, root_rtol, root_steps; coarse as the
-    oracle's name "dense" / "scg")."""
+    (mu_star, delta, s1, s2, sc, coarse, root_rtol, root_steps, projection;
+    coarse and projection by the oracle's names "dense" / "scg", "interp" /
+    "l2")."""
     from paper_2608_14123_b300 import dgfas
     pr = dict(cfg["params"])
     pr.update(over)
     kw = {k: pr[k] for k in SOLVER_KW if k in pr}
     if "coarse" in kw:
         kw["coarse"] = {"dense": dgfas.DGFAS_COARSE_DENSE, "scg": dgfas.DGFAS_COARSE_SCG}[kw["coarse"]]
+    if "projection" in kw:
+        kw["projection"] = {"interp": dgfas.DGFAS_P_INTERP, "l2": dgfas.DGFAS_P_L2}[kw["projection"]]
     return dgfas.Solver(cfg["levels"], pr["mu_star"], pr["delta"], pr["s1"], pr["s2"], pr["sc"],
                         precision=precision, smoother=smoother, **kw)
 

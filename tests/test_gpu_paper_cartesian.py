@@ -17,19 +17,64 @@ pytestmark = pytest.mark.gpu
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_uniform_cartesian_n10.txt")
 
 
-def _paper_n10():
+def _paper_rows():
+    """(kind, p, s1, s2, sc, start, smoother, P) -> n10 as printed by the paper."""
     out = {}
     for line in open(GOLDEN):
         if line.startswith("#") or not line.strip():
             continue
-        kind, p, s1, s2, sc, n10 = line.split()
-        out[(kind, int(p), int(s1), int(s2), int(sc))] = int(n10)
+        kind, p, s1, s2, sc, start, sm, P, n10 = line.split()
+        out[(kind, int(p), int(s1), int(s2), int(sc), start, sm, P)] = int(n10)
     return out
 
 
-def _solver(cfg, s1, s2, sc, prec):
+def _paper_n10():
+    return {k[:5]: v for k, v in _paper_rows().items() if k[5:] == ("mg", "was", "I")}
+
+
+def _solver(cfg, s1, s2, sc, prec, smoother=dgfas.DGFAS_WAS, projection=dgfas.DGFAS_P_INTERP):
     return dgfas.Solver(cfg["levels"], cfg["params"]["mu_star"], cfg["params"]["delta"], s1, s2, sc,
-                        precision=prec)
+                        precision=prec, smoother=smoother, projection=projection)
+
+
+def _level_rhs(cfg, S):
+    """Each level's own right-hand side, projected to zero sum (the full
+    multigrid startup's inputs on the periodic box)."""
+    torch = torch_cuda()
+    out = []
+    for l in range(S.n_levels):
+        xyz = S.node_coords(l)
+        fn = torch.from_numpy(wl.eval_f(cfg["rhs"], xyz.cpu().numpy())).cuda()
+        b = torch.empty_like(fn)
+        S.dgfas_assemble_rhs_level(l, fn, None, b)
+        out.append(b - b.mean())
+    return out
+
+
+def n10_of(kind, p, s1, s2, sc, start, smoother, P, prec=dgfas.DGFAS_FP64):
+    """Cycles to reduce the residual by 1e10 on the paper's periodic workload:
+    from the random start, or from the full multigrid start value (Alg. 4),
+    measured against the random start's residual (the reference of the
+    paper's counts)."""
+    torch = torch_cuda()
+    cfg = wl.paper_cartesian_periodic(p, kind)
+    S = _solver(cfg, s1, s2, sc, prec,
+                dgfas.DGFAS_SCG if smoother == "scg" else dgfas.DGFAS_WAS,
+                dgfas.DGFAS_P_L2 if P == "L" else dgfas.DGFAS_P_INTERP)
+    b = _rhs(cfg, S)
+    u = torch.from_numpy(cfg["u0"]).cuda()
+    r = torch.empty_like(u)
+    S.dgfas_apply_op(-1, u, b, r)
+    r_rand = S.dgfas_norm(-1, r)
+    if start == "fmg":
+        S.dgfas_fmg(_level_rhs(cfg, S), u, 1)
+        S.dgfas_apply_op(-1, u, b, r)
+        rtol = 1e-10 * r_rand / S.dgfas_norm(-1, r)
+    else:
+        rtol = 1e-10
+    info = S.dgfas_solve(u, b, rtol, 60)
+    S.close()
+    return info["cycles"]
 
 
 def _rhs(cfg, S):
@@ -94,3 +139,21 @@ def test_p_multigrid_cycle_counts_near_the_paper(p, s):
     u = torch.from_numpy(cfg["u0"]).cuda()
     info = S.dgfas_solve(u, b, 1e-10, 60)
     assert abs(info["cycles"] - _paper_n10()[("p", p) + s]) <= 2
+
+
+# SCG smoother, full multigrid startup and the L2 projection variant: every
+# row of the paper's tables at p = 4 and 8 with mu_star = 2, delta = 0.08.
+# Tolerances (cycles): h-multigrid at p = 4 exact for WAS (one overlap layer,
+# where the weights reading is pinned), one cycle otherwise; p-multigrid two
+# cycles (the paper solves the p = 1 level by SCG to a tolerance, this
+# hierarchy continues with h-levels to a 2^3 root).
+OTHER_ROWS = [k for k in _paper_rows() if k[5:] != ("mg", "was", "I")]
+
+
+@pytest.mark.parametrize("row", OTHER_ROWS, ids=lambda k: "-".join(str(x) for x in k))
+def test_scg_fmg_and_l2_rows_match_the_paper(row):
+    want = _paper_rows()[row]
+    got = n10_of(*row)
+    kind, p, *_ = row
+    tol = 2 if kind == "p" else (0 if (p == 4 and row[6] == "was") else 1)
+    assert abs(got - want) <= tol, (row, got, want)

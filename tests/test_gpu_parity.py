@@ -127,3 +127,21 @@ def test_graph_replay_matches_direct_launches():
     i1 = S1.dgfas_solve(u1.clone(), b, 1e-10, 30)
     i2 = S2.dgfas_solve(u2.clone(), b, 1e-10, 30)
     assert i1["cycles"] == i2["cycles"] and i1["history"] == i2["history"]
+
+
+@pytest.mark.parametrize("cid,small", CASES, ids=lambda c: str(c))
+def test_vcycle_iterates_l2_projection(cid, small):
+    """The L2 projection variant of P (Sec. 3.2): V-cycle iterates match the
+    oracle's with the same variant (p- and h-transfers)."""
+    cfg = wl.config(cid, small=small)
+    torch = torch_cuda()
+    S = make_solver(cfg, projection="l2")
+    H = make_oracle(cfg, projection="l2")
+    b, b_or = rhs_both(cfg, S, H)
+    u = torch.from_numpy(cfg["u0"].copy()).cuda()
+    uo = H.zero_levels(cfg["u0"])
+    for k in range(2):
+        rn = S.dgfas_fas_vcycle(u, b)
+        uo, rno = H.fas_vcycle(uo, b_or)
+        assert abs(rn - rno) <= 1e-10 * rno
+        assert rel(u.cpu().numpy(), uo[-1]) < 1e-10, k

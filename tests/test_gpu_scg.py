@@ -110,10 +110,11 @@ def test_scg_graph_replay_bit_identical(prec):
 
 @pytest.mark.parametrize("case,prec", [((3, True, "p1"), 1), ((3, True, "p1"), 2),
                                        ((5, True, "p1"), 1), ((5, True, "p1"), 2)])
-def test_scg_mixed_precision_solve_matches_oracle(case, prec):
-    """FP32 / BF16 Schwarz sweeps inside SCG (FP64 recurrences, residual, tau,
-    restriction and root): the solve reaches 1e-10 and its solution agrees
-    with the FP64 oracle's to 1e-8."""
+def test_scg_mixed_precision_solve_cycles(case, prec):
+    """SCG in correction form on FP32 vectors (FP32 operator, FP32 / BF16
+    Schwarz sweep) inside the FP64 outer cycle: the solve reaches 1e-10 in at
+    most two cycles more than the FP64 oracle (the solutions at 1e-12 are
+    compared in test_gpu_mixed_precision)."""
     cid, small, root = case
     cfg = wl.config(cid, small=small, root=root)
     torch = torch_cuda()
@@ -124,4 +125,3 @@ def test_scg_mixed_precision_solve_matches_oracle(case, prec):
     uo, hist = H.solve(cfg["u0"], b_or, max_cycles=40)
     assert info["r_final"] <= 1e-10 * info["r0"]
     assert info["cycles"] <= len(hist) - 1 + 2
-    assert rel(u.cpu().numpy(), uo) < 1e-8
