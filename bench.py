@@ -315,7 +315,7 @@ SURR_SET = 100000
 GOLD = os.path.join(ROOT, "tests", "golden")
 
 
-def train_surrogates(torch, degrees=(7, 3), epochs=40):
+def train_surrogates(torch, degrees=(7, 3), epochs=80):
     """The learned surrogate per degree: the MLP trained on the GPU by the
     library's kernels on the 10^5 oracle Kronecker-sum fits (stored targets;
     inputs regenerated from the seeded training elements by the library)."""
@@ -474,9 +474,11 @@ def config4_record(dgfas, torch):
 def curvilinear_records(dgfas, torch, dev, cid, surr, arms):
     """Per arm (name, precision, surrogate) on workload cid: ms per V-cycle
     (3 graph replays) and time to 1e-10 from the random start."""
-    cfg = wl.config(cid, root="p1")
+    cfg = wl.config(cid)
+    pr = cfg["params"]
     rec = {"dof": int(cfg["u0"].size), "levels": [lv["p"] for lv in cfg["levels"]],
-           "smoother": "SCG (Alg. 6) V(2,2), n_sc = 4", "root": "SCG at p = 1"}
+           "smoother": f"SCG (Alg. 6) ({pr['s1']}, {pr['s2']}, {pr['sc']}), mu_star = {pr['mu_star']}",
+           "root": "p = 1 h-coarsened to 4^3, exact"}
     for name, prec, use in arms:
         S, fb = build_solver(dgfas, cfg, prec, dgfas.DGFAS_SCG, surr if use else None)
         S.dgfas_use_graph(True)
@@ -484,7 +486,7 @@ def curvilinear_records(dgfas, torch, dev, cid, surr, arms):
         u0 = torch.from_numpy(cfg["u0"]).to(dev)
         u = u0.clone()
         ms, _, _ = time_vcycles(S, u, b, 3, 1, torch, dgfas)
-        r = solve_record(S, u0.clone(), b, torch)
+        r = solve_record(S, u0.clone(), b, torch, max_cycles=80)
         r["ms_per_vcycle"] = ms
         r["dof_per_s_per_vcycle"] = rec["dof"] / (ms * 1e-3)
         if use:
@@ -572,7 +574,7 @@ def run_gpu(args):
     # ---- set-up (outside every timed region): the learned surrogate trained on
     # the GPU from the oracle's 10^5 fits, the solver, the right-hand side
     surr, train_info = train_surrogates(torch)
-    cfg = wl.config(5, root="p1")
+    cfg = wl.config(5)
     levels = cfg["levels"]
     top = levels[-1]
     N = top["p"] + 1
@@ -607,7 +609,11 @@ def run_gpu(args):
     m = 2
     ns = N + 2 * m
     smooth = cfg["params"]["s1"] + cfg["params"]["s2"]
-    counts = {"residual_fp64": 2, "apply_fp32": smooth, "fd_tc": smooth, "combine": smooth,
+    # per V-cycle on the top level: one FP64 residual (the cycle's start), the
+    # s1 + s2 SCG steps, and two more smoother-precision operators (the
+    # residual after pre-smoothing and the start of post-smoothing, formed as
+    # r - A d in the smoother precision)
+    counts = {"residual_fp64": 1, "apply_fp32": smooth + 2, "fd_tc": smooth, "combine": smooth,
               "scg_zr_dir": smooth, "scg_pq_update": smooth}
     kt = kernel_table(prof, ndof, N, ns, fp64_tf, pk["hbm"], counts)
     dom = max(kt, key=lambda k: kt[k]["count_per_vcycle"] * kt[k]["ms"])
@@ -626,11 +632,15 @@ def run_gpu(args):
     torch.cuda.empty_cache()
     arms = []
     if not args.skip_fp64:
-        arms.append(("fp64_geometric", dgfas.DGFAS_FP64, None))
+        arms.append(("fp64_geometric", dgfas.DGFAS_FP64, None, cfg))
     if not args.geometric and not args.skip_geometric:
-        arms.append(("mixed_geometric", prec, None))
-    for name, pm, sur in arms:
-        S2, _ = build_solver(dgfas, cfg, pm, dgfas.DGFAS_SCG, sur)
+        arms.append(("mixed_geometric", prec, None, cfg))
+    if not args.skip_geometric:
+        # the p-multigrid hierarchy 7 -> 3 -> 1 with the SCG root at p = 1
+        arms.append(("mixed_learned_scg_root_p1", prec, None if args.geometric else surr,
+                     wl.config(5, root="p1")))
+    for name, pm, sur, cf in arms:
+        S2, _ = build_solver(dgfas, cf, pm, dgfas.DGFAS_SCG, sur)
         S2.dgfas_use_graph(True)
         ms2, _, _ = time_vcycles(S2, u0.clone(), b, 3, 1, torch, dgfas)
         r = solve_record(S2, u0.clone(), b, torch)
@@ -671,7 +681,7 @@ def run_gpu(args):
                        "elements": top["corners"].shape[0], "p": top["p"], "dof": ndof,
                        "levels": [lv["p"] for lv in levels],
                        "smoother": "SCG (Alg. 6) V(2,2), n_sc = 4, delta = 0.08",
-                       "root": "FP64 SCG at p = 1 (rtol 1e-3, <= 64 steps)",
+                       "root": "p = 1 h-coarsened to 4^3 (every other vertex), exact dense root",
                        "surrogate": "geometric" if args.geometric else "learned MLP (24-64-64-6)",
                        "precision": args.precision, "graph": True,
                        "global_batch": 1, "seq_len": 0,

@@ -1,5 +1,6 @@
 // sm_103a kernels of the hot path:
-//  k_apply    SIP operator / residual by sum factorization (Sec. 2.2, Eq. (2))
+//  k_apply_curv_eo / k_apply_box_eo   SIP operator / residual by sum
+//             factorization (Sec. 2.2, Eq. (2)), curvilinear and box elements
 //  k_fd       Schwarz gather + fast-diagonalization solve + weighting (Eqs. (9)-(11))
 //  k_combine  deterministic pull of the weighted subdomain corrections (Eq. (11))
 //  k_project / k_restrict / k_prolong   FAS transfers (Sec. 3.2, Alg. 2)
@@ -31,184 +32,6 @@ __device__ __forceinline__ double fd_div(double x, double y) { return x / y; }
 __device__ __forceinline__ float fd_div(float x, float y) { return __fdividef(x, y); }
 
 // ============================================================================ apply
-// Team of N*N threads (tx, ty) per element, looping over k; EPB teams per CTA.
-// Shared memory per team: u, neighbour buffer, F1, F2, F3, face-flux R (6 N^3).
-// out = b + alpha * A u   (b may be null); rows of frozen elements are 0.
-template <int N, typename T, typename TU, typename TB, typename TO, bool BOX>
-__global__ void k_apply(const LevelView<T> L, const TU* __restrict__ u,
-                        const TB* __restrict__ b, TO* __restrict__ out, T alpha) {
-  constexpr int N2 = N * N, N3 = N * N * N;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* sD = reinterpret_cast<T*>(smem_raw);
-  T* sw = sD + N2;
-  T* base = sw + 16;
-  const int team = threadIdx.y;
-  T* us = base + team * 6 * N3;
-  T* nb = us + N3;
-  T* F1 = nb + N3;
-  T* F2 = F1 + N3;
-  T* F3 = F2 + N3;
-  T* Rf = F3 + N3;
-  const int tx = threadIdx.x % N, ty = threadIdx.x / N;
-  const int e = blockIdx.x * blockDim.y + team;
-  const bool valid = e < L.ne;
-  const int tid = threadIdx.y * blockDim.x + threadIdx.x, nth = blockDim.x * blockDim.y;
-  for (int t = tid; t < N2; t += nth) sD[t] = L.D[t];
-  for (int t = tid; t < N; t += nth) sw[t] = L.w[t];
-  const size_t eo = (size_t)e * N3;
-  if (valid)
-    for (int k = 0; k < N; ++k) us[(k * N + ty) * N + tx] = (T)u[eo + (k * N + ty) * N + tx];
-  __syncthreads();
-  T hx = 0, hy = 0, hz = 0, g0 = 0, g1 = 0, g2 = 0;
-  if (BOX && valid) {
-    hx = L.h[3 * e];
-    hy = L.h[3 * e + 1];
-    hz = L.h[3 * e + 2];
-    g0 = L.nu * hy * hz / (T(2) * hx);
-    g1 = L.nu * hx * hz / (T(2) * hy);
-    g2 = L.nu * hx * hy / (T(2) * hz);
-  }
-  // ---- volume term: F = G grad_xi u
-  if (valid) {
-    for (int k = 0; k < N; ++k) {
-      const int n = (k * N + ty) * N + tx;
-      T d0 = 0, d1 = 0, d2 = 0;
-#pragma unroll
-      for (int l = 0; l < N; ++l) {
-        d0 += sD[tx * N + l] * us[(k * N + ty) * N + l];
-        d1 += sD[ty * N + l] * us[(k * N + l) * N + tx];
-        d2 += sD[k * N + l] * us[(l * N + ty) * N + tx];
-      }
-      T mass_u = 0;
-      if (BOX) {
-        const T w3 = sw[tx] * sw[ty] * sw[k];
-        F1[n] = g0 * w3 * d0;
-        F2[n] = g1 * w3 * d1;
-        F3[n] = g2 * w3 * d2;
-        if (L.kappa != T(0)) mass_u = L.kappa * w3 * hx * hy * hz * T(0.125) * us[n];
-      } else {
-        const T* G = L.G + (size_t)e * 6 * N3 + n;
-        const T G00 = ld(G), G11 = ld(G + N3), G22 = ld(G + 2 * N3), G01 = ld(G + 3 * N3),
-                G02 = ld(G + 4 * N3), G12 = ld(G + 5 * N3);
-        F1[n] = G00 * d0 + G01 * d1 + G02 * d2;
-        F2[n] = G01 * d0 + G11 * d1 + G12 * d2;
-        F3[n] = G02 * d0 + G12 * d1 + G22 * d2;
-        if (L.kappa != T(0)) mass_u = L.kappa * ld(L.mass + eo + n) * us[n];
-      }
-      Rf[n] = mass_u;
-    }
-  }
-  __syncthreads();
-  // ---- face terms, one face per pass (edge/corner nodes belong to several faces)
-  for (int f = 0; f < 6; ++f) {
-    const int d = f >> 1, side = f & 1;
-    const int nbid = valid ? L.nbr[6 * e + f] : -2;
-    if (nbid >= 0) {
-      const size_t no = (size_t)nbid * N3;
-      for (int k = 0; k < N; ++k) nb[(k * N + ty) * N + tx] = (T)u[no + (k * N + ty) * N + tx];
-    }
-    __syncthreads();
-    if (valid && nbid != -2) {
-      const int a = tx, bb = ty;
-      const int end = side ? N - 1 : 0, endp = N - 1 - end;
-      int i, j, k, ip, jp, kp;
-      if (d == 0) { i = end; j = a; k = bb; ip = endp; jp = a; kp = bb; }
-      else if (d == 1) { i = a; j = end; k = bb; ip = a; jp = endp; kp = bb; }
-      else { i = a; j = bb; k = end; ip = a; jp = bb; kp = endp; }
-      const int n = (k * N + j) * N + i;
-      const T um = us[n];
-      T c0, c1, c2, W, mu;
-      mu = L.mu[6 * e + f];
-      if (BOX) {
-        const T sgn = side ? T(1) : T(-1);
-        const T wab = sw[a] * sw[bb];
-        const T gd = d == 0 ? g0 : (d == 1 ? g1 : g2);
-        const T hd = d == 0 ? hx : (d == 1 ? hy : hz);
-        W = L.nu * wab * (hx * hy * hz / hd) * T(0.25);   // nu * surface weight
-        c0 = d == 0 ? sgn * gd * wab : T(0);
-        c1 = d == 1 ? sgn * gd * wab : T(0);
-        c2 = d == 2 ? sgn * gd * wab : T(0);
-      } else {
-        const size_t fo = ((size_t)e * 6 + f) * N2 + bb * N + a;
-        W = L.nu * ld(L.fW + fo);
-        const T* fc = L.fc + ((size_t)e * 6 + f) * 3 * N2 + bb * N + a;
-        c0 = ld(fc);
-        c1 = ld(fc + N2);
-        c2 = ld(fc + 2 * N2);
-      }
-      // own normal flux q- = sum_t c_t du/dxi_t
-      T qm = 0;
-      {
-        T d0 = 0, d1 = 0, d2 = 0;
-        if (!BOX || d == 0)
-          for (int l = 0; l < N; ++l) d0 += sD[i * N + l] * us[(k * N + j) * N + l];
-        if (!BOX || d == 1)
-          for (int l = 0; l < N; ++l) d1 += sD[j * N + l] * us[(k * N + l) * N + i];
-        if (!BOX || d == 2)
-          for (int l = 0; l < N; ++l) d2 += sD[k * N + l] * us[(l * N + j) * N + i];
-        qm = c0 * d0 + c1 * d1 + c2 * d2;
-      }
-      T flux, lift;
-      if (nbid >= 0) {
-        const int np = (kp * N + jp) * N + ip;
-        const T up = nb[np];
-        T cp0, cp1, cp2;
-        if (BOX) {
-          const T sgn = side ? T(-1) : T(1);
-          const T wab = sw[a] * sw[bb];
-          const T phx = L.h[3 * nbid], phy = L.h[3 * nbid + 1], phz = L.h[3 * nbid + 2];
-          const T gp = d == 0 ? L.nu * phy * phz / (T(2) * phx)
-                              : (d == 1 ? L.nu * phx * phz / (T(2) * phy)
-                                        : L.nu * phx * phy / (T(2) * phz));
-          cp0 = d == 0 ? sgn * gp * wab : T(0);
-          cp1 = d == 1 ? sgn * gp * wab : T(0);
-          cp2 = d == 2 ? sgn * gp * wab : T(0);
-        } else {
-          const T* fc = L.fc + ((size_t)nbid * 6 + (f ^ 1)) * 3 * N2 + bb * N + a;
-          cp0 = ld(fc);
-          cp1 = ld(fc + N2);
-          cp2 = ld(fc + 2 * N2);
-        }
-        T d0 = 0, d1 = 0, d2 = 0;
-        if (!BOX || d == 0)
-          for (int l = 0; l < N; ++l) d0 += sD[ip * N + l] * nb[(kp * N + jp) * N + l];
-        if (!BOX || d == 1)
-          for (int l = 0; l < N; ++l) d1 += sD[jp * N + l] * nb[(kp * N + l) * N + ip];
-        if (!BOX || d == 2)
-          for (int l = 0; l < N; ++l) d2 += sD[kp * N + l] * nb[(l * N + jp) * N + ip];
-        const T qp = cp0 * d0 + cp1 * d1 + cp2 * d2;
-        const T jump = um - up;
-        flux = mu * W * jump - T(0.5) * (qm - qp);
-        lift = T(-0.5) * jump;
-      } else {   // Dirichlet
-        flux = T(2) * mu * W * um - qm;
-        lift = -um;
-      }
-      Rf[n] += flux;
-      F1[n] += c0 * lift;
-      F2[n] += c1 * lift;
-      F3[n] += c2 * lift;
-    }
-    __syncthreads();
-  }
-  // ---- transposed reference gradient
-  if (!valid) return;
-  const bool frozen = L.cls[e] == DGFAS_FROZEN;
-  for (int k = 0; k < N; ++k) {
-    const int n = (k * N + ty) * N + tx;
-    T r = Rf[n];
-#pragma unroll
-    for (int l = 0; l < N; ++l) {
-      r += sD[l * N + tx] * F1[(k * N + ty) * N + l];
-      r += sD[l * N + ty] * F2[(k * N + l) * N + tx];
-      r += sD[l * N + k] * F3[(l * N + ty) * N + tx];
-    }
-    T o = alpha * r;
-    if (b) o += (T)b[eo + n];
-    out[eo + n] = frozen ? TO(0) : (TO)o;
-  }
-}
-
 // Line form of the curvilinear operator with even-odd derivative products.
 // A team of N^2 threads per element; in each pass thread (a, b) owns one node
 // line along the pass direction (x: (k, j) = (b, a); y: (k, i); z: (j, i)).

@@ -7,7 +7,8 @@ with a few GB on the device at most.
 
 apply_fp64: the FP64 curvilinear operator on 16^3 trilinear elements
 (+-0.15h perturbation, p = 7, 2.1M DoF, about 0.25 GB of vectors and
-geometry), `reps` applications.  scg_bf16: the top-level SCG steps of the
+geometry), `reps` applications inside the NVTX range "profiled" (the set-up's
+own operator launches, on the root, stay outside it).  scg_bf16: the top-level SCG steps of the
 mixed-precision smoother (BF16 tensor-core Schwarz sweep) on the same mesh.
 """
 import sys
@@ -23,7 +24,7 @@ def main():
     reps = int(sys.argv[2]) if len(sys.argv) > 2 else 3
     rng = np.random.default_rng(wl.SEED_BASE + 5)
     V = wl.perturbed_vertices(16, 0.15, rng)
-    levels = wl.hierarchy(V, [7, 3])
+    levels = wl.hierarchy(V, [7, 3, 1], h_root=4)
     prec = dgfas.DGFAS_BF16 if case == "scg_bf16" else dgfas.DGFAS_FP64
     S = dgfas.Solver(levels, 5.0, 0.08, 2, 2, 4, precision=prec, smoother=dgfas.DGFAS_SCG)
     n = S.ndof(-1)
