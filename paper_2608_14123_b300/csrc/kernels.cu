@@ -85,20 +85,44 @@ __device__ __forceinline__ void acs_line(const T (*me)[(N / 2) > 0 ? N / 2 : 1],
   }
 }
 
+// Shared-memory layout of the curvilinear kernel: node (i, j, k) of an element
+// at (k N + j)(N + 1) + i, i.e. every x-row padded to N + 1 entries, so that
+// the lanes of a warp reading or writing whole lines in any of the three
+// directions hit different banks (the x-lines of consecutive lanes start
+// N + 1 entries apart, coprime to the bank count).
+template <int N>
+struct CurvLine {
+  static constexpr int NP = N + 1, NP3 = N * N * NP;
+  int bg, sg, bp, sp;   // global (unpadded) and shared (padded) base and stride of a line
+  __device__ CurvLine(int d, int a, int b) {
+    if (d == 0) {        // x-line (j, k) = (a, b)
+      bg = (b * N + a) * N; sg = 1; bp = (b * N + a) * NP; sp = 1;
+    } else if (d == 1) { // y-line (i, k) = (a, b)
+      bg = b * N * N + a; sg = N; bp = b * N * NP + a; sp = NP;
+    } else {             // z-line (i, j) = (a, b)
+      bg = b * N + a; sg = N * N; bp = b * NP + a; sp = N * NP;
+    }
+  }
+};
+
+template <int N>
+__device__ __forceinline__ int cpad(int i, int j, int k) { return (k * N + j) * (N + 1) + i; }
+
 template <int N, typename T, typename TU, typename TB, typename TO>
 __global__ void __launch_bounds__(256) k_apply_curv_eo(const LevelView<T> L, const TU* __restrict__ u,
                                                        const TB* __restrict__ b, TO* __restrict__ out,
                                                        T alpha) {
   constexpr int N2 = N * N, N3 = N * N * N, H = N / 2, HC = (N + 1) / 2;
+  constexpr int NP3 = CurvLine<N>::NP3;
   __shared__ CurvEo<N, T> M;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int team = threadIdx.y, tid = threadIdx.y * blockDim.x + threadIdx.x;
   const int nth = blockDim.x * blockDim.y;
-  T* us = reinterpret_cast<T*>(smem_raw) + (size_t)team * (6 * N3 + 6 * N2);
-  T* nb = us + N3;
-  T* F[3] = {nb + N3, nb + 2 * N3, nb + 3 * N3};
-  T* R = nb + 4 * N3;
-  T* Q = nb + 5 * N3;   // [6][N2] own normal flux at the face nodes
+  T* us = reinterpret_cast<T*>(smem_raw) + (size_t)team * (6 * NP3 + 6 * N2);
+  T* nb = us + NP3;
+  T* F[3] = {nb + NP3, nb + 2 * NP3, nb + 3 * NP3};
+  T* R = nb + 4 * NP3;
+  T* Q = nb + 5 * NP3;   // [6][N2] own normal flux at the face nodes
   for (int t = tid; t < N2; t += nth) M.D[t] = L.D[t];
   for (int t = tid; t < HC * N; t += nth) {
     const int r = t / N, q = t % N;
@@ -118,21 +142,20 @@ __global__ void __launch_bounds__(256) k_apply_curv_eo(const LevelView<T> L, con
   const bool valid = e < L.ne && threadIdx.x < N2;
   const size_t eo = (size_t)e * N3;
   if (e < L.ne)
-    for (int t = threadIdx.x; t < N3; t += blockDim.x) us[t] = (T)u[eo + t];
+    for (int t = threadIdx.x; t < N3; t += blockDim.x) us[t + t / N] = (T)u[eo + t];
   __syncthreads();
   const int a = threadIdx.x % N, bb = threadIdx.x / N;
   // ---- 1: reference gradient, one line per thread and direction
 #pragma unroll 1
   for (int d = 0; d < 3; ++d) {
     if (!valid) continue;
-    const int st = d == 0 ? 1 : (d == 1 ? N : N2);
-    const int base = d == 0 ? (bb * N + a) * N : (d == 1 ? bb * N2 + a : bb * N + a);
+    const CurvLine<N> ln(d, a, bb);
     T x[N], y[N];
 #pragma unroll
-    for (int l = 0; l < N; ++l) x[l] = us[base + l * st];
+    for (int l = 0; l < N; ++l) x[l] = us[ln.bp + l * ln.sp];
     acs_line<N, T>(M.de, M.dO, M.dm, x, y);
 #pragma unroll
-    for (int l = 0; l < N; ++l) F[d][base + l * st] = y[l];
+    for (int l = 0; l < N; ++l) F[d][ln.bp + l * ln.sp] = y[l];
   }
   __syncthreads();
   // ---- 2: own normal flux at the face nodes, then the metric node by node
@@ -140,8 +163,7 @@ __global__ void __launch_bounds__(256) k_apply_curv_eo(const LevelView<T> L, con
 #pragma unroll 1
     for (int f = 0; f < 6; ++f) {
       const int d = f >> 1, end = (f & 1) ? N - 1 : 0;
-      const int n = d == 0 ? (bb * N + a) * N + end : (d == 1 ? (bb * N + end) * N + a
-                                                              : (end * N + bb) * N + a);
+      const int n = d == 0 ? cpad<N>(end, a, bb) : (d == 1 ? cpad<N>(a, end, bb) : cpad<N>(a, bb, end));
       const T* fc = L.fc + ((size_t)e * 6 + f) * 3 * N2 + bb * N + a;
       Q[f * N2 + threadIdx.x] = ld(fc) * F[0][n] + ld(fc + N2) * F[1][n] + ld(fc + 2 * N2) * F[2][n];
     }
@@ -149,15 +171,15 @@ __global__ void __launch_bounds__(256) k_apply_curv_eo(const LevelView<T> L, con
   __syncthreads();
   if (valid) {
     for (int k = 0; k < N; ++k) {
-      const int n = (k * N + bb) * N + a;
+      const int n = (k * N + bb) * N + a, np = cpad<N>(a, bb, k);
       const T* G = L.G + (size_t)e * 6 * N3 + n;
       const T G00 = ld(G), G11 = ld(G + N3), G22 = ld(G + 2 * N3), G01 = ld(G + 3 * N3),
               G02 = ld(G + 4 * N3), G12 = ld(G + 5 * N3);
-      const T d0 = F[0][n], d1 = F[1][n], d2 = F[2][n];
-      F[0][n] = G00 * d0 + G01 * d1 + G02 * d2;
-      F[1][n] = G01 * d0 + G11 * d1 + G12 * d2;
-      F[2][n] = G02 * d0 + G12 * d1 + G22 * d2;
-      R[n] = L.kappa != T(0) ? L.kappa * ld(L.mass + eo + n) * us[n] : T(0);
+      const T d0 = F[0][np], d1 = F[1][np], d2 = F[2][np];
+      F[0][np] = G00 * d0 + G01 * d1 + G02 * d2;
+      F[1][np] = G01 * d0 + G11 * d1 + G12 * d2;
+      F[2][np] = G02 * d0 + G12 * d1 + G22 * d2;
+      R[np] = L.kappa != T(0) ? L.kappa * ld(L.mass + eo + n) * us[np] : T(0);
     }
   }
   // ---- 3: faces, one per pass (edge / corner nodes belong to several faces)
@@ -167,7 +189,7 @@ __global__ void __launch_bounds__(256) k_apply_curv_eo(const LevelView<T> L, con
     __syncthreads();
     if (nbid >= 0) {
       const size_t no = (size_t)nbid * N3;
-      for (int t = threadIdx.x; t < N3; t += blockDim.x) nb[t] = (T)u[no + t];
+      for (int t = threadIdx.x; t < N3; t += blockDim.x) nb[t + t / N] = (T)u[no + t];
     }
     __syncthreads();
     if (valid && nbid != -2) {
@@ -176,7 +198,7 @@ __global__ void __launch_bounds__(256) k_apply_curv_eo(const LevelView<T> L, con
       if (d == 0) { i = end; j = a; k = bb; ip = endp; jp = a; kp = bb; }
       else if (d == 1) { i = a; j = end; k = bb; ip = a; jp = endp; kp = bb; }
       else { i = a; j = bb; k = end; ip = a; jp = bb; kp = endp; }
-      const int n = (k * N + j) * N + i;
+      const int n = cpad<N>(i, j, k);
       const T um = us[n];
       const size_t fo = ((size_t)e * 6 + f) * N2 + bb * N + a;
       const T W = L.nu * ld(L.fW + fo);
@@ -186,15 +208,15 @@ __global__ void __launch_bounds__(256) k_apply_curv_eo(const LevelView<T> L, con
       const T qm = Q[f * N2 + threadIdx.x];
       T flux, lift;
       if (nbid >= 0) {
-        const T up = nb[(kp * N + jp) * N + ip];
+        const T up = nb[cpad<N>(ip, jp, kp)];
         const T* fn = L.fc + ((size_t)nbid * 6 + (f ^ 1)) * 3 * N2 + bb * N + a;
         const T cp0 = ld(fn), cp1 = ld(fn + N2), cp2 = ld(fn + 2 * N2);
         T d0 = 0, d1 = 0, d2 = 0;
 #pragma unroll
         for (int l = 0; l < N; ++l) {
-          d0 += M.D[ip * N + l] * nb[(kp * N + jp) * N + l];
-          d1 += M.D[jp * N + l] * nb[(kp * N + l) * N + ip];
-          d2 += M.D[kp * N + l] * nb[(l * N + jp) * N + ip];
+          d0 += M.D[ip * N + l] * nb[cpad<N>(l, jp, kp)];
+          d1 += M.D[jp * N + l] * nb[cpad<N>(ip, l, kp)];
+          d2 += M.D[kp * N + l] * nb[cpad<N>(ip, jp, l)];
         }
         const T qp = cp0 * d0 + cp1 * d1 + cp2 * d2;
         const T jump = um - up;
@@ -214,27 +236,26 @@ __global__ void __launch_bounds__(256) k_apply_curv_eo(const LevelView<T> L, con
   // ---- 4: transposed reference gradient, one line per thread and direction
 #pragma unroll 1
   for (int d = 0; d < 3; ++d) {
-    const int st = d == 0 ? 1 : (d == 1 ? N : N2);
-    const int base = d == 0 ? (bb * N + a) * N : (d == 1 ? bb * N2 + a : bb * N + a);
+    const CurvLine<N> ln(d, a, bb);
     T y[N];
     if (valid) {
       T x[N];
 #pragma unroll
-      for (int l = 0; l < N; ++l) x[l] = F[d][base + l * st];
+      for (int l = 0; l < N; ++l) x[l] = F[d][ln.bp + l * ln.sp];
       acs_line<N, T>(M.te, M.tO, M.tm, x, y);
     }
     if (d < 2) {
       if (valid) {
 #pragma unroll
-        for (int l = 0; l < N; ++l) R[base + l * st] += y[l];
+        for (int l = 0; l < N; ++l) R[ln.bp + l * ln.sp] += y[l];
       }
       __syncthreads();
     } else if (valid) {
       const bool frozen = L.cls[e] == DGFAS_FROZEN;
 #pragma unroll
       for (int l = 0; l < N; ++l) {
-        const int n = base + l * st;
-        T o = alpha * (R[n] + y[l]);
+        const int n = ln.bg + l * ln.sg;
+        T o = alpha * (R[ln.bp + l * ln.sp] + y[l]);
         if (b) o += (T)b[eo + n];
         out[eo + n] = frozen ? TO(0) : (TO)o;
       }
@@ -463,10 +484,11 @@ static int apply_N(const LevelView<T>& L, const TU* u, const TB* b, TO* out, T a
     // line form (even-odd products, own face derivatives from the volume pass)
     int epb3 = (128 + N2 - 1) / N2;
     if (epb_req > 0) epb3 = std::max(1, std::min(epb_req, 256 / N2));
-    size_t smem3 = (size_t)(6 * N3 + 6 * N2) * epb3 * sizeof(T);
+    constexpr int NP3 = CurvLine<N>::NP3;
+    size_t smem3 = (size_t)(6 * NP3 + 6 * N2) * epb3 * sizeof(T);
     while (epb3 > 1 && smem3 > 100 * 1024) {
       --epb3;
-      smem3 = (size_t)(6 * N3 + 6 * N2) * epb3 * sizeof(T);
+      smem3 = (size_t)(6 * NP3 + 6 * N2) * epb3 * sizeof(T);
     }
     auto kf = k_apply_curv_eo<N, T, TU, TB, TO>;
     static bool attr = false;

@@ -91,6 +91,16 @@ __global__ void k_scg_init(const T* __restrict__ r, long long n, double rtol2, d
   }
 }
 
+// no exit test (rtol = 0): the scalars start from "not done", no reduction
+// (a zero residual then gives gamma = p.q = 0 and alpha = 0, so nothing moves)
+__global__ void k_scg_reset(double* scal) {
+  if (threadIdx.x == 0) {
+    scal[S_RMAX2] = 0.0;
+    scal[S_DONE] = 0.0;
+    scal[S_STEPS] = 0.0;
+  }
+}
+
 // gamma_new = z.r; for step > 1 also z.r0 and beta = (z.r - z.r0) / gamma_old
 // (products and sums in FP64)
 template <typename T, bool FIRST>
@@ -174,11 +184,13 @@ __global__ void k_scg_pq(const T* __restrict__ p, const T* __restrict__ q, long 
   }
 }
 
-// r0 = r; r -= alpha q; x += alpha p; |r|^2 and the exit test |r| <= r_max
+// r0 = r; r -= alpha q; x += alpha p; |r|^2 and the exit test |r| <= r_max.
+// With uout (the last step of a correction-form block, no exit test):
+// uout += x + alpha p instead of storing x.
 template <typename T>
 __global__ void k_scg_update(T* __restrict__ r, T* __restrict__ r0, T* __restrict__ x,
                              const T* __restrict__ p, const T* __restrict__ q, long long n,
-                             double* part, int* counter, double* scal) {
+                             double* part, int* counter, double* scal, double* __restrict__ uout) {
   const T alpha = (T)scal[S_ALPHA];
   double v[1] = {0.0};
   const long long S = (long long)gridDim.x * kThreads;
@@ -197,7 +209,9 @@ __global__ void k_scg_update(T* __restrict__ r, T* __restrict__ r0, T* __restric
       const T rn = rr[u] - alpha * qq[u];
       r0[i + u * S] = rr[u];
       r[i + u * S] = rn;
-      x[i + u * S] = xx[u] + alpha * pp[u];
+      const T xn = xx[u] + alpha * pp[u];
+      if (uout) uout[i + u * S] += (double)xn;
+      else x[i + u * S] = xn;
       v[0] += (double)rn * (double)rn;
     }
   }
@@ -206,7 +220,9 @@ __global__ void k_scg_update(T* __restrict__ r, T* __restrict__ r0, T* __restric
     const T rn = ri - alpha * q[i];
     r0[i] = ri;
     r[i] = rn;
-    x[i] += alpha * p[i];
+    const T xn = x[i] + alpha * p[i];
+    if (uout) uout[i] += (double)xn;
+    else x[i] = xn;
     v[0] += (double)rn * (double)rn;
   }
   double t[1];
@@ -217,6 +233,13 @@ __global__ void k_scg_update(T* __restrict__ r, T* __restrict__ r0, T* __restric
       if (t[0] <= scal[S_RMAX2]) scal[S_DONE] = 1.0;
     }
   }
+}
+
+// y = (double) x
+__global__ void k_scg_to_double(const float* __restrict__ x, double* __restrict__ y, long long n) {
+  const long long S = (long long)gridDim.x * kThreads;
+  for (long long i = (long long)blockIdx.x * kThreads + threadIdx.x; i < n; i += S)
+    y[i] = (double)x[i];
 }
 
 }  // namespace
@@ -260,7 +283,7 @@ static int scg_apply(Ctx& c, int l, const float* p, float* q) { return launch_ap
 // updated in place; p, q, z, r0 work vectors of the level's size.
 template <typename T>
 static int scg_steps(Ctx& c, int l, int prec, T* x, T* r, T* p, T* q, T* z, T* r0, int n,
-                     double rtol) {
+                     double rtol, double* uout = nullptr) {
   const long long nd = c.lv[l].ndof;
   double* scal = c.dscal;
   int* cnt = c.dcnt;
@@ -268,7 +291,11 @@ static int scg_steps(Ctx& c, int l, int prec, T* x, T* r, T* p, T* q, T* z, T* r
   // SCG's partial sums live past the first G entries of the reduction buffer,
   // which hold the cycle's residual norm partials until the host reads them
   double* part = c.red + G;
-  k_scg_init<T><<<G, kThreads, 0, c.stream>>>(r, nd, rtol * rtol, part, cnt, scal);
+  if (rtol > 0.0) {
+    k_scg_init<T><<<G, kThreads, 0, c.stream>>>(r, nd, rtol * rtol, part, cnt, scal);
+  } else {
+    k_scg_reset<<<1, 32, 0, c.stream>>>(scal);
+  }
   LAUNCH_CHECK();
   for (int i = 1; i <= n; ++i) {
     int rc = scg_sweep(c, l, prec, r, z);
@@ -288,7 +315,8 @@ static int scg_steps(Ctx& c, int l, int prec, T* x, T* r, T* p, T* q, T* z, T* r
     if (rc != DGFAS_OK) return rc;
     k_scg_pq<T><<<G, kThreads, 0, c.stream>>>(p, q, nd, part, cnt, scal);
     LAUNCH_CHECK();
-    k_scg_update<T><<<G, kThreads, 0, c.stream>>>(r, r0, x, p, q, nd, part, cnt, scal);
+    k_scg_update<T><<<G, kThreads, 0, c.stream>>>(r, r0, x, p, q, nd, part, cnt, scal,
+                                                   i == n ? uout : nullptr);
     LAUNCH_CHECK();
   }
   return DGFAS_OK;
@@ -306,8 +334,8 @@ static int scg_steps(Ctx& c, int l, int prec, T* x, T* r, T* p, T* q, T* z, T* r
 // zero, or with `pending` at the correction already in lv[l].delta (the
 // prolongation, not yet in u; lv[l].r is then the residual of u without it),
 // the start residual r - A d being formed in the smoother precision.  With
-// want_res, lv[l].r becomes r - A d (smoother-precision operator, FP64
-// result), the residual of the new u as the WAS smoother forms it; otherwise
+// want_res, lv[l].r becomes SCG's recursive residual r - A d (FP32, widened
+// to FP64), the residual of the new u in the smoother precision; otherwise
 // lv[l].r is stale afterwards.
 // fp64_vectors: FP64 iteration (vectors, operator, recurrences) whatever
 // prec is; prec then only sets the precision of the Schwarz sweep (the
@@ -340,9 +368,16 @@ int scg_run(Ctx& c, int l, double* u, int n, double rtol, int prec, bool pending
     }
     rc = launch_to_float(c, H.r, r, nd);
   }
-  if (rc == DGFAS_OK) rc = scg_steps<float>(c, l, prec, d, r, p, q, z, r0, n, rtol);
-  if (rc == DGFAS_OK && want_res) rc = launch_apply_corr(c, l, prec, d, H.r, H.r, 1);
-  if (rc == DGFAS_OK) rc = launch_add_delta(c, nd, prec, d, u);
+  // without an exit test the last step adds the correction to u directly
+  const bool fuse = n > 0 && !(rtol > 0.0);
+  if (rc == DGFAS_OK) rc = scg_steps<float>(c, l, prec, d, r, p, q, z, r0, n, rtol,
+                                            fuse ? u : nullptr);
+  if (rc == DGFAS_OK && want_res) {
+    // the residual of the new u: SCG's recursive residual r_start - A d
+    k_scg_to_double<<<c.red_blocks, kThreads, 0, c.stream>>>(r, H.r, nd);
+    LAUNCH_CHECK();
+  }
+  if (rc == DGFAS_OK && !fuse) rc = launch_add_delta(c, nd, prec, d, u);
   return rc;
 }
 
@@ -392,7 +427,8 @@ extern "C" int dgfas_profile_scg(void* ctx, int level, double* u, const double* 
       if (e == DGFAS_OK) e = scg_apply(*c, level, p, q);
       cudaEventRecord(ev[4], c->stream);
       k_scg_pq<T><<<G, kThreads, 0, c->stream>>>(p, q, nd, part, c->dcnt, c->dscal);
-      k_scg_update<T><<<G, kThreads, 0, c->stream>>>(r, r0, x, p, q, nd, part, c->dcnt, c->dscal);
+      k_scg_update<T><<<G, kThreads, 0, c->stream>>>(r, r0, x, p, q, nd, part, c->dcnt, c->dscal,
+                                                      nullptr);
       cudaEventRecord(ev[5], c->stream);
       if (e == DGFAS_OK) e = launch_apply(*c, level, DGFAS_FP64, u, g, H.t ? H.t : H.r, -1.0);
       cudaEventRecord(ev[6], c->stream);
