@@ -609,11 +609,11 @@ def run_gpu(args):
     m = 2
     ns = N + 2 * m
     smooth = cfg["params"]["s1"] + cfg["params"]["s2"]
-    # per V-cycle on the top level: one FP64 residual (the cycle's start), the
-    # s1 + s2 SCG steps, and two more smoother-precision operators (the
-    # residual after pre-smoothing and the start of post-smoothing, formed as
-    # r - A d in the smoother precision)
-    counts = {"residual_fp64": 1, "apply_fp32": smooth + 2, "fd_tc": smooth, "combine": smooth,
+    # per V-cycle on the top level: one FP64 residual (the cycle's start, the
+    # two kernels of the two-pass form), the s1 + s2 SCG steps, and one more
+    # smoother-precision operator (the start of post-smoothing, r - A d; the
+    # residual after pre-smoothing is SCG's recursive one)
+    counts = {"residual_fp64": 1, "apply_fp32": smooth + 1, "fd_tc": smooth, "combine": smooth,
               "scg_zr_dir": smooth, "scg_pq_update": smooth}
     kt = kernel_table(prof, ndof, N, ns, fp64_tf, pk["hbm"], counts)
     dom = max(kt, key=lambda k: kt[k]["count_per_vcycle"] * kt[k]["ms"])

@@ -113,6 +113,8 @@ struct Ctx {
                                 // [0, G), SCG's scalar products [G, 3G)
   double* red_host = nullptr;   // pinned
   double* scg_buf = nullptr;    // SCG vectors (p, q, z, r0) for the largest level
+  double* apply_scratch = nullptr;   // two-pass FP64 curvilinear operator: F [e][3][N^3]
+  size_t apply_scratch_n = 0;        // and face data [e][6][2][N^2] of the largest level
   double* dscal = nullptr;      // device scalars of the SCG recurrences
   int* dcnt = nullptr;          // ticket counters of the single-pass reductions
   int* tc_err = nullptr;        // set by the tensor-core FD kernel when a wait ran out

@@ -490,7 +490,8 @@ extern "C" void dgfas_destroy(void* vctx) {
   if (c->ev_in) cudaEventDestroy(c->ev_in);
   if (c->ev_out) cudaEventDestroy(c->ev_out);
   for (auto& H : c->lv) free_level(H);
-  void* ptrs[] = {c->patch, c->rw, c->red, c->scg_buf, c->dscal, c->dcnt, c->Ainv, c->tc_err};
+  void* ptrs[] = {c->patch, c->rw, c->red, c->scg_buf, c->dscal, c->dcnt, c->Ainv, c->tc_err,
+                  c->apply_scratch};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->red_host) cudaFreeHost(c->red_host);
@@ -593,6 +594,15 @@ extern "C" int dgfas_setup_levels(const dgfas_mesh* mesh, const dgfas_params* pr
   }
   if (rc == DGFAS_OK && (prm->smoother == DGFAS_SCG || prm->coarse == DGFAS_COARSE_SCG))
     rc = dalloc(&c->scg_buf, 4 * maxdof);
+  if (rc == DGFAS_OK) {
+    size_t need = 0;
+    for (const LevelHost& H : c->lv)
+      if (!H.box) need = std::max(need, (size_t)H.ne * (3 * H.N * H.N * H.N + 12 * H.N * H.N));
+    if (need > 0) {
+      rc = dalloc(&c->apply_scratch, need);
+      c->apply_scratch_n = need;
+    }
+  }
   if (rc == DGFAS_OK) rc = dalloc(&c->dscal, 64);
   if (rc == DGFAS_OK) {
     if (cudaMalloc((void**)&c->dcnt, 8 * sizeof(int)) != cudaSuccess ||

@@ -263,6 +263,187 @@ __global__ void __launch_bounds__(256) k_apply_curv_eo(const LevelView<T> L, con
   }
 }
 
+// Two-pass form of the curvilinear operator (FP64, where the operator is
+// bound by the FP64 pipe).  The single-pass kernel evaluates the normal flux
+// of every face twice, once from each side, and for the neighbour's side it
+// needs 3 N multiply-adds per face node.  Here each element evaluates its own
+// faces once:
+//   pass 1 (k_curv_grad): reference gradient (line form), the trace u and the
+//     normal flux q = c . grad u at the nodes of its six faces -> face buffer
+//     [e][6][2][N^2], and the metric F = G grad u -> [e][3][N^3];
+//   pass 2 (k_curv_div): the flux mu W [[u]] - (q_m - q_p)/2 and the lifting
+//     from both sides' face data (the two faces normal to a direction in one
+//     pass, their node sets are disjoint), then the transposed gradient.
+// The arithmetic is the single-pass kernel's, term by term.
+template <int N, typename T, typename TU>
+__global__ void __launch_bounds__(256) k_curv_grad(const LevelView<T> L, const TU* __restrict__ u,
+                                                   T* __restrict__ Fg, T* __restrict__ Fc) {
+  constexpr int N2 = N * N, N3 = N * N * N, H = N / 2, HC = (N + 1) / 2;
+  constexpr int NP3 = CurvLine<N>::NP3;
+  __shared__ CurvEo<N, T> M;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int team = threadIdx.y, tid = threadIdx.y * blockDim.x + threadIdx.x;
+  const int nth = blockDim.x * blockDim.y;
+  T* us = reinterpret_cast<T*>(smem_raw) + (size_t)team * 4 * NP3;
+  T* F[3] = {us + NP3, us + 2 * NP3, us + 3 * NP3};
+  for (int t = tid; t < HC * N; t += nth) {
+    const int r = t / N, q = t % N;
+    const T d1 = L.D[r * N + q], d2 = L.D[r * N + N - 1 - q];
+    if (q < H) {
+      M.de[r][q] = T(0.5) * (d1 + d2);
+      M.dO[r][q] = T(0.5) * (d1 - d2);
+    } else if ((N & 1) && q == H) {
+      M.dm[r] = d1;
+    }
+  }
+  const int e = blockIdx.x * blockDim.y + team;
+  const bool valid = e < L.ne && threadIdx.x < N2;
+  const size_t eo = (size_t)e * N3;
+  if (e < L.ne)
+    for (int t = threadIdx.x; t < N3; t += blockDim.x) us[t + t / N] = (T)u[eo + t];
+  __syncthreads();
+  const int a = threadIdx.x % N, bb = threadIdx.x / N;
+#pragma unroll 1
+  for (int d = 0; d < 3; ++d) {
+    if (!valid) continue;
+    const CurvLine<N> ln(d, a, bb);
+    T x[N], y[N];
+#pragma unroll
+    for (int l = 0; l < N; ++l) x[l] = us[ln.bp + l * ln.sp];
+    acs_line<N, T>(M.de, M.dO, M.dm, x, y);
+#pragma unroll
+    for (int l = 0; l < N; ++l) F[d][ln.bp + l * ln.sp] = y[l];
+  }
+  __syncthreads();
+  if (!valid) return;
+#pragma unroll 1
+  for (int f = 0; f < 6; ++f) {
+    const int d = f >> 1, end = (f & 1) ? N - 1 : 0;
+    const int n = d == 0 ? cpad<N>(end, a, bb) : (d == 1 ? cpad<N>(a, end, bb) : cpad<N>(a, bb, end));
+    const T* fc = L.fc + ((size_t)e * 6 + f) * 3 * N2 + threadIdx.x;
+    T* o = Fc + ((size_t)e * 6 + f) * 2 * N2 + threadIdx.x;
+    o[0] = us[n];
+    o[N2] = ld(fc) * F[0][n] + ld(fc + N2) * F[1][n] + ld(fc + 2 * N2) * F[2][n];
+  }
+  for (int k = 0; k < N; ++k) {
+    const int n = (k * N + bb) * N + a, np = cpad<N>(a, bb, k);
+    const T* G = L.G + (size_t)e * 6 * N3 + n;
+    const T G00 = ld(G), G11 = ld(G + N3), G22 = ld(G + 2 * N3), G01 = ld(G + 3 * N3),
+            G02 = ld(G + 4 * N3), G12 = ld(G + 5 * N3);
+    const T d0 = F[0][np], d1 = F[1][np], d2 = F[2][np];
+    T* fo = Fg + (size_t)e * 3 * N3 + n;
+    fo[0] = G00 * d0 + G01 * d1 + G02 * d2;
+    fo[N3] = G01 * d0 + G11 * d1 + G12 * d2;
+    fo[2 * N3] = G02 * d0 + G12 * d1 + G22 * d2;
+  }
+}
+
+template <int N, typename T, typename TU, typename TB, typename TO>
+__global__ void __launch_bounds__(256) k_curv_div(const LevelView<T> L, const TU* __restrict__ u,
+                                                  const T* __restrict__ Fg,
+                                                  const T* __restrict__ Fc,
+                                                  const TB* __restrict__ b, TO* __restrict__ out,
+                                                  T alpha) {
+  constexpr int N2 = N * N, N3 = N * N * N, H = N / 2, HC = (N + 1) / 2;
+  constexpr int NP3 = CurvLine<N>::NP3;
+  __shared__ CurvEo<N, T> M;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int team = threadIdx.y, tid = threadIdx.y * blockDim.x + threadIdx.x;
+  const int nth = blockDim.x * blockDim.y;
+  T* F0 = reinterpret_cast<T*>(smem_raw) + (size_t)team * 4 * NP3;
+  T* F[3] = {F0, F0 + NP3, F0 + 2 * NP3};
+  T* R = F0 + 3 * NP3;
+  for (int t = tid; t < HC * N; t += nth) {
+    const int r = t / N, q = t % N;
+    const T t1 = L.D[q * N + r], t2 = L.D[(N - 1 - q) * N + r];
+    if (q < H) {
+      M.te[r][q] = T(0.5) * (t1 + t2);
+      M.tO[r][q] = T(0.5) * (t1 - t2);
+    } else if ((N & 1) && q == H) {
+      M.tm[r] = t1;
+    }
+  }
+  const int e = blockIdx.x * blockDim.y + team;
+  const bool valid = e < L.ne && threadIdx.x < N2;
+  const size_t eo = (size_t)e * N3;
+  if (e < L.ne) {
+    const T* fe = Fg + (size_t)e * 3 * N3;
+    for (int t = threadIdx.x; t < N3; t += blockDim.x) {
+      const int tp = t + t / N;
+      F[0][tp] = fe[t];
+      F[1][tp] = fe[N3 + t];
+      F[2][tp] = fe[2 * N3 + t];
+      R[tp] = L.kappa != T(0) ? L.kappa * ld(L.mass + eo + t) * (T)u[eo + t] : T(0);
+    }
+  }
+  __syncthreads();
+  const int a = threadIdx.x % N, bb = threadIdx.x / N;
+  // faces: the two faces normal to direction d in one pass
+#pragma unroll 1
+  for (int d = 0; d < 3; ++d) {
+    if (valid) {
+#pragma unroll
+      for (int side = 0; side < 2; ++side) {
+        const int f = 2 * d + side;
+        const int nbid = L.nbr[6 * e + f];
+        if (nbid == -2) continue;   // Neumann: no face term
+        const int end = side ? N - 1 : 0;
+        const int n = d == 0 ? cpad<N>(end, a, bb) : (d == 1 ? cpad<N>(a, end, bb) : cpad<N>(a, bb, end));
+        const T* own = Fc + ((size_t)e * 6 + f) * 2 * N2 + threadIdx.x;
+        const T um = own[0], qm = own[N2];
+        const T* fcp = L.fc + ((size_t)e * 6 + f) * 3 * N2 + threadIdx.x;
+        const T c0 = ld(fcp), c1 = ld(fcp + N2), c2 = ld(fcp + 2 * N2);
+        const T W = L.nu * ld(L.fW + ((size_t)e * 6 + f) * N2 + threadIdx.x);
+        const T mu = L.mu[6 * e + f];
+        T flux, lift;
+        if (nbid >= 0) {
+          const T* oth = Fc + ((size_t)nbid * 6 + (f ^ 1)) * 2 * N2 + threadIdx.x;
+          const T up = oth[0], qp = oth[N2];
+          const T jump = um - up;
+          flux = mu * W * jump - T(0.5) * (qm - qp);
+          lift = T(-0.5) * jump;
+        } else {   // Dirichlet
+          flux = T(2) * mu * W * um - qm;
+          lift = -um;
+        }
+        R[n] += flux;
+        F[0][n] += c0 * lift;
+        F[1][n] += c1 * lift;
+        F[2][n] += c2 * lift;
+      }
+    }
+    __syncthreads();
+  }
+  // transposed reference gradient, one line per thread and direction
+#pragma unroll 1
+  for (int d = 0; d < 3; ++d) {
+    const CurvLine<N> ln(d, a, bb);
+    T y[N];
+    if (valid) {
+      T x[N];
+#pragma unroll
+      for (int l = 0; l < N; ++l) x[l] = F[d][ln.bp + l * ln.sp];
+      acs_line<N, T>(M.te, M.tO, M.tm, x, y);
+    }
+    if (d < 2) {
+      if (valid) {
+#pragma unroll
+        for (int l = 0; l < N; ++l) R[ln.bp + l * ln.sp] += y[l];
+      }
+      __syncthreads();
+    } else if (valid) {
+      const bool frozen = L.cls[e] == DGFAS_FROZEN;
+#pragma unroll
+      for (int l = 0; l < N; ++l) {
+        const int n = ln.bg + l * ln.sg;
+        T o = alpha * (R[ln.bp + l * ln.sp] + y[l]);
+        if (b) o += (T)b[eo + n];
+        out[eo + n] = frozen ? TO(0) : (TO)o;
+      }
+    }
+  }
+}
+
 // Axis-aligned box elements: the volume term is the exact Kronecker form
 // sum_d g_d (W x W x Lhat_d) u with Lhat = D^T W D; bx[e] = {g_1, g_2, g_3,
 // a_1, a_2, a_3} with g_d = nu h_j h_k / (2 h_d) and a_d = nu h_j h_k / 4 (the
@@ -454,7 +635,7 @@ static int apply_epb_max(int N, size_t tsz) {
 
 template <int N, typename T, typename TU, typename TB, typename TO>
 static int apply_N(const LevelView<T>& L, const TU* u, const TB* b, TO* out, T alpha,
-                   cudaStream_t st, int epb_req) {
+                   cudaStream_t st, int epb_req, T* scratch) {
   constexpr int N2 = N * N, N3 = N * N * N;
   int epb = (128 + N2 - 1) / N2;
   if (epb_req > 0) epb = std::max(1, std::min(epb_req, 256 / N2));
@@ -480,6 +661,32 @@ static int apply_N(const LevelView<T>& L, const TU* u, const TB* b, TO* out, T a
     }
     dim3 blk2(N2, epb2), grd2((L.ne + epb2 - 1) / epb2);
     kf<<<grd2, blk2, smem2, st>>>(L, L.bx, L.Lhat, u, b, out, alpha);
+  } else if (scratch) {
+    // two passes through the scratch (gradient and face data, then fluxes and
+    // the transposed gradient); one element per team of N^2 threads
+    constexpr int NP3 = CurvLine<N>::NP3;
+    int epb4 = (128 + N2 - 1) / N2;
+    if (epb_req > 0) epb4 = std::max(1, std::min(epb_req, 256 / N2));
+    size_t smem4 = (size_t)4 * NP3 * epb4 * sizeof(T);
+    while (epb4 > 1 && smem4 > 100 * 1024) {
+      --epb4;
+      smem4 = (size_t)4 * NP3 * epb4 * sizeof(T);
+    }
+    T* Fg = scratch;
+    T* Fc = scratch + (size_t)L.ne * 3 * N3;
+    auto k1 = k_curv_grad<N, T, TU>;
+    auto k2 = k_curv_div<N, T, TU, TB, TO>;
+    static bool attr = false;
+    if (!attr) {
+      CK(cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024));
+      CK(cudaFuncSetAttribute(k2, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024));
+      attr = true;
+    }
+    dim3 blk4(N2, epb4), grd4((L.ne + epb4 - 1) / epb4);
+    k1<<<grd4, blk4, smem4, st>>>(L, u, Fg, Fc);
+    ++g_kernels;
+    CK(cudaGetLastError());
+    k2<<<grd4, blk4, smem4, st>>>(L, u, Fg, Fc, b, out, alpha);
   } else {
     // line form (even-odd products, own face derivatives from the volume pass)
     int epb3 = (128 + N2 - 1) / N2;
@@ -506,18 +713,18 @@ static int apply_N(const LevelView<T>& L, const TU* u, const TB* b, TO* out, T a
 
 template <typename T, typename TU, typename TB, typename TO>
 static int apply_disp(const LevelView<T>& L, const TU* u, const TB* b, TO* out, T alpha,
-                      cudaStream_t st, int epb = 0) {
+                      cudaStream_t st, int epb = 0, T* scratch = nullptr) {
   switch (L.N) {
-    case 2: return apply_N<2, T, TU, TB, TO>(L, u, b, out, alpha, st, epb);
-    case 3: return apply_N<3, T, TU, TB, TO>(L, u, b, out, alpha, st, epb);
-    case 4: return apply_N<4, T, TU, TB, TO>(L, u, b, out, alpha, st, epb);
-    case 5: return apply_N<5, T, TU, TB, TO>(L, u, b, out, alpha, st, epb);
-    case 6: return apply_N<6, T, TU, TB, TO>(L, u, b, out, alpha, st, epb);
-    case 7: return apply_N<7, T, TU, TB, TO>(L, u, b, out, alpha, st, epb);
-    case 8: return apply_N<8, T, TU, TB, TO>(L, u, b, out, alpha, st, epb);
-    case 9: return apply_N<9, T, TU, TB, TO>(L, u, b, out, alpha, st, epb);
-    case 10: return apply_N<10, T, TU, TB, TO>(L, u, b, out, alpha, st, epb);
-    case 11: return apply_N<11, T, TU, TB, TO>(L, u, b, out, alpha, st, epb);
+    case 2: return apply_N<2, T, TU, TB, TO>(L, u, b, out, alpha, st, epb, scratch);
+    case 3: return apply_N<3, T, TU, TB, TO>(L, u, b, out, alpha, st, epb, scratch);
+    case 4: return apply_N<4, T, TU, TB, TO>(L, u, b, out, alpha, st, epb, scratch);
+    case 5: return apply_N<5, T, TU, TB, TO>(L, u, b, out, alpha, st, epb, scratch);
+    case 6: return apply_N<6, T, TU, TB, TO>(L, u, b, out, alpha, st, epb, scratch);
+    case 7: return apply_N<7, T, TU, TB, TO>(L, u, b, out, alpha, st, epb, scratch);
+    case 8: return apply_N<8, T, TU, TB, TO>(L, u, b, out, alpha, st, epb, scratch);
+    case 9: return apply_N<9, T, TU, TB, TO>(L, u, b, out, alpha, st, epb, scratch);
+    case 10: return apply_N<10, T, TU, TB, TO>(L, u, b, out, alpha, st, epb, scratch);
+    case 11: return apply_N<11, T, TU, TB, TO>(L, u, b, out, alpha, st, epb, scratch);
   }
   set_error("apply: unsupported N");
   return DGFAS_ERR_UNSUPPORTED;
@@ -527,8 +734,13 @@ static int apply_disp(const LevelView<T>& L, const TU* u, const TB* b, TO* out, 
 int launch_apply(Ctx& c, int l, int prec, const double* u, const double* b, void* out,
                  double alpha) {
   (void)prec;
-  return apply_disp<double, double, double, double>(c.lv[l].v64, u, b, (double*)out, alpha,
-                                                    c.stream, c.lv[l].tune.apply64);
+  LevelHost& H = c.lv[l];
+  // curvilinear levels use the two-pass form when the context holds its scratch
+  double* scratch = (!H.box && c.apply_scratch &&
+                     (size_t)H.ne * (3 * H.N * H.N * H.N + 12 * H.N * H.N) <= c.apply_scratch_n)
+                        ? c.apply_scratch : nullptr;
+  return apply_disp<double, double, double, double>(H.v64, u, b, (double*)out, alpha, c.stream,
+                                                    H.tune.apply64, scratch);
 }
 
 // Smoother-precision operator on a correction: out = b - A delta with b FP64,
@@ -537,9 +749,14 @@ int launch_apply(Ctx& c, int l, int prec, const double* u, const double* b, void
 int launch_apply_corr(Ctx& c, int l, int prec, const void* delta, const double* b, void* out,
                       int out_fp64) {
   LevelHost& H = c.lv[l];
-  if (prec == DGFAS_FP64)
+  if (prec == DGFAS_FP64) {
+    double* scratch = (!H.box && c.apply_scratch &&
+                       (size_t)H.ne * (3 * H.N * H.N * H.N + 12 * H.N * H.N) <= c.apply_scratch_n)
+                          ? c.apply_scratch : nullptr;
     return apply_disp<double, double, double, double>(H.v64, (const double*)delta, b,
-                                                      (double*)out, -1.0, c.stream, H.tune.apply64);
+                                                      (double*)out, -1.0, c.stream, H.tune.apply64,
+                                                      scratch);
+  }
   if (out_fp64)
     return apply_disp<float, float, double, double>(H.v32, (const float*)delta, b, (double*)out,
                                                     -1.0f, c.stream, H.tune.apply32);
