@@ -64,9 +64,12 @@ def apply_flops_per_dof(N, box=True):
 
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
-# dominant kernel on this workload, from one ncu capture of the current kernel
-# (32^3 elements, p = 8, BF16 smoother run); to be retaken whenever the kernel changes
-NCU_TRAFFIC = {"residual_fp64": 387000320 + 168229632}
+# dominant kernel, from one ncu capture of the current kernels on a 16^3,
+# p = 7 curvilinear case (2,097,152 DoF, vectors and geometry larger than L2:
+# k_curv_grad 155.3 + 48.1 MB, k_curv_div 143.0 + 9.5 MB), scaled by the DoF
+# of the 64^3 level (x 64; the per-element data grow in proportion); to be
+# retaken whenever the kernels change
+NCU_TRAFFIC = {"residual_fp64": int((155259136 + 48112640 + 142958080 + 9480960) * 64)}
 
 
 def fd_flops_per_dof(N, m):
@@ -625,9 +628,29 @@ def run_gpu(args):
                                 if kd["bound"] == "alu" else f"{pk['src']} HBM copy (MEASURED_PEAKS.json)")}
 
     # ---- time to 1e-10: the headline arm, then the plain FP64 GPU path
-    tts = {"mixed_learned" if not args.geometric else "mixed_geometric":
-           solve_record(S, u0.clone(), b, torch)}
-    tts[next(iter(tts))]["ms_per_vcycle"] = ms
+    head = "mixed_learned" if not args.geometric else "mixed_geometric"
+    tts = {head: solve_record(S, u0.clone(), b, torch)}
+    tts[head]["ms_per_vcycle"] = ms
+    if not args.skip_fmg:
+        # the same target (1e-10 of the random start's residual) from the full
+        # multigrid start value (Alg. 4); the per-level right-hand sides are
+        # problem set-up, outside the timing
+        rr = torch.empty_like(b)
+        S.dgfas_apply_op(-1, u0, b, rr)
+        r_rand = S.dgfas_norm(-1, rr)
+        f_lv = level_rhs(S, cfg, torch)
+        uf = torch.zeros_like(u0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        S.dgfas_fmg(f_lv, uf)
+        S.dgfas_apply_op(-1, uf, b, rr)
+        r_fmg = S.dgfas_norm(-1, rr)
+        info = S.dgfas_solve(uf, b, 1e-10 * r_rand / r_fmg, 40, raise_on_fail=False)
+        torch.cuda.synchronize()
+        tts[head + "_fmg"] = {"seconds": time.perf_counter() - t0, "cycles": info["cycles"],
+                              "rel_residual": info["r_final"] / r_rand, "code": info["code"],
+                              "fmg_start_rel_residual": r_fmg / r_rand}
+        del f_lv, uf, rr
     S.close()
     torch.cuda.empty_cache()
     arms = []
@@ -722,6 +745,7 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-others", action="store_true")
     ap.add_argument("--skip-geometric", action="store_true")
+    ap.add_argument("--skip-fmg", action="store_true")
     ap.add_argument("--geometric", action="store_true",
                     help="headline with the geometric instead of the learned surrogate")
     ap.add_argument("--no-autotune", action="store_true",

@@ -109,8 +109,9 @@ struct Ctx {
   cudaStream_t cap = nullptr;   // internal stream for graph capture / replay
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
   int red_blocks = 0;           // CTAs of the reductions: 4 per SM of the device
-  double* red = nullptr;        // reduction partials [3 * red_blocks + 64]: norms use
-                                // [0, G), SCG's scalar products [G, 3G)
+  double* red = nullptr;        // reduction partials [5 * red_blocks + 64]: norms use
+                                // [0, G), SCG's scalar products [G, 5G) (2G CTAs, two
+                                // sums each), G = red_blocks
   double* red_host = nullptr;   // pinned
   double* scg_buf = nullptr;    // SCG vectors (p, q, z, r0) for the largest level
   double* apply_scratch = nullptr;   // two-pass FP64 curvilinear operator: F [e][3][N^3]
@@ -170,7 +171,10 @@ int launch_rhs(Ctx& c, int l, const double* f, const double* uD, double* b);
 int launch_sumsq_leaf(Ctx& c, int l, const double* v, double* part);
 int launch_leaf_rhs(Ctx& c, int l, const double* f, double* g);
 int launch_to_float(Ctx& c, const double* x, float* y, long long n);
-// scg.cu: Alg. 6 with device-resident scalars (no host synchronization)
+// scg.cu: Alg. 6 with device-resident scalars (no host synchronization);
+// the SCG work buffer holds 4 FP64 (or 5 FP32) vectors of the largest level,
+// each followed by kScgPad doubles of padding
+constexpr long long kScgPad = 768;
 int scg_run(Ctx& c, int l, double* u, int n, double rtol, int prec, bool pending = false,
             bool want_res = false, bool fp64_vectors = false);
 extern std::atomic<long long> g_kernels;   // kernels launched (graph replays included)

@@ -587,13 +587,13 @@ extern "C" int dgfas_setup_levels(const dgfas_mesh* mesh, const dgfas_params* pr
     set_error("stream/event creation");
     rc = DGFAS_ERR_CUDA;
   }
-  if (rc == DGFAS_OK) rc = dalloc(&c->red, 3 * c->red_blocks + 64);
-  if (rc == DGFAS_OK && cudaMallocHost((void**)&c->red_host, (3 * c->red_blocks + 64) * sizeof(double)) != cudaSuccess) {
+  if (rc == DGFAS_OK) rc = dalloc(&c->red, 5 * c->red_blocks + 64);
+  if (rc == DGFAS_OK && cudaMallocHost((void**)&c->red_host, (5 * c->red_blocks + 64) * sizeof(double)) != cudaSuccess) {
     set_error("pinned host buffer");
     rc = DGFAS_ERR_OOM;
   }
   if (rc == DGFAS_OK && (prm->smoother == DGFAS_SCG || prm->coarse == DGFAS_COARSE_SCG))
-    rc = dalloc(&c->scg_buf, 4 * maxdof);
+    rc = dalloc(&c->scg_buf, 4 * (maxdof + kScgPad) + 64);
   if (rc == DGFAS_OK) {
     size_t need = 0;
     for (const LevelHost& H : c->lv)

@@ -274,9 +274,7 @@ __device__ __forceinline__ void tc_read1(uint32_t tmem, int t, float* v) {
 // TN, TM > 0: instantiation for N = TN nodes and TM overlap layers, whose
 // gather resolves the row's three source segments at compile time; TN = 0:
 // any N and m (per-position gather maps).
-// VEC (TN a multiple of 4, TM even, r 16-byte aligned): the row's own
-// segment is read with 16-byte loads and the overlap layers with 8-byte loads.
-template <int TN, int TM, bool VEC = false>
+template <int TN, int TM>
 __global__ void __launch_bounds__(128, 8) k_fd_tc(const LevelView<float> L, const float* __restrict__ r,
                                                   float* __restrict__ patch, int* __restrict__ err) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -362,37 +360,7 @@ __global__ void __launch_bounds__(128, 8) k_fd_tc(const LevelView<float> L, cons
           const float* p1 = nb[1] >= 0 ? r + (long long)nb[1] * N3 + line : nullptr;
           const float* p2 = nb[2] >= 0 ? r + (long long)nb[2] * N3 + line : nullptr;
           const bool li = (v1 >> 2) == 0, ri = (v1 & 3) == 0;
-          if constexpr (VEC) {
-            static_assert(TN % 4 == 0 && TM % 2 == 0 && TN + 2 * TM <= 16, "vector gather");
-            // element offsets are multiples of TN^3 floats and lines of TN
-            // floats, so the own segment starts on 16 bytes, the left layers
-            // (TN - TM floats in) and the right ones on 8 bytes
-            float own[TN], lft[TM], rgt[TM];
-#pragma unroll
-            for (int q = 0; q < TN / 4; ++q) {
-              const float4 v4 = p1 ? __ldg(reinterpret_cast<const float4*>(p1) + q)
-                                   : make_float4(0.f, 0.f, 0.f, 0.f);
-              own[4 * q] = v4.x; own[4 * q + 1] = v4.y; own[4 * q + 2] = v4.z; own[4 * q + 3] = v4.w;
-            }
-#pragma unroll
-            for (int q = 0; q < TM / 2; ++q) {
-              const float2 a2 = (li && p0) ? __ldg(reinterpret_cast<const float2*>(p0 + TN - TM) + q)
-                                           : make_float2(0.f, 0.f);
-              const float2 b2 = (ri && p2) ? __ldg(reinterpret_cast<const float2*>(p2) + q)
-                                           : make_float2(0.f, 0.f);
-              lft[2 * q] = a2.x; lft[2 * q + 1] = a2.y;
-              rgt[2 * q] = b2.x; rgt[2 * q + 1] = b2.y;
-            }
-            const int o = li ? TM : 0;
-#pragma unroll
-            for (int a = 0; a < TM; ++a) vals[a] = li ? lft[a] : own[a];
-#pragma unroll
-            for (int a = 0; a < TN; ++a)
-              if (a >= TM || li) vals[o + a] = own[a];
-#pragma unroll
-            for (int a = 0; a < TM; ++a)
-              if (ri) vals[o + TN + a] = rgt[a];
-          } else if (li) {
+          if (li) {
 #pragma unroll
             for (int a = 0; a < TM; ++a) vals[a] = p0 ? p0[TN - TM + a] : 0.0f;
 #pragma unroll
@@ -528,9 +496,7 @@ int launch_fd_tc(Ctx& c, int l, const float* r) {
   int rc;
   const int key = 16 * H.N + H.m;
   switch (key) {
-    case 16 * 8 + 2:
-      rc = ((uintptr_t)r & 15) == 0 ? go(k_fd_tc<8, 2, true>) : go(k_fd_tc<8, 2>);
-      break;
+    case 16 * 8 + 2: rc = go(k_fd_tc<8, 2>); break;
     case 16 * 9 + 2: rc = go(k_fd_tc<9, 2>); break;
     case 16 * 10 + 2: rc = go(k_fd_tc<10, 2>); break;
     case 16 * 11 + 2: rc = go(k_fd_tc<11, 2>); break;

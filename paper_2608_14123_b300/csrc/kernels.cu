@@ -743,6 +743,15 @@ int launch_apply(Ctx& c, int l, int prec, const double* u, const double* b, void
                                                     H.tune.apply64, scratch);
 }
 
+// The two-pass scratch of a curvilinear level in FP32 (the context's FP64
+// scratch holds twice the floats the level needs), or null.
+static float* scratch32(Ctx& c, int l) {
+  LevelHost& H = c.lv[l];
+  return (!H.box && c.apply_scratch &&
+          (size_t)H.ne * (3 * H.N * H.N * H.N + 12 * H.N * H.N) <= c.apply_scratch_n)
+             ? (float*)c.apply_scratch : nullptr;
+}
+
 // Smoother-precision operator on a correction: out = b - A delta with b FP64,
 // delta and the arithmetic in the smoother precision, out in the smoother
 // precision (out_fp64 = 0) or FP64 (out_fp64 = 1).
@@ -757,11 +766,12 @@ int launch_apply_corr(Ctx& c, int l, int prec, const void* delta, const double* 
                                                       (double*)out, -1.0, c.stream, H.tune.apply64,
                                                       scratch);
   }
+  float* s32 = scratch32(c, l);
   if (out_fp64)
     return apply_disp<float, float, double, double>(H.v32, (const float*)delta, b, (double*)out,
-                                                    -1.0f, c.stream, H.tune.apply32);
+                                                    -1.0f, c.stream, H.tune.apply32, s32);
   return apply_disp<float, float, double, float>(H.v32, (const float*)delta, b, (float*)out,
-                                                 -1.0f, c.stream, H.tune.apply32);
+                                                 -1.0f, c.stream, H.tune.apply32, s32);
 }
 
 // ============================================================================ FD
@@ -1374,7 +1384,7 @@ int launch_combine_to32(Ctx& c, int l, float* z) {
 int launch_apply32(Ctx& c, int l, const float* u, float* out) {
   LevelHost& H = c.lv[l];
   return apply_disp<float, float, double, float>(H.v32, u, nullptr, out, 1.0f, c.stream,
-                                                 H.tune.apply32);
+                                                 H.tune.apply32, scratch32(c, l));
 }
 
 // ============================================================================ transfers

@@ -72,16 +72,37 @@ __device__ bool partials_and_ticket(double (&v)[K], double* part, int* counter,
   return true;
 }
 
+// Per-thread sum of products in the vectors' precision: FP64 for FP64
+// vectors; for FP32 vectors a compensated (Kahan) FP32 sum, widened to FP64
+// once per thread - B300's FP64 rate is 1/62 of its FP32 rate, so FP64
+// products per element would bound these streaming kernels.
+template <typename T>
+struct Acc {
+  double s = 0.0;
+  __device__ __forceinline__ void add(T a, T b) { s += (double)a * (double)b; }
+  __device__ __forceinline__ double get() const { return s; }
+};
+template <>
+struct Acc<float> {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(float a, float b) {
+    const float y = __fmaf_rn(a, b, -c);
+    const float t = s + y;
+    c = (t - s) - y;
+    s = t;
+  }
+  __device__ __forceinline__ double get() const { return (double)s - (double)c; }
+};
+
 // |r|^2 of the start residual: r_max^2 = rtol^2 |r|^2, done = (r == 0), steps = 0
 template <typename T>
 __global__ void k_scg_init(const T* __restrict__ r, long long n, double rtol2, double* part,
                            int* counter, double* scal) {
-  double v[1] = {0.0};
+  Acc<T> a0;
   for (long long i = (long long)blockIdx.x * kThreads + threadIdx.x; i < n;
-       i += (long long)gridDim.x * kThreads) {
-    const double ri = r[i];
-    v[0] += ri * ri;
-  }
+       i += (long long)gridDim.x * kThreads)
+    a0.add(r[i], r[i]);
+  double v[1] = {a0.get()};
   double t[1];
   if (partials_and_ticket<1>(v, part, counter, t) && threadIdx.x == 0) {
     scal[S_RR] = t[0];
@@ -107,7 +128,7 @@ template <typename T, bool FIRST>
 __global__ void k_scg_zr(const T* __restrict__ z, const T* __restrict__ r,
                          const T* __restrict__ r0, long long n, double* part, int* counter,
                          double* scal) {
-  double v[2] = {0.0, 0.0};
+  Acc<T> a0, a1;
   const long long S = (long long)gridDim.x * kThreads;
   long long i = (long long)blockIdx.x * kThreads + threadIdx.x;
   // four independent strided elements per iteration keep more loads in flight
@@ -121,15 +142,15 @@ __global__ void k_scg_zr(const T* __restrict__ z, const T* __restrict__ r,
     }
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-      v[0] += (double)zz[u] * (double)rr[u];
-      if (!FIRST) v[1] += (double)zz[u] * (double)qq[u];
+      a0.add(zz[u], rr[u]);
+      if (!FIRST) a1.add(zz[u], qq[u]);
     }
   }
   for (; i < n; i += S) {
-    const double zi = z[i];
-    v[0] += zi * (double)r[i];
-    if (!FIRST) v[1] += zi * (double)r0[i];
+    a0.add(z[i], r[i]);
+    if (!FIRST) a1.add(z[i], r0[i]);
   }
+  double v[2] = {a0.get(), a1.get()};
   double t[2];
   if (partials_and_ticket<2>(v, part, counter, t) && threadIdx.x == 0) {
     const bool done = scal[S_DONE] != 0.0;
@@ -162,7 +183,7 @@ __global__ void k_scg_dir(T* __restrict__ p, const T* __restrict__ z, long long 
 template <typename T>
 __global__ void k_scg_pq(const T* __restrict__ p, const T* __restrict__ q, long long n,
                          double* part, int* counter, double* scal) {
-  double v[1] = {0.0};
+  Acc<T> a0;
   const long long S = (long long)gridDim.x * kThreads;
   long long i = (long long)blockIdx.x * kThreads + threadIdx.x;
   for (; i + 3 * S < n; i += 4 * S) {
@@ -173,9 +194,10 @@ __global__ void k_scg_pq(const T* __restrict__ p, const T* __restrict__ q, long 
       qq[u] = q[i + u * S];
     }
 #pragma unroll
-    for (int u = 0; u < 4; ++u) v[0] += (double)pp[u] * (double)qq[u];
+    for (int u = 0; u < 4; ++u) a0.add(pp[u], qq[u]);
   }
-  for (; i < n; i += S) v[0] += (double)p[i] * (double)q[i];
+  for (; i < n; i += S) a0.add(p[i], q[i]);
+  double v[1] = {a0.get()};
   double t[1];
   if (partials_and_ticket<1>(v, part, counter, t) && threadIdx.x == 0) {
     scal[S_PQ] = t[0];
@@ -192,7 +214,7 @@ __global__ void k_scg_update(T* __restrict__ r, T* __restrict__ r0, T* __restric
                              const T* __restrict__ p, const T* __restrict__ q, long long n,
                              double* part, int* counter, double* scal, double* __restrict__ uout) {
   const T alpha = (T)scal[S_ALPHA];
-  double v[1] = {0.0};
+  Acc<T> a0;
   const long long S = (long long)gridDim.x * kThreads;
   long long i = (long long)blockIdx.x * kThreads + threadIdx.x;
   for (; i + 3 * S < n; i += 4 * S) {
@@ -212,7 +234,7 @@ __global__ void k_scg_update(T* __restrict__ r, T* __restrict__ r0, T* __restric
       const T xn = xx[u] + alpha * pp[u];
       if (uout) uout[i + u * S] += (double)xn;
       else x[i + u * S] = xn;
-      v[0] += (double)rn * (double)rn;
+      a0.add(rn, rn);
     }
   }
   for (; i < n; i += S) {
@@ -223,8 +245,9 @@ __global__ void k_scg_update(T* __restrict__ r, T* __restrict__ r0, T* __restric
     const T xn = x[i] + alpha * p[i];
     if (uout) uout[i] += (double)xn;
     else x[i] = xn;
-    v[0] += (double)rn * (double)rn;
+    a0.add(rn, rn);
   }
+  double v[1] = {a0.get()};
   double t[1];
   if (partials_and_ticket<1>(v, part, counter, t) && threadIdx.x == 0) {
     if (scal[S_DONE] == 0.0) {
@@ -287,10 +310,12 @@ static int scg_steps(Ctx& c, int l, int prec, T* x, T* r, T* p, T* q, T* z, T* r
   const long long nd = c.lv[l].ndof;
   double* scal = c.dscal;
   int* cnt = c.dcnt;
-  const int G = c.red_blocks;
-  // SCG's partial sums live past the first G entries of the reduction buffer,
-  // which hold the cycle's residual norm partials until the host reads them
-  double* part = c.red + G;
+  // 8 CTAs of 256 threads per SM for the streaming kernels; their partial
+  // sums (two per CTA at most) live past the first red_blocks entries of the
+  // reduction buffer, which hold the cycle's residual norm partials until the
+  // host reads them
+  const int G = 2 * c.red_blocks;
+  double* part = c.red + c.red_blocks;
   if (rtol > 0.0) {
     k_scg_init<T><<<G, kThreads, 0, c.stream>>>(r, nd, rtol * rtol, part, cnt, scal);
   } else {
@@ -348,16 +373,21 @@ int scg_run(Ctx& c, int l, double* u, int n, double rtol, int prec, bool pending
     set_error("scg: no SCG work vectors (context not set up for SCG)");
     return DGFAS_ERR_INVALID;
   }
+  // consecutive work vectors are staggered by a few KB (kScgPad doubles) so
+  // that the same index of the streams does not fall at the same offset of a
+  // large power of two (the vectors of a big level are 2^29 bytes long)
   if (prec == DGFAS_FP64 || fp64_vectors) {
     if (pending) {
       set_error("scg: a pending correction needs the smoother-precision path");
       return DGFAS_ERR_INVALID;
     }
-    double *p = c.scg_buf, *q = p + nd, *z = q + nd, *r0 = z + nd;
+    const long long s = nd + kScgPad;
+    double *p = c.scg_buf, *q = p + s, *z = q + s, *r0 = z + s;
     return scg_steps<double>(c, l, prec, u, H.r, p, q, z, r0, n, rtol);
   }
   float* d = (float*)H.delta;
-  float *r = (float*)c.scg_buf, *p = r + nd, *q = p + nd, *z = q + nd, *r0 = z + nd;
+  const long long s = nd + 2 * kScgPad;
+  float *r = (float*)c.scg_buf, *p = r + s, *q = p + s, *z = q + s, *r0 = z + s;
   int rc = DGFAS_OK;
   if (pending) {
     rc = launch_apply_corr(c, l, prec, d, H.r, r, 0);   // r = r_u - A d
@@ -397,8 +427,8 @@ extern "C" int dgfas_profile_scg(void* ctx, int level, double* u, const double* 
   LevelHost& H = c->lv[level];
   const long long nd = H.ndof;
   const int prec = c->prm.precision;
-  const int G = c->red_blocks;
-  double* part = c->red + G;
+  const int G = 2 * c->red_blocks;
+  double* part = c->red + c->red_blocks;
   cudaEvent_t ev[7];
   for (auto& e : ev)
     if (cudaEventCreate(&e) != cudaSuccess) return DGFAS_ERR_CUDA;
@@ -443,7 +473,8 @@ extern "C" int dgfas_profile_scg(void* ctx, int level, double* u, const double* 
   };
   if (rc == DGFAS_OK) {
     if (prec == DGFAS_FP64) {
-      double *p = c->scg_buf, *q = p + nd, *z = q + nd, *r0 = z + nd;
+      const long long s = nd + kScgPad;
+      double *p = c->scg_buf, *q = p + s, *z = q + s, *r0 = z + s;
       cudaMemcpyAsync(r0, H.r, nd * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
       cudaMemcpyAsync(p, H.r, nd * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
       cudaMemcpyAsync(H.delta, u, nd * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
@@ -451,7 +482,8 @@ extern "C" int dgfas_profile_scg(void* ctx, int level, double* u, const double* 
       // u stays as it was
       rc = step((double*)H.delta, H.r, p, q, z, r0);
     } else {
-      float *r = (float*)c->scg_buf, *p = r + nd, *q = p + nd, *z = q + nd, *r0 = z + nd;
+      const long long s = nd + 2 * kScgPad;
+      float *r = (float*)c->scg_buf, *p = r + s, *q = p + s, *z = q + s, *r0 = z + s;
       cudaMemsetAsync(H.delta, 0, nd * sizeof(float), c->stream);
       rc = launch_to_float(*c, H.r, r, nd);
       cudaMemcpyAsync(r0, r, nd * sizeof(float), cudaMemcpyDeviceToDevice, c->stream);
