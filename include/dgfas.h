@@ -169,6 +169,13 @@ int dgfas_get_level_solution(void* ctx, int level, double* u);
    [ndof] device; out must not alias u. */
 int dgfas_apply_op(void* ctx, int level, const double* u, const double* g, double* out);
 
+/* The smoother-precision operator of the same equation: out = g - A u (g != NULL)
+   or A u (g == NULL) with u, out and the arithmetic in FP32 and g FP64; the
+   form every FP32 / BF16 smoother applies to its corrections (on curvilinear
+   levels the metric is recomputed in FP32 from the trilinear map).  u, out
+   [ndof] FP32, g [ndof] FP64, all device; out must not alias u. */
+int dgfas_apply_op32(void* ctx, int level, const float* u, const double* g, float* out);
+
 /* n sweeps of the level smoother (Alg. 5 WAS, or Alg. 6 SCG if selected) on
    A u = g: each WAS sweep computes r = g - A u and adds the weighted Schwarz
    correction sum_e R_s^T W^e (A~_s^e)^-1 R_s r of Eq. (11); frozen entries of u
@@ -223,6 +230,14 @@ int dgfas_profile_sweep(void* ctx, int level, double* u, const double* g, int re
    the level's work vectors are scratch afterwards.  INVALID unless the
    context was set up with SCG (smoother or root). */
 int dgfas_profile_scg(void* ctx, int level, double* u, const double* g, int reps, double* ms_out);
+
+/* Outcome of the last SCG block run on the context's stream (the root solve of
+   the last V-cycle when the root solver is DGFAS_COARSE_SCG): out_host[0] =
+   |r|^2 when its exit test last ran, out_host[1] = the steps taken before the
+   test |r| <= root_rtol |r_start| held (the step cap if it never did),
+   out_host[2] = 1 if it held, 0 if the visit ended at its step cap.
+   Synchronizes the stream. */
+int dgfas_scg_info(void* ctx, double* out_host);
 
 /* Full multigrid startup (FAS-FMG, Alg. 4): the root is solved exactly for
    its own right-hand side f_levels[0]; then for l = 1 .. L-1 the root's (or

@@ -21,11 +21,12 @@ def cut_cells(spec, n, cells):
 
 
 def level_rhs(S, spec):
-    """Per-level right-hand sides (leaf rows use them below the top) and the
-    top one, assembled on the GPU from the exact f and u_D."""
+    """Per-level right-hand sides, assembled on the GPU from the exact f and
+    u_D, root first; the ones below the top are also handed to the library
+    (their leaf rows use them)."""
     import torch
     L = S.n_levels - 1
-    top = None
+    out = []
     for l in range(S.n_levels):
         xyz = S.node_coords(l).cpu().numpy()
         fn = torch.from_numpy(wl.eval_front_f(spec, xyz)).cuda()
@@ -34,8 +35,8 @@ def level_rhs(S, spec):
         S.dgfas_assemble_rhs_level(l, fn, un, b)
         if l < L:
             S.dgfas_set_level_rhs(l, b)
-        top = b
-    return top
+        out.append(b)
+    return out
 
 
 def indicators(S, spec, u_top):
@@ -81,10 +82,14 @@ def new_marks(levels, marks, ind, base, max_ref, spec, n_base, frac=0.7):
     return marks
 
 
-def run(spec, n_base=4, p=3, n_root=2, max_ref=2, rounds=3, cycles=3, mu_star=5.0,
-        delta=0.08, s=(2, 2, 2), precision=dgfas.DGFAS_FP64):
+def run(spec, n_base=4, p=3, n_root=2, max_ref=2, rounds=3, cycles=2, mu_star=5.0,
+        delta=0.08, s=(2, 2, 2), precision=dgfas.DGFAS_FP64, smoother=dgfas.DGFAS_SCG,
+        start="fmg"):
     """The loop; returns one record per round (closed marks, leaf elements per
-    level, composite energy norm of the error) and the final marks."""
+    level, composite energy norm of the error) and the final marks.  Each
+    round solves as the paper's loop does: the full multigrid startup (Alg. 4)
+    and `cycles` = 2 FAS V-cycles with the SCG(2, 2, 2) smoother (start =
+    "zero": the cycles from u = 0 instead)."""
     import torch
     marks = [cut_cells(spec, n_base, {(x, y, z) for z in range(n_base) for y in range(n_base)
                                        for x in range(n_base)})]
@@ -93,11 +98,13 @@ def run(spec, n_base=4, p=3, n_root=2, max_ref=2, rounds=3, cycles=3, mu_star=5.
         marks = wl.close_marks(marks, n_base)
         levels = wl.hierarchy_from_marks(marks, n_base=n_base, p=p, n_root=n_root)
         base = len(levels) - 1 - len(marks)
-        S = dgfas.Solver(levels, mu_star, delta, *s, precision=precision)
+        S = dgfas.Solver(levels, mu_star, delta, *s, precision=precision, smoother=smoother)
         try:
-            b = level_rhs(S, spec)
-            u = torch.zeros_like(b)
-            S.dgfas_solve(u, b, 1e-300, cycles, raise_on_fail=False)   # exactly `cycles` cycles
+            f = level_rhs(S, spec)
+            u = torch.zeros_like(f[-1])
+            if start == "fmg":
+                S.dgfas_fmg(f, u, 1)
+            S.dgfas_solve(u, f[-1], 1e-300, cycles, raise_on_fail=False)   # exactly `cycles` cycles
             ind = indicators(S, spec, u)
         finally:
             S.close()

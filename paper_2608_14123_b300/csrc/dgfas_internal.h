@@ -28,6 +28,12 @@ struct LevelView {
   const T* fc;                // [ne][6][3][N^2] W n . grad xi_t (general)
   const T* mu;                // [ne][6] face penalty
   const T* mass;              // [ne][N^3] lumped mass (kappa != 0, general) or null
+  const T* tri;               // [ne][24] trilinear map x = a0 + a1 xi + a2 eta + a3 zeta
+                              // + a4 xi eta + a5 xi zeta + a6 eta zeta + a7 xi eta zeta:
+                              // a1..a7 (x, y, z each) and 3 pad (general levels)
+  const void* coff;           // [ne][27] combine offsets (int, or long long when
+                              // ne NS^3 >= 2^31): patch index of the element's node
+                              // (0,0,0) in neighbour slot s's patch, or the minimum
   const T* D;                 // [N][N]
   const T* w;                 // [N] GLL weights
   const T* x;                 // [N] GLL nodes
@@ -81,6 +87,11 @@ struct LevelHost {
   float *f_h = nullptr, *f_G = nullptr, *f_fW = nullptr, *f_fc = nullptr, *f_mu = nullptr,
         *f_mass = nullptr, *f_D = nullptr, *f_w = nullptr, *f_g = nullptr, *f_S = nullptr,
         *f_lam = nullptr, *f_W = nullptr, *f_x = nullptr;
+  double* d_tri = nullptr;
+  float* f_tri = nullptr;
+  int* d_coff32 = nullptr;          // combine offsets (one of the two)
+  long long* d_coff64 = nullptr;
+  bool coff32 = true;
   uint4* d_Btc = nullptr;                  // BF16 FD operand tiles per variant
   double *d_I = nullptr, *d_P = nullptr;   // transfer from level-1 to this level
   // work vectors

@@ -1,6 +1,7 @@
 // C ABI of the hot path: level setup, operator, smoother, FAS V-cycle (Alg. 2)
 // and solve with crossover smoothing; CUDA-graph replay of the cycle body.
 #include <algorithm>
+#include <limits>
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -214,6 +215,43 @@ static int build_level(Ctx& c, const dgfas_level& in, const dgfas_params& prm, L
     g[4 * e] = c.kappa * dx[0] * dx[1] * dx[2] / 8.0;
     for (int i = 0; i < 3; ++i) g[4 * e + 1 + i] = nu * dx[(i + 1) % 3] * dx[(i + 2) % 3] / (2.0 * dx[i]);
   }
+  // combine offsets: for element e and neighbour slot (ox, oy, oz) the patch
+  // index of e's node (0, 0, 0) inside that neighbour's weighted patch (the
+  // neighbour's index NS^3 plus the shift of e's nodes in its subdomain), or
+  // the sentinel (the type's minimum) when the slot contributes nothing: no
+  // neighbour, a frozen one, or a side of the neighbour without layers
+  {
+    const long long NS3 = (long long)nsm * nsm * nsm;
+    std::vector<long long> off(27 * (size_t)ne, std::numeric_limits<long long>::min());
+    for (int e = 0; e < ne; ++e)
+      for (int slot = 0; slot < 27; ++slot) {
+        const int src = H.nbr27[27 * (size_t)e + slot];
+        if (src < 0 || H.cls[src] == DGFAS_FROZEN) continue;
+        const int o[3] = {slot % 3 - 1, (slot / 3) % 3 - 1, slot / 9 - 1};
+        int shift[3];
+        bool reach = true;
+        for (int d = 0; d < 3; ++d) {
+          const int v = var[3 * (size_t)src + d];
+          const bool left_i = (v >> 2) == 0, right_i = (v & 3) == 0;
+          const int ml = left_i ? H.m : 0;   // the neighbour's left layers
+          if ((o[d] < 0 && !right_i) || (o[d] > 0 && !left_i)) reach = false;
+          shift[d] = o[d] == 0 ? ml : (o[d] < 0 ? ml + N : -(N - H.m));
+        }
+        if (reach)
+          off[27 * (size_t)e + slot] =
+              (long long)src * NS3 + ((long long)shift[2] * nsm + shift[1]) * nsm + shift[0];
+      }
+    H.coff32 = (long long)ne * NS3 < (1LL << 31);
+    if (H.coff32) {
+      std::vector<int> o32(off.size());
+      for (size_t t = 0; t < off.size(); ++t)
+        o32[t] = off[t] == std::numeric_limits<long long>::min() ? std::numeric_limits<int>::min()
+                                                                  : (int)off[t];
+      RET(upload(&H.d_coff32, o32));
+    } else {
+      RET(upload(&H.d_coff64, off));
+    }
+  }
   // ---- uploads
   RET(upload(&H.d_nbr, H.nbr));
   RET(upload(&H.d_nbr27, H.nbr27));
@@ -256,6 +294,20 @@ static int build_level(Ctx& c, const dgfas_level& in, const dgfas_params& prm, L
     RET(upload(&H.d_bx, bx));
     RET(upload_f(&H.f_bx, bx));
   } else {
+    // coefficients of the trilinear map in monomial form (the FP32 operator
+    // recomputes the metric from them instead of reading it)
+    std::vector<double> tri(24 * (size_t)ne, 0.0);
+    for (int e = 0; e < ne; ++e)
+      for (int c = 0; c < 8; ++c) {
+        const double s0 = (c & 1) ? 1.0 : -1.0, s1 = (c & 2) ? 1.0 : -1.0,
+                     s2 = (c & 4) ? 1.0 : -1.0;
+        const double sg[7] = {s0, s1, s2, s0 * s1, s0 * s2, s1 * s2, s0 * s1 * s2};
+        for (int k = 0; k < 7; ++k)
+          for (int a = 0; a < 3; ++a)
+            tri[24 * (size_t)e + 3 * k + a] += 0.125 * sg[k] * H.corners[24 * (size_t)e + 3 * c + a];
+      }
+    RET(upload(&H.d_tri, tri));
+    RET(upload_f(&H.f_tri, tri));
     RET(upload(&H.d_G, G));
     RET(upload(&H.d_fW, fW));
     RET(upload(&H.d_fc, fc));
@@ -302,6 +354,9 @@ static int build_level(Ctx& c, const dgfas_level& in, const dgfas_params& prm, L
        H.d_lam, H.d_W);
   fill(H.v32, H.f_bx, H.f_Lhat, H.f_h, H.f_G, H.f_fW, H.f_fc, H.f_mu, H.f_mass, H.f_D, H.f_w, H.f_x, H.f_g, H.f_S,
        H.f_lam, H.f_W);
+  H.v64.tri = H.d_tri;
+  H.v32.tri = H.f_tri;
+  H.v64.coff = H.v32.coff = H.coff32 ? (const void*)H.d_coff32 : (const void*)H.d_coff64;
   return DGFAS_OK;
 }
 
@@ -476,7 +531,7 @@ static void free_level(LevelHost& H) {
                   H.d_h, H.d_G, H.d_fW, H.d_fc, H.d_mu, H.d_mass, H.d_D, H.d_w, H.d_g, H.d_S,
                   H.d_lam, H.d_W, H.d_x, H.f_h, H.f_G, H.f_fW, H.f_fc, H.f_mu, H.f_mass, H.f_D,
                   H.f_w, H.f_g, H.f_S, H.f_lam, H.f_W, H.f_x, H.d_I, H.d_P, H.u, H.gv, H.r,
-                  H.ubar, H.t, H.delta, H.fl};
+                  H.ubar, H.t, H.delta, H.fl, H.d_tri, H.f_tri, H.d_coff32, H.d_coff64};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -740,8 +795,16 @@ static int down_up(Ctx& c, double* uL, const double* fL, int top = -1) {
     }
     RET(launch_project(c, l, ul));                                   // u_{l-1} = P u_l
     RET(launch_restrict(c, l, c.lv[l].r, c.lv[l - 1].t));           // R r_l
-    RET(launch_apply(c, l - 1, DGFAS_FP64, c.lv[l - 1].u, c.lv[l - 1].t, c.lv[l - 1].gv, 1.0));
-    if (c.lv[l - 1].has_leaf) RET(launch_leaf_rhs(c, l - 1, c.lv[l - 1].fl, c.lv[l - 1].gv));
+    // the parent right-hand side g_{l-1} = A ubar_{l-1} + R r_l (tau correction).
+    // Smoothing on an all-twig level below the top starts from its residual
+    // R r_l and runs in correction form (WAS, and SCG in FP32 / BF16), so it
+    // never reads g: the FP64 operator is needed only for the root, levels
+    // with leaf or frozen rows, and the FP64 SCG smoother (residual from g)
+    const LevelHost& P = c.lv[l - 1];
+    if (l - 1 == 0 || P.has_leaf || P.has_frozen ||
+        (c.prm.smoother == DGFAS_SCG && prec == DGFAS_FP64))
+      RET(launch_apply(c, l - 1, DGFAS_FP64, P.u, P.t, P.gv, 1.0));
+    if (P.has_leaf) RET(launch_leaf_rhs(c, l - 1, P.fl, P.gv));
   }
   RET(root_solve(c, false));
   for (int l = 1; l <= L; ++l) {
@@ -998,6 +1061,18 @@ extern "C" int dgfas_apply_op(void* ctx, int level, const double* u, const doubl
   }
   return g ? launch_apply(*c, level, DGFAS_FP64, u, g, out, -1.0)
            : launch_apply(*c, level, DGFAS_FP64, u, nullptr, out, 1.0);
+}
+
+extern "C" int dgfas_apply_op32(void* ctx, int level, const float* u, const double* g,
+                                float* out) {
+  Ctx* c = (Ctx*)ctx;
+  if (!c || !u || !out || (const void*)u == (const void*)out || level < 0 ||
+      level >= (int)c->lv.size()) {
+    set_error("apply_op32: invalid argument");
+    return DGFAS_ERR_INVALID;
+  }
+  return g ? launch_apply_corr(*c, level, DGFAS_FP32, u, g, out, 0)
+           : launch_apply32(*c, level, u, out);
 }
 
 extern "C" int dgfas_schwarz_smooth(void* ctx, int level, double* u, const double* g, int n) {

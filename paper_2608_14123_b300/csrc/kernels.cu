@@ -10,6 +10,7 @@
 #include <atomic>
 #include <cstdio>
 #include <limits>
+#include <type_traits>
 
 #include "dgfas_internal.h"
 
@@ -285,7 +286,7 @@ __global__ void __launch_bounds__(256) k_curv_grad(const LevelView<T> L, const T
   const int team = threadIdx.y, tid = threadIdx.y * blockDim.x + threadIdx.x;
   const int nth = blockDim.x * blockDim.y;
   T* us = reinterpret_cast<T*>(smem_raw) + (size_t)team * 4 * NP3;
-  T* F[3] = {us + NP3, us + 2 * NP3, us + 3 * NP3};
+  T* F = us + NP3;   // component d at F + d NP3
   for (int t = tid; t < HC * N; t += nth) {
     const int r = t / N, q = t % N;
     const T d1 = L.D[r * N + q], d2 = L.D[r * N + N - 1 - q];
@@ -312,7 +313,7 @@ __global__ void __launch_bounds__(256) k_curv_grad(const LevelView<T> L, const T
     for (int l = 0; l < N; ++l) x[l] = us[ln.bp + l * ln.sp];
     acs_line<N, T>(M.de, M.dO, M.dm, x, y);
 #pragma unroll
-    for (int l = 0; l < N; ++l) F[d][ln.bp + l * ln.sp] = y[l];
+    for (int l = 0; l < N; ++l) F[d * NP3 + ln.bp + l * ln.sp] = y[l];
   }
   __syncthreads();
   if (!valid) return;
@@ -323,14 +324,14 @@ __global__ void __launch_bounds__(256) k_curv_grad(const LevelView<T> L, const T
     const T* fc = L.fc + ((size_t)e * 6 + f) * 3 * N2 + threadIdx.x;
     T* o = Fc + ((size_t)e * 6 + f) * 2 * N2 + threadIdx.x;
     o[0] = us[n];
-    o[N2] = ld(fc) * F[0][n] + ld(fc + N2) * F[1][n] + ld(fc + 2 * N2) * F[2][n];
+    o[N2] = ld(fc) * F[n] + ld(fc + N2) * F[NP3 + n] + ld(fc + 2 * N2) * F[2 * NP3 + n];
   }
   for (int k = 0; k < N; ++k) {
     const int n = (k * N + bb) * N + a, np = cpad<N>(a, bb, k);
     const T* G = L.G + (size_t)e * 6 * N3 + n;
     const T G00 = ld(G), G11 = ld(G + N3), G22 = ld(G + 2 * N3), G01 = ld(G + 3 * N3),
             G02 = ld(G + 4 * N3), G12 = ld(G + 5 * N3);
-    const T d0 = F[0][np], d1 = F[1][np], d2 = F[2][np];
+    const T d0 = F[np], d1 = F[NP3 + np], d2 = F[2 * NP3 + np];
     T* fo = Fg + (size_t)e * 3 * N3 + n;
     fo[0] = G00 * d0 + G01 * d1 + G02 * d2;
     fo[N3] = G01 * d0 + G11 * d1 + G12 * d2;
@@ -351,7 +352,7 @@ __global__ void __launch_bounds__(256) k_curv_div(const LevelView<T> L, const TU
   const int team = threadIdx.y, tid = threadIdx.y * blockDim.x + threadIdx.x;
   const int nth = blockDim.x * blockDim.y;
   T* F0 = reinterpret_cast<T*>(smem_raw) + (size_t)team * 4 * NP3;
-  T* F[3] = {F0, F0 + NP3, F0 + 2 * NP3};
+  T* F = F0;   // component d at F + d NP3
   T* R = F0 + 3 * NP3;
   for (int t = tid; t < HC * N; t += nth) {
     const int r = t / N, q = t % N;
@@ -370,9 +371,9 @@ __global__ void __launch_bounds__(256) k_curv_div(const LevelView<T> L, const TU
     const T* fe = Fg + (size_t)e * 3 * N3;
     for (int t = threadIdx.x; t < N3; t += blockDim.x) {
       const int tp = t + t / N;
-      F[0][tp] = fe[t];
-      F[1][tp] = fe[N3 + t];
-      F[2][tp] = fe[2 * N3 + t];
+      F[tp] = fe[t];
+      F[NP3 + tp] = fe[N3 + t];
+      F[2 * NP3 + tp] = fe[2 * N3 + t];
       R[tp] = L.kappa != T(0) ? L.kappa * ld(L.mass + eo + t) * (T)u[eo + t] : T(0);
     }
   }
@@ -407,9 +408,9 @@ __global__ void __launch_bounds__(256) k_curv_div(const LevelView<T> L, const TU
           lift = -um;
         }
         R[n] += flux;
-        F[0][n] += c0 * lift;
-        F[1][n] += c1 * lift;
-        F[2][n] += c2 * lift;
+        F[n] += c0 * lift;
+        F[NP3 + n] += c1 * lift;
+        F[2 * NP3 + n] += c2 * lift;
       }
     }
     __syncthreads();
@@ -422,7 +423,7 @@ __global__ void __launch_bounds__(256) k_curv_div(const LevelView<T> L, const TU
     if (valid) {
       T x[N];
 #pragma unroll
-      for (int l = 0; l < N; ++l) x[l] = F[d][ln.bp + l * ln.sp];
+      for (int l = 0; l < N; ++l) x[l] = F[d * NP3 + ln.bp + l * ln.sp];
       acs_line<N, T>(M.te, M.tO, M.tm, x, y);
     }
     if (d < 2) {
@@ -438,6 +439,260 @@ __global__ void __launch_bounds__(256) k_curv_div(const LevelView<T> L, const TU
         const int n = ln.bg + l * ln.sg;
         T o = alpha * (R[ln.bp + l * ln.sp] + y[l]);
         if (b) o += (T)b[eo + n];
+        out[eo + n] = frozen ? TO(0) : (TO)o;
+      }
+    }
+  }
+}
+
+// Two-pass FP32 form with the volume metric recomputed from the element's
+// trilinear map.  In FP32 the operator is bound by memory, not arithmetic, and
+// the stored volume metric is the largest part of its bytes (24 of about 44
+// B/DoF at p = 7); the map's seven coefficient vectors give the Jacobian J of
+// any node in a few multiply-adds, and with the columns J_d = dx/dxi_d the
+// rows of adj(J) = det J (J^-1) are C_0 = J_1 x J_2, C_1 = J_2 x J_0,
+// C_2 = J_0 x J_1, so that the metric is
+//   G_df = nu w_i w_j w_k (C_d . C_f) / det J,
+// its definition evaluated in FP32.  The face factors (normal-flux factors and
+// quadrature weights, 12 B/DoF) stay stored: recomputing them per face node
+// costs more instructions than their bytes cost time.
+//   pass 1 (k_curv_trace32): reference gradient, then the trace u and the
+//     normal flux q = c . grad u at the nodes of the six faces -> [e][6][2][N^2];
+//   pass 2 (k_curv_apply32): reference gradient, the recomputed metric node by
+//     node, the face fluxes and liftings from both sides' face data (the two
+//     faces normal to a direction in one pass), the transposed gradient.
+// About 56 B/DoF at p = 7 instead of 103.
+
+// Columns J_0, J_1, J_2 of the trilinear map's Jacobian at (xi, eta, zeta)
+// are affine in zeta along a z-line: J_0 = P_0 + zeta Q_0, J_1 = P_1 + zeta
+// Q_1, J_2 constant, with a = the element's coefficients a1..a7 (x, y, z each).
+__device__ __forceinline__ void cross3(const float* x, const float* y, float* z) {
+  z[0] = x[1] * y[2] - x[2] * y[1];
+  z[1] = x[2] * y[0] - x[0] * y[2];
+  z[2] = x[0] * y[1] - x[1] * y[0];
+}
+
+__device__ __forceinline__ float dot3(const float* x, const float* y) {
+  return x[0] * y[0] + x[1] * y[1] + x[2] * y[2];
+}
+
+// shared memory per element of the FP32 two-pass kernels (floats): u and the
+// gradient (pass 1); u, gradient / flux, accumulator and map coefficients (pass 2)
+template <int N>
+__host__ __device__ constexpr int c32_trace_floats() { return 4 * CurvLine<N>::NP3; }
+template <int N>
+__host__ __device__ constexpr int c32_team_floats() { return 5 * CurvLine<N>::NP3 + 24; }
+
+// reference gradient of the element in us into F (component d at F + d NP3),
+// one line per thread
+template <int N>
+__device__ __forceinline__ void c32_gradient(const CurvEo<N, float>& M, const float* us,
+                                             float* F, int a, int bb, bool valid) {
+  constexpr int NP3 = CurvLine<N>::NP3;
+  if (!valid) return;
+#pragma unroll 1
+  for (int d = 0; d < 3; ++d) {
+    const CurvLine<N> ln(d, a, bb);
+    float x[N], y[N];
+#pragma unroll
+    for (int l = 0; l < N; ++l) x[l] = us[ln.bp + l * ln.sp];
+    acs_line<N, float>(M.de, M.dO, M.dm, x, y);
+#pragma unroll
+    for (int l = 0; l < N; ++l) F[d * NP3 + ln.bp + l * ln.sp] = y[l];
+  }
+}
+
+template <int N>
+__device__ __forceinline__ void c32_tables(CurvEo<N, float>& M, float* xs, float* ws,
+                                           const LevelView<float>& L, int tid, int nth,
+                                           bool transposed) {
+  constexpr int H = N / 2, HC = (N + 1) / 2;
+  for (int t = tid; t < HC * N; t += nth) {
+    const int r = t / N, q = t % N;
+    const float d1 = L.D[r * N + q], d2 = L.D[r * N + N - 1 - q];
+    if (q < H) {
+      M.de[r][q] = 0.5f * (d1 + d2);
+      M.dO[r][q] = 0.5f * (d1 - d2);
+    } else if ((N & 1) && q == H) {
+      M.dm[r] = d1;
+    }
+    if (transposed) {
+      const float t1 = L.D[q * N + r], t2 = L.D[(N - 1 - q) * N + r];
+      if (q < H) {
+        M.te[r][q] = 0.5f * (t1 + t2);
+        M.tO[r][q] = 0.5f * (t1 - t2);
+      } else if ((N & 1) && q == H) {
+        M.tm[r] = t1;
+      }
+    }
+  }
+  for (int t = tid; t < N; t += nth) {
+    xs[t] = L.x[t];
+    ws[t] = L.w[t];
+  }
+}
+
+template <int N, typename TU>
+__global__ void __launch_bounds__(256) k_curv_trace32(const LevelView<float> L,
+                                                      const TU* __restrict__ u,
+                                                      float* __restrict__ Fc) {
+  constexpr int N2 = N * N, N3 = N * N * N;
+  constexpr int NP3 = CurvLine<N>::NP3;
+  __shared__ CurvEo<N, float> M;
+  __shared__ float xs[N], ws[N];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int team = threadIdx.y, tid = threadIdx.y * blockDim.x + threadIdx.x;
+  const int nth = blockDim.x * blockDim.y;
+  float* us = reinterpret_cast<float*>(smem_raw) + (size_t)team * c32_trace_floats<N>();
+  float* F = us + NP3;   // gradient component d at F + d NP3
+  c32_tables<N>(M, xs, ws, L, tid, nth, false);
+  const int e = blockIdx.x * blockDim.y + team;
+  const bool valid = e < L.ne && threadIdx.x < N2;
+  const size_t eo = (size_t)e * N3;
+  if (e < L.ne)
+    for (int t = threadIdx.x; t < N3; t += blockDim.x) us[t + t / N] = (float)u[eo + t];
+  __syncthreads();
+  const int a = threadIdx.x % N, bb = threadIdx.x / N;
+  c32_gradient<N>(M, us, F, a, bb, valid);
+  __syncthreads();
+  if (!valid) return;
+#pragma unroll 1
+  for (int f = 0; f < 6; ++f) {
+    const int d = f >> 1, end = (f & 1) ? N - 1 : 0;
+    const int n = d == 0 ? cpad<N>(end, a, bb) : (d == 1 ? cpad<N>(a, end, bb) : cpad<N>(a, bb, end));
+    const float* fc = L.fc + ((size_t)e * 6 + f) * 3 * N2 + threadIdx.x;
+    float* o = Fc + ((size_t)e * 6 + f) * 2 * N2 + threadIdx.x;
+    o[0] = us[n];
+    o[N2] = ld(fc) * F[n] + ld(fc + N2) * F[NP3 + n] + ld(fc + 2 * N2) * F[2 * NP3 + n];
+  }
+}
+
+template <int N, typename TU, typename TB, typename TO>
+__global__ void __launch_bounds__(256) k_curv_apply32(const LevelView<float> L,
+                                                      const TU* __restrict__ u,
+                                                      const float* __restrict__ Fc,
+                                                      const TB* __restrict__ b,
+                                                      TO* __restrict__ out, float alpha) {
+  constexpr int N2 = N * N, N3 = N * N * N;
+  constexpr int NP3 = CurvLine<N>::NP3;
+  __shared__ CurvEo<N, float> M;
+  __shared__ float xs[N], ws[N];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int team = threadIdx.y, tid = threadIdx.y * blockDim.x + threadIdx.x;
+  const int nth = blockDim.x * blockDim.y;
+  float* us = reinterpret_cast<float*>(smem_raw) + (size_t)team * c32_team_floats<N>();
+  float* F = us + NP3;       // gradient, then flux, component d at F + d NP3
+  float* R = us + 4 * NP3;   // volume reaction and face terms
+  float* tri = us + 5 * NP3;
+  c32_tables<N>(M, xs, ws, L, tid, nth, true);
+  const int e = blockIdx.x * blockDim.y + team;
+  const bool valid = e < L.ne && threadIdx.x < N2;
+  const size_t eo = (size_t)e * N3;
+  if (e < L.ne) {
+    for (int t = threadIdx.x; t < N3; t += blockDim.x) us[t + t / N] = (float)u[eo + t];
+    for (int t = threadIdx.x; t < 21; t += blockDim.x) tri[t] = L.tri[(size_t)e * 24 + t];
+  }
+  __syncthreads();
+  const int a = threadIdx.x % N, bb = threadIdx.x / N;
+  c32_gradient<N>(M, us, F, a, bb, valid);
+  __syncthreads();
+  if (valid) {
+    // the metric at the nodes (a, bb, k) of this thread's z-line
+    const float xi = xs[a], eta = xs[bb], nwij = L.nu * ws[a] * ws[bb], kap = L.kappa;
+    float P0[3], Q0[3], P1[3], Q1[3], J2[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      P0[c] = tri[c] + tri[9 + c] * eta;
+      Q0[c] = tri[12 + c] + tri[18 + c] * eta;
+      P1[c] = tri[3 + c] + tri[9 + c] * xi;
+      Q1[c] = tri[15 + c] + tri[18 + c] * xi;
+      J2[c] = tri[6 + c] + tri[12 + c] * xi + tri[15 + c] * eta + tri[18 + c] * xi * eta;
+    }
+#pragma unroll 2
+    for (int k = 0; k < N; ++k) {
+      const float zeta = xs[k];
+      float J0[3], J1[3], C0[3], C1[3], C2[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        J0[c] = P0[c] + Q0[c] * zeta;
+        J1[c] = P1[c] + Q1[c] * zeta;
+      }
+      cross3(J1, J2, C0);
+      cross3(J2, J0, C1);
+      cross3(J0, J1, C2);
+      const float det = dot3(J0, C0);
+      const float s = __fdividef(nwij * ws[k], det);
+      const int np = cpad<N>(a, bb, k);
+      const float d0 = F[np], d1 = F[NP3 + np], d2 = F[2 * NP3 + np];
+      const float g00 = s * dot3(C0, C0), g11 = s * dot3(C1, C1), g22 = s * dot3(C2, C2),
+                  g01 = s * dot3(C0, C1), g02 = s * dot3(C0, C2), g12 = s * dot3(C1, C2);
+      F[np] = g00 * d0 + g01 * d1 + g02 * d2;
+      F[NP3 + np] = g01 * d0 + g11 * d1 + g12 * d2;
+      F[2 * NP3 + np] = g02 * d0 + g12 * d1 + g22 * d2;
+      // reaction kappa w det u (the lumped mass, recomputed as well)
+      R[np] = kap != 0.f ? kap * ws[a] * ws[bb] * ws[k] * det * us[np] : 0.f;
+    }
+  }
+  __syncthreads();
+  // faces: the two faces normal to direction d in one pass
+#pragma unroll 1
+  for (int d = 0; d < 3; ++d) {
+    if (valid) {
+#pragma unroll
+      for (int side = 0; side < 2; ++side) {
+        const int f = 2 * d + side;
+        const int nbid = L.nbr[6 * e + f];
+        if (nbid == -2) continue;   // Neumann: no face term
+        const int end = side ? N - 1 : 0;
+        const int n = d == 0 ? cpad<N>(end, a, bb) : (d == 1 ? cpad<N>(a, end, bb) : cpad<N>(a, bb, end));
+        const float um = us[n];
+        const float qm = Fc[((size_t)e * 6 + f) * 2 * N2 + N2 + threadIdx.x];
+        const float* fcp = L.fc + ((size_t)e * 6 + f) * 3 * N2 + threadIdx.x;
+        const float c0 = ld(fcp), c1 = ld(fcp + N2), c2 = ld(fcp + 2 * N2);
+        const float W = L.nu * ld(L.fW + ((size_t)e * 6 + f) * N2 + threadIdx.x);
+        const float mu = L.mu[6 * e + f];
+        float flux, lift;
+        if (nbid >= 0) {
+          const float* oth = Fc + ((size_t)nbid * 6 + (f ^ 1)) * 2 * N2 + threadIdx.x;
+          const float jump = um - oth[0];
+          flux = mu * W * jump - 0.5f * (qm - oth[N2]);
+          lift = -0.5f * jump;
+        } else {   // Dirichlet
+          flux = 2.f * mu * W * um - qm;
+          lift = -um;
+        }
+        R[n] += flux;
+        F[n] += c0 * lift;
+        F[NP3 + n] += c1 * lift;
+        F[2 * NP3 + n] += c2 * lift;
+      }
+    }
+    __syncthreads();
+  }
+  // transposed reference gradient, one line per thread and direction
+#pragma unroll 1
+  for (int d = 0; d < 3; ++d) {
+    const CurvLine<N> ln(d, a, bb);
+    float y[N];
+    if (valid) {
+      float x[N];
+#pragma unroll
+      for (int l = 0; l < N; ++l) x[l] = F[d * NP3 + ln.bp + l * ln.sp];
+      acs_line<N, float>(M.te, M.tO, M.tm, x, y);
+    }
+    if (d < 2) {
+      if (valid) {
+#pragma unroll
+        for (int l = 0; l < N; ++l) R[ln.bp + l * ln.sp] += y[l];
+      }
+      __syncthreads();
+    } else if (valid) {
+      const bool frozen = L.cls[e] == DGFAS_FROZEN;
+#pragma unroll
+      for (int l = 0; l < N; ++l) {
+        const int n = ln.bg + l * ln.sg;
+        float o = alpha * (R[ln.bp + l * ln.sp] + y[l]);
+        if (b) o += (float)b[eo + n];
         out[eo + n] = frozen ? TO(0) : (TO)o;
       }
     }
@@ -633,6 +888,43 @@ static int apply_epb_max(int N, size_t tsz) {
   return e < 1 ? 1 : e;
 }
 
+// FP32 curvilinear operator: two passes with the metric recomputed from the
+// trilinear map (face data through the scratch); one element per team of N^2
+// threads.  Only the FP32 instantiation launches anything.
+template <int N, typename T, typename TU, typename TB, typename TO>
+static int launch_curv32(const LevelView<T>& L, const TU* u, const TB* b, TO* out, T alpha,
+                         cudaStream_t st, int epb_req, T* scratch) {
+  if constexpr (std::is_same<T, float>::value) {
+    constexpr int N2 = N * N;
+    int epb = (128 + N2 - 1) / N2;
+    if (epb_req > 0) epb = std::max(1, std::min(epb_req, 256 / N2));
+    const size_t smem1 = (size_t)c32_trace_floats<N>() * epb * sizeof(float);
+    const size_t smem = (size_t)c32_team_floats<N>() * epb * sizeof(float);
+    auto k1 = k_curv_trace32<N, TU>;
+    auto k2 = k_curv_apply32<N, TU, TB, TO>;
+    if (smem > 40 * 1024) {
+      static bool attr = false;
+      if (!attr) {
+        CK(cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024));
+        CK(cudaFuncSetAttribute(k2, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024));
+        attr = true;
+      }
+    }
+    dim3 blk(N2, epb), grd((L.ne + epb - 1) / epb);
+    k1<<<grd, blk, smem1, st>>>(L, u, scratch);
+    ++g_kernels;
+    CK(cudaGetLastError());
+    k2<<<grd, blk, smem, st>>>(L, u, scratch, b, out, alpha);
+    ++g_kernels;
+    CK(cudaGetLastError());
+    return DGFAS_OK;
+  } else {
+    (void)L; (void)u; (void)b; (void)out; (void)alpha; (void)st; (void)epb_req; (void)scratch;
+    set_error("apply: FP32 curvilinear form called for another type");
+    return DGFAS_ERR_INVALID;
+  }
+}
+
 template <int N, typename T, typename TU, typename TB, typename TO>
 static int apply_N(const LevelView<T>& L, const TU* u, const TB* b, TO* out, T alpha,
                    cudaStream_t st, int epb_req, T* scratch) {
@@ -661,6 +953,8 @@ static int apply_N(const LevelView<T>& L, const TU* u, const TB* b, TO* out, T a
     }
     dim3 blk2(N2, epb2), grd2((L.ne + epb2 - 1) / epb2);
     kf<<<grd2, blk2, smem2, st>>>(L, L.bx, L.Lhat, u, b, out, alpha);
+  } else if (std::is_same<T, float>::value && scratch && L.tri) {
+    return launch_curv32<N, T, TU, TB, TO>(L, u, b, out, alpha, st, epb_req, scratch);
   } else if (scratch) {
     // two passes through the scratch (gradient and face data, then fluxes and
     // the transposed gradient); one element per team of N^2 threads
@@ -730,26 +1024,25 @@ static int apply_disp(const LevelView<T>& L, const TU* u, const TB* b, TO* out, 
   return DGFAS_ERR_UNSUPPORTED;
 }
 
+// The two-pass scratch of a curvilinear level (gradient, 3 N^3 values, and
+// face data, 12 N^2 values, per element), or null: box levels, and contexts
+// without it, take the single-pass form.  The FP32 form reads the same
+// buffer as floats (it needs half of it).
+static double* scratch64(Ctx& c, int l) {
+  LevelHost& H = c.lv[l];
+  const size_t per = 3 * (size_t)H.N * H.N * H.N + 12 * (size_t)H.N * H.N;
+  return (!H.box && c.apply_scratch && (size_t)H.ne * per <= c.apply_scratch_n)
+             ? c.apply_scratch : nullptr;
+}
+static float* scratch32(Ctx& c, int l) { return (float*)scratch64(c, l); }
+
 // FP64 operator: out = b + alpha A u, everything FP64.
 int launch_apply(Ctx& c, int l, int prec, const double* u, const double* b, void* out,
                  double alpha) {
   (void)prec;
   LevelHost& H = c.lv[l];
-  // curvilinear levels use the two-pass form when the context holds its scratch
-  double* scratch = (!H.box && c.apply_scratch &&
-                     (size_t)H.ne * (3 * H.N * H.N * H.N + 12 * H.N * H.N) <= c.apply_scratch_n)
-                        ? c.apply_scratch : nullptr;
   return apply_disp<double, double, double, double>(H.v64, u, b, (double*)out, alpha, c.stream,
-                                                    H.tune.apply64, scratch);
-}
-
-// The two-pass scratch of a curvilinear level in FP32 (the context's FP64
-// scratch holds twice the floats the level needs), or null.
-static float* scratch32(Ctx& c, int l) {
-  LevelHost& H = c.lv[l];
-  return (!H.box && c.apply_scratch &&
-          (size_t)H.ne * (3 * H.N * H.N * H.N + 12 * H.N * H.N) <= c.apply_scratch_n)
-             ? (float*)c.apply_scratch : nullptr;
+                                                    H.tune.apply64, scratch64(c, l));
 }
 
 // Smoother-precision operator on a correction: out = b - A delta with b FP64,
@@ -758,14 +1051,10 @@ static float* scratch32(Ctx& c, int l) {
 int launch_apply_corr(Ctx& c, int l, int prec, const void* delta, const double* b, void* out,
                       int out_fp64) {
   LevelHost& H = c.lv[l];
-  if (prec == DGFAS_FP64) {
-    double* scratch = (!H.box && c.apply_scratch &&
-                       (size_t)H.ne * (3 * H.N * H.N * H.N + 12 * H.N * H.N) <= c.apply_scratch_n)
-                          ? c.apply_scratch : nullptr;
+  if (prec == DGFAS_FP64)
     return apply_disp<double, double, double, double>(H.v64, (const double*)delta, b,
                                                       (double*)out, -1.0, c.stream, H.tune.apply64,
-                                                      scratch);
-  }
+                                                      scratch64(c, l));
   float* s32 = scratch32(c, l);
   if (out_fp64)
     return apply_disp<float, float, double, double>(H.v32, (const float*)delta, b, (double*)out,
@@ -1240,12 +1529,12 @@ int tune_candidates(Ctx& c, int l, int kernel, int* out, int max_out) {
 // of the up to 26 neighbours whose overlap layers reach it (at most 2
 // candidates per direction, 8 in all).  The patch position of own node
 // (i, j, k) inside neighbour slot (ox, oy, oz)'s patch is (i, j, k) plus a
-// per-slot shift, so each slot is reduced once per element to one offset
-// (src NS^3 + shift, or a sentinel when the slot contributes nothing: no neighbour, a
-// frozen one, or a boundary side that carries no layers) staged in shared
-// memory; per node only the candidate test and the load remain.  Elements of
-// small degree are packed several to a CTA.  Frozen elements are left
-// untouched (ADD) or zeroed (!ADD).
+// per-slot shift, so each slot reduces to one offset per element (src NS^3 +
+// shift, or a sentinel when the slot contributes nothing: no neighbour, a
+// frozen one, or a boundary side that carries no layers), tabulated at setup
+// (L.coff) and staged in shared memory; per node only the candidate test and
+// the load remain.  Elements of small degree are packed several to a CTA.
+// Frozen elements are left untouched (ADD) or zeroed (!ADD).
 // IDX: offset type (32-bit when every patch index of the level fits)
 template <int N, typename T, bool ADD, typename TO, typename IDX>
 __global__ void __launch_bounds__(256) k_combine(const LevelView<T> L, const T* __restrict__ patch,
@@ -1265,27 +1554,10 @@ __global__ void __launch_bounds__(256) k_combine(const LevelView<T> L, const T* 
   // be negative (a neighbour of small index whose layers precede this element's
   // nodes in its patch, e.g. across a periodic boundary)
   constexpr IDX kNone = std::numeric_limits<IDX>::min();
+  const IDX* coff = reinterpret_cast<const IDX*>(L.coff);
   for (int t = threadIdx.x; t < EPB * 27; t += blockDim.x) {
-    const int el = t / 27, slot = t % 27, e = e0 + el;
-    IDX off = kNone;
-    if (e < L.ne) {
-      const int src = L.nbr27[27 * e + slot];
-      if (src >= 0 && L.cls[src] != DGFAS_FROZEN) {
-        const int o[3] = {slot % 3 - 1, (slot / 3) % 3 - 1, slot / 9 - 1};
-        int shift[3];
-        bool reach = true;
-        for (int d = 0; d < 3; ++d) {
-          const int v = L.var[3 * src + d];
-          const bool left_i = (v >> 2) == 0, right_i = (v & 3) == 0;
-          const int ml = left_i ? m : 0;   // the neighbour's left layers
-          // the neighbour's patch reaches this element only through interior sides
-          if ((o[d] < 0 && !right_i) || (o[d] > 0 && !left_i)) reach = false;
-          shift[d] = o[d] == 0 ? ml : (o[d] < 0 ? ml + N : -(N - m));
-        }
-        if (reach) off = (IDX)src * NS3 + ((IDX)shift[2] * nsm + shift[1]) * nsm + shift[0];
-      }
-    }
-    s_off[el][slot] = off;
+    const int el = t / 27, e = e0 + el;
+    s_off[el][t % 27] = e < L.ne ? coff[27 * (size_t)e0 + t] : kNone;
   }
   __syncthreads();
   for (int t = threadIdx.x; t < EPB * N3; t += blockDim.x) {

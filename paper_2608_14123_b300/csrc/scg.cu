@@ -411,6 +411,25 @@ int scg_run(Ctx& c, int l, double* u, int n, double rtol, int prec, bool pending
   return rc;
 }
 
+// Outcome of the last SCG block on the context's stream (synchronizes):
+// out[0] = |r|^2 when its exit test last ran (or at the start), out[1] = steps
+// taken before the exit test held (all steps if it never did), out[2] = 1 if
+// the exit test |r| <= rtol |r_start| held, else 0.
+extern "C" int dgfas_scg_info(void* ctx, double* out_host) {
+  Ctx* c = (Ctx*)ctx;
+  if (!c || !out_host) return DGFAS_ERR_INVALID;
+  double s[8];
+  if (cudaMemcpyAsync(s, c->dscal, sizeof(s), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+      cudaStreamSynchronize(c->stream) != cudaSuccess) {
+    set_error("scg_info: copy");
+    return DGFAS_ERR_CUDA;
+  }
+  out_host[0] = s[S_RR];
+  out_host[1] = s[S_STEPS];
+  out_host[2] = s[S_DONE];
+  return DGFAS_OK;
+}
+
 // Per-kernel timing of one SCG step on `level` in the context's smoother
 // precision, with CUDA events on the context's stream, averaged over `reps`
 // steps from the residual g - A u: ms_out[0..5] = the FD kernel of the Schwarz

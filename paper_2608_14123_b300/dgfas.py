@@ -56,9 +56,9 @@ class dgfas_info(ctypes.Structure):
 
 
 SYMBOLS = ["dgfas_setup_levels", "dgfas_destroy", "dgfas_level_ndof", "dgfas_node_coords",
-           "dgfas_assemble_rhs", "dgfas_apply_op", "dgfas_schwarz_smooth", "dgfas_fas_vcycle",
+           "dgfas_assemble_rhs", "dgfas_apply_op", "dgfas_apply_op32", "dgfas_schwarz_smooth", "dgfas_fas_vcycle",
            "dgfas_solve", "dgfas_norm", "dgfas_set_surrogate", "dgfas_get_surrogate",
-           "dgfas_use_graph", "dgfas_profile_sweep", "dgfas_profile_scg", "dgfas_fma_peak", "dgfas_schwarz_correct_static", "dgfas_kernel_launches", "dgfas_mlp_param_count",
+           "dgfas_use_graph", "dgfas_profile_sweep", "dgfas_profile_scg", "dgfas_scg_info", "dgfas_fma_peak", "dgfas_schwarz_correct_static", "dgfas_kernel_launches", "dgfas_mlp_param_count",
            "dgfas_mlp_forward", "dgfas_mlp_grad", "dgfas_mlp_inputs", "dgfas_mlp_train", "dgfas_learned_surrogate",
            "dgfas_assemble_rhs_level", "dgfas_set_level_rhs", "dgfas_composite_residual",
            "dgfas_get_level_solution", "dgfas_tc_selftest", "dgfas_tc_selftest_mn", "dgfas_tc_error", "dgfas_host_fd_variant", "dgfas_autotune", "dgfas_set_tuning",
@@ -85,6 +85,7 @@ def load():
         "dgfas_node_coords": (I, [P, I, P]),
         "dgfas_assemble_rhs": (I, [P, P, P, P]),
         "dgfas_apply_op": (I, [P, I, P, P, P]),
+        "dgfas_apply_op32": (I, [P, I, P, P, P]),
         "dgfas_schwarz_smooth": (I, [P, I, P, P, I]),
         "dgfas_fas_vcycle": (I, [P, P, P, ctypes.POINTER(D)]),
         "dgfas_solve": (I, [P, P, P, D, I, ctypes.POINTER(dgfas_info)]),
@@ -95,6 +96,7 @@ def load():
         "dgfas_host_fd_variant": (I, [I, D, D, I, P, P, P, ctypes.POINTER(I)]),
         "dgfas_profile_sweep": (I, [P, I, P, P, I, P]),
         "dgfas_profile_scg": (I, [P, I, P, P, I, P]),
+        "dgfas_scg_info": (I, [P, P]),
         "dgfas_fma_peak": (I, [ctypes.POINTER(D), ctypes.POINTER(D)]),
         "dgfas_schwarz_correct_static": (I, [P, I, P, P]),
         "dgfas_kernel_launches": (LL, []),
@@ -225,6 +227,13 @@ class Solver:
                                      _ptr(out, n)),
                "apply_op")
 
+    def dgfas_apply_op32(self, level, u, g, out):
+        """FP32 operator: out = g - A u (g FP64) or A u (g None); u, out FP32."""
+        n = self.ndof(level)
+        _check(load().dgfas_apply_op32(self.ctx, level % self.n_levels, _ptr(u, n, "float32"),
+                                       _ptr(g, n), _ptr(out, n, "float32")),
+               "apply_op32")
+
     def dgfas_schwarz_smooth(self, level, u, g, n):
         nd = self.ndof(level)
         _check(load().dgfas_schwarz_smooth(self.ctx, level % self.n_levels, _ptr(u, nd), _ptr(g, nd),
@@ -277,6 +286,12 @@ class Solver:
                                         ms.ctypes.data_as(ctypes.c_void_p)), "profile_scg")
         return dict(fd=ms[0], combine=ms[1], zr_dir=ms[2], apply_smoother=ms[3],
                     pq_update=ms[4], residual_fp64=ms[5])
+
+    def dgfas_scg_info(self):
+        """(|r|^2, steps, reached) of the last SCG block (synchronizes)."""
+        out = np.zeros(3)
+        _check(load().dgfas_scg_info(self.ctx, out.ctypes.data_as(ctypes.c_void_p)), "scg_info")
+        return float(out[0]), int(out[1]), bool(out[2])
 
     def dgfas_fmg(self, f_levels, u_top, cycles_per_level=1):
         """Full multigrid startup (Alg. 4): u_top <- the FMG start value from the

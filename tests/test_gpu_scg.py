@@ -125,3 +125,51 @@ def test_scg_mixed_precision_solve_cycles(case, prec):
     uo, hist = H.solve(cfg["u0"], b_or, max_cycles=40)
     assert info["r_final"] <= 1e-10 * info["r0"]
     assert info["cycles"] <= len(hist) - 1 + 2
+
+
+
+@pytest.mark.parametrize("steps,rtol,reached", [(200, 1e-6, True), (2, 1e-14, False)])
+def test_scg_root_reports_whether_it_reached_its_tolerance(steps, rtol, reached):
+    """The root SCG's step cap and exit test (Sec. 4.3.2): with the Schwarz
+    smoother the root solve is the last SCG block of a V-cycle, and
+    dgfas_scg_info reports its steps, final |r|^2 and whether it stopped at
+    |r| <= root_rtol |r_start| (reached) or at its step cap; the steps and
+    |r|^2 match the oracle's loop from the same projected start."""
+    torch = torch_cuda()
+    cfg = wl.config(5, small=True, root="p1")
+    S = make_solver(cfg, smoother=0, coarse="scg", root_steps=steps, root_rtol=rtol)
+    H = make_oracle(cfg, smoother="was", coarse="scg", root_steps=steps, root_rtol=rtol)
+    calls = [0]
+    sweep = H.sw[0].correction
+
+    def counted(r):
+        calls[0] += 1
+        return sweep(r)
+
+    H.sw[0].correction = counted
+    last = {}
+    scg = H.scg
+
+    def scg_rr(l, u, f, n, r_max, precond=None, first=None):
+        out = scg(l, u, f, n, r_max, precond, first)
+        if l == 0:
+            calls_then = calls[0]
+            last.update(steps=calls_then, rr=float(np.sum((f - H.A(0, out)) ** 2)),
+                        r_max=r_max)
+            calls[0] = 0
+        return out
+
+    H.scg = scg_rr
+    b, b_or = rhs_both(cfg, S, H)
+    u = torch.from_numpy(cfg["u0"].copy()).cuda()
+    S.dgfas_fas_vcycle(u, b)
+    H.fas_vcycle(H.zero_levels(cfg["u0"]), b_or)
+    rr, n, done = S.dgfas_scg_info()
+    assert done == reached
+    assert n == last["steps"] == (n if reached else steps)
+    # the device's |r|^2 is the recursive residual's, the oracle's the true
+    # one; they part by about steps * eps * |A| |u|, 1e-5 of |r|^2 here
+    assert abs(rr - last["rr"]) <= 1e-3 * last["rr"]
+    if reached:
+        assert rr <= last["r_max"] ** 2 * (1 + 1e-9)
+    S.close()
