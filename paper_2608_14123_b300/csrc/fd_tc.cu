@@ -273,8 +273,11 @@ __device__ __forceinline__ void tc_read1(uint32_t tmem, int t, float* v) {
 
 // TN, TM > 0: instantiation for N = TN nodes and TM overlap layers, whose
 // gather resolves the row's three source segments at compile time; TN = 0:
-// any N and m (per-position gather maps).
-template <int TN, int TM>
+// any N and m (per-position gather maps).  VEC (TN % 4 == 0, TM even, r
+// 16-byte aligned): the segments are read as float4 (own nodes) and float2
+// (layers), 4 loads per row at p = 7 instead of 12 (each lane's loads touch
+// distinct 32-byte sectors, so the load count sets the L1 traffic).
+template <int TN, int TM, bool VEC = false>
 __global__ void __launch_bounds__(128, 8) k_fd_tc(const LevelView<float> L, const float* __restrict__ r,
                                                   float* __restrict__ patch, int* __restrict__ err) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -360,7 +363,38 @@ __global__ void __launch_bounds__(128, 8) k_fd_tc(const LevelView<float> L, cons
           const float* p1 = nb[1] >= 0 ? r + (long long)nb[1] * N3 + line : nullptr;
           const float* p2 = nb[2] >= 0 ? r + (long long)nb[2] * N3 + line : nullptr;
           const bool li = (v1 >> 2) == 0, ri = (v1 & 3) == 0;
-          if (li) {
+          if constexpr (VEC) {
+            static_assert(TN % 4 == 0 && TM % 2 == 0 && TN + 2 * TM <= 16, "vector gather");
+            float own[TN], lft[TM], rgt[TM];
+#pragma unroll
+            for (int v = 0; v < TN / 4; ++v) {
+              const float4 t = p1 ? __ldg(reinterpret_cast<const float4*>(p1) + v)
+                                  : make_float4(0.f, 0.f, 0.f, 0.f);
+              own[4 * v] = t.x; own[4 * v + 1] = t.y; own[4 * v + 2] = t.z; own[4 * v + 3] = t.w;
+            }
+#pragma unroll
+            for (int v = 0; v < TM / 2; ++v) {
+              const float2 t0 = (li && p0) ? __ldg(reinterpret_cast<const float2*>(p0 + TN - TM) + v)
+                                           : make_float2(0.f, 0.f);
+              const float2 t2 = (ri && p2) ? __ldg(reinterpret_cast<const float2*>(p2) + v)
+                                           : make_float2(0.f, 0.f);
+              lft[2 * v] = t0.x; lft[2 * v + 1] = t0.y;
+              rgt[2 * v] = t2.x; rgt[2 * v + 1] = t2.y;
+            }
+            if (li) {
+#pragma unroll
+              for (int q = 0; q < TM; ++q) vals[q] = lft[q];
+#pragma unroll
+              for (int q = 0; q < TN; ++q) vals[TM + q] = own[q];
+#pragma unroll
+              for (int q = 0; q < TM; ++q) vals[TM + TN + q] = rgt[q];   // zero unless ri
+            } else {
+#pragma unroll
+              for (int q = 0; q < TN; ++q) vals[q] = own[q];
+#pragma unroll
+              for (int q = 0; q < TM; ++q) vals[TN + q] = rgt[q];
+            }
+          } else if (li) {
 #pragma unroll
             for (int a = 0; a < TM; ++a) vals[a] = p0 ? p0[TN - TM + a] : 0.0f;
 #pragma unroll
@@ -496,7 +530,11 @@ int launch_fd_tc(Ctx& c, int l, const float* r) {
   int rc;
   const int key = 16 * H.N + H.m;
   switch (key) {
-    case 16 * 8 + 2: rc = go(k_fd_tc<8, 2>); break;
+    case 16 * 8 + 2:
+      // the vector gather needs r 16-byte aligned (element and line offsets
+      // are multiples of 8 floats)
+      rc = ((uintptr_t)r % 16 == 0) ? go(k_fd_tc<8, 2, true>) : go(k_fd_tc<8, 2>);
+      break;
     case 16 * 9 + 2: rc = go(k_fd_tc<9, 2>); break;
     case 16 * 10 + 2: rc = go(k_fd_tc<10, 2>); break;
     case 16 * 11 + 2: rc = go(k_fd_tc<11, 2>); break;
