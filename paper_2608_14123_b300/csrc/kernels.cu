@@ -551,19 +551,27 @@ __global__ void __launch_bounds__(256) k_curv_trace32(const LevelView<float> L,
   const size_t eo = (size_t)e * N3;
   if (e < L.ne)
     for (int t = threadIdx.x; t < N3; t += blockDim.x) us[t + t / N] = (float)u[eo + t];
+  // this thread's face factors, requested now so that they arrive while the
+  // gradient is formed (the kernel is otherwise bound by load latency)
+  float cf[6][3];
+  if (valid) {
+#pragma unroll
+    for (int f = 0; f < 6; ++f)
+#pragma unroll
+      for (int t = 0; t < 3; ++t) cf[f][t] = ld(L.fc + (((size_t)e * 6 + f) * 3 + t) * N2 + threadIdx.x);
+  }
   __syncthreads();
   const int a = threadIdx.x % N, bb = threadIdx.x / N;
   c32_gradient<N>(M, us, F, a, bb, valid);
   __syncthreads();
   if (!valid) return;
-#pragma unroll 1
+#pragma unroll
   for (int f = 0; f < 6; ++f) {
     const int d = f >> 1, end = (f & 1) ? N - 1 : 0;
     const int n = d == 0 ? cpad<N>(end, a, bb) : (d == 1 ? cpad<N>(a, end, bb) : cpad<N>(a, bb, end));
-    const float* fc = L.fc + ((size_t)e * 6 + f) * 3 * N2 + threadIdx.x;
     float* o = Fc + ((size_t)e * 6 + f) * 2 * N2 + threadIdx.x;
     o[0] = us[n];
-    o[N2] = ld(fc) * F[n] + ld(fc + N2) * F[NP3 + n] + ld(fc + 2 * N2) * F[2 * NP3 + n];
+    o[N2] = cf[f][0] * F[n] + cf[f][1] * F[NP3 + n] + cf[f][2] * F[2 * NP3 + n];
   }
 }
 
@@ -592,8 +600,12 @@ __global__ void __launch_bounds__(256) k_curv_apply32(const LevelView<float> L,
     for (int t = threadIdx.x; t < N3; t += blockDim.x) us[t + t / N] = (float)u[eo + t];
     for (int t = threadIdx.x; t < 21; t += blockDim.x) tri[t] = L.tri[(size_t)e * 24 + t];
   }
-  __syncthreads();
   const int a = threadIdx.x % N, bb = threadIdx.x / N;
+  // b on this thread's z-line (the nodes it writes), requested early
+  float bz[N];
+#pragma unroll
+  for (int l = 0; l < N; ++l) bz[l] = (b && valid) ? (float)b[eo + bb * N + a + (size_t)l * N2] : 0.f;
+  __syncthreads();
   c32_gradient<N>(M, us, F, a, bb, valid);
   __syncthreads();
   if (valid) {
@@ -690,9 +702,8 @@ __global__ void __launch_bounds__(256) k_curv_apply32(const LevelView<float> L,
       const bool frozen = L.cls[e] == DGFAS_FROZEN;
 #pragma unroll
       for (int l = 0; l < N; ++l) {
-        const int n = ln.bg + l * ln.sg;
-        float o = alpha * (R[ln.bp + l * ln.sp] + y[l]);
-        if (b) o += (float)b[eo + n];
+        const int n = ln.bg + l * ln.sg;   // = bb N + a + l N^2
+        const float o = alpha * (R[ln.bp + l * ln.sp] + y[l]) + bz[l];
         out[eo + n] = frozen ? TO(0) : (TO)o;
       }
     }
@@ -1536,15 +1547,22 @@ int tune_candidates(Ctx& c, int l, int kernel, int* out, int max_out) {
 // the load remain.  Elements of small degree are packed several to a CTA.
 // Frozen elements are left untouched (ADD) or zeroed (!ADD).
 // IDX: offset type (32-bit when every patch index of the level fits)
+// threads per CTA of the one-element-per-CTA combine (N^3 >= 256)
+__host__ __device__ constexpr int combine_threads(int n3) { return n3 > 512 ? 256 : 128; }
+
 template <int N, typename T, bool ADD, typename TO, typename IDX>
 __global__ void __launch_bounds__(256) k_combine(const LevelView<T> L, const T* __restrict__ patch,
                                                   TO* __restrict__ u) {
   constexpr int N3 = N * N * N;
+  // small elements: several per CTA, one node per thread; large ones: one per
+  // CTA of combine_threads(N3) threads with NPT nodes each, whose (up to
+  // 8 NPT) loads are all issued before the first sum (the kernel is bound by
+  // load latency)
   constexpr int EPB = N3 >= 256 ? 1 : 256 / N3;
+  constexpr int NPT = N3 >= 256 ? (N3 + combine_threads(N3) - 1) / combine_threads(N3) : 1;
   __shared__ IDX s_off[EPB][27];
   __shared__ int s_frz[EPB];
   const int m = L.m, nsm = L.nsm;
-  const IDX NS3 = (IDX)nsm * nsm * nsm;
   const int e0 = blockIdx.x * EPB;
   if (threadIdx.x < EPB) {
     const int e = e0 + threadIdx.x;
@@ -1560,34 +1578,47 @@ __global__ void __launch_bounds__(256) k_combine(const LevelView<T> L, const T* 
     s_off[el][t % 27] = e < L.ne ? coff[27 * (size_t)e0 + t] : kNone;
   }
   __syncthreads();
-  for (int t = threadIdx.x; t < EPB * N3; t += blockDim.x) {
-    const int el = EPB == 1 ? 0 : t / N3, n = EPB == 1 ? t : t % N3;
-    const int e = e0 + el;
-    if (e >= L.ne) continue;
-    const size_t g = (size_t)e * N3 + n;
-    if (s_frz[el]) {
-      if (!ADD) u[g] = TO(0);
-      continue;
-    }
+  const int stride = EPB == 1 ? (int)blockDim.x : 0;
+  const int el = EPB == 1 ? 0 : (int)threadIdx.x / N3;
+  const int e = e0 + el;
+  if (EPB > 1 && ((int)threadIdx.x >= EPB * N3)) return;
+  if (e >= L.ne) return;
+  const int n0 = EPB == 1 ? (int)threadIdx.x : (int)threadIdx.x % N3;
+  if (s_frz[el]) {
+    if (!ADD)
+#pragma unroll
+      for (int q = 0; q < NPT; ++q)
+        if (n0 + q * stride < N3) u[(size_t)e * N3 + n0 + q * stride] = TO(0);
+    return;
+  }
+  // per node and direction the own slot (1) and at most one neighbour slot (0
+  // or 2): the 8 candidates of every node, loads first
+  T v[NPT][8];
+#pragma unroll
+  for (int q = 0; q < NPT; ++q) {
+    const int n = n0 + q * stride;
+    const bool in = n < N3;
     const int i = n % N, j = (n / N) % N, k = n / (N * N);
-    // per direction the own slot (1) and at most one neighbour slot (0 or 2)
     const int cx = i < m ? 0 : (i >= N - m ? 2 : -1);
     const int cy = j < m ? 0 : (j >= N - m ? 2 : -1);
     const int cz = k < m ? 0 : (k >= N - m ? 2 : -1);
     const IDX loc = ((IDX)k * nsm + j) * nsm + i;
-    // the (up to) 8 candidate loads are independent: unrolled so that they are
-    // all in flight together
-    T v[8];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const int sx = (q & 1) ? cx : 1, sy = (q & 2) ? cy : 1, sz = (q & 4) ? cz : 1;
-      const IDX off = (sx < 0 || sy < 0 || sz < 0) ? kNone : s_off[el][sx + 3 * sy + 9 * sz];
-      v[q] = off != kNone ? patch[off + loc] : T(0);
+    for (int c = 0; c < 8; ++c) {
+      const int sx = (c & 1) ? cx : 1, sy = (c & 2) ? cy : 1, sz = (c & 4) ? cz : 1;
+      const IDX off = (!in || sx < 0 || sy < 0 || sz < 0) ? kNone : s_off[el][sx + 3 * sy + 9 * sz];
+      v[q][c] = off != kNone ? patch[off + loc] : T(0);
     }
+  }
+#pragma unroll
+  for (int q = 0; q < NPT; ++q) {
+    const int n = n0 + q * stride;
+    if (n >= N3) continue;
     // summed in the fixed order own, x, y, xy, z, ... (deterministic)
     T s = T(0);   // accumulated in the smoother precision
 #pragma unroll
-    for (int q = 0; q < 8; ++q) s += v[q];
+    for (int c = 0; c < 8; ++c) s += v[q][c];
+    const size_t g = (size_t)e * N3 + n;
     if (ADD) u[g] += (TO)s;
     else u[g] = (TO)s;
   }
@@ -1597,7 +1628,7 @@ template <typename T, bool ADD, typename TO>
 static int combine_launch(const LevelView<T>& L, int N, const T* patch, TO* u, cudaStream_t st) {
   auto go = [&](auto k32, auto k64, int n3) {
     const int epb = n3 >= 256 ? 1 : 256 / n3;
-    const int bs = n3 >= 256 ? 256 : ((epb * n3 + 31) / 32) * 32;
+    const int bs = n3 >= 256 ? combine_threads(n3) : ((epb * n3 + 31) / 32) * 32;
     const unsigned grid = (unsigned)((L.ne + epb - 1) / epb);
     const long long nsm = L.nsm;
     if ((long long)L.ne * nsm * nsm * nsm < (1LL << 31))
@@ -2049,15 +2080,39 @@ int prepare_transfer(const TransferView& T) {
   ptransfer_launch<2, float>(T, nullptr, nullptr, nullptr, nullptr, (float*)nullptr, nullptr, true);
   ptransfer_launch<2, float, float>(T, nullptr, nullptr, nullptr, nullptr, (float*)nullptr, nullptr,
                                     true);
+  ptransfer_launch<0, double, float>(T, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, true);
+  ptransfer_launch<1, double, float>(T, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, true);
   CK(cudaGetLastError());
   return DGFAS_OK;
+}
+
+// Transfers below the top in a mixed-precision context may run in FP32
+// arithmetic (FP64 vectors in and out), as the smoothers do:
+//  - the restriction R r feeds only the parent's correction problem, whose
+//    right-hand side needs the accuracy of r relative to |r| (iterative
+//    refinement: the FP64 top residual of the next cycle removes the rest);
+//  - the projection ubar = P u onto a level that, like every level below it,
+//    has neither leaf nor frozen elements only sets where that level's
+//    correction starts (its residual is R r, its correction returns as
+//    u - ubar with ubar stored as given, and the root's right-hand side
+//    A ubar + R r is formed from the same ubar).
+// Projections onto or above levels with leaf or frozen elements (whose rows
+// see the projected values as data) and FP64 contexts keep FP64 arithmetic.
+static bool transfer32(const Ctx& c, int lc, bool projection) {
+  if (c.prm.precision == DGFAS_FP64) return false;
+  if (projection)
+    for (int k = 0; k <= lc; ++k)
+      if (c.lv[k].has_leaf || c.lv[k].has_frozen) return false;
+  return true;
 }
 
 int launch_project(Ctx& c, int l, const double* uf) {
   LevelHost& F = c.lv[l];
   LevelHost& C = c.lv[l - 1];
-  if (!ptransfer_launch<0, double>(F.tr, uf, nullptr, C.u, C.ubar, nullptr, c.stream) &&
-      !htransfer_launch<0, double>(F.tr, uf, nullptr, C.u, C.ubar, nullptr, c.stream))
+  const bool done = transfer32(c, l - 1, true)
+      ? ptransfer_launch<0, double, float>(F.tr, uf, nullptr, C.u, C.ubar, nullptr, c.stream)
+      : ptransfer_launch<0, double>(F.tr, uf, nullptr, C.u, C.ubar, nullptr, c.stream);
+  if (!done && !htransfer_launch<0, double>(F.tr, uf, nullptr, C.u, C.ubar, nullptr, c.stream))
     k_gather_children<false><<<C.ne, 256, transfer_smem(F.tr), c.stream>>>(F.tr, uf, C.u, C.ubar);
   ++g_kernels;
   CK(cudaGetLastError());
@@ -2067,8 +2122,10 @@ int launch_project(Ctx& c, int l, const double* uf) {
 int launch_restrict(Ctx& c, int l, const double* rf, double* rc) {
   LevelHost& F = c.lv[l];
   LevelHost& C = c.lv[l - 1];
-  if (!ptransfer_launch<1, double>(F.tr, rf, nullptr, rc, nullptr, nullptr, c.stream) &&
-      !htransfer_launch<1, double>(F.tr, rf, nullptr, rc, nullptr, nullptr, c.stream))
+  const bool done = transfer32(c, l - 1, false)
+      ? ptransfer_launch<1, double, float>(F.tr, rf, nullptr, rc, nullptr, nullptr, c.stream)
+      : ptransfer_launch<1, double>(F.tr, rf, nullptr, rc, nullptr, nullptr, c.stream);
+  if (!done && !htransfer_launch<1, double>(F.tr, rf, nullptr, rc, nullptr, nullptr, c.stream))
     k_gather_children<true><<<C.ne, 256, transfer_smem(F.tr), c.stream>>>(F.tr, rf, rc, nullptr);
   ++g_kernels;
   CK(cudaGetLastError());

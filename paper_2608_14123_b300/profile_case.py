@@ -13,7 +13,8 @@ own operator launches, on the root, stay outside it).  apply_fp32: the
 smoothers' FP32 operator (g - A u, metric recomputed from the trilinear map)
 on 32^3 such elements (16.8M DoF; its FP32 vectors and face data, about
 0.6 GB, exceed L2 as well).  scg_bf16: the top-level SCG steps of the
-mixed-precision smoother (BF16 tensor-core Schwarz sweep) on the same mesh.
+mixed-precision smoother (BF16 tensor-core Schwarz sweep) on the 32^3 mesh
+(the weighted patches alone take 0.23 GB).
 """
 import sys
 
@@ -27,7 +28,7 @@ def main():
     case = sys.argv[1] if len(sys.argv) > 1 else "apply_fp64"
     reps = int(sys.argv[2]) if len(sys.argv) > 2 else 3
     rng = np.random.default_rng(wl.SEED_BASE + 5)
-    V = wl.perturbed_vertices(32 if case == "apply_fp32" else 16, 0.15, rng)
+    V = wl.perturbed_vertices(16 if case == "apply_fp64" else 32, 0.15, rng)
     levels = wl.hierarchy(V, [7, 3, 1], h_root=4)
     prec = dgfas.DGFAS_FP64 if case == "apply_fp64" else dgfas.DGFAS_BF16
     S = dgfas.Solver(levels, 5.0, 0.08, 2, 2, 4, precision=prec, smoother=dgfas.DGFAS_SCG)
