@@ -297,6 +297,20 @@ __global__ void __launch_bounds__(128, 8) k_fd_tc(const LevelView<float> L, cons
   __syncthreads();
   fence_after();
   const uint32_t tmem = s.tslot;
+  // Subdomains of width <= 12: every row index (X, Y) of the six products
+  // with X >= 12 (rows 192..255: warps 2 and 3 of the second M tile) belongs
+  // to no patch position, so those rows are neither read back from TMEM nor
+  // written as the next operand.  Their operand entries keep whatever they
+  // hold, finite since the buffers are zeroed here: rows of A with X >= 12
+  // only produce such rows of D, and columns (K) >= 12 meet the zero-padded
+  // rows of the S tiles.
+  constexpr bool kSkipHi = TN > 0 && TN + 2 * TM <= 12;
+  if (kSkipHi) {
+    uint4* z = reinterpret_cast<uint4*>(&s.A[0][0][0]);
+    for (int t = tid; t < (int)(sizeof(s.A) / sizeof(uint4)); t += 128) z[t] = make_uint4(0, 0, 0, 0);
+    fence_async_smem();
+    __syncthreads();
+  }
   uint32_t phase = 0;
   bool alive = true;
   int prev = -1;   // variant triple of the tables currently in shared memory
@@ -438,6 +452,7 @@ __global__ void __launch_bounds__(128, 8) k_fd_tc(const LevelView<float> L, cons
     if (!(alive = tc_step(s, 0, 0, false, tmem, phase))) break;
 #pragma unroll
     for (int t = 0; t < 2; ++t) {
+      if (kSkipHi && t == 1 && warp >= 2) continue;   // rows with first index >= 12
       const int rr = 128 * t + 32 * warp + lane;
       tc_read1(tmem, t, x);
       st_mn(s.A[1][0], 16 * (rr >> 4), rr & 15, x);
@@ -446,6 +461,7 @@ __global__ void __launch_bounds__(128, 8) k_fd_tc(const LevelView<float> L, cons
     if (!(alive = tc_step(s, 1, 2, true, tmem, phase))) break;
 #pragma unroll
     for (int t = 0; t < 2; ++t) {
+      if (kSkipHi && t == 1 && warp >= 2) continue;   // rows with first index >= 12
       const int rr = 128 * t + 32 * warp + lane;
       tc_read1(tmem, t, x);
       st_mn(s.A[0][0], 16 * (rr & 15), rr >> 4, x);
@@ -454,6 +470,7 @@ __global__ void __launch_bounds__(128, 8) k_fd_tc(const LevelView<float> L, cons
     if (!(alive = tc_step(s, 0, 4, true, tmem, phase))) break;
 #pragma unroll
     for (int t = 0; t < 2; ++t) {
+      if (kSkipHi && t == 1 && warp >= 2) continue;   // rows with first index >= 12
       const int rr = 128 * t + 32 * warp + lane;
       tc_read1(tmem, t, x);
       const float d0 = g0 + g1 * s.lam[0][rr >> 4] + g2 * s.lam[1][rr & 15];
@@ -465,6 +482,7 @@ __global__ void __launch_bounds__(128, 8) k_fd_tc(const LevelView<float> L, cons
     if (!(alive = tc_step(s, 1, 5, false, tmem, phase))) break;
 #pragma unroll
     for (int t = 0; t < 2; ++t) {
+      if (kSkipHi && t == 1 && warp >= 2) continue;   // rows with first index >= 12
       const int rr = 128 * t + 32 * warp + lane;
       tc_read1(tmem, t, x);
       st_mn(s.A[0][0], 16 * (rr >> 4), rr & 15, x);
@@ -473,6 +491,7 @@ __global__ void __launch_bounds__(128, 8) k_fd_tc(const LevelView<float> L, cons
     if (!(alive = tc_step(s, 0, 3, true, tmem, phase))) break;
 #pragma unroll
     for (int t = 0; t < 2; ++t) {
+      if (kSkipHi && t == 1 && warp >= 2) continue;   // rows with first index >= 12
       const int rr = 128 * t + 32 * warp + lane;
       tc_read1(tmem, t, x);
       st_mn(s.A[1][0], 16 * (rr & 15), rr >> 4, x);
@@ -486,6 +505,7 @@ __global__ void __launch_bounds__(128, 8) k_fd_tc(const LevelView<float> L, cons
       float* Pst = reinterpret_cast<float*>(&s.A[0][0][0]);
 #pragma unroll
       for (int t = 0; t < 2; ++t) {
+        if (kSkipHi && t == 1 && warp >= 2) continue;   // rows with first index >= 12
         const int rr = 128 * t + 32 * warp + lane;
         tc_read1(tmem, t, x);
         const int cc = rr >> 4, bb = rr & 15;
