@@ -399,6 +399,9 @@ def solve_record(S, u, b, torch, rtol=1e-10, max_cycles=40):
     t0 = time.perf_counter()
     info = S.dgfas_solve(u, b, rtol, max_cycles, raise_on_fail=False)
     torch.cuda.synchronize()
+    if info["code"] != 0:
+        print(f"bench: solve stopped with code {info['code']} after {info['cycles']} cycles "
+              f"(relative residual {info['r_final'] / info['r0']:.3e})", file=sys.stderr)
     return {"seconds": time.perf_counter() - t0, "cycles": info["cycles"],
             "rel_residual": info["r_final"] / info["r0"], "code": info["code"],
             "history": [h / info["history"][0] for h in info["history"][1:]]}

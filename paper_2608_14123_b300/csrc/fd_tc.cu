@@ -298,13 +298,19 @@ __global__ void __launch_bounds__(128, 8) k_fd_tc(const LevelView<float> L, cons
   fence_after();
   const uint32_t tmem = s.tslot;
   // Subdomains of width <= 12: every row index (X, Y) of the six products
-  // with X >= 12 (rows 192..255: warps 2 and 3 of the second M tile) belongs
-  // to no patch position, so those rows are neither read back from TMEM nor
-  // written as the next operand.  Their operand entries keep whatever they
-  // hold, finite since the buffers are zeroed here: rows of A with X >= 12
-  // only produce such rows of D, and columns (K) >= 12 meet the zero-padded
-  // rows of the S tiles.
+  // with X >= 12 (rows 192..255: warps 2 and 3 of the second M tile) or
+  // Y >= 12 (lanes 12..15 of every 16) belongs to no patch position, so those
+  // rows are not read back from TMEM (whole warps) or not written as the next
+  // operand (single lanes).  Their operand entries keep whatever they hold,
+  // which must be finite: such rows of A only produce such rows of D, and
+  // such columns (K) meet the zero-padded rows of the S tiles, where 0 x Inf
+  // or 0 x NaN would poison the sum.  The buffers are zeroed here, every
+  // later write is a finite BF16 value except the FP32 patch staging, whose
+  // only bytes outside the regions rewritten before the next product are
+  // zeroed again per element (below).
   constexpr bool kSkipHi = TN > 0 && TN + 2 * TM <= 12;
+  constexpr int kStagedTail = TC_TILE - 4096;   // bytes of a tile beyond the K-major span
+  static_assert(kStagedTail % 16 == 0 && kStagedTail / 16 <= 128, "tail zeroing");
   if (kSkipHi) {
     uint4* z = reinterpret_cast<uint4*>(&s.A[0][0][0]);
     for (int t = tid; t < (int)(sizeof(s.A) / sizeof(uint4)); t += 128) z[t] = make_uint4(0, 0, 0, 0);
@@ -317,6 +323,13 @@ __global__ void __launch_bounds__(128, 8) k_fd_tc(const LevelView<float> L, cons
   for (int e = blockIdx.x; e < L.ne && alive; e += gridDim.x) {
     if (L.cls[e] == DGFAS_FROZEN) continue;
     __syncthreads();   // the previous element's patch store has read s.W
+    if (kSkipHi && tid < kStagedTail / 16) {
+      // the FP32 patch staging overwrote bytes [4096, TC_TILE) of A[0]'s
+      // first tile, which the K-major gather does not rewrite and the
+      // skipped rows of the MN-major products would leave in place: FP32 bit
+      // patterns read as BF16 can be Inf or NaN, and 0 x NaN is NaN
+      reinterpret_cast<uint4*>(s.A[0][0] + 4096)[tid] = make_uint4(0, 0, 0, 0);
+    }
     const int v1 = L.var[3 * e], v2 = L.var[3 * e + 1], v3 = L.var[3 * e + 2];
     const int key = v1 | (v2 << 4) | (v3 << 8);
     if (tid < 27) s.nb[tid] = L.nbr27[27 * e + tid];
@@ -454,7 +467,8 @@ __global__ void __launch_bounds__(128, 8) k_fd_tc(const LevelView<float> L, cons
     for (int t = 0; t < 2; ++t) {
       if (kSkipHi && t == 1 && warp >= 2) continue;   // rows with first index >= 12
       const int rr = 128 * t + 32 * warp + lane;
-      tc_read1(tmem, t, x);
+      tc_read1(tmem, t, x);   // warp-collective: every lane reads
+      if (kSkipHi && (rr & 15) >= 12) continue;   // second index >= 12: no patch position
       st_mn(s.A[1][0], 16 * (rr >> 4), rr & 15, x);
     }
     // 2: S2^T along b: rows (c, a') -> x b'; write rows (a', b'), K = c (MN-major)
@@ -463,7 +477,8 @@ __global__ void __launch_bounds__(128, 8) k_fd_tc(const LevelView<float> L, cons
     for (int t = 0; t < 2; ++t) {
       if (kSkipHi && t == 1 && warp >= 2) continue;   // rows with first index >= 12
       const int rr = 128 * t + 32 * warp + lane;
-      tc_read1(tmem, t, x);
+      tc_read1(tmem, t, x);   // warp-collective: every lane reads
+      if (kSkipHi && (rr & 15) >= 12) continue;   // second index >= 12: no patch position
       st_mn(s.A[0][0], 16 * (rr & 15), rr >> 4, x);
     }
     // 3: S3^T along c: rows (a', b') -> x c'; scale by D^-1 in FP32; same rows, K = c' (K-major)
@@ -472,7 +487,8 @@ __global__ void __launch_bounds__(128, 8) k_fd_tc(const LevelView<float> L, cons
     for (int t = 0; t < 2; ++t) {
       if (kSkipHi && t == 1 && warp >= 2) continue;   // rows with first index >= 12
       const int rr = 128 * t + 32 * warp + lane;
-      tc_read1(tmem, t, x);
+      tc_read1(tmem, t, x);   // warp-collective: every lane reads
+      if (kSkipHi && (rr & 15) >= 12) continue;   // second index >= 12: no patch position
       const float d0 = g0 + g1 * s.lam[0][rr >> 4] + g2 * s.lam[1][rr & 15];
 #pragma unroll
       for (int q = 0; q < 16; ++q) x[q] = __fdividef(x[q], d0 + g3 * s.lam[2][q]);
@@ -484,7 +500,8 @@ __global__ void __launch_bounds__(128, 8) k_fd_tc(const LevelView<float> L, cons
     for (int t = 0; t < 2; ++t) {
       if (kSkipHi && t == 1 && warp >= 2) continue;   // rows with first index >= 12
       const int rr = 128 * t + 32 * warp + lane;
-      tc_read1(tmem, t, x);
+      tc_read1(tmem, t, x);   // warp-collective: every lane reads
+      if (kSkipHi && (rr & 15) >= 12) continue;   // second index >= 12: no patch position
       st_mn(s.A[0][0], 16 * (rr >> 4), rr & 15, x);
     }
     // 5: S2 along b: rows (a', c'') -> x b''; write rows (c'', b''), K = a' (MN-major)
@@ -493,7 +510,8 @@ __global__ void __launch_bounds__(128, 8) k_fd_tc(const LevelView<float> L, cons
     for (int t = 0; t < 2; ++t) {
       if (kSkipHi && t == 1 && warp >= 2) continue;   // rows with first index >= 12
       const int rr = 128 * t + 32 * warp + lane;
-      tc_read1(tmem, t, x);
+      tc_read1(tmem, t, x);   // warp-collective: every lane reads
+      if (kSkipHi && (rr & 15) >= 12) continue;   // second index >= 12: no patch position
       st_mn(s.A[1][0], 16 * (rr & 15), rr >> 4, x);
     }
     // 6: S1 along a: rows (c'', b'') -> x a''; weight, stage the patch in the

@@ -1624,8 +1624,93 @@ __global__ void __launch_bounds__(256) k_combine(const LevelView<T> L, const T* 
   }
 }
 
+// FP32 combine of an even-degree-count level (N even) with even overlap m
+// and even subdomain width: nodes i and i + 1 (i even) lie in the same
+// candidate subdomains (m and N - m are even), and every patch offset and
+// node position is even, so each pair is read as one float2 per candidate.
+// One element per CTA of 128 threads, PPT pairs per thread, loads first;
+// the sums are those of k_combine, in the same order.
+template <int N, bool ADD, typename TO, typename IDX>
+__global__ void __launch_bounds__(128) k_combine_pair(const LevelView<float> L,
+                                                       const float* __restrict__ patch,
+                                                       TO* __restrict__ u) {
+  constexpr int N3 = N * N * N, NP = N3 / 2;
+  constexpr int PPT = (NP + 127) / 128;
+  __shared__ IDX s_off[27];
+  const int m = L.m, nsm = L.nsm;
+  const int e = blockIdx.x;
+  constexpr IDX kNone = std::numeric_limits<IDX>::min();
+  const IDX* coff = reinterpret_cast<const IDX*>(L.coff);
+  if (threadIdx.x < 27) s_off[threadIdx.x] = coff[27 * (size_t)e + threadIdx.x];
+  __syncthreads();
+  const size_t base = (size_t)e * N3;
+  if (L.cls[e] == DGFAS_FROZEN) {
+    if (!ADD)
+      for (int t = threadIdx.x; t < N3; t += blockDim.x) u[base + t] = TO(0);
+    return;
+  }
+  float2 v[PPT][8];
+#pragma unroll
+  for (int q = 0; q < PPT; ++q) {
+    const int pr = threadIdx.x + q * 128;
+    const bool in = pr < NP;
+    const int n = 2 * pr;
+    const int i = n % N, j = (n / N) % N, k = n / (N * N);
+    const int cx = i < m ? 0 : (i >= N - m ? 2 : -1);
+    const int cy = j < m ? 0 : (j >= N - m ? 2 : -1);
+    const int cz = k < m ? 0 : (k >= N - m ? 2 : -1);
+    const IDX loc = ((IDX)k * nsm + j) * nsm + i;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      const int sx = (c & 1) ? cx : 1, sy = (c & 2) ? cy : 1, sz = (c & 4) ? cz : 1;
+      const IDX off = (!in || sx < 0 || sy < 0 || sz < 0) ? kNone : s_off[sx + 3 * sy + 9 * sz];
+      v[q][c] = off != kNone ? __ldg(reinterpret_cast<const float2*>(patch + off + loc))
+                             : make_float2(0.f, 0.f);
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < PPT; ++q) {
+    const int pr = threadIdx.x + q * 128;
+    if (pr >= NP) continue;
+    float s0 = 0.f, s1 = 0.f;   // the fixed order own, x, y, xy, z, ... (deterministic)
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      s0 += v[q][c].x;
+      s1 += v[q][c].y;
+    }
+    const size_t g = base + 2 * (size_t)pr;
+    if (ADD) {
+      u[g] += (TO)s0;
+      u[g + 1] += (TO)s1;
+    } else {
+      u[g] = (TO)s0;
+      u[g + 1] = (TO)s1;
+    }
+  }
+}
+
 template <typename T, bool ADD, typename TO>
 static int combine_launch(const LevelView<T>& L, int N, const T* patch, TO* u, cudaStream_t st) {
+  if constexpr (std::is_same<T, float>::value) {
+    // paired form: FP32 patches, N = 8 or 10, even m and subdomain width,
+    // 8-byte aligned patch and output
+    const bool pair_ok = (N == 8 || N == 10) && L.m % 2 == 0 && L.nsm % 2 == 0 &&
+                         (uintptr_t)patch % 8 == 0 && (uintptr_t)u % (2 * sizeof(TO)) == 0;
+    if (pair_ok) {
+      const long long nsm = L.nsm;
+      const bool i32 = (long long)L.ne * nsm * nsm * nsm < (1LL << 31);
+      if (N == 8) {
+        if (i32) k_combine_pair<8, ADD, TO, int><<<L.ne, 128, 0, st>>>(L, patch, u);
+        else k_combine_pair<8, ADD, TO, long long><<<L.ne, 128, 0, st>>>(L, patch, u);
+      } else {
+        if (i32) k_combine_pair<10, ADD, TO, int><<<L.ne, 128, 0, st>>>(L, patch, u);
+        else k_combine_pair<10, ADD, TO, long long><<<L.ne, 128, 0, st>>>(L, patch, u);
+      }
+      ++g_kernels;
+      CK(cudaGetLastError());
+      return DGFAS_OK;
+    }
+  }
   auto go = [&](auto k32, auto k64, int n3) {
     const int epb = n3 >= 256 ? 1 : 256 / n3;
     const int bs = n3 >= 256 ? combine_threads(n3) : ((epb * n3 + 31) / 32) * 32;

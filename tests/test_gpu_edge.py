@@ -1,5 +1,6 @@
 """Edge cases and full-size sampled parity of the CUDA path against the oracle:
-maximum degree (p = 10, N = 11), a ragged 3 x 5 x 2 mesh, a single element,
+maximum degree (p = 10, N = 11; FP64 and the FP32 smoother operator), a
+ragged 3 x 5 x 2 mesh, a single element,
 invalid arguments, and the full 32^3, p = 8 workload (the bench's launch
 configuration) checked on sampled elements."""
 import numpy as np
@@ -28,7 +29,15 @@ def _apply_and_sweep(S, H, seed=1):
         ud, gd = torch.from_numpy(u).cuda(), torch.from_numpy(g).cuda()
         out = torch.empty_like(ud)
         S.dgfas_apply_op(l, ud, gd, out)
-        assert rel(out.cpu().numpy(), g - H.A(l, u)) < 1e-12, l
+        Au = H.A(l, u)
+        assert rel(out.cpu().numpy(), g - Au) < 1e-12, l
+        # the smoothers' FP32 operator on the FP32-rounded u (curvilinear
+        # levels: metric recomputed from the trilinear map), 3e-5 of max |A u|
+        u32 = u.astype(np.float32)
+        Au32 = H.A(l, u32.astype(np.float64))
+        o32 = torch.empty(n, dtype=torch.float32, device="cuda")
+        S.dgfas_apply_op32(l, torch.from_numpy(u32).cuda(), gd, o32)
+        assert np.abs(o32.cpu().numpy() - (g - Au32)).max() <= 3e-5 * (np.abs(Au32).max() + 1.0), l
         if l > 0:
             S.dgfas_schwarz_smooth(l, ud, gd, 1)
             ref = H.was(l, u, g, 1)

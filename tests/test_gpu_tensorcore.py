@@ -76,3 +76,43 @@ def test_tcgen05_mn_major_operand_selftest():
     n = np.arange(16)[:, None]
     B = ((3 * n + k) % 5 - 2).astype(np.float64)
     np.testing.assert_array_equal(out.reshape(2, 128, 16)[1], A @ B.T)
+
+
+def test_bf16_sweep_many_elements_per_cta():
+    """The tensor-core FD keeps one CTA per SM slot and walks several elements
+    per CTA (about 3.5 here: 4096 elements, p = 7, curvilinear), reusing its
+    shared operand buffers; the small workloads give most CTAs one element.
+    The sweep must stay finite and within BF16 rounding of the FP32 SIMT sweep
+    on every node block, and a BF16 SCG solve must reach 1e-10."""
+    from paper_2608_14123_b300 import workloads as wl
+    from tests.gpu_helpers import torch_cuda
+    torch = torch_cuda()
+    rng = np.random.default_rng(wl.SEED_BASE + 5)
+    V = wl.perturbed_vertices(16, 0.15, rng)
+    levels = wl.hierarchy(V, [7, 3, 1], h_root=4)
+    top = len(levels) - 1
+    n = levels[top]["corners"].shape[0] * 8 ** 3
+    u = rng.uniform(-1, 1, n)
+    g = rng.uniform(-1, 1, n)
+    d = {}
+    for prec in (dgfas.DGFAS_FP32, dgfas.DGFAS_BF16):
+        S = dgfas.Solver(levels, 5.0, 0.08, 2, 2, 4, precision=prec, smoother=dgfas.DGFAS_SCG)
+        ud = torch.from_numpy(u).cuda()
+        S.dgfas_schwarz_smooth(top, ud, torch.from_numpy(g).cuda(), 1)
+        assert S.dgfas_tc_error() == 0
+        d[prec] = ud.cpu().numpy() - u
+        S.close()
+    d16, d32 = d[dgfas.DGFAS_BF16], d[dgfas.DGFAS_FP32]
+    assert np.all(np.isfinite(d16))
+    # per element: BF16 rounding of the six mode products, well below 10%
+    e16, e32 = d16.reshape(-1, 512), d32.reshape(-1, 512)
+    per = np.linalg.norm(e16 - e32, axis=1) / np.linalg.norm(e32, axis=1)
+    assert per.max() < 0.1, per.max()
+    S = dgfas.Solver(levels, 5.0, 0.08, 2, 2, 4, precision=dgfas.DGFAS_BF16,
+                     smoother=dgfas.DGFAS_SCG)
+    b = torch.from_numpy(g).cuda()
+    x = torch.zeros(n, dtype=torch.float64, device="cuda")
+    info = S.dgfas_solve(x, b, 1e-10, 20)
+    assert info["r_final"] <= 1e-10 * info["r0"]
+    assert S.dgfas_tc_error() == 0
+    S.close()
