@@ -66,10 +66,10 @@ def apply_flops_per_dof(N, box=True):
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
 # dominant kernel, from one ncu capture of the current kernels on a 16^3,
 # p = 7 curvilinear case (2,097,152 DoF, vectors and geometry larger than L2:
-# k_curv_grad 155.3 + 48.1 MB, k_curv_div 143.0 + 9.5 MB), scaled by the DoF
+# k_curv_grad 155.2 + 45.4 MB, k_curv_div 142.9 + 4.5 MB), scaled by the DoF
 # of the 64^3 level (x 64; the per-element data grow in proportion); to be
 # retaken whenever the kernels change
-NCU_TRAFFIC = {"residual_fp64": int((155259136 + 48112640 + 142958080 + 9480960) * 64)}
+NCU_TRAFFIC = {"residual_fp64": int((155234560 + 45440768 + 142932480 + 4498688) * 64)}
 
 
 def fd_flops_per_dof(N, m):
