@@ -940,15 +940,8 @@ template <int N, typename T, typename TU, typename TB, typename TO>
 static int apply_N(const LevelView<T>& L, const TU* u, const TB* b, TO* out, T alpha,
                    cudaStream_t st, int epb_req, T* scratch) {
   constexpr int N2 = N * N, N3 = N * N * N;
-  int epb = (128 + N2 - 1) / N2;
-  if (epb_req > 0) epb = std::max(1, std::min(epb_req, 256 / N2));
-  size_t smem = (N2 + 16 + (size_t)6 * N3 * epb) * sizeof(T);
-  while (epb > 1 && smem > 100 * 1024) {
-    --epb;
-    smem = (N2 + 16 + (size_t)6 * N3 * epb) * sizeof(T);
-  }
-  dim3 blk(N2, epb), grd((L.ne + epb - 1) / epb);
-  // the attribute is set once per instantiation (never inside a graph capture)
+  // each branch sizes its own launch; the shared-memory attribute is set once
+  // per instantiation (never inside a graph capture)
   if (L.box) {
     int epb2 = (128 + N2 - 1) / N2;
     if (epb_req > 0) epb2 = epb_req;
