@@ -139,3 +139,50 @@ def test_full_size_config2_sampled_parity():
         sw = schwarz.Schwarz(sub, pr["delta"], pr["mu_star"])
         ref = sw.correction(r).reshape(-1, N3)[k]
         assert rel(du.reshape(-1, N3)[e], ref) < 1e-10, e
+
+
+def test_full_size_config5_sampled_parity():
+    """The bench's headline level, 64^3 curvilinear elements at p = 7 (134M
+    DoF): the FP64 residual (two-pass operator), the FP32 operator of the
+    smoothers (metric recomputed from the trilinear map) and one FP64 Schwarz
+    sweep on the GPU at full size, compared on sampled elements (corner, edge,
+    face, interior) with the oracle evaluated on the 7^3-element patch around
+    each sample."""
+    torch = torch_cuda()
+    from oracle import schwarz, sip
+    cfg = wl.config(5)
+    pr = cfg["params"]
+    S = dgfas.Solver(cfg["levels"], pr["mu_star"], pr["delta"], pr["s1"], pr["s2"], pr["sc"],
+                     precision=dgfas.DGFAS_FP64)
+    top = cfg["levels"][-1]
+    L = S.n_levels - 1
+    N3 = 8 ** 3
+    rng = np.random.default_rng(6)
+    n = S.ndof(L)
+    u = rng.uniform(-1, 1, n)
+    g = rng.uniform(-1, 1, n)
+    u32 = u.astype(np.float32)
+    ud, gd = torch.from_numpy(u).cuda(), torch.from_numpy(g).cuda()
+    out = torch.empty_like(ud)
+    S.dgfas_apply_op(L, ud, gd, out)
+    o32 = torch.empty(n, dtype=torch.float32, device="cuda")
+    S.dgfas_apply_op32(L, torch.from_numpy(u32).cuda(), gd, o32)
+    us = ud.clone()
+    S.dgfas_schwarz_smooth(L, us, gd, 1)
+    out, o32, du = out.cpu().numpy(), o32.cpu().numpy(), (us - ud).cpu().numpy()
+    S.close()
+    samples = [0, 63, 64 * 64 * 32 + 31, 64 * 64 * 32 + 64 * 32 + 32, 64 ** 3 - 1]
+    for e in samples:
+        sub, sel = _patch_level(top, e, 3)
+        k = int(np.nonzero(sel == e)[0][0])
+        ops = sip.LevelOps(sub, pr["mu_star"])
+        gs_ = g.reshape(-1, N3)[sel].reshape(-1)
+        r = gs_ - sip.apply(ops, u.reshape(-1, N3)[sel].reshape(-1)).reshape(-1)
+        assert rel(out.reshape(-1, N3)[e], r.reshape(-1, N3)[k]) < 1e-12, e
+        Au32 = sip.apply(ops, u32.astype(np.float64).reshape(-1, N3)[sel].reshape(-1))
+        ref32 = (gs_ - Au32.reshape(-1)).reshape(-1, N3)[k]
+        scale = np.abs(Au32.reshape(-1, N3)[k]).max() + 1.0
+        assert np.abs(o32.reshape(-1, N3)[e] - ref32).max() <= 3e-5 * scale, e
+        sw = schwarz.Schwarz(sub, pr["delta"], pr["mu_star"])
+        ref = sw.correction(r).reshape(-1, N3)[k]
+        assert rel(du.reshape(-1, N3)[e], ref) < 1e-10, e
