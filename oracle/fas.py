@@ -155,6 +155,23 @@ class Hierarchy:
                 u[l] = self.smooth(l, u[l], f_levels[l], self.s2)
         return self.tr[L].interpolate(u[L - 1])
 
+    def cmg(self, f_levels, sc=None):
+        """Alg. 3 (FAS-CMG, the cascadic startup).  f_levels: each level's own
+        right-hand side, root first.  The root is solved for its right-hand
+        side; then for l = 1 .. L-1 (root = 0) the solution is interpolated,
+        u_l = I_l u_{l-1} (the whole level, frozen elements included), and
+        improved by n_sc smoothing steps (`sc`, default the hierarchy's n_sc)
+        with f_l; the top receives I_L u_{L-1} (the same end as Alg. 4).
+        Returns the list of level vectors, root first, the top's last."""
+        n = self.sc if sc is None else sc
+        L = self.L
+        u = [np.zeros(o.ndof) for o in self.ops]
+        u[0] = self.root_solve(f_levels[0])
+        for l in range(1, L):
+            u[l] = self.smooth(l, self.tr[l].interpolate(u[l - 1]), f_levels[l], n)
+        u[L] = self.tr[L].interpolate(u[L - 1])
+        return u
+
     def cs_vcycle(self, u_top, f_top):
         """Alg. 1."""
         s1, s2 = self.s1, self.s2
