@@ -256,6 +256,16 @@ int dgfas_scg_info(void* ctx, double* out_host);
    Stream-ordered, not captured. */
 int dgfas_fmg(void* ctx, const double* const* f_levels, int cycles_per_level, double* u_top);
 
+/* Cascadic startup (FAS-CMG, Alg. 3): the root is solved for its own
+   right-hand side f_levels[0] (as by the root solver of the context); then
+   for l = 1 .. L-1 the previous level's solution is interpolated to level l
+   (the whole level, frozen elements included), u_l = I u_{l-1}, and improved
+   by n_sc steps of the level smoother (WAS or SCG, in the context's
+   precision) on A_l u_l = f_levels[l]; finally u_top = I u_{L-1}.  Same
+   arguments, level solutions and stream ordering as dgfas_fmg; n_sc >= 0
+   (0: interpolation only).  DGFAS_ERR_UNSUPPORTED for a single level. */
+int dgfas_cmg(void* ctx, const double* const* f_levels, int n_sc, double* u_top);
+
 /* Element error indicators of the adaptive loop (Sec. 6.4): the level-l
    operator applied to the complete error vector eps [ndof(level)] (device),
    restricted to each element and weighted with that element's error

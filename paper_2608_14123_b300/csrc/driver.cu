@@ -1021,6 +1021,31 @@ extern "C" int dgfas_fmg(void* ctx, const double* const* f_levels, int cycles_pe
   return interpolate_solution(*c, L, u_top);
 }
 
+extern "C" int dgfas_cmg(void* ctx, const double* const* f_levels, int n_sc, double* u_top) {
+  Ctx* c = (Ctx*)ctx;
+  if (!c || !f_levels || !u_top || n_sc < 0) return DGFAS_ERR_INVALID;
+  const int L = (int)c->lv.size() - 1;
+  for (int l = 0; l <= L; ++l)
+    if (!f_levels[l]) return DGFAS_ERR_INVALID;
+  if (L < 1) {
+    set_error("cmg: needs at least two levels");
+    return DGFAS_ERR_UNSUPPORTED;
+  }
+  CK(cudaMemcpyAsync(c->lv[0].gv, f_levels[0], c->lv[0].ndof * sizeof(double),
+                     cudaMemcpyDeviceToDevice, c->stream));
+  RET(root_solve(*c, true));
+  for (int l = 1; l < L; ++l) {
+    LevelHost& H = c->lv[l];
+    RET(interpolate_solution(*c, l, H.u));
+    if (n_sc > 0) {
+      // the smoothers start from the residual f_l - A_l u_l in lv[l].r
+      RET(launch_apply(*c, l, DGFAS_FP64, H.u, f_levels[l], H.r, -1.0));
+      RET(smooth(*c, l, H.u, f_levels[l], n_sc, true, false));
+    }
+  }
+  return interpolate_solution(*c, L, u_top);
+}
+
 extern "C" int dgfas_element_energy(void* ctx, int level, const double* eps, double* out) {
   Ctx* c = (Ctx*)ctx;
   if (!c || !eps || !out || level < 0 || level >= (int)c->lv.size()) return DGFAS_ERR_INVALID;

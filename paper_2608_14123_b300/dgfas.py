@@ -62,7 +62,7 @@ SYMBOLS = ["dgfas_setup_levels", "dgfas_destroy", "dgfas_level_ndof", "dgfas_nod
            "dgfas_mlp_forward", "dgfas_mlp_grad", "dgfas_mlp_inputs", "dgfas_mlp_train", "dgfas_learned_surrogate",
            "dgfas_assemble_rhs_level", "dgfas_set_level_rhs", "dgfas_composite_residual",
            "dgfas_get_level_solution", "dgfas_tc_selftest", "dgfas_tc_selftest_mn", "dgfas_tc_error", "dgfas_host_fd_variant", "dgfas_autotune", "dgfas_set_tuning",
-           "dgfas_get_tuning", "dgfas_fmg", "dgfas_element_energy", "dgfas_strerror",
+           "dgfas_get_tuning", "dgfas_fmg", "dgfas_cmg", "dgfas_element_energy", "dgfas_strerror",
            "dgfas_last_error"]
 
 _lib = None
@@ -115,6 +115,7 @@ def load():
         "dgfas_tc_selftest_mn": (I, [P, ctypes.POINTER(I)]),
         "dgfas_autotune": (I, [P, I, P, I, ctypes.POINTER(I)]),
         "dgfas_fmg": (I, [P, ctypes.POINTER(P), I, P]),
+        "dgfas_cmg": (I, [P, ctypes.POINTER(P), I, P]),
         "dgfas_element_energy": (I, [P, I, P, P]),
         "dgfas_set_tuning": (I, [P, I, I, I]),
         "dgfas_get_tuning": (I, [P, I, I, ctypes.POINTER(I), P, I, ctypes.POINTER(I)]),
@@ -300,6 +301,15 @@ class Solver:
         arr = (ctypes.c_void_p * self.n_levels)(*[_ptr(f, self.ndof(l)).value
                                                   for l, f in enumerate(f_levels)])
         _check(load().dgfas_fmg(self.ctx, arr, cycles_per_level, _ptr(u_top, self.ndof())), "fmg")
+
+    def dgfas_cmg(self, f_levels, u_top, n_sc):
+        """Cascadic startup (Alg. 3): u_top <- the CMG start value from the
+        per-level right-hand sides f_levels (root first, device FP64), with
+        n_sc smoothing steps on every intermediate level."""
+        assert len(f_levels) == self.n_levels
+        arr = (ctypes.c_void_p * self.n_levels)(*[_ptr(f, self.ndof(l)).value
+                                                  for l, f in enumerate(f_levels)])
+        _check(load().dgfas_cmg(self.ctx, arr, n_sc, _ptr(u_top, self.ndof())), "cmg")
 
     def dgfas_element_energy(self, level, eps, out):
         """out[e] = eps_e . (A eps)_e on `level` (element error indicators)."""

@@ -103,3 +103,44 @@ def test_fmg_on_local_refinement_matches_oracle():
             r_f = S.dgfas_composite_residual(u, f_gpu[-1])
             info = S.dgfas_solve(u, f_gpu[-1], 1e-10 * r_zero / r_f, 40)
             assert info["r_final"] <= 1e-10 * r_zero * (1 + 1e-9)
+
+
+@pytest.mark.parametrize("cid,small,root,smoother", [(1, False, None, "was"), (2, True, None, "was"),
+                                                     (5, True, "p1", "scg")])
+def test_cmg_start_matches_oracle_fp64(cid, small, root, smoother):
+    """Cascadic startup (Alg. 3): the top start value and the level solutions
+    it leaves below the top match the oracle's (FP64; WAS, and SCG with the
+    SCG root at p = 1), for n_sc = 0 (interpolation only) and the workload's
+    n_sc."""
+    torch = torch_cuda()
+    cfg = wl.config(cid, small=small, root=root)
+    sm = dgfas.DGFAS_SCG if smoother == "scg" else dgfas.DGFAS_WAS
+    S = make_solver(cfg, precision=dgfas.DGFAS_FP64, smoother=sm)
+    H = make_oracle(cfg, smoother=smoother)
+    f_or, f_gpu = _level_rhs(cfg, S, H)
+    for sc in (0, cfg["params"]["sc"]):
+        u = torch.zeros(S.ndof(-1), dtype=torch.float64, device="cuda")
+        S.dgfas_cmg(f_gpu, u, sc)
+        u_or = H.cmg(f_or, sc=sc)
+        assert rel(u.cpu().numpy(), u_or[-1]) < 1e-10, sc
+        for l in range(S.n_levels - 1):
+            ul = torch.empty(S.ndof(l), dtype=torch.float64, device="cuda")
+            S.dgfas_get_level_solution(l, ul)
+            assert rel(ul.cpu().numpy(), u_or[l]) < 1e-10, (sc, l)
+
+
+def test_cmg_then_mixed_solve_reaches_1e10():
+    torch = torch_cuda()
+    cfg = wl.config(2, small=True)
+    S, H = make_solver(cfg, precision=dgfas.DGFAS_BF16), make_oracle(cfg)
+    _, f_gpu = _level_rhs(cfg, S, H)
+    b = f_gpu[-1]
+    r_zero = float(torch.linalg.norm(b))
+    u = torch.zeros_like(b)
+    S.dgfas_cmg(f_gpu, u, cfg["params"]["sc"])
+    r = torch.empty_like(b)
+    S.dgfas_apply_op(-1, u, b, r)
+    r_c = S.dgfas_norm(-1, r)
+    assert r_c < r_zero
+    info = S.dgfas_solve(u, b, 1e-10 * r_zero / r_c, 40)
+    assert info["r_final"] <= 1e-10 * r_zero * (1 + 1e-9)
