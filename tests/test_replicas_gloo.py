@@ -44,3 +44,29 @@ def test_reference_arm_rank_1_does_no_work(capsys, monkeypatch):
         steps, warmup = 1, 0
     bench.run_reference(A())
     assert capsys.readouterr().out == ""
+
+
+def test_reference_arm_prints_the_contract_line(capsys, monkeypatch):
+    """At N = 1 the reference arm (the FP64 oracle on the host cores, a
+    bounded sample of the headline workload) prints one JSON line with the
+    keys of the benchmark contract, the same metric and unit as the GPU arm,
+    and a positive rate."""
+    import json
+
+    import bench
+    monkeypatch.delenv("WORLD_SIZE", raising=False)
+    monkeypatch.delenv("RANK", raising=False)
+
+    class A:
+        steps, warmup = 1, 0
+    bench.run_reference(A())
+    lines = [l for l in capsys.readouterr().out.splitlines() if l.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for k in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+              "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config",
+              "cpu_baseline", "e2e"):
+        assert k in d, k
+    assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["unit"] == bench.UNIT
+    assert d["value"] > 0 and d["cpu_baseline"]["kind"] == "oracle"
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and "workload" in d["config"]
