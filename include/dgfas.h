@@ -33,7 +33,8 @@ extern "C" {
 #define DGFAS_ERR_INVALID -1        /* bad argument or inconsistent mesh arrays */
 #define DGFAS_ERR_OOM -2            /* device allocation failed */
 #define DGFAS_ERR_CUDA -3           /* a CUDA runtime call failed */
-#define DGFAS_ERR_MESH -4           /* non-positive Jacobian at a GLL node */
+#define DGFAS_ERR_MESH -4           /* non-positive Jacobian at a GLL node, or faces
+                                       not shared with aligned local axes */
 #define DGFAS_ERR_NOT_CONVERGED -5  /* max_cycles reached before rtol */
 #define DGFAS_ERR_DIVERGED -6       /* NaN/Inf or residual growth > 1e3 x r_0 */
 #define DGFAS_ERR_UNSUPPORTED -7    /* p > 10, subdomain width > 16, ... */
@@ -130,6 +131,15 @@ typedef struct {
    Errors: INVALID (arrays inconsistent), UNSUPPORTED, MESH, OOM, CUDA. */
 int dgfas_setup_levels(const dgfas_mesh* mesh, const dgfas_params* prm,
                        void* cuda_stream, void** out_ctx);
+
+/* Host-only validation of a hierarchy's input arrays, also run first by
+   dgfas_setup_levels (no device work, callable without a GPU): arrays present,
+   1 <= p <= 10, neighbour indices in range (INVALID / UNSUPPORTED), and the
+   face-neighbour relation reciprocal through the opposite face with the two
+   faces' corners coinciding corner by corner up to one translation (aligned
+   local axes; periodic identification by translation), else DGFAS_ERR_MESH
+   with the element and face in dgfas_last_error(). */
+int dgfas_check_mesh(const dgfas_mesh* mesh);
 
 void dgfas_destroy(void* ctx);
 

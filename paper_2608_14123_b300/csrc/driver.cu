@@ -553,6 +553,89 @@ extern "C" void dgfas_destroy(void* vctx) {
   delete c;
 }
 
+// Host-only checks of one level's input arrays (no device work).  The
+// kernels read a neighbour's data through its opposite face (f ^ 1) in the
+// same face-local node order, so the face-neighbour relation must be
+// reciprocal through the opposite face and the two elements' face corners
+// must coincide corner by corner, up to one translation (periodic meshes
+// identify opposite boundary faces by a translation): aligned local axes.
+static int check_level(const dgfas_level& in, int l) {
+  if (!in.corners || !in.nbr || !in.nbr27 || !in.cls || (l > 0 && (!in.parent || !in.octant))) {
+    set_error("setup: level arrays missing");
+    return DGFAS_ERR_INVALID;
+  }
+  if (in.p < 1 || in.p > 10 || in.n_elem <= 0) {
+    set_error("level: need 1 <= p <= 10 and n_elem > 0");
+    return DGFAS_ERR_UNSUPPORTED;
+  }
+  const int ne = in.n_elem;
+  for (size_t q = 0; q < 27 * (size_t)ne; ++q)
+    if (in.nbr27[q] >= ne || in.nbr27[q] < -1) {
+      set_error("nbr27 out of range");
+      return DGFAS_ERR_INVALID;
+    }
+  for (int e = 0; e < ne; ++e)
+    for (int f = 0; f < 6; ++f) {
+      const int nb = in.nbr[6 * e + f];
+      if (nb >= ne || nb < -2) {
+        set_error("nbr out of range");
+        return DGFAS_ERR_INVALID;
+      }
+    }
+  for (int e = 0; e < ne; ++e) {
+    const double* xe = in.corners + 24 * (size_t)e;
+    double scale = 0.0;   // the element's largest corner-to-corner extent
+    for (int c = 0; c < 8; ++c)
+      for (int k = 0; k < 3; ++k) scale = std::max(scale, std::fabs(xe[3 * c + k] - xe[k]));
+    for (int f = 0; f < 6; ++f) {
+      const int nb = in.nbr[6 * e + f];
+      if (nb < 0) continue;
+      if (in.nbr[6 * (size_t)nb + (f ^ 1)] != e) {
+        set_error("level " + std::to_string(l) + ": face " + std::to_string(f) + " of element " +
+                  std::to_string(e) + " has neighbour " + std::to_string(nb) +
+                  ", whose opposite face does not point back");
+        return DGFAS_ERR_MESH;
+      }
+      const int d = f >> 1, side = f & 1;
+      const double* xn = in.corners + 24 * (size_t)nb;
+      double t0[3] = {0, 0, 0};
+      bool first = true;
+      for (int c = 0; c < 8; ++c) {
+        if (((c >> d) & 1) != side) continue;
+        const int cn = c ^ (1 << d);
+        double t[3];
+        for (int k = 0; k < 3; ++k) t[k] = xe[3 * c + k] - xn[3 * cn + k];
+        if (first) {
+          for (int k = 0; k < 3; ++k) t0[k] = t[k];
+          first = false;
+        } else {
+          for (int k = 0; k < 3; ++k)
+            if (std::fabs(t[k] - t0[k]) > 1e-8 * scale) {
+              set_error("level " + std::to_string(l) + ": face " + std::to_string(f) +
+                        " of element " + std::to_string(e) + " and the opposite face of element " +
+                        std::to_string(nb) +
+                        " do not coincide corner by corner (neighbours must share aligned local axes)");
+              return DGFAS_ERR_MESH;
+            }
+        }
+      }
+    }
+  }
+  return DGFAS_OK;
+}
+
+extern "C" int dgfas_check_mesh(const dgfas_mesh* mesh) {
+  if (!mesh || mesh->n_levels < 1 || !mesh->levels) {
+    set_error("check_mesh: null argument or no levels");
+    return DGFAS_ERR_INVALID;
+  }
+  for (int l = 0; l < mesh->n_levels; ++l) {
+    const int rc = check_level(mesh->levels[l], l);
+    if (rc != DGFAS_OK) return rc;
+  }
+  return DGFAS_OK;
+}
+
 extern "C" int dgfas_setup_levels(const dgfas_mesh* mesh, const dgfas_params* prm,
                                   void* stream, void** out) {
   if (!mesh || !prm || !out || mesh->n_levels < 1 || !mesh->levels) {
@@ -576,6 +659,10 @@ extern "C" int dgfas_setup_levels(const dgfas_mesh* mesh, const dgfas_params* pr
   if (prm->projection != DGFAS_P_INTERP && prm->projection != DGFAS_P_L2) {
     set_error("setup: unknown solution projection");
     return DGFAS_ERR_INVALID;
+  }
+  {
+    const int rc = dgfas_check_mesh(mesh);   // host-only, before any device work
+    if (rc != DGFAS_OK) return rc;
   }
   Ctx* c = new Ctx();
   c->stream = (cudaStream_t)stream;

@@ -18,6 +18,8 @@ DGFAS_FP64, DGFAS_FP32, DGFAS_BF16 = 0, 1, 2
 DGFAS_WAS, DGFAS_SCG = 0, 1
 DGFAS_COARSE_DENSE, DGFAS_COARSE_SCG = 0, 1
 DGFAS_P_INTERP, DGFAS_P_L2 = 0, 1
+(DGFAS_OK, DGFAS_ERR_INVALID, DGFAS_ERR_OOM, DGFAS_ERR_CUDA, DGFAS_ERR_MESH,
+ DGFAS_ERR_NOT_CONVERGED, DGFAS_ERR_DIVERGED, DGFAS_ERR_UNSUPPORTED) = 0, -1, -2, -3, -4, -5, -6, -7
 ERRORS = {0: "ok", -1: "INVALID", -2: "OOM", -3: "CUDA", -4: "MESH", -5: "NOT_CONVERGED",
           -6: "DIVERGED", -7: "UNSUPPORTED"}
 
@@ -55,7 +57,7 @@ class dgfas_info(ctypes.Structure):
                 ("seconds", ctypes.c_double), ("history", ctypes.c_double * 128)]
 
 
-SYMBOLS = ["dgfas_setup_levels", "dgfas_destroy", "dgfas_level_ndof", "dgfas_node_coords",
+SYMBOLS = ["dgfas_setup_levels", "dgfas_check_mesh", "dgfas_destroy", "dgfas_level_ndof", "dgfas_node_coords",
            "dgfas_assemble_rhs", "dgfas_apply_op", "dgfas_apply_op32", "dgfas_schwarz_smooth", "dgfas_fas_vcycle",
            "dgfas_solve", "dgfas_norm", "dgfas_set_surrogate", "dgfas_get_surrogate",
            "dgfas_use_graph", "dgfas_profile_sweep", "dgfas_profile_scg", "dgfas_scg_info", "dgfas_fma_peak", "dgfas_schwarz_correct_static", "dgfas_kernel_launches", "dgfas_mlp_param_count",
@@ -78,6 +80,7 @@ def load():
     lib = ctypes.CDLL(LIB_PATH)
     P, I, D, LL = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_longlong
     sig = {
+        "dgfas_check_mesh": (I, [ctypes.POINTER(dgfas_mesh)]),
         "dgfas_setup_levels": (I, [ctypes.POINTER(dgfas_mesh), ctypes.POINTER(dgfas_params), P,
                                    ctypes.POINTER(P)]),
         "dgfas_destroy": (None, [P]),
