@@ -7,6 +7,8 @@
   (independent of the cycle code).  A wrong right-hand side per level, a
   missing final interpolation or a cycle that does not treat level l as the
   top all fail it.
+* Closed form: with linear Dirichlet data on box meshes the start is that
+  linear function (SIP-DG reproduces it, every step preserves it).
 * Use: started from the FMG value, the V-cycles reach 1e-10 of the residual
   of a zero start in fewer cycles than from the zero start itself.
 """
@@ -77,3 +79,21 @@ def test_local_fmg_start_saves_cycles():
     _, h_f = H.solve_local(u_f, f, rtol=1e-10 * r_zero / r_f)
     _, h_z = H.solve_local(zero, f, rtol=1e-10)
     assert h_f[-1] <= 1e-10 * r_zero * (1 + 1e-9) and len(h_f) < len(h_z)
+
+
+def test_fmg_reproduces_a_linear_solution():
+    """Closed form: on box elements the SIP-DG solution of -lap u = 0 with
+    linear Dirichlet data is that linear function at the nodes, the root is
+    solved exactly, interpolation is exact for it and a V-cycle leaves an
+    exact solution unchanged: the FMG start is the linear function."""
+    def lin(X):
+        return 0.3 + 1.1 * X[..., 0] - 0.7 * X[..., 1] + 0.4 * X[..., 2]
+    for cid, small in ((1, False), (2, True)):
+        cfg = wl.config(cid, small=small)
+        pr = cfg["params"]
+        H = fas.Hierarchy(cfg["levels"], pr["mu_star"], pr["delta"], pr["s1"], pr["s2"], pr["sc"])
+        fl = [sip.rhs(op, np.zeros(op.geo["x"].shape[:-1]), lin(op.geo["x"])).reshape(-1)
+              for op in H.ops]
+        u = H.fmg(fl, cycles=1)
+        ex = lin(H.ops[-1].geo["x"]).reshape(-1)
+        assert np.abs(u - ex).max() <= 1e-10 * np.abs(ex).max(), cid
