@@ -134,7 +134,9 @@ int dgfas_setup_levels(const dgfas_mesh* mesh, const dgfas_params* prm,
 
 /* Host-only validation of a hierarchy's input arrays, also run first by
    dgfas_setup_levels (no device work, callable without a GPU): arrays present,
-   1 <= p <= 10, neighbour indices in range (INVALID / UNSUPPORTED), and the
+   1 <= p <= 10, neighbour indices in range, the 27-neighbourhood's centre slot
+   the element and its face slots the face neighbours (-1 on boundary faces)
+   (INVALID / UNSUPPORTED), and the
    face-neighbour relation reciprocal through the opposite face with the two
    faces' corners coinciding corner by corner up to one translation (aligned
    local axes; periodic identification by translation), else DGFAS_ERR_MESH

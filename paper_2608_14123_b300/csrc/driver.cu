@@ -582,6 +582,28 @@ static int check_level(const dgfas_level& in, int l) {
         return DGFAS_ERR_INVALID;
       }
     }
+  // the 27-neighbourhood (read by the Schwarz gather and combine) must agree
+  // with the face neighbours: the centre slot is the element itself, a face
+  // slot holds the face neighbour or -1 on a boundary face
+  for (int e = 0; e < ne; ++e) {
+    const int* n27 = in.nbr27 + 27 * (size_t)e;
+    if (n27[13] != e) {
+      set_error("level " + std::to_string(l) + ": nbr27 centre slot of element " +
+                std::to_string(e) + " is not the element");
+      return DGFAS_ERR_INVALID;
+    }
+    for (int f = 0; f < 6; ++f) {
+      const int d = f >> 1, o = (f & 1) ? 2 : 0;
+      const int slot = d == 0 ? o + 3 + 9 : (d == 1 ? 1 + 3 * o + 9 : 1 + 3 + 9 * o);
+      const int nb = in.nbr[6 * e + f];
+      if (n27[slot] != (nb >= 0 ? nb : -1)) {
+        set_error("level " + std::to_string(l) + ": nbr27 face slot " + std::to_string(slot) +
+                  " of element " + std::to_string(e) + " disagrees with face neighbour " +
+                  std::to_string(nb));
+        return DGFAS_ERR_INVALID;
+      }
+    }
+  }
   for (int e = 0; e < ne; ++e) {
     const double* xe = in.corners + 24 * (size_t)e;
     double scale = 0.0;   // the element's largest corner-to-corner extent

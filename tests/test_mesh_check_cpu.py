@@ -64,7 +64,11 @@ def test_non_reciprocal_neighbour_is_rejected():
     f = int(np.nonzero(nbr[e] >= 0)[0][0])
     nb = nbr[e, f]
     nbr[nb, f ^ 1] = -1          # the neighbour no longer points back
-    rc, msg = _check([dict(lv, nbr=nbr)])
+    n27 = lv["nbr27"].copy()     # (its 27-neighbourhood kept consistent with that)
+    g = f ^ 1
+    d, o = g >> 1, 2 if g & 1 else 0
+    n27[nb, [o + 12, 1 + 3 * o + 9, 4 + 9 * o][d]] = -1
+    rc, msg = _check([dict(lv, nbr=nbr, nbr27=n27)])
     assert rc == dgfas.DGFAS_ERR_MESH and "point back" in msg
 
 
@@ -87,3 +91,20 @@ def test_out_of_range_neighbour_is_invalid():
     nbr[1, 0] = nbr.shape[0] + 5
     rc, _ = _check([dict(lv, nbr=nbr)])
     assert rc == dgfas.DGFAS_ERR_INVALID
+
+
+def test_inconsistent_27_neighbourhood_is_invalid():
+    """The Schwarz gather and combine read the 27-neighbourhood: its face
+    slots must hold the face neighbours and its centre the element itself."""
+    lv = _level()
+    n27 = lv["nbr27"].copy()
+    n27[0, 13] = 1
+    rc, msg = _check([dict(lv, nbr27=n27)])
+    assert rc == dgfas.DGFAS_ERR_INVALID and "centre" in msg
+    n27 = lv["nbr27"].copy()
+    f = int(np.nonzero(lv["nbr"][0] >= 0)[0][0])
+    d, o = f >> 1, 2 if f & 1 else 0
+    slot = [o + 12, 1 + 3 * o + 9, 4 + 9 * o][d]
+    n27[0, slot] = -1
+    rc, msg = _check([dict(lv, nbr27=n27)])
+    assert rc == dgfas.DGFAS_ERR_INVALID and "disagrees" in msg
